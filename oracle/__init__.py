@@ -1,0 +1,388 @@
+"""FP64 CPU oracle for model-based iterative reconstruction in x-ray
+edge-illumination (EI) tomography, after Modregger et al., arXiv:2202.08627.
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  The CUDA library and its
+Python binding never import it and share no code with it; the only thing both
+sides consume is the seeded input generator, which holds none of the method's
+arithmetic.
+
+What it computes, in the paper's order and notation:
+
+* ``project`` / ``backproject`` — the Radon transform R of Eq. 1 (a line
+  integral, computed by ray-driven linear interpolation, see ``ei_oracle.c``)
+  and its transpose, which the analytic gradient of Eq. 5 needs.
+* ``deriv`` / ``deriv_T`` — the finite-difference detector derivative d/dt of
+  Eq. 2 / Eq. 4 (the "Experimental improvements" section says the derivative is
+  implemented as finite differences) and its transpose.
+* ``ic_model`` — the illumination-curve model of Eq. 2: attenuation
+  exp(-R[mu]) times the flat IC f(t, m) shifted by z d/dt R[delta] (shift in
+  mask periods: z/period), extended by the drift m_o(theta) and ring term
+  m_r(t) of Eq. 4 and by a scatter broadening: the Gaussian flat IC
+  f(t, m) = A_t exp(-(m - c_t)^2 / (2 w_t^2)) is convolved with a Gaussian of
+  variance kappa R[sigma], which keeps its area.
+* ``objective_grad`` — the cost S of Eq. 5 (sum of squared residuals plus an
+  L2 regulariser) and its analytic gradient.
+* ``lbfgs`` / ``reconstruct`` — the L-BFGS minimisation the paper uses
+  ("Theoretical basis" section, [Byrd 1995] via SciPy), written out.
+
+Parity: every function here is pinned by the ``-m "not gpu"`` tests against
+closed forms, invariants or brute force (see tests/test_oracle_*.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        for name in ("eio_project", "eio_backproject"):
+            fn = getattr(lib, name)
+            fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                           dp, dp, dp]
+            fn.restype = None
+        for name in ("eio_deriv", "eio_deriv_T"):
+            fn = getattr(lib, name)
+            fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+            fn.restype = None
+        lib.eio_num_threads.restype = ctypes.c_int
+        lib.eio_set_num_threads.argtypes = [ctypes.c_int]
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_threads() -> int:
+    return _lib().eio_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    _lib().eio_set_num_threads(int(t))
+
+
+# --------------------------------------------------------------------------
+# Problem description
+# --------------------------------------------------------------------------
+@dataclass
+class Geometry:
+    """One slice's acquisition geometry and model constants (FP64).
+
+    n            slice is n x n voxels
+    n_theta      projection angles, ``theta`` [n_theta] in rad
+    n_det        detector pixels; voxel pitch = detector pitch = ``pitch`` (cm)
+    m            [M] mask positions in IC periods
+    z_cm         sample-detector distance; ``period_cm`` the mask period the
+                 IC shift is measured in (shift = (z/period) d/dt R[delta])
+    kappa        IC variance added per unit R[sigma] (period^2 / unit)
+    flat_A/c/w   [n_det] Gaussian flat IC per pixel: amplitude, centre, width
+    lam, scale   per channel (mu, delta, sigma): regulariser weight and the
+                 variable scaling u = x / scale the solver works in
+    m_o, m_r     optional drift [n_theta] and ring [n_det] offsets (Eq. 4)
+    """
+    n: int
+    n_theta: int
+    n_det: int
+    pitch: float
+    theta: np.ndarray
+    m: np.ndarray
+    z_cm: float
+    period_cm: float
+    kappa: float
+    flat_A: np.ndarray
+    flat_c: np.ndarray
+    flat_w: np.ndarray
+    lam: np.ndarray = field(default_factory=lambda: np.full(3, 1e-2))
+    scale: np.ndarray = field(default_factory=lambda: np.array([1.0, 1e-6, 1.0]))
+    m_o: Optional[np.ndarray] = None
+    m_r: Optional[np.ndarray] = None
+
+    @property
+    def n_m(self) -> int:
+        return int(len(self.m))
+
+    @property
+    def z_over_p(self) -> float:
+        return self.z_cm / self.period_cm
+
+
+# --------------------------------------------------------------------------
+# Linear operators (C core)
+# --------------------------------------------------------------------------
+def project(x: np.ndarray, geom: Geometry) -> np.ndarray:
+    """R[x](t_j, theta_a) for one channel (Eq. 1).  x: [n][n] -> [n_theta][n_det]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.shape == (geom.n, geom.n)
+    th = np.ascontiguousarray(geom.theta, dtype=np.float64)
+    p = np.empty((geom.n_theta, geom.n_det))
+    _lib().eio_project(geom.n, geom.n_theta, geom.n_det, float(geom.pitch),
+                       _ptr(th), _ptr(x), _ptr(p))
+    return p
+
+
+def backproject(g: np.ndarray, geom: Geometry) -> np.ndarray:
+    """R^T g for one channel.  g: [n_theta][n_det] -> [n][n]."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    assert g.shape == (geom.n_theta, geom.n_det)
+    th = np.ascontiguousarray(geom.theta, dtype=np.float64)
+    x = np.empty((geom.n, geom.n))
+    _lib().eio_backproject(geom.n, geom.n_theta, geom.n_det, float(geom.pitch),
+                           _ptr(th), _ptr(g), _ptr(x))
+    return x
+
+
+def deriv(p: np.ndarray, pitch: float) -> np.ndarray:
+    """Finite-difference d/dt along the last axis (rows of a sinogram)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    rows, nd = (1, p.shape[0]) if p.ndim == 1 else p.shape
+    out = np.empty_like(p)
+    _lib().eio_deriv(rows, nd, float(pitch), _ptr(p), _ptr(out))
+    return out
+
+
+def deriv_T(g: np.ndarray, pitch: float) -> np.ndarray:
+    """Transpose of ``deriv``."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    rows, nd = (1, g.shape[0]) if g.ndim == 1 else g.shape
+    out = np.empty_like(g)
+    _lib().eio_deriv_T(rows, nd, float(pitch), _ptr(g), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# IC model (Eq. 2, Eq. 4) and cost (Eq. 5)
+# --------------------------------------------------------------------------
+def _shift_terms(geom: Geometry, P_delta: np.ndarray) -> np.ndarray:
+    """Total IC shift in periods: m_o(theta) + m_r(t) + (z/period) d/dt R[delta]."""
+    shift = geom.z_over_p * deriv(P_delta, geom.pitch)
+    if geom.m_o is not None:
+        shift = shift + np.asarray(geom.m_o, dtype=np.float64)[:, None]
+    if geom.m_r is not None:
+        shift = shift + np.asarray(geom.m_r, dtype=np.float64)[None, :]
+    return shift
+
+
+def ic_model(P: np.ndarray, geom: Geometry) -> np.ndarray:
+    """s_mod(t, theta, m) from the three projections P = [R mu, R delta, R sigma].
+
+    P: [3][n_theta][n_det] -> [M][n_theta][n_det].
+      s = exp(-R[mu]) * A (w / sqrt(V)) exp(-(m - c - shift)^2 / (2 V)),
+      V = w^2 + kappa R[sigma].
+    """
+    P_mu, P_delta, P_sigma = P
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
+    shift = _shift_terms(geom, P_delta)
+    V = w * w + geom.kappa * P_sigma
+    out = np.empty((geom.n_m,) + P_mu.shape)
+    for k, mk in enumerate(geom.m):
+        q = mk - c - shift
+        out[k] = np.exp(-P_mu) * A * (w / np.sqrt(V)) * np.exp(-q * q / (2.0 * V))
+    return out
+
+
+def ic_objective_grad(P: np.ndarray, s_exp: np.ndarray, geom: Geometry,
+                      want_grad: bool = True):
+    """Data term of Eq. 5 and its gradient with respect to the projections.
+
+    Returns (S_data, dS/dP [3][n_theta][n_det] or None).  S_data is +inf when
+    the broadened variance leaves its domain (V <= 0.01 w^2 anywhere).
+      e = s_mod - s_exp,  q = m - c - shift
+      dS/dR[mu]    = sum_m 2 e (-s)
+      dS/dR[delta] = (z/period) D^T sum_m 2 e s q / V
+      dS/dR[sigma] = kappa sum_m 2 e s (q^2 - V) / (2 V^2)
+    """
+    P_mu, P_delta, P_sigma = P
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
+    shift = _shift_terms(geom, P_delta)
+    V = w * w + geom.kappa * P_sigma
+    if np.any(V <= 0.01 * w * w):
+        return np.inf, (np.zeros_like(P) if want_grad else None)
+    S = 0.0
+    G_mu = np.zeros_like(P_mu)
+    G_shift = np.zeros_like(P_mu)
+    G_V = np.zeros_like(P_mu)
+    for k, mk in enumerate(geom.m):
+        q = mk - c - shift
+        s = np.exp(-P_mu) * A * (w / np.sqrt(V)) * np.exp(-q * q / (2.0 * V))
+        e = s - s_exp[k]
+        S += float(np.sum(e * e))
+        if want_grad:
+            G_mu += 2.0 * e * (-s)
+            G_shift += 2.0 * e * s * q / V
+            G_V += 2.0 * e * s * (q * q - V) / (2.0 * V * V)
+    if not want_grad:
+        return S, None
+    g = np.empty_like(P)
+    g[0] = G_mu
+    g[1] = geom.z_over_p * deriv_T(G_shift, geom.pitch)
+    g[2] = geom.kappa * G_V
+    return S, g
+
+
+def forward(x: np.ndarray, geom: Geometry) -> np.ndarray:
+    """s_mod for a physical volume x [3][n][n] (mu, delta, sigma)."""
+    P = np.stack([project(x[ch], geom) for ch in range(3)])
+    return ic_model(P, geom)
+
+
+def objective_grad(x: np.ndarray, s_exp: np.ndarray, geom: Geometry,
+                   want_grad: bool = True, scaled: bool = False):
+    """S of Eq. 5 and its gradient for one slice.
+
+    scaled=False: x is the physical volume [3][n][n]; S = data + sum_c lam_c
+    ||x_c / scale_c||^2 and the gradient is with respect to x.
+    scaled=True: x holds u = x_phys / scale (what the solver iterates on); same
+    S, gradient with respect to u.
+    """
+    scale = np.asarray(geom.scale, dtype=np.float64)
+    lam = np.asarray(geom.lam, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    u = x if scaled else x / scale[:, None, None]
+    xp = u * scale[:, None, None]
+    P = np.stack([project(xp[ch], geom) for ch in range(3)])
+    S_data, gP = ic_objective_grad(P, s_exp, geom, want_grad)
+    S = S_data + float(np.sum(lam * np.sum(u * u, axis=(1, 2))))
+    if not want_grad:
+        return S, None
+    grad_x = np.stack([backproject(gP[ch], geom) for ch in range(3)])
+    if scaled:
+        grad = scale[:, None, None] * grad_x + 2.0 * lam[:, None, None] * u
+    else:
+        grad = grad_x + 2.0 * lam[:, None, None] * u / scale[:, None, None]
+    return S, grad
+
+
+# --------------------------------------------------------------------------
+# L-BFGS (the paper minimises S with SciPy's L-BFGS implementation)
+# --------------------------------------------------------------------------
+@dataclass
+class SolveOptions:
+    tol: float = 1e-6          # stop when the relative decrease of f is below tol
+    max_iter: int = 100
+    lbfgs_m: int = 10          # pairs kept (SciPy's default maxcor)
+    c1: float = 1e-4           # Armijo sufficient-decrease constant
+    max_trials: int = 20       # step halvings per line search
+    curv_eps: float = 1e-10    # keep (s, y) only if s.y > curv_eps |s| |y|
+
+
+@dataclass
+class SolveReport:
+    iterations: int
+    f_history: list
+    status: str                # "converged", "max_iter", "linesearch", "nonfinite"
+    evaluations: int
+
+
+def lbfgs(fun: Callable[[np.ndarray], tuple], u0: np.ndarray,
+          opts: SolveOptions = SolveOptions()):
+    """Minimise fun (returning (f, grad)) from u0.
+
+    Steps per iteration k:
+      1. d = -H g by the two-loop recursion over the kept (s_i, y_i) pairs, with
+         H_0 = (s.y / y.y) I of the newest pair (I when none is kept);
+      2. Armijo backtracking from alpha = 1/|g| when no pair is kept, else 1:
+         accept the first alpha with f(u + alpha d) <= f + c1 alpha g.d, else
+         halve, at most max_trials times;
+      3. s = alpha d, y = g_new - g; keep the pair if s.y > curv_eps |s| |y|
+         (oldest dropped beyond lbfgs_m);
+      4. stop when (f - f_new) / max(|f|, |f_new|, 1) < tol, or after max_iter
+         accepted steps.
+    Returns (u, SolveReport).
+    """
+    u = np.array(u0, dtype=np.float64, copy=True)
+    f, g = fun(u)
+    n_eval = 1
+    hist = [f]
+    if not np.isfinite(f):
+        return u, SolveReport(0, hist, "nonfinite", n_eval)
+    S_mem, Y_mem = [], []
+    k = 0
+    while k < opts.max_iter:
+        # 1. two-loop recursion
+        q = g.copy()
+        alphas = []
+        for s_i, y_i in reversed(list(zip(S_mem, Y_mem))):
+            rho = 1.0 / float(np.vdot(y_i, s_i))
+            a_i = rho * float(np.vdot(s_i, q))
+            q = q - a_i * y_i
+            alphas.append((rho, a_i))
+        if S_mem:
+            gamma = float(np.vdot(S_mem[-1], Y_mem[-1])) / float(np.vdot(Y_mem[-1], Y_mem[-1]))
+        else:
+            gamma = 1.0
+        r = gamma * q
+        for (s_i, y_i), (rho, a_i) in zip(zip(S_mem, Y_mem), reversed(alphas)):
+            b = rho * float(np.vdot(y_i, r))
+            r = r + (a_i - b) * s_i
+        d = -r
+        gd = float(np.vdot(g, d))
+        if not gd < 0.0:
+            # no descent (g == 0 or a broken memory): restart from steepest descent
+            S_mem, Y_mem = [], []
+            d = -g
+            gd = float(np.vdot(g, d))
+            if gd == 0.0:
+                return u, SolveReport(k, hist, "converged", n_eval)
+        # 2. Armijo backtracking
+        gnorm = float(np.sqrt(np.vdot(g, g)))
+        alpha = 1.0 / gnorm if not S_mem else 1.0
+        accepted = False
+        for _ in range(opts.max_trials):
+            u_new = u + alpha * d
+            f_new, g_new = fun(u_new)
+            n_eval += 1
+            if np.isfinite(f_new) and f_new <= f + opts.c1 * alpha * gd:
+                accepted = True
+                break
+            alpha *= 0.5
+        if not accepted:
+            return u, SolveReport(k, hist, "linesearch", n_eval)
+        # 3. memory update
+        s_new = u_new - u
+        y_new = g_new - g
+        sy = float(np.vdot(s_new, y_new))
+        if sy > opts.curv_eps * float(np.linalg.norm(s_new)) * float(np.linalg.norm(y_new)):
+            S_mem.append(s_new)
+            Y_mem.append(y_new)
+            if len(S_mem) > opts.lbfgs_m:
+                S_mem.pop(0)
+                Y_mem.pop(0)
+        rel = (f - f_new) / max(abs(f), abs(f_new), 1.0)
+        u, f, g = u_new, f_new, g_new
+        hist.append(f)
+        k += 1
+        # 4. stop rule
+        if rel < opts.tol:
+            return u, SolveReport(k, hist, "converged", n_eval)
+    return u, SolveReport(k, hist, "max_iter", n_eval)
+
+
+def reconstruct(s_exp: np.ndarray, geom: Geometry, x0: Optional[np.ndarray] = None,
+                opts: SolveOptions = SolveOptions()):
+    """Minimise Eq. 5 for one slice; returns (x_phys [3][n][n], SolveReport)."""
+    scale = np.asarray(geom.scale, dtype=np.float64)[:, None, None]
+    if x0 is None:
+        x0 = np.zeros((3, geom.n, geom.n))
+    u0 = np.asarray(x0, dtype=np.float64) / scale
+
+    def fun(u):
+        return objective_grad(u, s_exp, geom, want_grad=True, scaled=True)
+
+    u, rep = lbfgs(fun, u0, opts)
+    return u * scale, rep
