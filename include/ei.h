@@ -1,0 +1,241 @@
+/*
+ * ei.h — C ABI of libei.so: model-based iterative reconstruction for x-ray
+ * edge-illumination (EI) tomography on one NVIDIA GB300 (sm_103a), after
+ * Modregger et al., "Accelerated iterative tomographic reconstruction with
+ * x-ray edge illumination" (arXiv:2202.08627).
+ *
+ * The method ("Theoretical basis" section of the paper): for every slice, the
+ * volumes mu (attenuation, 1/cm), delta (refractive decrement) and sigma
+ * (scatter) are projected by the Radon transform R (Eq. 1); each detector
+ * pixel's flat illumination curve (IC) f(t, m) is attenuated by exp(-R[mu]),
+ * shifted by z d/dt R[delta] (Eq. 2; plus the drift m_o(theta) and ring term
+ * m_r(t) of Eq. 4) and broadened by scatter, and evaluated at every mask
+ * position m; the cost S of Eq. 5 (squared residual against the measured ICs
+ * s_exp plus an L2 regulariser) is minimised with L-BFGS using its analytic
+ * gradient.
+ *
+ * Discretisation (the paper leaves it open; this library's reading):
+ *   - voxel (r, c) of an n x n slice is centred at x = (c - (n-1)/2) pitch,
+ *     y = ((n-1)/2 - r) pitch; detector pixel j at t_j = (j - (n_det-1)/2) pitch;
+ *     angle theta_a = a pi / n_theta unless given; ray {x cos + y sin = t}.
+ *   - R: ray-driven linear interpolation ("Algorithmic improvements"
+ *     section: linear interpolation, indices computed on the fly), one sample
+ *     per voxel row (column when |sin| > |cos|), weight pitch / max(|cos|,|sin|).
+ *   - d/dt: central finite differences, one-sided at the detector ends
+ *     ("Experimental improvements" section).
+ *   - IC: f(t, m) = A_t exp(-(m - c_t)^2 / (2 w_t^2)) (Gaussian flat IC per
+ *     pixel, m in mask periods); with V = w_t^2 + kappa R[sigma] and
+ *     shift = (z / period) dR[delta]/dt + m_o(theta) + m_r(t):
+ *       s_mod = exp(-R[mu]) A_t (w_t / sqrt(V)) exp(-(m - c_t - shift)^2 / (2 V)).
+ *   - S = sum (s_exp - s_mod)^2 + sum_c lambda_c ||x_c / scale_c||^2, and
+ *     S = +inf where V <= 0.01 w_t^2 (outside the model's domain).
+ *
+ * Memory layout (all float32 unless stated; slices are stored one after the
+ * other in slice order, the offsets are reported by ei_get_slice_layout):
+ *   vol    per slice n*n float4 = (mu, delta, sigma, pad), row-major [r][c].
+ *          The pad lane is ignored on input and written as 0 on output.
+ *   proj   per slice 3 planes [channel][n_theta][n_dp], channel = mu, delta, sigma.
+ *   sino4  per slice [n_theta][n_dp] float4 = (mu, delta, sigma, pad).
+ *   s_exp, s_mod  per slice n_m planes [m][n_theta][n_dp].
+ *   n_dp = n_det rounded up to a multiple of 4; pixels n_det..n_dp-1 are
+ *   padding: ignored on input, written as 0 on output.
+ *   Every array pointer must be 16-byte aligned.
+ *
+ * Ownership: every array argument is caller-owned.  Unless a function says
+ * otherwise, array pointers are DEVICE pointers (cudaMalloc'd or a PyTorch
+ * CUDA tensor's storage) on the current device.  The geometry handle owns its
+ * own device workspace (allocated in ei_setup_geometry and ei_reconstruct,
+ * freed in ei_destroy_geometry).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls are stream-ordered and asynchronous unless stated.  A
+ * geometry's workspace is shared by its calls, so calls on one geometry must
+ * not overlap on the GPU (use one stream per geometry, or synchronise).
+ *
+ * Errors: every function returns an ei_status; nothing is thrown across the
+ * ABI.  EI_ERR_ARG is returned before any work is queued.  After EI_ERR_CUDA
+ * the contents of output arrays are unspecified.
+ */
+#ifndef EI_H
+#define EI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EI_OK = 0,
+    EI_ERR_ARG = 1,          /* invalid argument (null, size, layout, alignment) */
+    EI_ERR_CUDA = 2,         /* a CUDA call failed (launch, copy, allocation) */
+    EI_ERR_NONFINITE = 3,    /* the objective is NaN (non-finite data or iterate) */
+    EI_ERR_LINESEARCH = 4,   /* Armijo backtracking found no acceptable step */
+    EI_ERR_TIMEOUT = 5,      /* a bounded wait ran out (device or host watchdog) */
+    EI_ERR_DEVICE_CHECK = 6, /* a kernel's own bounds check fired */
+    EI_ERR_ALLOC = 7         /* workspace allocation failed */
+} ei_status;
+
+typedef struct ei_geometry ei_geometry;   /* opaque */
+
+/* Per-slice sizes for batches of uneven slices. */
+typedef struct {
+    int n;            /* slice is n x n voxels, n >= 1 */
+    int n_theta;      /* projection angles, >= 1 */
+    int n_det;        /* detector pixels, 1 <= n_det <= EI_MAX_NDET */
+    double pitch_cm;  /* voxel pitch = detector pitch (cm), > 0 */
+} ei_slice_dims;
+
+#define EI_MAX_NDET 8192
+#define EI_MAX_NM 32
+
+/*
+ * Acquisition geometry and model constants (Eq. 2, Eq. 4, Eq. 5).
+ * Host arrays are copied during ei_setup_geometry; flat_* / m_o / m_r may be
+ * host or device pointers (copied too).
+ */
+typedef struct {
+    int n, n_theta, n_det;     /* uniform batch: every slice n x n, n_theta angles, n_det pixels */
+    int n_m;                   /* mask positions M, 1 <= M <= EI_MAX_NM (all slices) */
+    double pitch_cm;           /* uniform batch: voxel = detector pitch (cm) */
+    const double *theta;       /* host; NULL = theta_a = a pi / n_theta.  Uniform batch:
+                                  [n_theta]; uneven batch: concatenated per slice */
+    const double *m;           /* host [n_m]: mask positions in IC periods */
+    double z_cm;               /* sample-detector distance z (cm) */
+    double period_cm;          /* IC period the shift is expressed in: shift = (z/period) dR[delta]/dt */
+    double kappa_sigma;        /* IC variance (period^2) added per unit of R[sigma] */
+    const float *flat_A;       /* Gaussian flat IC per pixel: amplitude, centre (periods), */
+    const float *flat_c;       /* width w > 0 (std, periods).  Uniform batch: [n_det] shared */
+    const float *flat_w;       /* by all slices; uneven batch: concatenated [n_det_s] per slice */
+    double lambda[3];          /* L2 weights (mu, delta, sigma); the paper uses 1e-2 */
+    double scale[3];           /* variable scaling u = x / scale for the solver and the
+                                  regulariser (e.g. 1, 1e-6, 1); > 0 */
+    const float *m_o;          /* optional drift m_o(theta) per angle (Eq. 4), NULL = 0;
+                                  layout like theta */
+    const float *m_r;          /* optional ring term m_r(t) per pixel (Eq. 4), NULL = 0;
+                                  layout like flat_* */
+} ei_geometry_desc;
+
+/*
+ * Build a geometry for a batch of n_slices slices and allocate its workspace
+ * on the current device.  per_slice == NULL: every slice takes desc->n,
+ * n_theta, n_det, pitch_cm.  Otherwise per_slice[n_slices] gives each slice's
+ * sizes (desc->n .. pitch_cm are ignored) and the per-slice arrays described
+ * above are concatenated in slice order.
+ * Returns EI_ERR_ARG on invalid sizes or constants, EI_ERR_ALLOC/EI_ERR_CUDA
+ * when the workspace cannot be allocated.  Synchronous.
+ */
+int ei_setup_geometry(const ei_geometry_desc *desc, int n_slices,
+                      const ei_slice_dims *per_slice, ei_geometry **out);
+
+/* Free a geometry and its workspace (synchronises the device first).  NULL is a no-op. */
+void ei_destroy_geometry(ei_geometry *g);
+
+/* Sizes of one slice's arrays, in ELEMENTS of the array's element type, and
+ * the element offset of the slice inside each batched array. */
+typedef struct {
+    int n, n_theta, n_det, n_dp, n_m;
+    double pitch_cm;
+    int64_t vol_offset, vol_count;     /* float4 elements */
+    int64_t proj_offset, proj_count;   /* floats (3 planes) */
+    int64_t sino4_offset, sino4_count; /* float4 elements */
+    int64_t meas_offset, meas_count;   /* floats (n_m planes): s_exp, s_mod */
+} ei_slice_layout;
+
+/* Totals for the whole batch, same units. */
+typedef struct {
+    int n_slices, n_m;
+    int64_t vol_count, proj_count, sino4_count, meas_count;
+    int64_t workspace_bytes;           /* device bytes the geometry holds */
+} ei_layout;
+
+int ei_get_layout(const ei_geometry *g, ei_layout *out);
+int ei_get_slice_layout(const ei_geometry *g, int slice, ei_slice_layout *out);
+
+/*
+ * proj = R[vol] for the three channels of every slice (Eq. 1).
+ * vol: device, vol layout; proj: device, proj layout.
+ */
+int ei_project(const ei_geometry *g, const float *vol, float *proj, void *stream);
+
+/*
+ * vol = R^T[sino4] for the three channels of every slice: the transpose of
+ * ei_project, which the analytic gradient of Eq. 5 needs.  Gather form, no
+ * atomics.  sino4: device, sino4 layout; vol: device, vol layout.
+ */
+int ei_backproject(const ei_geometry *g, const float *sino4, float *vol, void *stream);
+
+/*
+ * s_mod = IC model (Eq. 2 with the Eq. 4 offsets and scatter broadening)
+ * evaluated from given projections.  proj: device, proj layout;
+ * s_mod: device, measurement layout.
+ */
+int ei_ic_model(const ei_geometry *g, const float *proj, float *s_mod, void *stream);
+
+/* s_mod for a physical volume: ei_project followed by ei_ic_model. */
+int ei_forward(const ei_geometry *g, const float *vol, float *s_mod, void *stream);
+
+/*
+ * S (Eq. 5) of every slice and, if grad != NULL, its gradient with respect to
+ * the physical volume:
+ *   S_s    = sum_{t,theta,m} (s_exp - s_mod)^2 + sum_c lambda_c ||x_c / scale_c||^2
+ *   grad_c = R^T[dS/dR[x_c]] + 2 lambda_c x_c / scale_c^2
+ * vol, s_exp, grad: device (vol / measurement / vol layout).
+ * S_out: [n_slices] doubles, host or device memory.  The data term is
+ * accumulated in FP64 in a fixed order (deterministic).  When S_out is host
+ * memory the call synchronises the stream before returning.
+ * A slice outside the model's domain reports S = +inf; a NaN in s_exp or vol
+ * reports NaN (the call itself still returns EI_OK).
+ */
+int ei_objective_grad(const ei_geometry *g, const float *vol, const float *s_exp,
+                      double *S_out, float *grad, void *stream);
+
+/* L-BFGS options ("Theoretical basis" section: L-BFGS as in SciPy [Byrd 1995]). */
+typedef struct {
+    double tol;        /* stop when (f_k - f_k+1) / max(|f_k|, |f_k+1|, 1) < tol (e.g. 1e-6) */
+    int max_iter;      /* accepted steps per slice */
+    int lbfgs_m;       /* (s, y) pairs kept, 1..32 (SciPy default 10) */
+    double c1;         /* Armijo constant (1e-4) */
+    int max_trials;    /* step halvings per line search (20) */
+    double curv_eps;   /* keep a pair only if s.y > curv_eps |s| |y| (1e-10) */
+} ei_solve_opts;
+
+/* Per-slice results; every pointer is a caller-owned HOST array of n_slices
+ * entries, or NULL when not wanted. */
+typedef struct {
+    int *iterations;   /* accepted steps */
+    int *status;       /* ei_status per slice: EI_OK (converged or max_iter reached),
+                          EI_ERR_LINESEARCH, EI_ERR_NONFINITE */
+    int *converged;    /* 1 if the tol test stopped the slice, 0 if max_iter or an error did */
+    double *f_final;   /* final S */
+    double *f_initial; /* S at x0 */
+    int evaluations;   /* objective+gradient evaluations of the batch (out) */
+    double seconds;    /* wall time of the call (out) */
+} ei_solve_report;
+
+/*
+ * Minimise S (Eq. 5) for every slice independently with batched L-BFGS:
+ * two-loop recursion with H0 = (s.y / y.y) I, Armijo backtracking (first
+ * trial 1/|g| while no pair is kept, then 1, halving), pair kept when the
+ * curvature condition holds, stop on the relative decrease of S or max_iter.
+ * The iterate is u = x / scale.
+ * s_exp: measurement layout, vol_inout: vol layout (x0 in, solution out);
+ * both may be device or host memory (host arrays are staged through device
+ * memory inside the call).  report may be NULL.  Synchronous: returns when
+ * every slice has stopped.  Returns EI_OK when every slice converged or
+ * reached max_iter, else the first per-slice error.
+ */
+int ei_reconstruct(const ei_geometry *g, const float *s_exp, float *vol_inout,
+                   const ei_solve_opts *opts, ei_solve_report *report, void *stream);
+
+/* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10. */
+void ei_default_solve_opts(ei_solve_opts *opts);
+
+/* Human-readable name of a status code (static storage). */
+const char *ei_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EI_H */

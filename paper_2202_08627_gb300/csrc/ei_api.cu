@@ -1,0 +1,448 @@
+// C ABI of libei.so (declared in include/ei.h): geometry set-up, layouts and
+// the stream-ordered entry points.  All compute runs in the CUDA kernels of
+// this library; there is no CPU fallback.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ei_internal.h"
+
+namespace ei {
+
+cudaError_t ic_set_smem_limit();
+
+static int round_up4(int n) { return (n + 3) / 4 * 4; }
+
+template <class T>
+static cudaError_t dev_alloc(ei_geometry *g, T **p, size_t count)
+{
+    void *ptr = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) return e;
+    g->allocs.push_back(ptr);
+    g->workspace_bytes += (int64_t)bytes;
+    *p = static_cast<T *>(ptr);
+    return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t upload(ei_geometry *g, T **p, const std::vector<T> &h)
+{
+    EI_CUDA_TRY(dev_alloc(g, p, h.size()));
+    if (!h.empty())
+        EI_CUDA_TRY(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return cudaSuccess;
+}
+
+// Copy `count` floats from host or device memory to a host vector.
+static cudaError_t fetch_floats(const float *src, size_t count, std::vector<float> &dst)
+{
+    dst.resize(count);
+    if (count == 0) return cudaSuccess;
+    return cudaMemcpy(dst.data(), src, count * sizeof(float), cudaMemcpyDefault);
+}
+
+cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
+                     float4 *grad, bool scaled, const int *active, cudaStream_t st)
+{
+    float4 mult, out_mult, reg2, reg1;
+    if (scaled) {
+        mult = make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
+        out_mult = mult;
+        reg2 = make_float4(2.f * g->lambda[0], 2.f * g->lambda[1], 2.f * g->lambda[2], 0.f);
+        reg1 = make_float4(g->lambda[0], g->lambda[1], g->lambda[2], 0.f);
+    } else {
+        mult = make_float4(1.f, 1.f, 1.f, 0.f);
+        out_mult = mult;
+        float k[3];
+        for (int c = 0; c < 3; ++c) k[c] = (float)(1.0 / ((double)g->scale[c] * g->scale[c]));
+        reg2 = make_float4(2.f * g->lambda[0] * k[0], 2.f * g->lambda[1] * k[1],
+                           2.f * g->lambda[2] * k[2], 0.f);
+        reg1 = make_float4(g->lambda[0] * k[0], g->lambda[1] * k[1], g->lambda[2] * k[2], 0.f);
+    }
+    EI_CUDA_TRY(launch_prep(g, v, mult, g->xp, g->xt, active, st));
+    EI_CUDA_TRY(launch_project(g, g->xp, g->xt, g->proj, active, st));
+    EI_CUDA_TRY(launch_ic(g, g->proj, meas, nullptr, g->sino4, g->part_ic,
+                          grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, active, st));
+    EI_CUDA_TRY(launch_backproject(g, grad ? g->sino4 : nullptr, v, grad, out_mult, reg2, reg1,
+                                   g->part_adj, active, st));
+    EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, g->part_adj, S_dev, active, st));
+    return cudaSuccess;
+}
+
+}  // namespace ei
+
+using namespace ei;
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" {
+
+const char *ei_status_string(int status)
+{
+    switch (status) {
+    case EI_OK: return "EI_OK";
+    case EI_ERR_ARG: return "EI_ERR_ARG: invalid argument";
+    case EI_ERR_CUDA: return "EI_ERR_CUDA: a CUDA call failed";
+    case EI_ERR_NONFINITE: return "EI_ERR_NONFINITE: non-finite objective";
+    case EI_ERR_LINESEARCH: return "EI_ERR_LINESEARCH: no acceptable step";
+    case EI_ERR_TIMEOUT: return "EI_ERR_TIMEOUT: a bounded wait ran out";
+    case EI_ERR_DEVICE_CHECK: return "EI_ERR_DEVICE_CHECK: a kernel bounds check fired";
+    case EI_ERR_ALLOC: return "EI_ERR_ALLOC: workspace allocation failed";
+    default: return "unknown ei_status";
+    }
+}
+
+void ei_default_solve_opts(ei_solve_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-6;
+    o->max_iter = 100;
+    o->lbfgs_m = 10;
+    o->c1 = 1e-4;
+    o->max_trials = 20;
+    o->curv_eps = 1e-10;
+}
+
+void ei_destroy_geometry(ei_geometry *g)
+{
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    ei::destroy_solver(g);
+    for (void *p : g->allocs) cudaFree(p);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_dims *per_slice,
+                      ei_geometry **out)
+{
+    if (!d || !out || n_slices < 1) return EI_ERR_ARG;
+    *out = nullptr;
+    if (d->n_m < 1 || d->n_m > EI_MAX_NM || !d->m) return EI_ERR_ARG;
+    if (!(d->z_cm >= 0) || !(d->period_cm > 0) || !(d->kappa_sigma >= 0)) return EI_ERR_ARG;
+    if (!d->flat_A || !d->flat_c || !d->flat_w) return EI_ERR_ARG;
+    for (int c = 0; c < 3; ++c)
+        if (!(d->scale[c] > 0) || !(d->lambda[c] >= 0) || !isfinite(d->lambda[c])) return EI_ERR_ARG;
+    std::vector<ei_slice_dims> dims(n_slices);
+    for (int s = 0; s < n_slices; ++s) {
+        dims[s] = per_slice ? per_slice[s]
+                            : ei_slice_dims{d->n, d->n_theta, d->n_det, d->pitch_cm};
+        const ei_slice_dims &q = dims[s];
+        if (q.n < 1 || q.n > 16384 || q.n_theta < 1 || q.n_det < 1 || q.n_det > EI_MAX_NDET ||
+            !(q.pitch_cm > 0) || !isfinite(q.pitch_cm))
+            return EI_ERR_ARG;
+    }
+    ei_geometry *g = new ei_geometry();
+    cudaGetDevice(&g->device);
+    g->n_slices = n_slices;
+    g->n_m = d->n_m;
+    for (int c = 0; c < 3; ++c) {
+        g->lambda[c] = (float)d->lambda[c];
+        g->scale[c] = (float)d->scale[c];
+    }
+    // ---- host tables
+    const bool uniform = per_slice == nullptr;
+    int64_t ang_total = 0, pix_total = 0, pix_in_total = 0;
+    for (auto &q : dims) {
+        ang_total += q.n_theta;
+        pix_total += round_up4(q.n_det);
+        pix_in_total += q.n_det;
+    }
+    const size_t flat_count = uniform ? (size_t)d->n_det : (size_t)pix_in_total;
+    std::vector<float> fA, fc, fw, fmr, fmo;
+    cudaError_t ce = fetch_floats(d->flat_A, flat_count, fA);
+    if (ce == cudaSuccess) ce = fetch_floats(d->flat_c, flat_count, fc);
+    if (ce == cudaSuccess) ce = fetch_floats(d->flat_w, flat_count, fw);
+    if (ce == cudaSuccess && d->m_r) ce = fetch_floats(d->m_r, flat_count, fmr);
+    const size_t mo_count = uniform ? (size_t)d->n_theta : (size_t)ang_total;
+    if (ce == cudaSuccess && d->m_o) ce = fetch_floats(d->m_o, mo_count, fmo);
+    if (ce != cudaSuccess) {
+        delete g;
+        return EI_ERR_ARG;   // a pointer that is neither host nor device memory
+    }
+    for (size_t i = 0; i < flat_count; ++i)
+        if (!(fw[i] > 0) || !isfinite(fA[i]) || !isfinite(fc[i])) {
+            delete g;
+            return EI_ERR_ARG;
+        }
+
+    std::vector<AngleInfo> ang;
+    std::vector<float> m_o;
+    std::vector<float4> pix;
+    ang.reserve(ang_total);
+    pix.reserve(pix_total);
+    std::vector<int> fwd_p(1, 0), ic_p(1, 0), adj_p(1, 0), prep_p(1, 0), vec_p(1, 0);
+    int64_t vol_off = 0, pad_off = 0, sino_off = 0, proj_off = 0, meas_off = 0;
+    int ang_off = 0, pix_off = 0, pix_in_off = 0, max_ndp = 4, max_nth = 1;
+    const double TWO32 = 4294967296.0;
+    for (int s = 0; s < n_slices; ++s) {
+        const ei_slice_dims &q = dims[s];
+        SliceInfo si{};
+        si.n = q.n;
+        si.n_theta = q.n_theta;
+        si.n_det = q.n_det;
+        si.n_dp = round_up4(q.n_det);
+        si.pitch = (float)q.pitch_cm;
+        si.inv_pitch = (float)(1.0 / q.pitch_cm);
+        si.ang_off = ang_off;
+        si.pix_off = pix_off;
+        si.vol_off = vol_off;
+        si.pad_off = pad_off;
+        si.sino_off = sino_off;
+        si.proj_off = proj_off;
+        si.meas_off = meas_off;
+        g->h_slices.push_back(si);
+        const double hn = 0.5 * (q.n - 1);
+        for (int a = 0; a < q.n_theta; ++a) {
+            double th = d->theta ? d->theta[(uniform ? 0 : ang_off) + a] : a * M_PI / q.n_theta;
+            double ct = cos(th), st = sin(th);
+            AngleInfo an{};
+            const double ch = std::max(fabs(ct), fabs(st));
+            an.col_dom = fabs(st) > fabs(ct) ? 1 : 0;
+            if (!an.col_dom) {
+                an.inv_dom = 1.0 / ct;
+                an.p1 = st / ct;
+            } else {
+                an.inv_dom = -1.0 / st;
+                an.p1 = ct / st;
+            }
+            an.k0 = hn - hn * an.p1;
+            an.inv_p1 = an.p1 != 0.0 ? 1.0 / an.p1 : 0.0;
+            an.p1_fx = llrint(an.p1 * TWO32);
+            if (an.p1_fx == 0) an.p1 = 0.0, an.inv_p1 = 0.0;
+            an.cos_fx = llrint(ct * TWO32);
+            an.sin_fx = llrint(st * TWO32);
+            an.cosf = (float)ct;
+            an.sinf = (float)st;
+            an.inv_ch = (float)(1.0 / ch);
+            an.pch = (float)(q.pitch_cm / ch);
+            ang.push_back(an);
+            m_o.push_back(d->m_o ? fmo[(uniform ? 0 : ang_off) + a] : 0.f);
+        }
+        const int src_off = uniform ? 0 : pix_in_off;
+        for (int j = 0; j < si.n_dp; ++j) {
+            if (j < q.n_det)
+                pix.push_back(make_float4(fA[src_off + j], fc[src_off + j], fw[src_off + j],
+                                          d->m_r ? fmr[src_off + j] : 0.f));
+            else
+                pix.push_back(make_float4(0.f, 0.f, 1.f, 0.f));
+        }
+        const int nb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
+        fwd_p.push_back(fwd_p.back() + q.n_theta * nb);
+        ic_p.push_back(ic_p.back() + q.n_theta);
+        const int at = (q.n + ADJ_TILE - 1) / ADJ_TILE;
+        adj_p.push_back(adj_p.back() + at * at);
+        const int pt = (q.n + PREP_TILE - 1) / PREP_TILE;
+        prep_p.push_back(prep_p.back() + pt * pt);
+        const int64_t nvox = (int64_t)q.n * q.n;
+        vec_p.push_back(vec_p.back() + (int)((nvox + VEC_BLK - 1) / VEC_BLK));
+        vol_off += nvox;
+        pad_off += (int64_t)q.n * (q.n + 2);
+        sino_off += (int64_t)q.n_theta * si.n_dp;
+        proj_off += 3LL * q.n_theta * si.n_dp;
+        meas_off += (int64_t)d->n_m * q.n_theta * si.n_dp;
+        ang_off += q.n_theta;
+        pix_off += si.n_dp;
+        pix_in_off += q.n_det;
+        max_ndp = std::max(max_ndp, si.n_dp);
+        max_nth = std::max(max_nth, q.n_theta);
+    }
+    g->vol_count = vol_off;
+    g->pad_count = pad_off;
+    g->sino4_count = sino_off;
+    g->proj_count = proj_off;
+    g->meas_count = meas_off;
+    g->h_vec_prefix = vec_p;
+
+    DevGeom &dg = g->dg;
+    dg.n_slices = n_slices;
+    dg.total_fwd = fwd_p.back();
+    dg.total_ic = ic_p.back();
+    dg.total_adj = adj_p.back();
+    dg.total_prep = prep_p.back();
+    dg.total_vec = vec_p.back();
+    dg.max_ndp = max_ndp;
+    dg.max_n_theta = max_nth;
+    dg.mc.z_over_p = (float)(d->z_cm / d->period_cm);
+    dg.mc.kappa = (float)d->kappa_sigma;
+    dg.mc.n_m = d->n_m;
+    for (int k = 0; k < d->n_m; ++k) {
+        if (!isfinite(d->m[k])) {
+            delete g;
+            return EI_ERR_ARG;
+        }
+        dg.mc.m[k] = (float)d->m[k];
+    }
+
+    // ---- device tables and workspace
+    cudaError_t e = cudaSuccess;
+    SliceInfo *d_sl = nullptr;
+    AngleInfo *d_ang = nullptr;
+    float *d_mo = nullptr;
+    float4 *d_pix = nullptr;
+    int *d_fwd = nullptr, *d_ic = nullptr, *d_adj = nullptr, *d_prep = nullptr, *d_vec = nullptr;
+    if (e == cudaSuccess) e = upload(g, &d_sl, g->h_slices);
+    if (e == cudaSuccess) e = upload(g, &d_ang, ang);
+    if (e == cudaSuccess) e = upload(g, &d_mo, m_o);
+    if (e == cudaSuccess) e = upload(g, &d_pix, pix);
+    if (e == cudaSuccess) e = upload(g, &d_fwd, fwd_p);
+    if (e == cudaSuccess) e = upload(g, &d_ic, ic_p);
+    if (e == cudaSuccess) e = upload(g, &d_adj, adj_p);
+    if (e == cudaSuccess) e = upload(g, &d_prep, prep_p);
+    if (e == cudaSuccess) e = upload(g, &d_vec, vec_p);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xp, (size_t)g->pad_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xt, (size_t)g->pad_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->proj, (size_t)g->proj_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->sino4, (size_t)g->sino4_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->part_ic, (size_t)dg.total_ic);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->part_adj, (size_t)dg.total_adj);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
+    if (e == cudaSuccess) e = cudaMemset(g->xp, 0, (size_t)g->pad_count * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(g->xt, 0, (size_t)g->pad_count * sizeof(float4));
+    if (e == cudaSuccess) e = ic_set_smem_limit();
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        ei_destroy_geometry(g);
+        return oom ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    }
+    dg.slices = d_sl;
+    dg.ang = d_ang;
+    dg.m_o = d_mo;
+    dg.pix = d_pix;
+    dg.fwd_prefix = d_fwd;
+    dg.ic_prefix = d_ic;
+    dg.adj_prefix = d_adj;
+    dg.prep_prefix = d_prep;
+    dg.vec_prefix = d_vec;
+    *out = g;
+    return EI_OK;
+}
+
+int ei_get_layout(const ei_geometry *g, ei_layout *o)
+{
+    if (!g || !o) return EI_ERR_ARG;
+    o->n_slices = g->n_slices;
+    o->n_m = g->n_m;
+    o->vol_count = g->vol_count;
+    o->proj_count = g->proj_count;
+    o->sino4_count = g->sino4_count;
+    o->meas_count = g->meas_count;
+    o->workspace_bytes = g->workspace_bytes;
+    return EI_OK;
+}
+
+int ei_get_slice_layout(const ei_geometry *g, int s, ei_slice_layout *o)
+{
+    if (!g || !o || s < 0 || s >= g->n_slices) return EI_ERR_ARG;
+    const SliceInfo &si = g->h_slices[s];
+    o->n = si.n;
+    o->n_theta = si.n_theta;
+    o->n_det = si.n_det;
+    o->n_dp = si.n_dp;
+    o->n_m = g->n_m;
+    o->pitch_cm = si.pitch;
+    o->vol_offset = si.vol_off;
+    o->vol_count = (int64_t)si.n * si.n;
+    o->proj_offset = si.proj_off;
+    o->proj_count = 3LL * si.n_theta * si.n_dp;
+    o->sino4_offset = si.sino_off;
+    o->sino4_count = (int64_t)si.n_theta * si.n_dp;
+    o->meas_offset = si.meas_off;
+    o->meas_count = (int64_t)g->n_m * si.n_theta * si.n_dp;
+    return EI_OK;
+}
+
+static int status_from(cudaError_t e)
+{
+    if (e == cudaSuccess) return EI_OK;
+    return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+}
+
+int ei_project(const ei_geometry *gc, const float *vol, float *proj, void *stream)
+{
+    if (!gc || !vol || !proj || !aligned16(vol) || !aligned16(proj)) return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), g->xp,
+                                g->xt, nullptr, st);
+    if (e == cudaSuccess) e = launch_project(g, g->xp, g->xt, proj, nullptr, st);
+    return status_from(e);
+}
+
+int ei_backproject(const ei_geometry *gc, const float *sino4, float *vol, void *stream)
+{
+    if (!gc || !sino4 || !vol || !aligned16(sino4) || !aligned16(vol)) return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    cudaError_t e = launch_backproject(g, (const float4 *)sino4, nullptr, (float4 *)vol, one,
+                                       zero, zero, g->part_adj, nullptr, (cudaStream_t)stream);
+    return status_from(e);
+}
+
+int ei_ic_model(const ei_geometry *gc, const float *proj, float *s_mod, void *stream)
+{
+    if (!gc || !proj || !s_mod || !aligned16(proj) || !aligned16(s_mod)) return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    return status_from(launch_ic(g, proj, nullptr, s_mod, nullptr, g->part_ic, IC_MODEL, nullptr,
+                                 (cudaStream_t)stream));
+}
+
+int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stream)
+{
+    if (!gc || !vol || !s_mod || !aligned16(vol) || !aligned16(s_mod)) return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), g->xp,
+                                g->xt, nullptr, st);
+    if (e == cudaSuccess) e = launch_project(g, g->xp, g->xt, g->proj, nullptr, st);
+    if (e == cudaSuccess)
+        e = launch_ic(g, g->proj, nullptr, s_mod, nullptr, g->part_ic, IC_MODEL, nullptr, st);
+    return status_from(e);
+}
+
+int ei_objective_grad(const ei_geometry *gc, const float *vol, const float *s_exp,
+                      double *S_out, float *grad, void *stream)
+{
+    if (!gc || !vol || !s_exp || !S_out || !aligned16(vol) || !aligned16(s_exp) ||
+        (grad && !aligned16(grad)))
+        return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = evaluate(g, (const float4 *)vol, s_exp, g->S_dev, (float4 *)grad, false,
+                             nullptr, st);
+    if (e != cudaSuccess) return status_from(e);
+    cudaPointerAttributes attr{};
+    e = cudaPointerGetAttributes(&attr, S_out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    e = cudaMemcpyAsync(S_out, g->S_dev, sizeof(double) * g->n_slices, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        e = cudaStreamSynchronize(st);
+    return status_from(e);
+}
+
+int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
+                   const ei_solve_opts *opts, ei_solve_report *report, void *stream)
+{
+    if (!gc || !s_exp || !vol_inout || !aligned16(s_exp) || !aligned16(vol_inout)) return EI_ERR_ARG;
+    ei_solve_opts o;
+    ei_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol >= 0) || o.max_iter < 0 || o.lbfgs_m < 1 || o.lbfgs_m > 32 || !(o.c1 > 0) ||
+        o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0))
+        return EI_ERR_ARG;
+    return ei::reconstruct(const_cast<ei_geometry *>(gc), s_exp, vol_inout, &o, report,
+                           (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations shared by the CUDA translation units of libei.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ei.h"
+
+namespace ei {
+
+// Per-slice constants, resident in device memory (one entry per slice).
+struct SliceInfo {
+    int n, n_theta, n_det, n_dp;
+    float pitch, inv_pitch;  // voxel = detector pitch (cm) and its inverse
+    int ang_off;             // first angle of the slice in the angle tables
+    int pix_off;             // first pixel of the slice in the pixel table (n_dp stride)
+    int64_t vol_off;         // float4 elements (vol layout)
+    int64_t pad_off;         // float4 elements of the padded copies: n rows of n + 2
+    int64_t sino_off;        // pixels: base of [n_theta][n_dp] (sino4 and every plane)
+    int64_t proj_off;        // floats: 3 planes
+    int64_t meas_off;        // floats: n_m planes
+};
+
+// Per (slice, angle) constants, computed on the host in FP64.
+// The ray of pixel j samples the "outer" voxel index o = 0..n-1 (rows when
+// |cos| >= |sin|, else columns) at inner position s(o) = (j - hd) * inv_dom +
+// k0 + o * p1 (inner index units: columns, resp. rows).
+struct AngleInfo {
+    double inv_dom;     // 1/cos (row-dominant) or -1/sin (column-dominant)
+    double k0;          // hn - hn * p1
+    double p1;          // tan (row-dominant) or cot (column-dominant)
+    double inv_p1;      // 1/p1, 0 when p1 == 0
+    long long p1_fx;    // round(p1 * 2^32)
+    long long cos_fx;   // round(cos * 2^32)
+    long long sin_fx;   // round(sin * 2^32)
+    float cosf, sinf;   // cos, sin
+    float inv_ch, pch;  // 1/ch and pitch/ch, ch = max(|cos|, |sin|)
+    int col_dom;        // 1 when |sin| > |cos|
+    int pad_;
+};
+
+struct ModelConsts {
+    float z_over_p;       // shift in periods per unit dR[delta]/dt
+    float kappa;          // IC variance per unit R[sigma]
+    int n_m;
+    float m[EI_MAX_NM];
+};
+
+// Work decomposition sizes.
+constexpr int FWD_RAYS = 128;      // rays (threads) per forward work item
+constexpr int ADJ_TILE = 16;       // adjoint tile is ADJ_TILE x ADJ_TILE voxels
+constexpr int PREP_TILE = 32;      // transpose tile
+constexpr int VEC_BLK = 4096;      // float4 per vector-op block (one slice per block)
+constexpr int VEC_THREADS = 256;
+
+// Device-side view of a geometry, passed to kernels by value.
+struct DevGeom {
+    const SliceInfo *slices;
+    const AngleInfo *ang;        // [sum n_theta]
+    const float *m_o;            // [sum n_theta]
+    const float4 *pix;           // [sum n_dp]: (A, c, w, m_r)
+    const int *fwd_prefix;       // [n_slices + 1] work-item prefix sums
+    const int *ic_prefix;
+    const int *adj_prefix;
+    const int *prep_prefix;
+    const int *vec_prefix;
+    int n_slices;
+    int total_fwd, total_ic, total_adj, total_prep, total_vec;
+    int max_ndp, max_n_theta;
+    ModelConsts mc;
+};
+
+#ifdef __CUDACC__
+// Slice owning work item `item`: the largest s with prefix[s] <= item.
+__device__ __forceinline__ int find_slice(const int *prefix, int n_slices, int item)
+{
+    int lo = 0, hi = n_slices - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+
+struct Solver;
+
+}  // namespace ei
+
+// The opaque handle.
+struct ei_geometry {
+    int n_slices = 0;
+    int n_m = 0;
+    int device = 0;
+    std::vector<ei::SliceInfo> h_slices;
+    std::vector<int> h_vec_prefix;
+    float lambda[3], scale[3];
+    ei::DevGeom dg{};
+    std::vector<void *> allocs;    // device allocations owned by the geometry
+    // workspace for objective / forward evaluations
+    float4 *xp = nullptr;          // padded row-major copy of the volume (times mult)
+    float4 *xt = nullptr;          // padded transposed copy
+    float *proj = nullptr;         // proj layout
+    float4 *sino4 = nullptr;       // sino4 layout
+    double *part_ic = nullptr;     // [total_ic]
+    double *part_adj = nullptr;    // [total_adj]
+    double *S_dev = nullptr;       // [n_slices]
+    int64_t vol_count = 0, pad_count = 0, proj_count = 0, sino4_count = 0, meas_count = 0;
+    int64_t workspace_bytes = 0;
+    ei::Solver *solver = nullptr;      // allocated on first ei_reconstruct
+};
+
+namespace ei {
+
+enum IcMode { IC_MODEL = 0, IC_OBJECTIVE = 1, IC_OBJECTIVE_GRAD = 2 };
+
+// Kernel launchers (each returns cudaGetLastError()).
+// xp/xt = padded copies of mult * vol (row-major and transposed).
+cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, float4 *xp,
+                        float4 *xt, const int *active, cudaStream_t st);
+// proj = R[x] from the padded copies.
+cudaError_t launch_project(const ei_geometry *g, const float4 *xp, const float4 *xt,
+                           float *proj, const int *active, cudaStream_t st);
+cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
+                      float4 *sino4, double *part, IcMode mode, const int *active,
+                      cudaStream_t st);
+// out = out_mult * R^T sino4 + reg2 * v ; per-tile partial sums of sum_c reg1_c v_c^2.
+// sino4 == nullptr: only the regulariser (out is then not written).
+cudaError_t launch_backproject(const ei_geometry *g, const float4 *sino4, const float4 *v,
+                               float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                               double *part, const int *active, cudaStream_t st);
+// S[s] = sum of part_ic over the slice's rows + sum of part_adj over its tiles.
+cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_ic,
+                                      const double *part_adj, double *S, const int *active,
+                                      cudaStream_t st);
+
+// S (and grad when non-null) for every active slice, on the geometry's workspace.
+// scaled == false: v is the physical x (P = R x, grad wrt x, regulariser on x/scale).
+// scaled == true:  v is u = x/scale (P = R (scale u), grad wrt u, regulariser on u).
+cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
+                     float4 *grad, bool scaled, const int *active, cudaStream_t st);
+
+int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_solve_opts *opts,
+                ei_solve_report *report, cudaStream_t st);
+void destroy_solver(ei_geometry *g);
+
+}  // namespace ei
+
+#define EI_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return _e;                  \
+    } while (0)

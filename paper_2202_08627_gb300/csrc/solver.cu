@@ -1,0 +1,650 @@
+// Batched L-BFGS for the cost S of Eq. 5 (the paper minimises S with SciPy's
+// L-BFGS, [Byrd 1995]); every slice is an independent problem with its own
+// memory, step length and stop test.
+//
+// Per slice k, in the solver's scaled variables u = x / scale:
+//   1. d = -H g: two-loop recursion over the kept (s_i, y_i) pairs, newest
+//      first then oldest first, H0 = (s.y / y.y) I of the newest pair;
+//   2. Armijo backtracking: alpha0 = 1/|g| while no pair is kept, else 1;
+//      accept when S(u + alpha d) <= S(u) + c1 alpha g.d, else halve;
+//   3. s = alpha d, y = g_new - g; keep the pair when s.y > eps |s| |y|;
+//   4. stop when (f - f_new) / max(|f|, |f_new|, 1) < tol or after max_iter.
+//
+// Execution: one "round" per host iteration = direction for the slices that
+// need one, one trial step + objective/gradient evaluation for every slice in
+// line search, Armijo test, and the memory update of accepted slices.  All
+// per-slice decisions are taken on the device by one-thread-per-slice scalar
+// kernels; the host reads back one summary word per round to stop.
+//
+// Vectors are the batched vol layout (float4 per voxel, pad lane kept at 0);
+// vector kernels work on VEC_BLK-element blocks that each belong to one slice
+// and write one FP64 partial dot product per block.  A consumer block sums its
+// slice's partials itself in a fixed order (deterministic, no atomics); the
+// partial buffers alternate between launches so no kernel reads what it writes.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "ei_internal.h"
+
+namespace ei {
+
+struct SliceState {
+    double f, f_t, gd, gg, alpha, gamma, f0;
+    int k, count, head, trials;
+    int status, converged, reset, pad_;
+};
+
+struct Solver {
+    int m = 0, ring = 0;
+    int64_t vol_count = 0;
+    float4 *u = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
+    float4 *Sr = nullptr, *Yr = nullptr;    // rings of `ring` slots
+    float *meas_stage = nullptr;            // device copy of host s_exp
+    float4 *vol_stage = nullptr;            // device copy of host x0 / solution
+    double *part[4] = {nullptr, nullptr, nullptr, nullptr};
+    double *rho = nullptr;                  // [ring][S]
+    double *alpha_i = nullptr;              // [m][S]
+    SliceState *st = nullptr;               // [S]
+    int *mask_dir = nullptr, *mask_ls = nullptr, *mask_acc = nullptr;
+    int *summary = nullptr;                 // [2]: slices still running, slices in line search
+    int *summary_h = nullptr;               // pinned host copy
+    std::vector<void *> allocs;
+};
+
+struct SolverDev {
+    float4 *u, *g, *d, *xt, *gt, *Sr, *Yr;
+    int64_t vol_count;
+    int m, ring;
+    double *rho, *alpha_i;
+    SliceState *st;
+    int *mask_dir, *mask_ls, *mask_acc;
+};
+
+static SolverDev dev_view(const Solver *s)
+{
+    return SolverDev{s->u,  s->g,  s->d,   s->xt,     s->gt,      s->Sr,   s->Yr,
+                     s->vol_count, s->m, s->ring, s->rho, s->alpha_i, s->st,
+                     s->mask_dir, s->mask_ls, s->mask_acc};
+}
+
+// --------------------------------------------------------------------------
+// helpers
+// --------------------------------------------------------------------------
+struct VecBlock {
+    int s;            // slice
+    int64_t begin;    // first float4 (batched vol layout)
+    int64_t end;      // one past the last
+};
+
+__device__ __forceinline__ VecBlock vec_block(const DevGeom &dg)
+{
+    VecBlock b;
+    b.s = find_slice(dg.vec_prefix, dg.n_slices, blockIdx.x);
+    const SliceInfo &si = dg.slices[b.s];
+    const int64_t nvox = (int64_t)si.n * si.n;
+    const int64_t lb = blockIdx.x - dg.vec_prefix[b.s];
+    b.begin = si.vol_off + lb * VEC_BLK;
+    b.end = si.vol_off + min(nvox, (lb + 1) * (int64_t)VEC_BLK);
+    return b;
+}
+
+__device__ __forceinline__ double dot3(float4 a, float4 b)
+{
+    return (double)(a.x * b.x + a.y * b.y + a.z * b.z);
+}
+
+// Block-wide sum, result broadcast to every thread.
+__device__ double block_allsum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// Sum of a slice's per-block partials, fixed order, broadcast to the block.
+__device__ double slice_partials(const DevGeom &dg, const double *part, int s, double *red)
+{
+    double acc = 0.0;
+    for (int b = dg.vec_prefix[s] + threadIdx.x; b < dg.vec_prefix[s + 1]; b += blockDim.x)
+        acc += part[b];
+    return block_allsum(acc, red);
+}
+
+__device__ __forceinline__ int slot_of(const SolverDev &sv, int s, int i)
+{
+    const int h = sv.st[s].head;
+    return ((h - 1 - i) % sv.ring + sv.ring) % sv.ring;
+}
+
+__device__ __forceinline__ float4 f4(float x, float y, float z) { return make_float4(x, y, z, 0.f); }
+
+// --------------------------------------------------------------------------
+// vector kernels
+// --------------------------------------------------------------------------
+// u = x0 / scale (x0 in vol layout)
+__global__ void k_to_scaled(DevGeom dg, const float4 *__restrict__ x0, float4 *__restrict__ u, float4 inv)
+{
+    const VecBlock b = vec_block(dg);
+    for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
+        const float4 x = x0[i];
+        u[i] = f4(x.x * inv.x, x.y * inv.y, x.z * inv.z);
+    }
+}
+
+// x = u * scale
+__global__ void k_from_scaled(DevGeom dg, const float4 *__restrict__ u, float4 *__restrict__ x, float4 sc)
+{
+    const VecBlock b = vec_block(dg);
+    for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
+        const float4 v = u[i];
+        x[i] = f4(v.x * sc.x, v.y * sc.y, v.z * sc.z);
+    }
+}
+
+// two-loop, first pass start: d = g; pout = S_slot(0) . d
+__global__ void k_tl_first(DevGeom dg, SolverDev sv, double *__restrict__ pout)
+{
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_dir[s]) {
+        if (threadIdx.x == 0) pout[blockIdx.x] = 0.0;
+        return;
+    }
+    const bool pair = sv.st[s].count > 0;
+    const float4 *Sv = sv.Sr + (int64_t)(pair ? slot_of(sv, s, 0) : 0) * sv.vol_count;
+    double acc = 0.0;
+    for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
+        const float4 gv = sv.g[i];
+        sv.d[i] = gv;
+        if (pair) acc += dot3(Sv[i], gv);
+    }
+    __shared__ double red[32];
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
+}
+
+// two-loop, first pass step i (newest first):
+//   alpha_i = rho_i S_i.d ; d -= alpha_i Y_i ; pout = S_{i+1} . d
+__global__ void k_tl_down(DevGeom dg, SolverDev sv, int i, const double *__restrict__ pin,
+                          double *__restrict__ pout)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_dir[s] || i >= sv.st[s].count) {
+        if (threadIdx.x == 0) pout[blockIdx.x] = pin[blockIdx.x];
+        return;
+    }
+    const int slot = slot_of(sv, s, i);
+    const double sd = slice_partials(dg, pin, s, red);
+    const double al = sv.rho[(int64_t)slot * dg.n_slices + s] * sd;
+    if (blockIdx.x == dg.vec_prefix[s] && threadIdx.x == 0)
+        sv.alpha_i[(int64_t)i * dg.n_slices + s] = al;
+    const float alf = (float)al;
+    const float4 *Y = sv.Yr + (int64_t)slot * sv.vol_count;
+    const bool next = i + 1 < sv.st[s].count;
+    const float4 *Sn = sv.Sr + (int64_t)(next ? slot_of(sv, s, i + 1) : 0) * sv.vol_count;
+    double acc = 0.0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        const float4 y = Y[e];
+        float4 dv = sv.d[e];
+        dv = f4(fmaf(-alf, y.x, dv.x), fmaf(-alf, y.y, dv.y), fmaf(-alf, y.z, dv.z));
+        sv.d[e] = dv;
+        if (next) acc += dot3(Sn[e], dv);
+    }
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
+}
+
+// middle: d *= gamma (1 without pairs); pout = Y_{count-1} . d
+__global__ void k_tl_mid(DevGeom dg, SolverDev sv, double *__restrict__ pout)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_dir[s]) {
+        if (threadIdx.x == 0) pout[blockIdx.x] = 0.0;
+        return;
+    }
+    const int cnt = sv.st[s].count;
+    const float gam = cnt > 0 ? (float)sv.st[s].gamma : 1.f;
+    const float4 *Y = sv.Yr + (int64_t)(cnt > 0 ? slot_of(sv, s, cnt - 1) : 0) * sv.vol_count;
+    double acc = 0.0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        float4 dv = sv.d[e];
+        dv = f4(dv.x * gam, dv.y * gam, dv.z * gam);
+        sv.d[e] = dv;
+        if (cnt > 0) acc += dot3(Y[e], dv);
+    }
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
+}
+
+// two-loop, second pass step i (oldest first):
+//   beta = rho_i Y_i.d ; d += (alpha_i - beta) S_i ; pout = Y_{i-1} . d
+__global__ void k_tl_up(DevGeom dg, SolverDev sv, int i, const double *__restrict__ pin,
+                        double *__restrict__ pout)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_dir[s] || i >= sv.st[s].count) {
+        if (threadIdx.x == 0) pout[blockIdx.x] = pin[blockIdx.x];
+        return;
+    }
+    const int slot = slot_of(sv, s, i);
+    const double yd = slice_partials(dg, pin, s, red);
+    const double beta = sv.rho[(int64_t)slot * dg.n_slices + s] * yd;
+    const float coef = (float)(sv.alpha_i[(int64_t)i * dg.n_slices + s] - beta);
+    const float4 *Sv = sv.Sr + (int64_t)slot * sv.vol_count;
+    const bool next = i >= 1;
+    const float4 *Yn = sv.Yr + (int64_t)(next ? slot_of(sv, s, i - 1) : 0) * sv.vol_count;
+    double acc = 0.0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        const float4 sv4 = Sv[e];
+        float4 dv = sv.d[e];
+        dv = f4(fmaf(coef, sv4.x, dv.x), fmaf(coef, sv4.y, dv.y), fmaf(coef, sv4.z, dv.z));
+        sv.d[e] = dv;
+        if (next) acc += dot3(Yn[e], dv);
+    }
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) pout[blockIdx.x] = t;
+}
+
+// end: d = -d ; p_gd = g.d ; p_gg = g.g
+__global__ void k_tl_end(DevGeom dg, SolverDev sv, double *__restrict__ p_gd, double *__restrict__ p_gg)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_dir[s]) {
+        if (threadIdx.x == 0) p_gd[blockIdx.x] = 0.0, p_gg[blockIdx.x] = 0.0;
+        return;
+    }
+    double a_gd = 0.0, a_gg = 0.0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        float4 dv = sv.d[e];
+        dv = f4(-dv.x, -dv.y, -dv.z);
+        sv.d[e] = dv;
+        const float4 gv = sv.g[e];
+        a_gd += dot3(gv, dv);
+        a_gg += dot3(gv, gv);
+    }
+    const double t1 = block_allsum(a_gd, red);
+    const double t2 = block_allsum(a_gg, red);
+    if (threadIdx.x == 0) p_gd[blockIdx.x] = t1, p_gg[blockIdx.x] = t2;
+}
+
+// d = -g for slices whose direction was reset
+__global__ void k_reset_dir(DevGeom dg, SolverDev sv)
+{
+    const VecBlock b = vec_block(dg);
+    if (!sv.st[b.s].reset) return;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        const float4 gv = sv.g[e];
+        sv.d[e] = f4(-gv.x, -gv.y, -gv.z);
+    }
+}
+
+// trial point xt = u + alpha d
+__global__ void k_trial(DevGeom dg, SolverDev sv)
+{
+    const VecBlock b = vec_block(dg);
+    if (!sv.mask_ls[b.s]) return;
+    const float al = (float)sv.st[b.s].alpha;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        const float4 uv = sv.u[e], dv = sv.d[e];
+        sv.xt[e] = f4(fmaf(al, dv.x, uv.x), fmaf(al, dv.y, uv.y), fmaf(al, dv.z, uv.z));
+    }
+}
+
+// accepted step: S_head = xt - u, Y_head = gt - g, u = xt, g = gt; partial s.y, s.s, y.y
+__global__ void k_accept(DevGeom dg, SolverDev sv, double *__restrict__ p_sy,
+                         double *__restrict__ p_ss, double *__restrict__ p_yy)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    const int s = b.s;
+    if (!sv.mask_acc[s]) return;
+    const int slot = sv.st[s].head;
+    float4 *Sv = sv.Sr + (int64_t)slot * sv.vol_count;
+    float4 *Yv = sv.Yr + (int64_t)slot * sv.vol_count;
+    double a_sy = 0.0, a_ss = 0.0, a_yy = 0.0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+        const float4 x = sv.xt[e], uv = sv.u[e], gn = sv.gt[e], go = sv.g[e];
+        const float4 sd = f4(x.x - uv.x, x.y - uv.y, x.z - uv.z);
+        const float4 yd = f4(gn.x - go.x, gn.y - go.y, gn.z - go.z);
+        Sv[e] = sd;
+        Yv[e] = yd;
+        sv.u[e] = x;
+        sv.g[e] = gn;
+        a_sy += dot3(sd, yd);
+        a_ss += dot3(sd, sd);
+        a_yy += dot3(yd, yd);
+    }
+    const double t1 = block_allsum(a_sy, red);
+    const double t2 = block_allsum(a_ss, red);
+    const double t3 = block_allsum(a_yy, red);
+    if (threadIdx.x == 0) p_sy[blockIdx.x] = t1, p_ss[blockIdx.x] = t2, p_yy[blockIdx.x] = t3;
+}
+
+// --------------------------------------------------------------------------
+// scalar kernels (one block, one thread per slice)
+// --------------------------------------------------------------------------
+struct Opts {
+    double tol, c1, curv_eps;
+    int max_iter, max_trials;
+};
+
+__device__ double serial_sum(const DevGeom &dg, const double *part, int s)
+{
+    double acc = 0.0;
+    for (int b = dg.vec_prefix[s]; b < dg.vec_prefix[s + 1]; ++b) acc += part[b];
+    return acc;
+}
+
+// initial evaluation done: f0 = S, state reset
+__global__ void k_init_state(DevGeom dg, SolverDev sv, const double *__restrict__ S, int *summary)
+{
+    int running = 0;
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        SliceState &q = sv.st[s];
+        q = SliceState{};
+        q.f = q.f0 = S[s];
+        q.gamma = 1.0;
+        const bool ok = isfinite(q.f);
+        q.status = ok ? EI_OK : EI_ERR_NONFINITE;
+        sv.mask_dir[s] = ok;
+        sv.mask_ls[s] = 0;
+        sv.mask_acc[s] = 0;
+        running += ok;
+    }
+    __shared__ int acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    atomicAdd(&acc, running);
+    __syncthreads();
+    if (threadIdx.x == 0) summary[0] = acc, summary[1] = 0;
+}
+
+// direction finished: choose the first trial step
+__global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ p_gd,
+                           const double *__restrict__ p_gg)
+{
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        SliceState &q = sv.st[s];
+        q.reset = 0;
+        if (!sv.mask_dir[s]) continue;
+        sv.mask_dir[s] = 0;
+        const double gd = serial_sum(dg, p_gd, s), gg = serial_sum(dg, p_gg, s);
+        q.gg = gg;
+        q.gd = gd;
+        if (!(gd < 0.0)) {
+            if (!(gg > 0.0)) {            // zero gradient: stationary point
+                q.converged = 1;
+                continue;
+            }
+            q.reset = 1;                  // not a descent direction: restart from -g
+            q.count = 0;
+            q.gd = -gg;
+        }
+        q.alpha = q.count == 0 ? 1.0 / sqrt(gg) : 1.0;
+        q.trials = 0;
+        sv.mask_ls[s] = 1;
+    }
+}
+
+// Armijo test of the trial point
+__global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S, Opts o)
+{
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        if (!sv.mask_ls[s]) continue;
+        SliceState &q = sv.st[s];
+        const double ft = S[s];
+        if (isfinite(ft) && ft <= q.f + o.c1 * q.alpha * q.gd) {
+            q.f_t = ft;
+            sv.mask_ls[s] = 0;
+            sv.mask_acc[s] = 1;
+        } else {
+            q.alpha *= 0.5;
+            if (++q.trials >= o.max_trials) {
+                q.status = EI_ERR_LINESEARCH;
+                sv.mask_ls[s] = 0;
+            }
+        }
+    }
+}
+
+// memory update and stop test of accepted slices; summary of what still runs
+__global__ void k_update(DevGeom dg, SolverDev sv, const double *__restrict__ p_sy,
+                         const double *__restrict__ p_ss, const double *__restrict__ p_yy, Opts o,
+                         int *summary)
+{
+    int running = 0, in_ls = 0;
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        SliceState &q = sv.st[s];
+        if (sv.mask_acc[s]) {
+            sv.mask_acc[s] = 0;
+            const double sy = serial_sum(dg, p_sy, s), ss = serial_sum(dg, p_ss, s),
+                         yy = serial_sum(dg, p_yy, s);
+            if (sy > o.curv_eps * sqrt(ss) * sqrt(yy)) {
+                sv.rho[(int64_t)q.head * dg.n_slices + s] = 1.0 / sy;
+                q.gamma = sy / yy;
+                q.head = (q.head + 1) % sv.ring;
+                q.count = min(q.count + 1, sv.m);
+            }
+            const double rel = (q.f - q.f_t) / fmax(fmax(fabs(q.f), fabs(q.f_t)), 1.0);
+            q.f = q.f_t;
+            q.k += 1;
+            if (rel < o.tol) q.converged = 1;
+            else if (q.k < o.max_iter) sv.mask_dir[s] = 1;
+        }
+        running += sv.mask_dir[s] | sv.mask_ls[s];
+        in_ls += sv.mask_ls[s];
+    }
+    __shared__ int a0, a1;
+    if (threadIdx.x == 0) a0 = 0, a1 = 0;
+    __syncthreads();
+    atomicAdd(&a0, running);
+    atomicAdd(&a1, in_ls);
+    __syncthreads();
+    if (threadIdx.x == 0) summary[0] = a0, summary[1] = a1;
+}
+
+// --------------------------------------------------------------------------
+// host driver
+// --------------------------------------------------------------------------
+template <class T>
+static cudaError_t salloc(Solver *s, T **p, size_t count)
+{
+    void *ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) return e;
+    s->allocs.push_back(ptr);
+    *p = static_cast<T *>(ptr);
+    return cudaSuccess;
+}
+
+void destroy_solver(ei_geometry *g)
+{
+    if (!g->solver) return;
+    for (void *p : g->solver->allocs) cudaFree(p);
+    if (g->solver->summary_h) cudaFreeHost(g->solver->summary_h);
+    delete g->solver;
+    g->solver = nullptr;
+}
+
+static cudaError_t ensure_solver(ei_geometry *g, int m)
+{
+    if (g->solver && g->solver->m == m) return cudaSuccess;
+    destroy_solver(g);
+    Solver *s = new Solver();
+    g->solver = s;
+    s->m = m;
+    s->ring = m + 1;
+    s->vol_count = g->vol_count;
+    const size_t V = (size_t)g->vol_count, S = (size_t)g->n_slices;
+    const size_t NB = (size_t)g->dg.total_vec;
+    EI_CUDA_TRY(salloc(s, &s->u, V));
+    EI_CUDA_TRY(salloc(s, &s->g, V));
+    EI_CUDA_TRY(salloc(s, &s->d, V));
+    EI_CUDA_TRY(salloc(s, &s->xt, V));
+    EI_CUDA_TRY(salloc(s, &s->gt, V));
+    EI_CUDA_TRY(salloc(s, &s->Sr, V * s->ring));
+    EI_CUDA_TRY(salloc(s, &s->Yr, V * s->ring));
+    for (int k = 0; k < 4; ++k) EI_CUDA_TRY(salloc(s, &s->part[k], NB));
+    EI_CUDA_TRY(salloc(s, &s->rho, (size_t)s->ring * S));
+    EI_CUDA_TRY(salloc(s, &s->alpha_i, (size_t)m * S));
+    EI_CUDA_TRY(salloc(s, &s->st, S));
+    EI_CUDA_TRY(salloc(s, &s->mask_dir, S));
+    EI_CUDA_TRY(salloc(s, &s->mask_ls, S));
+    EI_CUDA_TRY(salloc(s, &s->mask_acc, S));
+    EI_CUDA_TRY(salloc(s, &s->summary, 2));
+    EI_CUDA_TRY(cudaMallocHost(&s->summary_h, 2 * sizeof(int)));
+    // pad lanes of every vector stay 0: start from zeroed memory
+    EI_CUDA_TRY(cudaMemset(s->d, 0, V * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->Sr, 0, V * s->ring * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->Yr, 0, V * s->ring * sizeof(float4)));
+    return cudaSuccess;
+}
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
+                              const ei_solve_opts *opts, int *evals, cudaStream_t st)
+{
+    Solver *sv = g->solver;
+    const SolverDev dv = dev_view(sv);
+    const DevGeom &dg = g->dg;
+    const int NB = dg.total_vec;
+    const int T = VEC_THREADS;
+    const float4 inv = make_float4(1.f / g->scale[0], 1.f / g->scale[1], 1.f / g->scale[2], 0.f);
+    const float4 sc = make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
+    Opts o{opts->tol, opts->c1, opts->curv_eps, opts->max_iter, opts->max_trials};
+    const int scalar_threads = 256;
+
+    k_to_scaled<<<NB, T, 0, st>>>(dg, x_dev, sv->u, inv);
+    EI_CUDA_TRY(cudaGetLastError());
+    EI_CUDA_TRY(evaluate(g, sv->u, meas, g->S_dev, sv->g, true, nullptr, st));
+    k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
+    EI_CUDA_TRY(cudaGetLastError());
+    *evals = 1;
+    EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    EI_CUDA_TRY(cudaStreamSynchronize(st));
+    const long long max_rounds = (long long)opts->max_iter * (opts->max_trials + 1) + 2;
+    for (long long round = 0; sv->summary_h[0] > 0 && round < max_rounds; ++round) {
+        // ---- direction (gated per slice on mask_dir)
+        double *pa = sv->part[0], *pb = sv->part[1];
+        k_tl_first<<<NB, T, 0, st>>>(dg, dv, pa);
+        for (int i = 0; i < sv->m; ++i) {
+            k_tl_down<<<NB, T, 0, st>>>(dg, dv, i, pa, pb);
+            std::swap(pa, pb);
+        }
+        k_tl_mid<<<NB, T, 0, st>>>(dg, dv, pa);
+        for (int i = sv->m - 1; i >= 0; --i) {
+            k_tl_up<<<NB, T, 0, st>>>(dg, dv, i, pa, pb);
+            std::swap(pa, pb);
+        }
+        k_tl_end<<<NB, T, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
+        k_ls_start<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
+        k_reset_dir<<<NB, T, 0, st>>>(dg, dv);
+        // ---- trial step for every slice in line search
+        k_trial<<<NB, T, 0, st>>>(dg, dv);
+        EI_CUDA_TRY(cudaGetLastError());
+        EI_CUDA_TRY(evaluate(g, sv->xt, meas, g->S_dev, sv->gt, true, sv->mask_ls, st));
+        k_armijo<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, o);
+        k_accept<<<NB, T, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2]);
+        k_update<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2], o,
+                                               sv->summary);
+        EI_CUDA_TRY(cudaGetLastError());
+        *evals += 1;
+        EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int),
+                                    cudaMemcpyDeviceToHost, st));
+        EI_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    k_from_scaled<<<NB, T, 0, st>>>(dg, sv->u, x_dev, sc);
+    return cudaGetLastError();
+}
+
+int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_solve_opts *opts,
+                ei_solve_report *report, cudaStream_t st)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = ensure_solver(g, opts->lbfgs_m);
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        destroy_solver(g);
+        return oom ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    }
+    Solver *sv = g->solver;
+    const bool meas_dev = is_device_ptr(s_exp), vol_dev = is_device_ptr(vol_inout);
+    const float *meas = s_exp;
+    float4 *x = (float4 *)vol_inout;
+    if (!meas_dev) {
+        if (!sv->meas_stage) e = salloc(sv, &sv->meas_stage, (size_t)g->meas_count);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sv->meas_stage, s_exp, (size_t)g->meas_count * sizeof(float),
+                                cudaMemcpyHostToDevice, st);
+        meas = sv->meas_stage;
+    }
+    if (e == cudaSuccess && !vol_dev) {
+        if (!sv->vol_stage) e = salloc(sv, &sv->vol_stage, (size_t)g->vol_count);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sv->vol_stage, vol_inout, (size_t)g->vol_count * sizeof(float4),
+                                cudaMemcpyHostToDevice, st);
+        x = sv->vol_stage;
+    }
+    int evals = 0;
+    if (e == cudaSuccess) e = run_solver(g, meas, x, opts, &evals, st);
+    if (e == cudaSuccess && !vol_dev)
+        e = cudaMemcpyAsync(vol_inout, sv->vol_stage, (size_t)g->vol_count * sizeof(float4),
+                            cudaMemcpyDeviceToHost, st);
+    std::vector<SliceState> hs(g->n_slices);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs.data(), sv->st, sizeof(SliceState) * g->n_slices,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    int first_err = EI_OK;
+    for (int s = 0; s < g->n_slices; ++s) {
+        int status = hs[s].status;
+        if (status == EI_OK && isnan(hs[s].f)) status = EI_ERR_NONFINITE;
+        if (status != EI_OK && first_err == EI_OK) first_err = status;
+        if (report) {
+            if (report->iterations) report->iterations[s] = hs[s].k;
+            if (report->status) report->status[s] = status;
+            if (report->converged) report->converged[s] = hs[s].converged;
+            if (report->f_final) report->f_final[s] = hs[s].f;
+            if (report->f_initial) report->f_initial[s] = hs[s].f0;
+        }
+    }
+    if (report) {
+        report->evaluations = evals;
+        report->seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return first_err;
+}
+
+}  // namespace ei

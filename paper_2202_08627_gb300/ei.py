@@ -1,0 +1,428 @@
+"""Thin Python binding of libei.so (C ABI in include/ei.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels behind the ABI.  Functions keep the ABI's names.  Arrays are PyTorch
+CUDA tensors (float32, contiguous, 16-byte aligned) in the layouts documented
+in include/ei.h; ``pack_volume`` / ``unpack_volume`` and friends convert
+between those layouts and per-slice arrays.
+
+The library is loaded on first use.  If it has not been built (see
+``paper_2202_08627_gb300.build``) the import of the library raises — there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libei.so")
+
+EI_OK, EI_ERR_ARG, EI_ERR_CUDA, EI_ERR_NONFINITE, EI_ERR_LINESEARCH = 0, 1, 2, 3, 4
+EI_ERR_TIMEOUT, EI_ERR_DEVICE_CHECK, EI_ERR_ALLOC = 5, 6, 7
+EI_MAX_NDET = 8192
+EI_MAX_NM = 32
+
+c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+
+
+class ei_slice_dims(ctypes.Structure):
+    _fields_ = [("n", c_int), ("n_theta", c_int), ("n_det", c_int), ("pitch_cm", c_double)]
+
+
+class ei_geometry_desc(ctypes.Structure):
+    _fields_ = [("n", c_int), ("n_theta", c_int), ("n_det", c_int), ("n_m", c_int),
+                ("pitch_cm", c_double),
+                ("theta", ctypes.POINTER(c_double)), ("m", ctypes.POINTER(c_double)),
+                ("z_cm", c_double), ("period_cm", c_double), ("kappa_sigma", c_double),
+                ("flat_A", c_void_p), ("flat_c", c_void_p), ("flat_w", c_void_p),
+                ("lambda_", c_double * 3), ("scale", c_double * 3),
+                ("m_o", c_void_p), ("m_r", c_void_p)]
+
+
+class ei_slice_layout(ctypes.Structure):
+    _fields_ = [("n", c_int), ("n_theta", c_int), ("n_det", c_int), ("n_dp", c_int),
+                ("n_m", c_int), ("pitch_cm", c_double),
+                ("vol_offset", c_int64), ("vol_count", c_int64),
+                ("proj_offset", c_int64), ("proj_count", c_int64),
+                ("sino4_offset", c_int64), ("sino4_count", c_int64),
+                ("meas_offset", c_int64), ("meas_count", c_int64)]
+
+
+class ei_layout(ctypes.Structure):
+    _fields_ = [("n_slices", c_int), ("n_m", c_int),
+                ("vol_count", c_int64), ("proj_count", c_int64), ("sino4_count", c_int64),
+                ("meas_count", c_int64), ("workspace_bytes", c_int64)]
+
+
+class ei_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int), ("lbfgs_m", c_int), ("c1", c_double),
+                ("max_trials", c_int), ("curv_eps", c_double)]
+
+
+class ei_solve_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.POINTER(c_int)), ("status", ctypes.POINTER(c_int)),
+                ("converged", ctypes.POINTER(c_int)), ("f_final", ctypes.POINTER(c_double)),
+                ("f_initial", ctypes.POINTER(c_double)), ("evaluations", c_int),
+                ("seconds", c_double)]
+
+
+EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get_slice_layout",
+            "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
+            "ei_reconstruct", "ei_default_solve_opts", "ei_status_string"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libei.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libei.so not found at %s: build it with "
+                           "paper_2202_08627_gb300.build.build() (there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.ei_setup_geometry.argtypes = [P(ei_geometry_desc), c_int, P(ei_slice_dims), P(c_void_p)]
+    lib.ei_setup_geometry.restype = c_int
+    lib.ei_destroy_geometry.argtypes = [c_void_p]
+    lib.ei_destroy_geometry.restype = None
+    lib.ei_get_layout.argtypes = [c_void_p, P(ei_layout)]
+    lib.ei_get_layout.restype = c_int
+    lib.ei_get_slice_layout.argtypes = [c_void_p, c_int, P(ei_slice_layout)]
+    lib.ei_get_slice_layout.restype = c_int
+    for name in ("ei_project", "ei_backproject", "ei_ic_model", "ei_forward"):
+        fn = getattr(lib, name)
+        fn.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        fn.restype = c_int
+    lib.ei_objective_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.ei_objective_grad.restype = c_int
+    lib.ei_reconstruct.argtypes = [c_void_p, c_void_p, c_void_p, P(ei_solve_opts),
+                                   P(ei_solve_report), c_void_p]
+    lib.ei_reconstruct.restype = c_int
+    lib.ei_default_solve_opts.argtypes = [P(ei_solve_opts)]
+    lib.ei_default_solve_opts.restype = None
+    lib.ei_status_string.argtypes = [c_int]
+    lib.ei_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class EIError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = load_library().ei_status_string(status).decode()
+        super().__init__("%s failed: %s" % (where, msg))
+
+
+def _check(status: int, where: str):
+    if status != EI_OK:
+        raise EIError(status, where)
+
+
+def ei_status_string(status: int) -> str:
+    return load_library().ei_status_string(status).decode()
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dptr(t, name: str, dtype=None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return int(t.data_ptr())
+
+
+@dataclass
+class SliceLayout:
+    n: int
+    n_theta: int
+    n_det: int
+    n_dp: int
+    n_m: int
+    pitch_cm: float
+    vol_offset: int
+    vol_count: int
+    proj_offset: int
+    proj_count: int
+    sino4_offset: int
+    sino4_count: int
+    meas_offset: int
+    meas_count: int
+
+
+class Geometry:
+    """Owns an ei_geometry handle (device workspace on the current device)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        lib = load_library()
+        lay = ei_layout()
+        _check(lib.ei_get_layout(handle, ctypes.byref(lay)), "ei_get_layout")
+        self.n_slices = lay.n_slices
+        self.n_m = lay.n_m
+        self.vol_count = lay.vol_count
+        self.proj_count = lay.proj_count
+        self.sino4_count = lay.sino4_count
+        self.meas_count = lay.meas_count
+        self.workspace_bytes = lay.workspace_bytes
+        self.slices: List[SliceLayout] = []
+        for s in range(self.n_slices):
+            sl = ei_slice_layout()
+            _check(lib.ei_get_slice_layout(handle, s, ctypes.byref(sl)), "ei_get_slice_layout")
+            self.slices.append(SliceLayout(*[getattr(sl, f) for f, _ in sl._fields_]))
+
+    def close(self):
+        if self.handle:
+            load_library().ei_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- layout marshalling (no arithmetic of the method)
+    def empty(self, what: str, device="cuda"):
+        import torch
+        if what == "vol":
+            return torch.zeros((self.vol_count, 4), dtype=torch.float32, device=device)
+        if what == "proj":
+            return torch.zeros(self.proj_count, dtype=torch.float32, device=device)
+        if what == "sino4":
+            return torch.zeros((self.sino4_count, 4), dtype=torch.float32, device=device)
+        if what == "meas":
+            return torch.zeros(self.meas_count, dtype=torch.float32, device=device)
+        raise ValueError(what)
+
+    def pack_volume(self, vols: Sequence[np.ndarray], device="cuda"):
+        """[3][n][n] arrays per slice -> vol layout tensor [vol_count][4]."""
+        import torch
+        out = np.zeros((self.vol_count, 4), dtype=np.float32)
+        for s, sl in enumerate(self.slices):
+            v = np.asarray(vols[s], dtype=np.float32).reshape(3, sl.n * sl.n)
+            out[sl.vol_offset:sl.vol_offset + sl.vol_count, :3] = v.T
+        return torch.from_numpy(out).to(device)
+
+    def unpack_volume(self, t) -> List[np.ndarray]:
+        a = t.detach().cpu().numpy().reshape(self.vol_count, 4)
+        return [a[sl.vol_offset:sl.vol_offset + sl.vol_count, :3].T.reshape(3, sl.n, sl.n).copy()
+                for sl in self.slices]
+
+    def pack_meas(self, meas: Sequence[np.ndarray], device="cuda"):
+        """[M][n_theta][n_det] arrays per slice -> measurement layout tensor."""
+        import torch
+        out = np.zeros(self.meas_count, dtype=np.float32)
+        for s, sl in enumerate(self.slices):
+            blk = np.zeros((sl.n_m, sl.n_theta, sl.n_dp), dtype=np.float32)
+            blk[:, :, :sl.n_det] = meas[s]
+            out[sl.meas_offset:sl.meas_offset + sl.meas_count] = blk.ravel()
+        return torch.from_numpy(out).to(device)
+
+    def unpack_meas(self, t) -> List[np.ndarray]:
+        a = t.detach().cpu().numpy()
+        return [a[sl.meas_offset:sl.meas_offset + sl.meas_count]
+                .reshape(sl.n_m, sl.n_theta, sl.n_dp)[:, :, :sl.n_det].copy() for sl in self.slices]
+
+    def pack_proj(self, projs: Sequence[np.ndarray], device="cuda"):
+        import torch
+        out = np.zeros(self.proj_count, dtype=np.float32)
+        for s, sl in enumerate(self.slices):
+            blk = np.zeros((3, sl.n_theta, sl.n_dp), dtype=np.float32)
+            blk[:, :, :sl.n_det] = projs[s]
+            out[sl.proj_offset:sl.proj_offset + sl.proj_count] = blk.ravel()
+        return torch.from_numpy(out).to(device)
+
+    def unpack_proj(self, t) -> List[np.ndarray]:
+        a = t.detach().cpu().numpy()
+        return [a[sl.proj_offset:sl.proj_offset + sl.proj_count]
+                .reshape(3, sl.n_theta, sl.n_dp)[:, :, :sl.n_det].copy() for sl in self.slices]
+
+    def pack_sino4(self, sinos: Sequence[np.ndarray], device="cuda"):
+        """[3][n_theta][n_det] arrays per slice -> sino4 layout tensor [sino4_count][4]."""
+        import torch
+        out = np.zeros((self.sino4_count, 4), dtype=np.float32)
+        for s, sl in enumerate(self.slices):
+            blk = np.zeros((sl.n_theta, sl.n_dp, 3), dtype=np.float32)
+            blk[:, :sl.n_det, :] = np.moveaxis(np.asarray(sinos[s]), 0, -1)
+            out[sl.sino4_offset:sl.sino4_offset + sl.sino4_count, :3] = blk.reshape(-1, 3)
+        return torch.from_numpy(out).to(device)
+
+
+def ei_setup_geometry(n_m: int, m: Sequence[float], z_cm: float, period_cm: float,
+                      kappa_sigma: float, flat_A, flat_c, flat_w, lam=(1e-2, 1e-2, 1e-2),
+                      scale=(1.0, 1e-6, 1.0), n: int = 0, n_theta: int = 0, n_det: int = 0,
+                      pitch_cm: float = 0.0, n_slices: int = 1,
+                      per_slice: Optional[Sequence[tuple]] = None, theta=None, m_o=None,
+                      m_r=None) -> Geometry:
+    """Create a geometry.  flat_* / m_o / m_r: numpy arrays (host) or CUDA
+    tensors; per_slice: list of (n, n_theta, n_det, pitch_cm) for uneven
+    batches (then n_slices = len(per_slice))."""
+    lib = load_library()
+    keep = []
+
+    def fptr(a):
+        if a is None:
+            return None
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                a = a.contiguous().float()
+                keep.append(a)
+                return a.data_ptr()
+        except ImportError:
+            pass
+        arr = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    d = ei_geometry_desc()
+    d.n, d.n_theta, d.n_det, d.n_m = int(n), int(n_theta), int(n_det), int(n_m)
+    d.pitch_cm = float(pitch_cm)
+    m_arr = np.ascontiguousarray(m, dtype=np.float64)
+    keep.append(m_arr)
+    d.m = m_arr.ctypes.data_as(ctypes.POINTER(c_double))
+    if theta is not None:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        keep.append(th)
+        d.theta = th.ctypes.data_as(ctypes.POINTER(c_double))
+    d.z_cm, d.period_cm, d.kappa_sigma = float(z_cm), float(period_cm), float(kappa_sigma)
+    d.flat_A, d.flat_c, d.flat_w = fptr(flat_A), fptr(flat_c), fptr(flat_w)
+    d.lambda_[:] = [float(v) for v in lam]
+    d.scale[:] = [float(v) for v in scale]
+    d.m_o, d.m_r = fptr(m_o), fptr(m_r)
+    ps = None
+    if per_slice is not None:
+        n_slices = len(per_slice)
+        ps = (ei_slice_dims * n_slices)(*[ei_slice_dims(int(a), int(b), int(c), float(e))
+                                          for (a, b, c, e) in per_slice])
+    h = c_void_p()
+    _check(lib.ei_setup_geometry(ctypes.byref(d), int(n_slices), ps, ctypes.byref(h)),
+           "ei_setup_geometry")
+    return Geometry(h.value)
+
+
+def ei_destroy_geometry(geom: Geometry) -> None:
+    geom.close()
+
+
+def _check_size(t, count: int, name: str):
+    if t.numel() < count:
+        raise ValueError("%s holds %d floats, the layout needs %d" % (name, t.numel(), count))
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+
+
+def ei_project(geom: Geometry, vol, proj, stream=None) -> None:
+    import torch
+    _check_size(vol, 4 * geom.vol_count, "vol")
+    _check_size(proj, geom.proj_count, "proj")
+    _check(load_library().ei_project(geom.handle, _dptr(vol, "vol", torch.float32),
+                                     _dptr(proj, "proj", torch.float32), _stream_ptr(stream)),
+           "ei_project")
+
+
+def ei_backproject(geom: Geometry, sino4, vol, stream=None) -> None:
+    import torch
+    _check_size(sino4, 4 * geom.sino4_count, "sino4")
+    _check_size(vol, 4 * geom.vol_count, "vol")
+    _check(load_library().ei_backproject(geom.handle, _dptr(sino4, "sino4", torch.float32),
+                                         _dptr(vol, "vol", torch.float32), _stream_ptr(stream)),
+           "ei_backproject")
+
+
+def ei_ic_model(geom: Geometry, proj, s_mod, stream=None) -> None:
+    import torch
+    _check_size(proj, geom.proj_count, "proj")
+    _check_size(s_mod, geom.meas_count, "s_mod")
+    _check(load_library().ei_ic_model(geom.handle, _dptr(proj, "proj", torch.float32),
+                                      _dptr(s_mod, "s_mod", torch.float32), _stream_ptr(stream)),
+           "ei_ic_model")
+
+
+def ei_forward(geom: Geometry, vol, s_mod, stream=None) -> None:
+    import torch
+    _check_size(vol, 4 * geom.vol_count, "vol")
+    _check_size(s_mod, geom.meas_count, "s_mod")
+    _check(load_library().ei_forward(geom.handle, _dptr(vol, "vol", torch.float32),
+                                     _dptr(s_mod, "s_mod", torch.float32), _stream_ptr(stream)),
+           "ei_forward")
+
+
+def ei_objective_grad(geom: Geometry, vol, s_exp, S_out, grad=None, stream=None) -> None:
+    """S_out: float64 tensor [n_slices] (CUDA or CPU); grad: vol-layout tensor or None."""
+    import torch
+    _check_size(vol, 4 * geom.vol_count, "vol")
+    _check_size(s_exp, geom.meas_count, "s_exp")
+    if S_out.dtype != torch.float64 or S_out.numel() < geom.n_slices:
+        raise ValueError("S_out must be a float64 tensor of n_slices entries")
+    gp = None
+    if grad is not None:
+        _check_size(grad, 4 * geom.vol_count, "grad")
+        gp = _dptr(grad, "grad", torch.float32)
+    _check(load_library().ei_objective_grad(geom.handle, _dptr(vol, "vol", torch.float32),
+                                            _dptr(s_exp, "s_exp", torch.float32),
+                                            _dptr(S_out, "S_out"), gp, _stream_ptr(stream)),
+           "ei_objective_grad")
+
+
+def ei_default_solve_opts() -> ei_solve_opts:
+    o = ei_solve_opts()
+    load_library().ei_default_solve_opts(ctypes.byref(o))
+    return o
+
+
+@dataclass
+class SolveReport:
+    iterations: np.ndarray
+    status: np.ndarray
+    converged: np.ndarray
+    f_final: np.ndarray
+    f_initial: np.ndarray
+    evaluations: int
+    seconds: float
+    return_status: int
+
+
+def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbfgs_m=10,
+                   c1=1e-4, max_trials=20, curv_eps=1e-10, stream=None,
+                   raise_on_error: bool = True) -> SolveReport:
+    """Batched L-BFGS minimisation of S.  s_exp / vol_inout: CUDA tensors, or
+    pinned/pageable CPU tensors (the library stages host arrays)."""
+    import torch
+    if s_exp.numel() < geom.meas_count or vol_inout.numel() < 4 * geom.vol_count:
+        raise ValueError("s_exp / vol_inout smaller than the layout")
+    o = ei_solve_opts(float(tol), int(max_iter), int(lbfgs_m), float(c1), int(max_trials),
+                      float(curv_eps))
+    S = geom.n_slices
+    it = np.zeros(S, np.int32)
+    st = np.zeros(S, np.int32)
+    cv = np.zeros(S, np.int32)
+    ff = np.zeros(S, np.float64)
+    f0 = np.zeros(S, np.float64)
+    ip = ctypes.POINTER(c_int)
+    dp = ctypes.POINTER(c_double)
+    rep = ei_solve_report(it.ctypes.data_as(ip), st.ctypes.data_as(ip), cv.ctypes.data_as(ip),
+                          ff.ctypes.data_as(dp), f0.ctypes.data_as(dp), 0, 0.0)
+    rc = load_library().ei_reconstruct(geom.handle, _dptr(s_exp, "s_exp", torch.float32),
+                                       _dptr(vol_inout, "vol_inout", torch.float32),
+                                       ctypes.byref(o), ctypes.byref(rep), _stream_ptr(stream))
+    out = SolveReport(it, st, cv, ff, f0, rep.evaluations, rep.seconds, rc)
+    if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE):
+        raise EIError(rc, "ei_reconstruct")
+    return out
