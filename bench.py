@@ -1,0 +1,356 @@
+"""Benchmark of the EI reconstruction hot path on GB300.
+
+One step = one batched L-BFGS iteration over the whole workload: forward
+projection of the three channels, IC model + residual + per-pixel gradient,
+adjoint back-projection, FP64 reductions and the solver update, for every
+slice (the library's ei_reconstruct with tol = 0 and max_iter = steps).
+
+Default workload: 256 slices, half 1024x1024 and half 512x512, 1800 angles,
+1024-1536 detector pixels, M = 7 (about 16.5 GB of measured ICs, far larger
+than L2, so no flush is needed between steps).
+
+Metric: algorithmic forward + adjoint bytes moved per second over the whole
+step (GB/s), plus the per-kernel CUDA-event timings, the dominant kernel's
+roofline, the same metric end to end through the C ABI with host buffers,
+and the FP64 CPU oracle timed on a bounded sample on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = ("time-to-tolerance per 1024² slice (warm-start vs plain GPU); fwd+adj HBM GB/s")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, max_mhz_default: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz_default, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append((float(parts[2]), float(parts[3]), parts[5:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz_default, "reasons": ["no samples"]}
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, r in rows:
+            for name, val in zip(names[1:], r[1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def _device_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ inputs
+def build_problem(wl, rank: int, device):
+    """Geometry + measured ICs on the device (seeded, per rank)."""
+    import torch
+    from paper_2202_08627_gb300 import ei, inputs
+    seeds = [wl.seed0 + 1000 * rank + s for s in range(wl.n_slices)]
+    fA, fc, fw, th = [], [], [], []
+    for s, (n, nth, nd) in enumerate(wl.slices):
+        A, c, w = inputs.flat_ic(seeds[s], nd)
+        fA.append(A), fc.append(c), fw.append(w), th.append(inputs.angles(nth))
+    G = ei.ei_setup_geometry(
+        n_m=wl.n_m, m=inputs.mask_positions(wl.n_m), z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM,
+        kappa_sigma=inputs.KAPPA, flat_A=np.concatenate(fA), flat_c=np.concatenate(fc),
+        flat_w=np.concatenate(fw), lam=(inputs.LAMBDA,) * 3, scale=inputs.SCALE,
+        per_slice=wl.per_slice(), theta=np.concatenate(th))
+    proj = G.empty("proj", device)
+    for s, (n, nth, nd) in enumerate(wl.slices):
+        sl = G.slices[s]
+        P = inputs.ellipse_line_integrals_torch(inputs.random_ellipses(seeds[s]), th[s], nd,
+                                                inputs.pitch_for(n), device)
+        proj[sl.proj_offset:sl.proj_offset + sl.proj_count].view(3, nth, sl.n_dp)[:, :, :nd] = P
+    clean = G.empty("meas", device)
+    ei.ei_ic_model(G, proj, clean)
+    del proj
+    s_exp = inputs.poisson_noise_torch(clean, seed=wl.seed0 + 1000 * rank)
+    del clean
+    torch.cuda.synchronize()
+    return G, s_exp
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_sample(wl, angle_fraction: int, evals: int = 1):
+    """Time the FP64 oracle (as it stands) on one 512x512 slice of the workload
+    with 1/angle_fraction of its angles; returns (seconds per evaluation,
+    algorithmic fwd+adj bytes of that sample, threads, description)."""
+    import oracle
+    from paper_2202_08627_gb300 import inputs
+    n, nth, nd = next(sl for sl in wl.slices if sl[0] == min(x[0] for x in wl.slices))
+    nth_s = max(1, nth // angle_fraction)
+    spec = inputs.make_slice(wl.seed0, n, nth, nd, wl.n_m)
+    th = spec.theta[::angle_fraction][:nth_s]
+    geom = oracle.Geometry(n=n, n_theta=nth_s, n_det=nd, pitch=spec.pitch, theta=th, m=spec.m,
+                           z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM, kappa=inputs.KAPPA,
+                           flat_A=spec.flat_A, flat_c=spec.flat_c, flat_w=spec.flat_w)
+    P = inputs.ellipse_line_integrals(spec.ellipses, th, nd, spec.pitch)
+    s_exp = inputs.poisson_noise(oracle.ic_model(P, geom), spec.seed)
+    x = spec.truth * 0.9
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        oracle.objective_grad(x, s_exp, geom)
+    dt = (time.perf_counter() - t0) / evals
+    nbytes = 16 * n * n + 12 * nth_s * nd + 32 * n * n + 16 * nth_s * nd
+    desc = ("one %dx%d slice, %d of its %d angles, %d pixels, M=%d: %d objective+gradient "
+            "evaluation(s), FP64" % (n, n, nth_s, nth, nd, wl.n_m, evals))
+    return dt, nbytes, oracle.num_threads(), desc
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2202_08627_gb300 import workloads
+    wl = workloads.WORKLOADS[args.workload]()
+    frac = 8 if wl.name == "uneven1024" else 1
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, frac)
+    times = []
+    for _ in range(args.steps):
+        dt, nbytes, cores, desc = cpu_oracle_sample(wl, frac)
+        times.append(dt)
+    t = sum(times) / len(times)
+    val = nbytes / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description,
+                   "sample": desc, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2202_08627_gb300 import build, ei, workloads
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    wl = workloads.WORKLOADS[args.workload]()
+    device = torch.device("cuda", local_rank)
+    G, s_exp = build_problem(wl, rank, device)
+    vol = G.empty("vol", device)
+    steps, warm = args.steps, args.warmup
+
+    # warm-up iterations (also allocate the solver state)
+    ei.ei_reconstruct(G, s_exp, vol, tol=0.0, max_iter=warm)
+    torch.cuda.synchronize()
+
+    # timed region: `steps` iterations from the warmed-up iterate
+    peaks, peak_kind = _peaks()
+    ei.ei_profile_enable(G, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(_device_uuid()) as clk:
+        e0.record()
+        rep = ei.ei_reconstruct(G, s_exp, vol, tol=0.0, max_iter=steps)
+        e1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    prof = ei.ei_profile_read(G)
+    ei.ei_profile_enable(G, False)
+    if dist:
+        t = torch.tensor([t_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+
+    # algorithmic bytes actually processed (per-slice evaluation counts)
+    per_slice_fa = np.array([48 * n * n + 28 * nth * nd for (n, nth, nd) in wl.slices], dtype=np.float64)
+    fa_bytes = float(np.sum(per_slice_fa * rep.slice_evaluations))
+    value = world * fa_bytes / (t_ms * 1e-3) / 1e9
+
+    # per-kernel CUDA-event timings inside the timed region
+    taps_eval = float(np.sum(np.array([2.0 * n * n * nth for (n, nth, nd) in wl.slices]) *
+                             rep.slice_evaluations)) / max(1, prof["project_launches"])
+    kern = {}
+    for k in ("project", "ic", "backproject"):
+        L = prof[k + "_launches"]
+        kern[k] = {"launches": L, "total_ms": prof[k + "_ms"],
+                   "avg_ms": prof[k + "_ms"] / L if L else None}
+    fa_kernel_gbs = fa_bytes / ((prof["project_ms"] + prof["backproject_ms"]) * 1e-3) / 1e9
+    dom = "backproject" if prof["backproject_ms"] >= prof["project_ms"] else "project"
+    flops_per_launch = 6.0 * taps_eval          # 3 channels x 1 FMA per matrix entry
+    achieved = flops_per_launch / (kern[dom]["avg_ms"] * 1e-3) / 1e12
+    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_kind": "nominal FP32 FMA rate: 152 SMs x 128 lanes x 2 x sm_max_mhz (%s clock)"
+                             % peak_kind}
+    # IC kernel: algorithmic bytes of the evaluated slices / its summed event time
+    ic_per_slice = np.array([(28 + 4 * wl.n_m) * nth * nd for (n, nth, nd) in wl.slices], dtype=np.float64)
+    ic_gbs = float(np.sum(ic_per_slice * rep.slice_evaluations)) / (prof["ic_ms"] * 1e-3) / 1e9 \
+        if prof["ic_ms"] else None
+    clocks = clk.summary(float(peaks.get("sm_max_mhz", 2070.0)))
+
+    # end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        s_host = s_exp.cpu().pin_memory()
+        v_host = torch.zeros((G.vol_count, 4), dtype=torch.float32).pin_memory()
+        del s_exp
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        rep2 = ei.ei_reconstruct(G, s_host, v_host, tol=0.0, max_iter=steps)
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device=device)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        fa2 = float(np.sum(per_slice_fa * rep2.slice_evaluations))
+        h2d = s_host.numel() * 4 + v_host.numel() * 4
+        d2h = v_host.numel() * 4 + G.n_slices * 8 * 2
+        e2e = {"value": world * fa2 / te / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
+               "seconds": te, "note": "ei_reconstruct on pinned host arrays: host-to-device copy of "
+                                      "s_exp and x0, the iterations, copy of the solution back"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description,
+                   "slices_per_gpu": wl.n_slices, "measured_ics_gb_per_gpu": wl.meas_bytes() / 1e9,
+                   "voxel_equiv_1024_per_gpu": wl.voxel_equiv_1024(),
+                   "l2": "inputs (16.5 GB) exceed L2; no flush",
+                   "parallelism": "slices sharded, one process per GPU, no collective"
+                                  if world > 1 else "single GPU",
+                   "value_definition": "algorithmic projector+adjoint bytes of all evaluated "
+                                       "slices / wall time of the whole step (solver included)"},
+        "kernels": kern,
+        "fwd_adj_kernel_gbs": fa_kernel_gbs,
+        "ic_kernel_gbs": ic_gbs,
+        "ms_per_iteration_per_1024_slice": t_ms / steps / wl.voxel_equiv_1024(),
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": int(prof["launches"]),
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        dt, nbytes, cores, desc = cpu_oracle_sample(wl, 2 if wl.name == "uneven1024" else 1, evals=2)
+        line["cpu_baseline"] = {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": cores,
+                                "kind": "oracle", "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uneven1024")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

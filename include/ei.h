@@ -210,7 +210,8 @@ typedef struct {
     int *converged;    /* 1 if the tol test stopped the slice, 0 if max_iter or an error did */
     double *f_final;   /* final S */
     double *f_initial; /* S at x0 */
-    int evaluations;   /* objective+gradient evaluations of the batch (out) */
+    int *slice_evaluations; /* objective+gradient evaluations of each slice */
+    int evaluations;   /* batched evaluation rounds, the initial one included (out) */
     double seconds;    /* wall time of the call (out) */
 } ei_solve_report;
 
@@ -231,6 +232,22 @@ int ei_reconstruct(const ei_geometry *g, const float *s_exp, float *vol_inout,
 
 /* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10. */
 void ei_default_solve_opts(ei_solve_opts *opts);
+
+/*
+ * Tracing: per-kernel CUDA-event timings and a count of every kernel this
+ * library launches.  ei_profile_enable(g, 1) resets the counters and starts
+ * recording events around the projector, IC and adjoint launches (on the
+ * stream they run on); 0 stops recording.  ei_profile_read synchronises the
+ * device and sums the recorded durations.  Not part of the paper's method.
+ */
+typedef struct {
+    int64_t launches;              /* all kernels launched while enabled */
+    int64_t project_launches, ic_launches, backproject_launches;
+    double project_ms, ic_ms, backproject_ms;   /* summed event durations */
+} ei_profile;
+
+int ei_profile_enable(ei_geometry *g, int on);
+int ei_profile_read(ei_geometry *g, ei_profile *out);
 
 /* Human-readable name of a status code (static storage). */
 const char *ei_status_string(int status);

@@ -45,6 +45,66 @@ static cudaError_t fetch_floats(const float *src, size_t count, std::vector<floa
     return cudaMemcpy(dst.data(), src, count * sizeof(float), cudaMemcpyDefault);
 }
 
+cudaEvent_t trace_begin(ei_geometry *g, cudaStream_t st)
+{
+    if (!g->prof_on) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!g->ev_pool.empty()) {
+        e = g->ev_pool.back();
+        g->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaEventRecord(e, st);
+    return e;
+}
+
+void trace_end(ei_geometry *g, TracedKernel k, cudaEvent_t begin, cudaStream_t st)
+{
+    if (!begin) return;
+    cudaEvent_t e = trace_begin(g, st);
+    if (e) g->ev_pairs[k].push_back({begin, e});
+}
+
+// Launch helpers that count and (when tracing) time the three path kernels.
+static cudaError_t traced_project(ei_geometry *g, float *proj, const int *active, cudaStream_t st)
+{
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_project(g, proj, active, st);
+    trace_end(g, TK_PROJECT, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
+static cudaError_t traced_ic(ei_geometry *g, const float *proj, const float *meas, float *s_mod,
+                             double *part, IcMode mode, const int *active, cudaStream_t st)
+{
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_ic(g, proj, meas, s_mod, part, mode, active, st);
+    trace_end(g, TK_IC, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
+static cudaError_t traced_backproject(ei_geometry *g, bool with_sino, const float4 *v,
+                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                                      double *part, const int *active, cudaStream_t st)
+{
+    cudaEvent_t b = with_sino ? trace_begin(g, st) : nullptr;
+    cudaError_t e = launch_backproject(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    if (with_sino) trace_end(g, TK_BACKPROJECT, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
+static cudaError_t counted_prep(ei_geometry *g, const float4 *vol, float4 mult, const int *active,
+                                cudaStream_t st)
+{
+    count_launches(g, 1);
+    return launch_prep(g, vol, mult, active, st);
+}
+
 cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
                      float4 *grad, bool scaled, const int *active, cudaStream_t st)
 {
@@ -63,12 +123,13 @@ cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double 
                            2.f * g->lambda[2] * k[2], 0.f);
         reg1 = make_float4(g->lambda[0] * k[0], g->lambda[1] * k[1], g->lambda[2] * k[2], 0.f);
     }
-    EI_CUDA_TRY(launch_prep(g, v, mult, g->xp, g->xt, active, st));
-    EI_CUDA_TRY(launch_project(g, g->xp, g->xt, g->proj, active, st));
-    EI_CUDA_TRY(launch_ic(g, g->proj, meas, nullptr, g->sino4, g->part_ic,
+    EI_CUDA_TRY(counted_prep(g, v, mult, active, st));
+    EI_CUDA_TRY(traced_project(g, g->proj, active, st));
+    EI_CUDA_TRY(traced_ic(g, g->proj, meas, nullptr, g->part_ic,
                           grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, active, st));
-    EI_CUDA_TRY(launch_backproject(g, grad ? g->sino4 : nullptr, v, grad, out_mult, reg2, reg1,
+    EI_CUDA_TRY(traced_backproject(g, grad != nullptr, v, grad, out_mult, reg2, reg1,
                                    g->part_adj, active, st));
+    count_launches(g, 1);
     EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, g->part_adj, S_dev, active, st));
     return cudaSuccess;
 }
@@ -107,6 +168,48 @@ void ei_default_solve_opts(ei_solve_opts *o)
     o->curv_eps = 1e-10;
 }
 
+static void release_events(ei_geometry *g)
+{
+    for (int k = 0; k < 3; ++k) {
+        for (auto &p : g->ev_pairs[k]) {
+            g->ev_pool.push_back(p.first);
+            g->ev_pool.push_back(p.second);
+        }
+        g->ev_pairs[k].clear();
+    }
+}
+
+int ei_profile_enable(ei_geometry *g, int on)
+{
+    if (!g) return EI_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EI_ERR_CUDA;
+    release_events(g);
+    g->launches = 0;
+    g->prof_on = on != 0;
+    return EI_OK;
+}
+
+int ei_profile_read(ei_geometry *g, ei_profile *o)
+{
+    if (!g || !o) return EI_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EI_ERR_CUDA;
+    double ms[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+        for (auto &p : g->ev_pairs[k]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.first, p.second) != cudaSuccess) return EI_ERR_CUDA;
+            ms[k] += t;
+        }
+    o->launches = g->launches;
+    o->project_launches = (int64_t)g->ev_pairs[TK_PROJECT].size();
+    o->ic_launches = (int64_t)g->ev_pairs[TK_IC].size();
+    o->backproject_launches = (int64_t)g->ev_pairs[TK_BACKPROJECT].size();
+    o->project_ms = ms[TK_PROJECT];
+    o->ic_ms = ms[TK_IC];
+    o->backproject_ms = ms[TK_BACKPROJECT];
+    return EI_OK;
+}
+
 void ei_destroy_geometry(ei_geometry *g)
 {
     if (!g) return;
@@ -114,6 +217,8 @@ void ei_destroy_geometry(ei_geometry *g)
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
+    release_events(g);
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     ei::destroy_solver(g);
     for (void *p : g->allocs) cudaFree(p);
     cudaSetDevice(prev);
@@ -179,7 +284,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     ang.reserve(ang_total);
     pix.reserve(pix_total);
     std::vector<int> fwd_p(1, 0), ic_p(1, 0), adj_p(1, 0), prep_p(1, 0), vec_p(1, 0);
-    int64_t vol_off = 0, pad_off = 0, sino_off = 0, proj_off = 0, meas_off = 0;
+    int64_t vol_off = 0, pp_off = 0, gp_off = 0, sino_off = 0, proj_off = 0, meas_off = 0;
     int ang_off = 0, pix_off = 0, pix_in_off = 0, max_ndp = 4, max_nth = 1;
     const double TWO32 = 4294967296.0;
     for (int s = 0; s < n_slices; ++s) {
@@ -193,8 +298,20 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         si.inv_pitch = (float)(1.0 / q.pitch_cm);
         si.ang_off = ang_off;
         si.pix_off = pix_off;
+        // zero margin of the packed gradient-sinogram rows: every voxel of the adjoint's
+        // (padded) tile grid projects within [hd - R, hd + R] pixels
+        {
+            const double hn_ = 0.5 * (q.n - 1);
+            const int cpad = (q.n + ADJ_TC - 1) / ADJ_TC * ADJ_TC;
+            const int rpad = (q.n + ADJ_TR - 1) / ADJ_TR * ADJ_TR;
+            const double mdx = std::max(hn_, cpad - 1 - hn_), mdy = std::max(hn_, rpad - 1 - hn_);
+            const double R = sqrt(mdx * mdx + mdy * mdy);
+            si.marg = std::max(2, (int)ceil(R - 0.5 * (q.n_det - 1)) + 3);
+        }
+        si.gw = si.n_dp + 2 * si.marg;
         si.vol_off = vol_off;
-        si.pad_off = pad_off;
+        si.pp_off = pp_off;
+        si.gp_off = gp_off;
         si.sino_off = sino_off;
         si.proj_off = proj_off;
         si.meas_off = meas_off;
@@ -234,17 +351,18 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
             else
                 pix.push_back(make_float4(0.f, 0.f, 1.f, 0.f));
         }
-        const int nb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
-        fwd_p.push_back(fwd_p.back() + q.n_theta * nb);
+        const int nrb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
+        const int nab = (q.n_theta + FWD_ANGLES - 1) / FWD_ANGLES;
+        fwd_p.push_back(fwd_p.back() + nab * nrb);
         ic_p.push_back(ic_p.back() + q.n_theta);
-        const int at = (q.n + ADJ_TILE - 1) / ADJ_TILE;
-        adj_p.push_back(adj_p.back() + at * at);
-        const int pt = (q.n + PREP_TILE - 1) / PREP_TILE;
+        adj_p.push_back(adj_p.back() + ((q.n + ADJ_TC - 1) / ADJ_TC) * ((q.n + ADJ_TR - 1) / ADJ_TR));
+        const int pt = (q.n + 1 + PREP_TILE - 1) / PREP_TILE;
         prep_p.push_back(prep_p.back() + pt * pt);
         const int64_t nvox = (int64_t)q.n * q.n;
         vec_p.push_back(vec_p.back() + (int)((nvox + VEC_BLK - 1) / VEC_BLK));
         vol_off += nvox;
-        pad_off += (int64_t)q.n * (q.n + 2);
+        pp_off += (int64_t)q.n * (q.n + 1);
+        gp_off += (int64_t)q.n_theta * si.gw;
         sino_off += (int64_t)q.n_theta * si.n_dp;
         proj_off += 3LL * q.n_theta * si.n_dp;
         meas_off += (int64_t)d->n_m * q.n_theta * si.n_dp;
@@ -255,7 +373,8 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         max_nth = std::max(max_nth, q.n_theta);
     }
     g->vol_count = vol_off;
-    g->pad_count = pad_off;
+    g->pp_count = pp_off;
+    g->gp_count = gp_off;
     g->sino4_count = sino_off;
     g->proj_count = proj_off;
     g->meas_count = meas_off;
@@ -297,15 +416,19 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = upload(g, &d_adj, adj_p);
     if (e == cudaSuccess) e = upload(g, &d_prep, prep_p);
     if (e == cudaSuccess) e = upload(g, &d_vec, vec_p);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->xp, (size_t)g->pad_count);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->xt, (size_t)g->pad_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xpA, (size_t)g->pp_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xpB, (size_t)g->pp_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xtA, (size_t)g->pp_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xtB, (size_t)g->pp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->proj, (size_t)g->proj_count);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->sino4, (size_t)g->sino4_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->gA, (size_t)g->gp_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->gB, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_ic, (size_t)dg.total_ic);
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_adj, (size_t)dg.total_adj);
     if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
-    if (e == cudaSuccess) e = cudaMemset(g->xp, 0, (size_t)g->pad_count * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMemset(g->xt, 0, (size_t)g->pad_count * sizeof(float4));
+    // the packed gradient sinogram's margins and padding pixels must read as zero
+    if (e == cudaSuccess) e = cudaMemset(g->gA, 0, (size_t)g->gp_count * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemset(g->gB, 0, (size_t)g->gp_count * sizeof(float2));
     if (e == cudaSuccess) e = ic_set_smem_limit();
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
@@ -371,9 +494,8 @@ int ei_project(const ei_geometry *gc, const float *vol, float *proj, void *strea
     if (!gc || !vol || !proj || !aligned16(vol) || !aligned16(proj)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), g->xp,
-                                g->xt, nullptr, st);
-    if (e == cudaSuccess) e = launch_project(g, g->xp, g->xt, proj, nullptr, st);
+    cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, proj, nullptr, st);
     return status_from(e);
 }
 
@@ -382,8 +504,12 @@ int ei_backproject(const ei_geometry *gc, const float *sino4, float *vol, void *
     if (!gc || !sino4 || !vol || !aligned16(sino4) || !aligned16(vol)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    cudaError_t e = launch_backproject(g, (const float4 *)sino4, nullptr, (float4 *)vol, one,
-                                       zero, zero, g->part_adj, nullptr, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    count_launches(g, 1);
+    cudaError_t e = launch_pack_sino(g, (const float4 *)sino4, st);
+    if (e == cudaSuccess)
+        e = traced_backproject(g, true, nullptr, (float4 *)vol, one, zero, zero, g->part_adj,
+                               nullptr, st);
     return status_from(e);
 }
 
@@ -391,7 +517,7 @@ int ei_ic_model(const ei_geometry *gc, const float *proj, float *s_mod, void *st
 {
     if (!gc || !proj || !s_mod || !aligned16(proj) || !aligned16(s_mod)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
-    return status_from(launch_ic(g, proj, nullptr, s_mod, nullptr, g->part_ic, IC_MODEL, nullptr,
+    return status_from(traced_ic(g, proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr,
                                  (cudaStream_t)stream));
 }
 
@@ -400,11 +526,10 @@ int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stre
     if (!gc || !vol || !s_mod || !aligned16(vol) || !aligned16(s_mod)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), g->xp,
-                                g->xt, nullptr, st);
-    if (e == cudaSuccess) e = launch_project(g, g->xp, g->xt, g->proj, nullptr, st);
+    cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, g->proj, nullptr, st);
     if (e == cudaSuccess)
-        e = launch_ic(g, g->proj, nullptr, s_mod, nullptr, g->part_ic, IC_MODEL, nullptr, st);
+        e = traced_ic(g, g->proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr, st);
     return status_from(e);
 }
 

@@ -16,12 +16,26 @@ struct SliceInfo {
     float pitch, inv_pitch;  // voxel = detector pitch (cm) and its inverse
     int ang_off;             // first angle of the slice in the angle tables
     int pix_off;             // first pixel of the slice in the pixel table (n_dp stride)
+    int marg;                // zero entries on each side of a packed gradient-sinogram row
+    int gw;                  // packed gradient-sinogram row width: n_dp + 2 marg entries
     int64_t vol_off;         // float4 elements (vol layout)
-    int64_t pad_off;         // float4 elements of the padded copies: n rows of n + 2
-    int64_t sino_off;        // pixels: base of [n_theta][n_dp] (sino4 and every plane)
+    int64_t pp_off;          // entries of the packed volume copies: n rows of n + 1
+    int64_t gp_off;          // entries of the packed gradient sinogram: n_theta rows of gw
+    int64_t sino_off;        // pixels: base of [n_theta][n_dp] (user sino4 and every plane)
     int64_t proj_off;        // floats: 3 planes
     int64_t meas_off;        // floats: n_m planes
 };
+
+// Pair-packed arrays.  Sampling a linear interpolation needs two neighbouring
+// (mu, delta, sigma) triples; entry e of a packed row holds the triple at
+// e - 1 and the one at e as a float4 (mu0, delta0, sigma0, mu1) plus a float2
+// (delta1, sigma1), so one sample is 24 bytes in two loads.
+//   packed volume copy (projector input): row o, entry e = i + 1 holds voxels
+//     i and i + 1 of that row, i in [-1, n - 1] (zero outside the slice);
+//     xpA/xpB row-major (o = r, i = c), xtA/xtB transposed (o = c, i = r).
+//   packed gradient sinogram (adjoint input): row a, entry e holds pixels
+//     j = e - marg and j + 1; pixels outside [0, n_det) are zero, and the
+//     margin covers every pixel a voxel of the slice can project to.
 
 // Per (slice, angle) constants, computed on the host in FP64.
 // The ray of pixel j samples the "outer" voxel index o = 0..n-1 (rows when
@@ -49,9 +63,29 @@ struct ModelConsts {
 };
 
 // Work decomposition sizes.
-constexpr int FWD_RAYS = 128;      // rays (threads) per forward work item
-constexpr int ADJ_TILE = 16;       // adjoint tile is ADJ_TILE x ADJ_TILE voxels
-constexpr int PREP_TILE = 32;      // transpose tile
+// (compile-time tunables; the defaults are the measured best on GB300)
+#ifndef EI_FWD_RAYS
+#define EI_FWD_RAYS 16
+#endif
+#ifndef EI_FWD_ANGLES
+#define EI_FWD_ANGLES 16
+#endif
+#ifndef EI_FWD_UNROLL
+#define EI_FWD_UNROLL 4
+#endif
+#ifndef EI_ADJ_PASSES
+#define EI_ADJ_PASSES 8
+#endif
+#ifndef EI_ADJ_MINBLOCKS
+#define EI_ADJ_MINBLOCKS 4
+#endif
+constexpr int FWD_RAYS = EI_FWD_RAYS;      // rays per forward work item (multiple of 8)
+constexpr int FWD_ANGLES = EI_FWD_ANGLES;  // angles per forward work item (multiple of 4);
+                                           // warp = 8 rays x 4 angles
+constexpr int ADJ_TC = 32;                 // adjoint tile: 32 columns x 8 * passes rows,
+constexpr int ADJ_TR = 8 * EI_ADJ_PASSES;  // one voxel per thread and pass
+constexpr int ADJ_THREADS = 256;
+constexpr int PREP_TILE = 32;      // staging tile
 constexpr int VEC_BLK = 4096;      // float4 per vector-op block (one slice per block)
 constexpr int VEC_THREADS = 256;
 
@@ -100,35 +134,50 @@ struct ei_geometry {
     ei::DevGeom dg{};
     std::vector<void *> allocs;    // device allocations owned by the geometry
     // workspace for objective / forward evaluations
-    float4 *xp = nullptr;          // padded row-major copy of the volume (times mult)
-    float4 *xt = nullptr;          // padded transposed copy
+    float4 *xpA = nullptr, *xtA = nullptr;   // packed volume copies (times mult)
+    float2 *xpB = nullptr, *xtB = nullptr;
     float *proj = nullptr;         // proj layout
-    float4 *sino4 = nullptr;       // sino4 layout
+    float4 *gA = nullptr;          // packed gradient sinogram
+    float2 *gB = nullptr;
     double *part_ic = nullptr;     // [total_ic]
     double *part_adj = nullptr;    // [total_adj]
     double *S_dev = nullptr;       // [n_slices]
-    int64_t vol_count = 0, pad_count = 0, proj_count = 0, sino4_count = 0, meas_count = 0;
+    int64_t vol_count = 0, pp_count = 0, gp_count = 0, proj_count = 0, sino4_count = 0,
+            meas_count = 0;
     int64_t workspace_bytes = 0;
     ei::Solver *solver = nullptr;      // allocated on first ei_reconstruct
+    // tracing (ei_profile_enable): launch counter and event pairs per traced kernel
+    bool prof_on = false;
+    int64_t launches = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs[3];
 };
 
 namespace ei {
 
 enum IcMode { IC_MODEL = 0, IC_OBJECTIVE = 1, IC_OBJECTIVE_GRAD = 2 };
 
+enum TracedKernel { TK_PROJECT = 0, TK_IC = 1, TK_BACKPROJECT = 2 };
+
+// Tracing helpers: count `n` launches; bracket a traced launch with events.
+inline void count_launches(ei_geometry *g, int n) { g->launches += n; }
+cudaEvent_t trace_begin(ei_geometry *g, cudaStream_t st);
+void trace_end(ei_geometry *g, TracedKernel k, cudaEvent_t begin, cudaStream_t st);
+
 // Kernel launchers (each returns cudaGetLastError()).
-// xp/xt = padded copies of mult * vol (row-major and transposed).
-cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, float4 *xp,
-                        float4 *xt, const int *active, cudaStream_t st);
-// proj = R[x] from the padded copies.
-cudaError_t launch_project(const ei_geometry *g, const float4 *xp, const float4 *xt,
-                           float *proj, const int *active, cudaStream_t st);
+// Packed volume copies of mult * vol (row-major and transposed) in the workspace.
+cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, const int *active,
+                        cudaStream_t st);
+// proj = R[x] from the packed copies.
+cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st);
+// IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram.
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                      float4 *sino4, double *part, IcMode mode, const int *active,
-                      cudaStream_t st);
-// out = out_mult * R^T sino4 + reg2 * v ; per-tile partial sums of sum_c reg1_c v_c^2.
-// sino4 == nullptr: only the regulariser (out is then not written).
-cudaError_t launch_backproject(const ei_geometry *g, const float4 *sino4, const float4 *v,
+                      double *part, IcMode mode, const int *active, cudaStream_t st);
+// Packed gradient sinogram from a user sino4 array.
+cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
+// out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial
+// sums of sum_c reg1_c v_c^2.  with_sino == false: only the regulariser (out not written).
+cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
                                float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                double *part, const int *active, cudaStream_t st);
 // S[s] = sum of part_ic over the slice's rows + sum of part_adj over its tiles.

@@ -8,12 +8,13 @@
 //   e_m   = s_m - s_exp_m ;  objective partial sum_m e_m^2 (FP64 per block)
 //   G_mu  = -sum 2 e s,  G_sh = sum 2 e s q / V,  G_V = sum 2 e s (q^2 - V) / (2 V^2)
 // and the gradient sinogram row
-//   g = (G_mu, (z/period) D^T G_sh, kappa G_V, 0)      (float4 per pixel).
+//   g = (G_mu, (z/period) D^T G_sh, kappa G_V),
+// written pair-packed (the adjoint's input layout, see ei_internal.h).
 // D needs R[delta] at t +- 1 and D^T needs G_sh at t +- 1, so the whole row
 // is staged in shared memory (no halo recompute, no atomics).
 //
 // Memory traffic per pixel (M = n_m): 12 B of projections + 4M B of s_exp
-// read, 16 B of g written; the per-pixel flat IC table is shared by all angles
+// read, 24 B of packed g written; the per-pixel flat IC table is shared by all angles
 // and stays in L2.  The kernel is HBM-bound.
 #include "ei_internal.h"
 
@@ -58,7 +59,7 @@ __device__ __forceinline__ float deriv_at(const float *ps, int j, int n, float i
 
 template <int MODE>
 __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
-                     float *__restrict__ s_mod, float4 *__restrict__ sino4,
+                     float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
                      double *__restrict__ part, const int *__restrict__ active)
 {
     extern __shared__ float sm[];
@@ -134,16 +135,21 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
     }
     if (MODE == IC_MODEL) return;
     if (MODE == IC_OBJECTIVE_GRAD) {
+        // g_delta = (z/period) D^T G_shift (into the R[delta] row, no longer needed) and
+        // g_sigma = kappa G_V; then the packed row: entry of pixel j holds g(j), g(j + 1)
         __syncthreads();
-        float4 *grow = sino4 + si.sino_off + rbase;
-        for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
-            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < nd) {
-                o.x = s_gmu[j];
-                o.y = zp * deriv_T_at(s_gsh, j, nd, si.inv_pitch);
-                o.z = kappa * s_gv[j];
-            }
-            grow[j] = o;
+        for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+            s_pd[j] = zp * deriv_T_at(s_gsh, j, nd, si.inv_pitch);
+            s_gv[j] *= kappa;
+        }
+        __syncthreads();
+        const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
+        for (int j = (int)threadIdx.x - 1; j < nd; j += blockDim.x) {
+            float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+            if (j >= 0) lx = s_gmu[j], ly = s_pd[j], lz = s_gv[j];
+            if (j + 1 < nd) hx = s_gmu[j + 1], hy = s_pd[j + 1], hz = s_gv[j + 1];
+            gA[dst + j] = make_float4(lx, ly, lz, hx);
+            gB[dst + j] = make_float2(hy, hz);
         }
     }
     const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
@@ -152,8 +158,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
 }
 
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                      float4 *sino4, double *part, IcMode mode, const int *active,
-                      cudaStream_t st)
+                      double *part, IcMode mode, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
     int threads = (g->dg.max_ndp + 31) / 32 * 32;
@@ -161,16 +166,16 @@ cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas
     const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
     switch (mode) {
     case IC_MODEL:
-        k_ic<IC_MODEL><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod, sino4,
-                                                               part, active);
+        k_ic<IC_MODEL><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA,
+                                                               g->gB, part, active);
         break;
     case IC_OBJECTIVE:
         k_ic<IC_OBJECTIVE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
-                                                                   sino4, part, active);
+                                                                   g->gA, g->gB, part, active);
         break;
     default:
         k_ic<IC_OBJECTIVE_GRAD><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
-                                                                        sino4, part, active);
+                                                                        g->gA, g->gB, part, active);
         break;
     }
     return cudaGetLastError();

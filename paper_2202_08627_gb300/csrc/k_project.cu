@@ -5,73 +5,104 @@
 // interpolates the two voxels it falls between; every sample carries the
 // path length pitch / max(|cos|, |sin|).
 //
-// Layout for the inner loop: the volume is first staged as two zero-padded
-// copies, row-major xp[r][1 + c] and transposed xt[c][1 + r] (n rows of
-// n + 2 float4), so that a ray always walks the contiguous ("inner") axis of
-// one of them: neighbouring rays read neighbouring float4, and the zero
-// border removes every bounds check from the loop.  The crossing position is
-// carried in 32.32 fixed point (int64): one integer add per sample, the
-// integer part is the voxel index and the low word the interpolation weight,
-// exact to ~1e-7 voxel for any slice size.
+// What bounds this kernel is the bytes the samples bring from L1 into
+// registers (a warp-wide load returns 16 B per lane per load, whatever the
+// addresses), not HBM: a 1024^2 slice with 1800 angles takes ~1.7e9 samples
+// from a 17 MB volume.  So:
+//  - the volume is staged once per evaluation as two pair-packed copies
+//    (row-major for rows-first rays, transposed for columns-first rays): one
+//    sample = one float4 + one float2 load (24 B instead of 32 B), and the
+//    zero border of the copies removes every bounds check from the loop;
+//  - a warp covers 8 neighbouring rays x 4 neighbouring angles, so at each
+//    row its lanes touch a compact run of voxels (few cache lines per load),
+//    and a block covers FWD_ANGLES angles so its warps re-use each other's
+//    lines in L1;
+//  - several samples per loop iteration keep independent loads in flight;
+//  - the crossing position is carried in 32.32 fixed point (int64): one
+//    integer add per sample; the integer part is the voxel index and the low
+//    word the interpolation weight, exact to ~1e-7 voxel at any slice size.
 #include "ei_internal.h"
 
 namespace ei {
 
 // --------------------------------------------------------------------------
-// Staging: xp = mult * vol (padded), xt = its transpose (padded).
-// One block per 32 x 32 tile of a slice.
+// Staging: packed row-major and transposed copies of mult * vol.
+// One block per 32 x 32 tile of entries; the tile loads the voxels it needs
+// (with a one-voxel halo above and to the left) into shared memory.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(PREP_TILE * 8)
-k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restrict__ xp,
-       float4 *__restrict__ xt, const int *__restrict__ active)
+k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restrict__ xpA,
+       float2 *__restrict__ xpB, float4 *__restrict__ xtA, float2 *__restrict__ xtB,
+       const int *__restrict__ active)
 {
-    __shared__ float4 tile[PREP_TILE][PREP_TILE + 1];
+    __shared__ float4 T[PREP_TILE + 1][PREP_TILE + 2];
     const int item = blockIdx.x;
     const int s = find_slice(dg.prep_prefix, dg.n_slices, item);
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
     const int n = si.n;
-    const int nt = (n + PREP_TILE - 1) / PREP_TILE;
+    const int nt = (n + 1 + PREP_TILE - 1) / PREP_TILE;      // tiles over n + 1 entries
     const int local = item - dg.prep_prefix[s];
-    const int r0 = (local / nt) * PREP_TILE, c0 = (local % nt) * PREP_TILE;
+    const int R0 = (local / nt) * PREP_TILE, C0 = (local % nt) * PREP_TILE;
     const float4 *v = vol + si.vol_off;
-    float4 *p = xp + si.pad_off;
-    float4 *t = xt + si.pad_off;
-    const int64_t w = n + 2;
-    for (int dy = threadIdx.y; dy < PREP_TILE; dy += blockDim.y) {
-        const int r = r0 + dy, c = c0 + threadIdx.x;
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < n && c < n) {
-            float4 x = v[(int64_t)r * n + c];
-            val = make_float4(x.x * mult.x, x.y * mult.y, x.z * mult.z, 0.f);
-            p[(int64_t)r * w + 1 + c] = val;
+    // T[y][x] = voxel (R0 - 1 + y, C0 - 1 + x), zero outside the slice
+    for (int y = threadIdx.y; y < PREP_TILE + 1; y += blockDim.y) {
+        const int r = R0 - 1 + y;
+        for (int x = threadIdx.x; x < PREP_TILE + 1; x += blockDim.x) {
+            const int c = C0 - 1 + x;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r >= 0 && r < n && c >= 0 && c < n) {
+                const float4 q = v[(int64_t)r * n + c];
+                val = make_float4(q.x * mult.x, q.y * mult.y, q.z * mult.z, 0.f);
+            }
+            T[y][x] = val;
         }
-        tile[dy][threadIdx.x] = val;
     }
     __syncthreads();
+    const int64_t w = n + 1;
+    // row-major entries (r, e): voxels (r, e - 1) and (r, e)
+    for (int dy = threadIdx.y; dy < PREP_TILE; dy += blockDim.y) {
+        const int r = R0 + dy, e = C0 + threadIdx.x;
+        if (r < n && e <= n) {
+            const float4 a = T[dy + 1][threadIdx.x], b = T[dy + 1][threadIdx.x + 1];
+            const int64_t k = si.pp_off + (int64_t)r * w + e;
+            xpA[k] = make_float4(a.x, a.y, a.z, b.x);
+            xpB[k] = make_float2(b.y, b.z);
+        }
+    }
+    // transposed entries (c, e): voxels (e - 1, c) and (e, c)
     for (int dx = threadIdx.y; dx < PREP_TILE; dx += blockDim.y) {
-        const int c = c0 + dx, r = r0 + threadIdx.x;
-        if (r < n && c < n) t[(int64_t)c * w + 1 + r] = tile[threadIdx.x][dx];
+        const int c = C0 + dx, e = R0 + threadIdx.x;
+        if (c < n && e <= n) {
+            const float4 a = T[threadIdx.x][dx + 1], b = T[threadIdx.x + 1][dx + 1];
+            const int64_t k = si.pp_off + (int64_t)c * w + e;
+            xtA[k] = make_float4(a.x, a.y, a.z, b.x);
+            xtB[k] = make_float2(b.y, b.z);
+        }
     }
 }
 
 // --------------------------------------------------------------------------
-// Projector: one thread per ray (slice, angle, pixel); a work item is
-// FWD_RAYS consecutive pixels of one angle.
+// Projector: one thread per ray; a work item is FWD_ANGLES angles x FWD_RAYS
+// pixels of one slice; warp = 8 pixels x 4 angles.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(FWD_RAYS)
-k_project(DevGeom dg, const float4 *__restrict__ xp, const float4 *__restrict__ xt,
-          float *__restrict__ proj, const int *__restrict__ active)
+__global__ void __launch_bounds__(FWD_RAYS * FWD_ANGLES)
+k_project(DevGeom dg, const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
+          const float4 *__restrict__ xtA, const float2 *__restrict__ xtB, float *__restrict__ proj,
+          const int *__restrict__ active)
 {
     const int item = blockIdx.x;
     const int s = find_slice(dg.fwd_prefix, dg.n_slices, item);
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
-    const int nb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
+    const int nrb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
     const int local = item - dg.fwd_prefix[s];
-    const int a = local / nb;
-    const int j = (local - a * nb) * FWD_RAYS + threadIdx.x;
-    if (j >= si.n_dp) return;
+    const int ab = local / nrb, rb = local - ab * nrb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int WR = FWD_RAYS / 8;                   // warps along the rays
+    const int a = ab * FWD_ANGLES + (warp / WR) * 4 + (lane >> 3);
+    const int j = rb * FWD_RAYS + (warp % WR) * 8 + (lane & 7);
+    if (a >= si.n_theta || j >= si.n_dp) return;
     const int64_t plane = (int64_t)si.n_theta * si.n_dp;
     float *out = proj + si.proj_off + (int64_t)a * si.n_dp + j;
     if (j >= si.n_det) {
@@ -88,63 +119,89 @@ k_project(DevGeom dg, const float4 *__restrict__ xp, const float4 *__restrict__ 
     const double TWO32 = 4294967296.0;
     const long long base = __double2ll_rn(P0 * TWO32);
     const long long p1 = an.p1_fx;
-    const long long lo_lim = -(1LL << 32);               // s >= -1
-    const long long hi_lim = (long long)n << 32;         // s <  n
-    // valid outer range [o_lo, o_hi]: first an FP64 estimate, then exact checks
+    const long long lo_lim = -(1LL << 32);               // position >= -1
+    const long long hi_lim = (long long)n << 32;         // position <  n
+    // valid outer range [o_lo, o_hi]: an FP64 estimate, then exact int64 checks
     int o_lo, o_hi;
     if (p1 == 0) {
         const bool in = base >= lo_lim && base < hi_lim;
         o_lo = in ? 0 : 1;
         o_hi = in ? n - 1 : 0;
     } else {
-        double e1 = (-1.0 - P0) * an.inv_p1, e2 = (n - P0) * an.inv_p1;
-        double lo = fmin(e1, e2), hi = fmax(e1, e2);
-        o_lo = (int)fmax(0.0, fmin((double)n, ceil(lo)));
-        o_hi = (int)fmin((double)(n - 1), fmax(-1.0, floor(hi)));
+        const double e1 = (-1.0 - P0) * an.inv_p1, e2 = (n - P0) * an.inv_p1;
+        o_lo = (int)fmax(0.0, fmin((double)n, ceil(fmin(e1, e2))));
+        o_hi = (int)fmin((double)(n - 1), fmax(-1.0, floor(fmax(e1, e2))));
         auto inr = [&](int o) {
-            long long v = base + (long long)o * p1;
-            return v >= lo_lim && v < hi_lim;
+            const long long q = base + (long long)o * p1;
+            return q >= lo_lim && q < hi_lim;
         };
         while (o_lo <= o_hi && !inr(o_lo)) ++o_lo;
         while (o_hi >= o_lo && !inr(o_hi)) --o_hi;
         while (o_lo > 0 && inr(o_lo - 1)) --o_lo;
         while (o_hi < n - 1 && inr(o_hi + 1)) ++o_hi;
     }
-    const float4 *src = (an.col_dom ? xt : xp) + si.pad_off;
-    const int64_t w = n + 2;
+    const int64_t w = n + 1;
+    const int64_t row0 = si.pp_off + (int64_t)o_lo * w + 1;   // entry of position i0 is i0 + 1
+    const float4 *rowA = (an.col_dom ? xtA : xpA) + row0;
+    const float2 *rowB = (an.col_dom ? xtB : xpB) + row0;
     float ax = 0.f, ay = 0.f, az = 0.f;
     long long pos = base + (long long)o_lo * p1;
     const float inv32 = 2.3283064365386963e-10f;   // 2^-32
-    const float4 *row = src + (int64_t)o_lo * w + 1;
-    for (int o = o_lo; o <= o_hi; ++o) {
-        const int i0 = (int)(pos >> 32);                       // floor of the position
+    // EI_FWD_UNROLL samples per iteration, their loads independent of each other
+    int o = o_lo;
+    for (; o + EI_FWD_UNROLL - 1 <= o_hi; o += EI_FWD_UNROLL) {
+        float4 va[EI_FWD_UNROLL];
+        float2 vb[EI_FWD_UNROLL];
+        float f[EI_FWD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < EI_FWD_UNROLL; ++u) {
+            const long long q = pos + u * p1;
+            const int i0 = (int)(q >> 32);                     // floor of the position
+            f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
+            va[u] = __ldg(rowA + u * w + i0);
+            vb[u] = __ldg(rowB + u * w + i0);
+        }
+#pragma unroll
+        for (int u = 0; u < EI_FWD_UNROLL; ++u) {
+            ax += fmaf(f[u], va[u].w - va[u].x, va[u].x);
+            ay += fmaf(f[u], vb[u].x - va[u].y, va[u].y);
+            az += fmaf(f[u], vb[u].y - va[u].z, va[u].z);
+        }
+        pos += EI_FWD_UNROLL * p1;
+        rowA += EI_FWD_UNROLL * w;
+        rowB += EI_FWD_UNROLL * w;
+    }
+    for (; o <= o_hi; ++o) {
+        const int i0 = (int)(pos >> 32);
         const float f = (float)(unsigned)(pos & 0xffffffffLL) * inv32;
-        const float4 v0 = __ldg(row + i0);
-        const float4 v1 = __ldg(row + i0 + 1);
-        ax += fmaf(f, v1.x - v0.x, v0.x);
-        ay += fmaf(f, v1.y - v0.y, v0.y);
-        az += fmaf(f, v1.z - v0.z, v0.z);
+        const float4 va = __ldg(rowA + i0);
+        const float2 vb = __ldg(rowB + i0);
+        ax += fmaf(f, va.w - va.x, va.x);
+        ay += fmaf(f, vb.x - va.y, va.y);
+        az += fmaf(f, vb.y - va.z, va.z);
         pos += p1;
-        row += w;
+        rowA += w;
+        rowB += w;
     }
     out[0] = ax * an.pch;
     out[plane] = ay * an.pch;
     out[2 * plane] = az * an.pch;
 }
 
-cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, float4 *xp,
-                        float4 *xt, const int *active, cudaStream_t st)
+cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, const int *active,
+                        cudaStream_t st)
 {
     if (g->dg.total_prep == 0) return cudaSuccess;
-    k_prep<<<g->dg.total_prep, dim3(PREP_TILE, 8), 0, st>>>(g->dg, vol, mult, xp, xt, active);
+    k_prep<<<g->dg.total_prep, dim3(PREP_TILE, 8), 0, st>>>(g->dg, vol, mult, g->xpA, g->xpB,
+                                                             g->xtA, g->xtB, active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const ei_geometry *g, const float4 *xp, const float4 *xt,
-                           float *proj, const int *active, cudaStream_t st)
+cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st)
 {
     if (g->dg.total_fwd == 0) return cudaSuccess;
-    k_project<<<g->dg.total_fwd, FWD_RAYS, 0, st>>>(g->dg, xp, xt, proj, active);
+    k_project<<<g->dg.total_fwd, FWD_RAYS * FWD_ANGLES, 0, st>>>(g->dg, g->xpA, g->xpB, g->xtA,
+                                                                  g->xtB, proj, active);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ namespace ei {
 struct SliceState {
     double f, f_t, gd, gg, alpha, gamma, f0;
     int k, count, head, trials;
-    int status, converged, reset, pad_;
+    int status, converged, reset, evals;
 };
 
 struct Solver {
@@ -364,6 +364,7 @@ __global__ void k_init_state(DevGeom dg, SolverDev sv, const double *__restrict_
         q = SliceState{};
         q.f = q.f0 = S[s];
         q.gamma = 1.0;
+        q.evals = 1;
         const bool ok = isfinite(q.f);
         q.status = ok ? EI_OK : EI_ERR_NONFINITE;
         sv.mask_dir[s] = ok;
@@ -413,6 +414,7 @@ __global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S,
         if (!sv.mask_ls[s]) continue;
         SliceState &q = sv.st[s];
         const double ft = S[s];
+        q.evals += 1;
         if (isfinite(ft) && ft <= q.f + o.c1 * q.alpha * q.gd) {
             q.f_t = ft;
             sv.mask_ls[s] = 0;
@@ -544,9 +546,11 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     const int scalar_threads = 256;
 
     k_to_scaled<<<NB, T, 0, st>>>(dg, x_dev, sv->u, inv);
+    count_launches(g, 1);
     EI_CUDA_TRY(cudaGetLastError());
     EI_CUDA_TRY(evaluate(g, sv->u, meas, g->S_dev, sv->g, true, nullptr, st));
     k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
+    count_launches(g, 1);
     EI_CUDA_TRY(cudaGetLastError());
     *evals = 1;
     EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -576,6 +580,9 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         k_accept<<<NB, T, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2]);
         k_update<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2], o,
                                                sv->summary);
+        // direction: first + m down + mid + m up + end + ls_start + reset; then trial,
+        // armijo, accept, update (the evaluation counts its own launches)
+        count_launches(g, 2 * sv->m + 5 + 4);
         EI_CUDA_TRY(cudaGetLastError());
         *evals += 1;
         EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int),
@@ -583,6 +590,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         EI_CUDA_TRY(cudaStreamSynchronize(st));
     }
     k_from_scaled<<<NB, T, 0, st>>>(dg, sv->u, x_dev, sc);
+    count_launches(g, 1);
     return cudaGetLastError();
 }
 
@@ -637,6 +645,7 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
             if (report->converged) report->converged[s] = hs[s].converged;
             if (report->f_final) report->f_final[s] = hs[s].f;
             if (report->f_initial) report->f_initial[s] = hs[s].f0;
+            if (report->slice_evaluations) report->slice_evaluations[s] = hs[s].evals;
         }
     }
     if (report) {

@@ -67,22 +67,32 @@ class ei_solve_opts(ctypes.Structure):
 class ei_solve_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.POINTER(c_int)), ("status", ctypes.POINTER(c_int)),
                 ("converged", ctypes.POINTER(c_int)), ("f_final", ctypes.POINTER(c_double)),
-                ("f_initial", ctypes.POINTER(c_double)), ("evaluations", c_int),
+                ("f_initial", ctypes.POINTER(c_double)),
+                ("slice_evaluations", ctypes.POINTER(c_int)), ("evaluations", c_int),
                 ("seconds", c_double)]
+
+
+class ei_profile(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("project_launches", c_int64), ("ic_launches", c_int64),
+                ("backproject_launches", c_int64), ("project_ms", c_double), ("ic_ms", c_double),
+                ("backproject_ms", c_double)]
 
 
 EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get_slice_layout",
             "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
-            "ei_reconstruct", "ei_default_solve_opts", "ei_status_string"]
+            "ei_reconstruct", "ei_default_solve_opts", "ei_status_string", "ei_profile_enable",
+            "ei_profile_read"]
 
 _lib = None
 
 
-def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libei.so; raises if it has not been built."""
+def load_library(path: str = None) -> ctypes.CDLL:
+    """Load libei.so (or the build at `path`, once, before any other call);
+    raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("EI_LIBRARY", LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError("libei.so not found at %s: build it with "
                            "paper_2202_08627_gb300.build.build() (there is no CPU fallback)" % path)
@@ -107,6 +117,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ei_reconstruct.restype = c_int
     lib.ei_default_solve_opts.argtypes = [P(ei_solve_opts)]
     lib.ei_default_solve_opts.restype = None
+    lib.ei_profile_enable.argtypes = [c_void_p, c_int]
+    lib.ei_profile_enable.restype = c_int
+    lib.ei_profile_read.argtypes = [c_void_p, P(ei_profile)]
+    lib.ei_profile_read.restype = c_int
     lib.ei_status_string.argtypes = [c_int]
     lib.ei_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -394,6 +408,7 @@ class SolveReport:
     converged: np.ndarray
     f_final: np.ndarray
     f_initial: np.ndarray
+    slice_evaluations: np.ndarray
     evaluations: int
     seconds: float
     return_status: int
@@ -415,14 +430,26 @@ def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbf
     cv = np.zeros(S, np.int32)
     ff = np.zeros(S, np.float64)
     f0 = np.zeros(S, np.float64)
+    ev = np.zeros(S, np.int32)
     ip = ctypes.POINTER(c_int)
     dp = ctypes.POINTER(c_double)
     rep = ei_solve_report(it.ctypes.data_as(ip), st.ctypes.data_as(ip), cv.ctypes.data_as(ip),
-                          ff.ctypes.data_as(dp), f0.ctypes.data_as(dp), 0, 0.0)
+                          ff.ctypes.data_as(dp), f0.ctypes.data_as(dp), ev.ctypes.data_as(ip),
+                          0, 0.0)
     rc = load_library().ei_reconstruct(geom.handle, _dptr(s_exp, "s_exp", torch.float32),
                                        _dptr(vol_inout, "vol_inout", torch.float32),
                                        ctypes.byref(o), ctypes.byref(rep), _stream_ptr(stream))
-    out = SolveReport(it, st, cv, ff, f0, rep.evaluations, rep.seconds, rc)
+    out = SolveReport(it, st, cv, ff, f0, ev, rep.evaluations, rep.seconds, rc)
     if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE):
         raise EIError(rc, "ei_reconstruct")
     return out
+
+
+def ei_profile_enable(geom: Geometry, on: bool = True) -> None:
+    _check(load_library().ei_profile_enable(geom.handle, int(bool(on))), "ei_profile_enable")
+
+
+def ei_profile_read(geom: Geometry) -> dict:
+    p = ei_profile()
+    _check(load_library().ei_profile_read(geom.handle, ctypes.byref(p)), "ei_profile_read")
+    return {f: getattr(p, f) for f, _ in p._fields_}

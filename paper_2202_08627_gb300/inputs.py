@@ -191,3 +191,57 @@ def make_slice(seed: int, n: int, n_theta: int, n_det: int, n_m: int,
     A, c, w = flat_ic(seed if flat_seed is None else flat_seed, n_det)
     return SliceSpec(seed, n, n_theta, n_det, n_m, pitch, th, mask_positions(n_m),
                      A, c, w, ell, voxelize(ell, n), ellipse_line_integrals(ell, th, n_det, pitch))
+
+
+# ---------------------------------------------------------------------------
+# Device versions (PyTorch on the GPU) of the same draws, for workloads too
+# large to generate on the host.  Same formulas as above; the ellipse
+# parameters and flat ICs still come from the seeded host draws.
+# ---------------------------------------------------------------------------
+def voxelize_torch(ellipses: Sequence[Ellipse], n: int, device, fov: float = FOV_CM,
+                   supersample: int = 4):
+    """[3][n][n] float32 tensor, as ``voxelize``."""
+    import torch
+    pitch = fov / n
+    sub = (torch.arange(supersample, device=device, dtype=torch.float64) + 0.5) / supersample - 0.5
+    idx = torch.arange(n, device=device, dtype=torch.float64) - 0.5 * (n - 1)
+    xs = ((idx[:, None] + sub[None, :]) * pitch).reshape(-1)          # (c, sc)
+    ys = (-(idx[:, None] + sub[None, :]) * pitch).reshape(-1)         # (r, sr)
+    out = torch.zeros((3, n, n), device=device, dtype=torch.float32)
+    for e in ellipses:
+        cp, sp = np.cos(e.phi), np.sin(e.phi)
+        dx = (xs - e.x0)[None, :]
+        dy = (ys - e.y0)[:, None]
+        xr = dx * cp + dy * sp
+        yr = -dx * sp + dy * cp
+        inside = ((xr / e.a) ** 2 + (yr / e.b) ** 2 <= 1.0).to(torch.float32)
+        frac = inside.reshape(n, supersample, n, supersample).mean(dim=(1, 3))
+        out += torch.tensor(e.values, device=device, dtype=torch.float32)[:, None, None] * frac[None]
+    return out
+
+
+def ellipse_line_integrals_torch(ellipses: Sequence[Ellipse], theta: np.ndarray, n_det: int,
+                                 pitch: float, device):
+    """[3][n_theta][n_det] float32 tensor, as ``ellipse_line_integrals``."""
+    import torch
+    t = (torch.arange(n_det, device=device, dtype=torch.float64) - 0.5 * (n_det - 1)) * pitch
+    th = torch.as_tensor(np.asarray(theta, dtype=np.float64), device=device)[:, None]
+    out = torch.zeros((3, th.shape[0], n_det), device=device, dtype=torch.float64)
+    for e in ellipses:
+        al = th - e.phi
+        a2 = (e.a * torch.cos(al)) ** 2 + (e.b * torch.sin(al)) ** 2
+        tp = t[None, :] - (e.x0 * torch.cos(th) + e.y0 * torch.sin(th))
+        rad = torch.clamp(a2 - tp * tp, min=0.0)
+        chord = 2.0 * e.a * e.b * torch.sqrt(rad) / a2
+        out += torch.as_tensor(e.values, device=device)[:, None, None] * chord[None]
+    return out.to(torch.float32)
+
+
+def poisson_noise_torch(expected, seed: int, a_ref: float = A_REF):
+    """Counts ~ Poisson(a_ref * expected) drawn on the expected tensor's device
+    with a seeded generator, returned divided by a_ref (float32)."""
+    import torch
+    gen = torch.Generator(device=expected.device)
+    gen.manual_seed(int(seed) * 1000003 + _PURPOSE_NOISE)
+    lam = torch.clamp(expected.to(torch.float32) * a_ref, min=0.0)
+    return torch.poisson(lam, generator=gen) / a_ref
