@@ -249,6 +249,40 @@ typedef struct {
 int ei_profile_enable(ei_geometry *g, int on);
 int ei_profile_read(ei_geometry *g, ei_profile *out);
 
+/*
+ * ei_objective_grad_noalloc — S and its gradient for ONE slice with no device
+ * allocation at all.  The paper has no counterpart; this exists for callers
+ * that cannot allocate GPU memory: code running while a stream is captured
+ * into a CUDA graph (cudaMalloc cannot be captured), frameworks that have
+ * reserved the device memory in their own pool and forbid allocations outside
+ * it, and latency-sensitive loops that cannot afford cudaMalloc's implicit
+ * device synchronisation.  Such callers cannot use ei_setup_geometry (it
+ * allocates a workspace), so the geometry description is passed directly.
+ *
+ * desc: as for ei_setup_geometry with a uniform batch of one slice (desc->n,
+ *   n_theta, n_det, pitch_cm; flat_*, m_o, m_r host or device).
+ * vol, s_exp, grad (nullable), S_out: as for ei_objective_grad, one slice.
+ * Scratch: every intermediate lives in one static device array of
+ *   EI_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until the
+ *   process exits.  A slice needs about 48 n(n+1) + 12 n_theta n_dp
+ *   + 24 n_theta (n_dp + 2 margin) bytes plus small tables (margin ~
+ *   max(2, 0.71 n - n_det/2 + 3) pixels); larger slices return EI_ERR_ARG
+ *   before any GPU work.  (A 256x256 slice with 720 angles and 384 pixels
+ *   needs ~14 MB.)
+ * First call on a device: resolves the array's device address
+ *   (cudaGetSymbolAddress) and sets a kernel attribute; make that first call
+ *   before any stream capture.  Later calls only copy the description's
+ *   arrays, clear the parts of the array that must start at zero, and launch
+ *   the same kernels as ei_objective_grad.
+ * Concurrency: every call uses the same array, and its contents are whatever
+ *   the last call left; calls that overlap on the GPU (other streams, other
+ *   threads) race and must be serialised by the caller.
+ * Host arrays in desc and a host S_out make the call synchronise the stream.
+ */
+#define EI_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ei_objective_grad_noalloc(const ei_geometry_desc *desc, const float *vol, const float *s_exp,
+                              double *S_out, float *grad, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *ei_status_string(int status);
 

@@ -81,7 +81,7 @@ class ei_profile(ctypes.Structure):
 EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get_slice_layout",
             "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
             "ei_reconstruct", "ei_default_solve_opts", "ei_status_string", "ei_profile_enable",
-            "ei_profile_read"]
+            "ei_profile_read", "ei_objective_grad_noalloc"]
 
 _lib = None
 
@@ -121,6 +121,9 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_profile_enable.restype = c_int
     lib.ei_profile_read.argtypes = [c_void_p, P(ei_profile)]
     lib.ei_profile_read.restype = c_int
+    lib.ei_objective_grad_noalloc.argtypes = [P(ei_geometry_desc), c_void_p, c_void_p, c_void_p,
+                                              c_void_p, c_void_p]
+    lib.ei_objective_grad_noalloc.restype = c_int
     lib.ei_status_string.argtypes = [c_int]
     lib.ei_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -453,3 +456,51 @@ def ei_profile_read(geom: Geometry) -> dict:
     p = ei_profile()
     _check(load_library().ei_profile_read(geom.handle, ctypes.byref(p)), "ei_profile_read")
     return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def ei_objective_grad_noalloc(n: int, n_theta: int, n_det: int, pitch_cm: float, n_m: int,
+                              m: Sequence[float], z_cm: float, period_cm: float,
+                              kappa_sigma: float, flat_A, flat_c, flat_w, vol, s_exp, S_out,
+                              grad=None, lam=(1e-2, 1e-2, 1e-2), scale=(1.0, 1e-6, 1.0),
+                              theta=None, m_o=None, m_r=None, stream=None) -> None:
+    """S and its gradient for one slice without any device allocation, for
+    callers that cannot allocate GPU memory (during stream capture, inside a
+    framework that owns the device memory, or in loops that cannot afford
+    cudaMalloc's synchronisation).  Arguments as ei_setup_geometry (one
+    uniform slice) plus ei_objective_grad's arrays; flat_* / m_o / m_r are
+    numpy arrays or CUDA tensors."""
+    import torch
+    keep = []
+
+    def fptr(a):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            a = a.contiguous().float()
+            keep.append(a)
+            return a.data_ptr()
+        arr = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    d = ei_geometry_desc()
+    d.n, d.n_theta, d.n_det, d.n_m = int(n), int(n_theta), int(n_det), int(n_m)
+    d.pitch_cm = float(pitch_cm)
+    m_arr = np.ascontiguousarray(m, dtype=np.float64)
+    keep.append(m_arr)
+    d.m = m_arr.ctypes.data_as(ctypes.POINTER(c_double))
+    if theta is not None:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        keep.append(th)
+        d.theta = th.ctypes.data_as(ctypes.POINTER(c_double))
+    d.z_cm, d.period_cm, d.kappa_sigma = float(z_cm), float(period_cm), float(kappa_sigma)
+    d.flat_A, d.flat_c, d.flat_w = fptr(flat_A), fptr(flat_c), fptr(flat_w)
+    d.lambda_[:] = [float(v) for v in lam]
+    d.scale[:] = [float(v) for v in scale]
+    d.m_o, d.m_r = fptr(m_o), fptr(m_r)
+    if S_out.dtype != torch.float64 or S_out.numel() < 1:
+        raise ValueError("S_out must be a float64 tensor")
+    gp = None if grad is None else _dptr(grad, "grad", torch.float32)
+    _check(load_library().ei_objective_grad_noalloc(
+        ctypes.byref(d), _dptr(vol, "vol", torch.float32), _dptr(s_exp, "s_exp", torch.float32),
+        _dptr(S_out, "S_out"), gp, _stream_ptr(stream)), "ei_objective_grad_noalloc")
