@@ -199,6 +199,7 @@ typedef struct {
     double c1;         /* Armijo constant (1e-4) */
     int max_trials;    /* step halvings per line search (20) */
     double curv_eps;   /* keep a pair only if s.y > curv_eps |s| |y| (1e-10) */
+    int use_graph;     /* 1: capture one solver round into a CUDA graph and replay it (1) */
 } ei_solve_opts;
 
 /* Per-slice results; every pointer is a caller-owned HOST array of n_slices
@@ -223,21 +224,25 @@ typedef struct {
  * The iterate is u = x / scale.
  * s_exp: measurement layout, vol_inout: vol layout (x0 in, solution out);
  * both may be device or host memory (host arrays are staged through device
- * memory inside the call).  report may be NULL.  Synchronous: returns when
- * every slice has stopped.  Returns EI_OK when every slice converged or
+ * memory inside the call).  report may be NULL.  Synchronous: `stream` is
+ * synchronised first, the iterations run on a stream the solver owns (one
+ * solver round is captured into a CUDA graph and replayed), and the call
+ * returns when every slice has stopped.  Returns EI_OK when every slice converged or
  * reached max_iter, else the first per-slice error.
  */
 int ei_reconstruct(const ei_geometry *g, const float *s_exp, float *vol_inout,
                    const ei_solve_opts *opts, ei_solve_report *report, void *stream);
 
-/* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10. */
+/* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10, graphs on. */
 void ei_default_solve_opts(ei_solve_opts *opts);
 
 /*
  * Tracing: per-kernel CUDA-event timings and a count of every kernel this
  * library launches.  ei_profile_enable(g, 1) resets the counters and starts
  * recording events around the projector, IC and adjoint launches (on the
- * stream they run on); 0 stops recording.  ei_profile_read synchronises the
+ * stream they run on); 0 resets the counters and stops recording events (the
+ * launch count goes on).  While events are recorded, ei_reconstruct runs its
+ * rounds without CUDA-graph replay so that every launch is timed.  ei_profile_read synchronises the
  * device and sums the recorded durations.  Not part of the paper's method.
  */
 typedef struct {
@@ -248,6 +253,31 @@ typedef struct {
 
 int ei_profile_enable(ei_geometry *g, int on);
 int ei_profile_read(ei_geometry *g, ei_profile *out);
+
+/*
+ * Kernel variants and autotuning (batched, serving-style launches).
+ * The projector and the adjoint each come in several tile shapes
+ * (projector: 16x16, 32x8, 32x16 rays x angles with a 4-sample unroll, and
+ * 16x16 with a 2-sample unroll; adjoint: 8, 4 or 16 voxels per thread), and
+ * either as one block per work item or as a persistent GPU-sized grid whose
+ * blocks take work items from a counter.  Projector variants compute every
+ * ray identically (bit-identical projections); adjoint variants sum every
+ * voxel's angles in the same order but round the detector coordinate from a
+ * different tile origin, so gradients agree to FP32 rounding (~1e-7
+ * relative).  Launch mode and graph replay never change results.
+ *
+ * ei_autotune times every candidate with CUDA events on this geometry's
+ * workspace (synchronises `stream`) and selects the fastest; the choice is
+ * cached in a text file (EI_TUNE_CACHE, default ~/.cache/ei_gb300_autotune.txt)
+ * keyed by the GPU name and the slice sizes, and read back on later calls
+ * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
+ * report a variant explicitly (ids: projector 0..3, adjoint 0..2).
+ */
+#define EI_TUNE_FORCE 1
+#define EI_TUNE_NO_CACHE_WRITE 2
+int ei_autotune(ei_geometry *g, int flags, void *stream);
+int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persistent);
+int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent);
 
 /*
  * ei_objective_grad_noalloc — S and its gradient for ONE slice with no device
@@ -282,6 +312,10 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
 #define EI_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ei_objective_grad_noalloc(const ei_geometry_desc *desc, const float *vol, const float *s_exp,
                               double *S_out, float *grad, void *stream);
+
+/* Name and text of the last CUDA error this thread's library calls met (for
+ * EI_ERR_CUDA / EI_ERR_ALLOC), or "" (thread-local storage). */
+const char *ei_last_error(void);
 
 /* Human-readable name of a status code (static storage). */
 const char *ei_status_string(int status);

@@ -36,6 +36,7 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 static double hat(double v)
 {
@@ -96,12 +97,17 @@ void eio_backproject(int n, int n_theta, int n_det, double pitch,
                      const double *theta, const double *g, double *x)
 {
     double hn = 0.5 * (n - 1), hd = 0.5 * (n_det - 1);
+    double *cs = (double *)malloc(sizeof(double) * 2 * (size_t)(n_theta > 0 ? n_theta : 1));
+    for (int a = 0; a < n_theta; ++a) {
+        cs[2 * a] = cos(theta[a]);
+        cs[2 * a + 1] = sin(theta[a]);
+    }
     #pragma omp parallel for schedule(static)
     for (int r = 0; r < n; ++r) {
         for (int c = 0; c < n; ++c) {
             double acc = 0.0;
             for (int a = 0; a < n_theta; ++a) {
-                double ct = cos(theta[a]), st = sin(theta[a]);
+                double ct = cs[2 * a], st = cs[2 * a + 1];
                 double ch = fmax(fabs(ct), fabs(st));
                 double u = (c - hn) * ct + (hn - r) * st + hd;
                 int j0 = (int)floor(u);
@@ -112,6 +118,7 @@ void eio_backproject(int n, int n_theta, int n_det, double pitch,
             x[(size_t)r * n + c] = acc;
         }
     }
+    free(cs);
 }
 
 /*

@@ -4,7 +4,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "ei_internal.h"
@@ -43,6 +48,24 @@ static cudaError_t fetch_floats(const float *src, size_t count, std::vector<floa
     dst.resize(count);
     if (count == 0) return cudaSuccess;
     return cudaMemcpy(dst.data(), src, count * sizeof(float), cudaMemcpyDefault);
+}
+
+static thread_local char g_last_error[256] = "";
+
+void record_error(cudaError_t e)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent)
+{
+    g->fwd_variant.id = fwd_id;
+    g->fwd_variant.prefix = g->fwd_prefixes[fwd_id];
+    g->fwd_variant.total = g->fwd_totals[fwd_id];
+    g->adj_variant.id = adj_id;
+    g->adj_variant.prefix = g->adj_prefixes[adj_id];
+    g->adj_variant.total = g->adj_totals[adj_id];
+    g->persistent = persistent;
 }
 
 cudaEvent_t trace_begin(ei_geometry *g, cudaStream_t st)
@@ -142,6 +165,8 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 extern "C" {
 
+const char *ei_last_error(void) { return g_last_error; }
+
 const char *ei_status_string(int status)
 {
     switch (status) {
@@ -166,6 +191,7 @@ void ei_default_solve_opts(ei_solve_opts *o)
     o->c1 = 1e-4;
     o->max_trials = 20;
     o->curv_eps = 1e-10;
+    o->use_graph = 1;
 }
 
 static void release_events(ei_geometry *g)
@@ -283,7 +309,16 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     std::vector<float4> pix;
     ang.reserve(ang_total);
     pix.reserve(pix_total);
-    std::vector<int> fwd_p(1, 0), ic_p(1, 0), adj_p(1, 0), prep_p(1, 0), vec_p(1, 0);
+    std::vector<int> ic_p(1, 0), prep_p(1, 0), vec_p(1, 0);
+    std::vector<std::vector<int>> fwd_p(N_FWD_VARIANTS, std::vector<int>(1, 0));
+    std::vector<std::vector<int>> adj_p(N_ADJ_VARIANTS, std::vector<int>(1, 0));
+    uint64_t hash = 1469598103934665603ULL;          // FNV-1a over the slice sizes
+    auto mix = [&hash](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            hash ^= (v >> (8 * b)) & 0xff;
+            hash *= 1099511628211ULL;
+        }
+    };
     int64_t vol_off = 0, pp_off = 0, gp_off = 0, sino_off = 0, proj_off = 0, meas_off = 0;
     int ang_off = 0, pix_off = 0, pix_in_off = 0, max_ndp = 4, max_nth = 1;
     const double TWO32 = 4294967296.0;
@@ -303,7 +338,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         {
             const double hn_ = 0.5 * (q.n - 1);
             const int cpad = (q.n + ADJ_TC - 1) / ADJ_TC * ADJ_TC;
-            const int rpad = (q.n + ADJ_TR - 1) / ADJ_TR * ADJ_TR;
+            const int rpad = (q.n + ADJ_MAX_TR - 1) / ADJ_MAX_TR * ADJ_MAX_TR;
             const double mdx = std::max(hn_, cpad - 1 - hn_), mdy = std::max(hn_, rpad - 1 - hn_);
             const double R = sqrt(mdx * mdx + mdy * mdy);
             si.marg = std::max(2, (int)ceil(R - 0.5 * (q.n_det - 1)) + 3);
@@ -351,11 +386,19 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
             else
                 pix.push_back(make_float4(0.f, 0.f, 1.f, 0.f));
         }
-        const int nrb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
-        const int nab = (q.n_theta + FWD_ANGLES - 1) / FWD_ANGLES;
-        fwd_p.push_back(fwd_p.back() + nab * nrb);
+        for (int v = 0; v < N_FWD_VARIANTS; ++v) {
+            int rays, angles;
+            project_variant_shape(v, &rays, &angles);
+            const int nrb = (si.n_dp + rays - 1) / rays;
+            const int nab = (q.n_theta + angles - 1) / angles;
+            fwd_p[v].push_back(fwd_p[v].back() + nab * nrb);
+        }
+        for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
+            const int tr = backproject_variant_rows(v);
+            adj_p[v].push_back(adj_p[v].back() + ((q.n + ADJ_TC - 1) / ADJ_TC) * ((q.n + tr - 1) / tr));
+        }
+        mix((uint64_t)q.n), mix((uint64_t)q.n_theta), mix((uint64_t)q.n_det);
         ic_p.push_back(ic_p.back() + q.n_theta);
-        adj_p.push_back(adj_p.back() + ((q.n + ADJ_TC - 1) / ADJ_TC) * ((q.n + ADJ_TR - 1) / ADJ_TR));
         const int pt = (q.n + 1 + PREP_TILE - 1) / PREP_TILE;
         prep_p.push_back(prep_p.back() + pt * pt);
         const int64_t nvox = (int64_t)q.n * q.n;
@@ -382,9 +425,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
 
     DevGeom &dg = g->dg;
     dg.n_slices = n_slices;
-    dg.total_fwd = fwd_p.back();
     dg.total_ic = ic_p.back();
-    dg.total_adj = adj_p.back();
     dg.total_prep = prep_p.back();
     dg.total_vec = vec_p.back();
     dg.max_ndp = max_ndp;
@@ -406,14 +447,27 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     AngleInfo *d_ang = nullptr;
     float *d_mo = nullptr;
     float4 *d_pix = nullptr;
-    int *d_fwd = nullptr, *d_ic = nullptr, *d_adj = nullptr, *d_prep = nullptr, *d_vec = nullptr;
+    int *d_ic = nullptr, *d_prep = nullptr, *d_vec = nullptr;
+    int max_adj_total = 0;
+    for (int v = 0; v < N_FWD_VARIANTS; ++v) {
+        int *dp = nullptr;
+        if (e == cudaSuccess) e = upload(g, &dp, fwd_p[v]);
+        g->fwd_prefixes[v] = dp;
+        g->fwd_totals[v] = fwd_p[v].back();
+    }
+    for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
+        int *dp = nullptr;
+        if (e == cudaSuccess) e = upload(g, &dp, adj_p[v]);
+        g->adj_prefixes[v] = dp;
+        g->adj_totals[v] = adj_p[v].back();
+        max_adj_total = std::max(max_adj_total, adj_p[v].back());
+    }
+    g->shape_hash = hash ^ (uint64_t)n_slices;
     if (e == cudaSuccess) e = upload(g, &d_sl, g->h_slices);
     if (e == cudaSuccess) e = upload(g, &d_ang, ang);
     if (e == cudaSuccess) e = upload(g, &d_mo, m_o);
     if (e == cudaSuccess) e = upload(g, &d_pix, pix);
-    if (e == cudaSuccess) e = upload(g, &d_fwd, fwd_p);
     if (e == cudaSuccess) e = upload(g, &d_ic, ic_p);
-    if (e == cudaSuccess) e = upload(g, &d_adj, adj_p);
     if (e == cudaSuccess) e = upload(g, &d_prep, prep_p);
     if (e == cudaSuccess) e = upload(g, &d_vec, vec_p);
     if (e == cudaSuccess) e = dev_alloc(g, &g->xpA, (size_t)g->pp_count);
@@ -424,7 +478,9 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = dev_alloc(g, &g->gA, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->gB, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_ic, (size_t)dg.total_ic);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->part_adj, (size_t)dg.total_adj);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->part_adj, (size_t)max_adj_total);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->work_counter, 2);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
     // the packed gradient sinogram's margins and padding pixels must read as zero
     if (e == cudaSuccess) e = cudaMemset(g->gA, 0, (size_t)g->gp_count * sizeof(float4));
@@ -440,12 +496,137 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     dg.ang = d_ang;
     dg.m_o = d_mo;
     dg.pix = d_pix;
-    dg.fwd_prefix = d_fwd;
     dg.ic_prefix = d_ic;
-    dg.adj_prefix = d_adj;
     dg.prep_prefix = d_prep;
     dg.vec_prefix = d_vec;
+    select_variants(g, 0, 0, false);
     *out = g;
+    return EI_OK;
+}
+
+int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persistent)
+{
+    if (!g || fwd_variant < 0 || fwd_variant >= N_FWD_VARIANTS || adj_variant < 0 ||
+        adj_variant >= N_ADJ_VARIANTS)
+        return EI_ERR_ARG;
+    select_variants(g, fwd_variant, adj_variant, persistent != 0);
+    return EI_OK;
+}
+
+int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent)
+{
+    if (!g || !fwd_variant || !adj_variant || !persistent) return EI_ERR_ARG;
+    *fwd_variant = g->fwd_variant.id;
+    *adj_variant = g->adj_variant.id;
+    *persistent = g->persistent ? 1 : 0;
+    return EI_OK;
+}
+
+static std::string tune_cache_path()
+{
+    const char *p = getenv("EI_TUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/ei_gb300_autotune.txt";
+}
+
+static std::string tune_key(const ei_geometry *g)
+{
+    cudaDeviceProp prop{};
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, g->device) == cudaSuccess) name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    char buf[64];
+    snprintf(buf, sizeof buf, "|%016llx|v1", (unsigned long long)g->shape_hash);
+    return name + buf;
+}
+
+// Mean duration (ms) of `reps` launches of the selected projector or adjoint variant.
+static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, double *ms)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return EI_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return EI_ERR_CUDA;
+    }
+    const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int reps_ = reps;
+    (void)reps_;
+    auto launch = [&]() {
+        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero,
+                                            g->part_adj, nullptr, st)
+                       : launch_project(g, g->proj, nullptr, st);
+    };
+    cudaError_t e = launch();                       // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / reps;
+    return e == cudaSuccess ? EI_OK : EI_ERR_CUDA;
+}
+
+int ei_autotune(ei_geometry *g, int flags, void *stream)
+{
+    if (!g) return EI_ERR_ARG;
+    const std::string key = tune_key(g), path = tune_cache_path();
+    if (!(flags & EI_TUNE_FORCE)) {
+        FILE *f = fopen(path.c_str(), "r");
+        if (f) {
+            char k[512];
+            int fv, av, pv;
+            double fm, am;
+            bool found = false;
+            while (fscanf(f, "%511s %d %d %d %lf %lf", k, &fv, &av, &pv, &fm, &am) == 6)
+                if (key == k && fv >= 0 && fv < N_FWD_VARIANTS && av >= 0 && av < N_ADJ_VARIANTS) {
+                    select_variants(g, fv, av, pv != 0);      // the last matching line wins
+                    found = true;
+                }
+            fclose(f);
+            if (found) return EI_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double best_total = 1e300, best_f = 0, best_a = 0;
+    int bf = 0, ba = 0, bp = 0;
+    for (int pers = 0; pers < 2; ++pers) {
+        double fbest = 1e300, abest = 1e300;
+        int fid = 0, aid = 0;
+        for (int v = 0; v < N_FWD_VARIANTS; ++v) {
+            select_variants(g, v, 0, pers != 0);
+            double ms = 0;
+            const int rc = time_kernel(g, false, st, 3, &ms);
+            if (rc != EI_OK) return rc;
+            if (ms < fbest) fbest = ms, fid = v;
+        }
+        for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
+            select_variants(g, fid, v, pers != 0);
+            double ms = 0;
+            const int rc = time_kernel(g, true, st, 3, &ms);
+            if (rc != EI_OK) return rc;
+            if (ms < abest) abest = ms, aid = v;
+        }
+        if (fbest + abest < best_total) {
+            best_total = fbest + abest;
+            bf = fid, ba = aid, bp = pers, best_f = fbest, best_a = abest;
+        }
+    }
+    select_variants(g, bf, ba, bp != 0);
+    if (!(flags & EI_TUNE_NO_CACHE_WRITE)) {
+        const size_t slash = path.find_last_of('/');
+        if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+        FILE *f = fopen(path.c_str(), "a");       // best effort: no cache if not writable
+        if (f) {
+            fprintf(f, "%s %d %d %d %.6f %.6f\n", key.c_str(), bf, ba, bp, best_f, best_a);
+            fclose(f);
+        }
+    }
     return EI_OK;
 }
 
@@ -486,6 +667,7 @@ int ei_get_slice_layout(const ei_geometry *g, int s, ei_slice_layout *o)
 static int status_from(cudaError_t e)
 {
     if (e == cudaSuccess) return EI_OK;
+    ei::record_error(e);
     return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
 }
 

@@ -63,31 +63,30 @@ struct ModelConsts {
 };
 
 // Work decomposition sizes.
-// (compile-time tunables; the defaults are the measured best on GB300)
-#ifndef EI_FWD_RAYS
-#define EI_FWD_RAYS 16
-#endif
-#ifndef EI_FWD_ANGLES
-#define EI_FWD_ANGLES 16
-#endif
-#ifndef EI_FWD_UNROLL
-#define EI_FWD_UNROLL 4
-#endif
-#ifndef EI_ADJ_PASSES
-#define EI_ADJ_PASSES 8
-#endif
-#ifndef EI_ADJ_MINBLOCKS
-#define EI_ADJ_MINBLOCKS 4
-#endif
-constexpr int FWD_RAYS = EI_FWD_RAYS;      // rays per forward work item (multiple of 8)
-constexpr int FWD_ANGLES = EI_FWD_ANGLES;  // angles per forward work item (multiple of 4);
-                                           // warp = 8 rays x 4 angles
-constexpr int ADJ_TC = 32;                 // adjoint tile: 32 columns x 8 * passes rows,
-constexpr int ADJ_TR = 8 * EI_ADJ_PASSES;  // one voxel per thread and pass
+constexpr int ADJ_TC = 32;                 // adjoint tile: 32 columns x (8 x passes) rows
+constexpr int ADJ_MAX_TR = 128;            // tallest adjoint tile among the variants
 constexpr int ADJ_THREADS = 256;
-constexpr int PREP_TILE = 32;      // staging tile
-constexpr int VEC_BLK = 4096;      // float4 per vector-op block (one slice per block)
+constexpr int PREP_TILE = 32;              // staging tile
+constexpr int VEC_BLK = 4096;              // float4 per vector-op block (one slice per block)
 constexpr int VEC_THREADS = 256;
+
+// Kernel variants the autotuner chooses among (instantiated in k_project.cu /
+// k_backproject.cu).  Each has its own work decomposition.
+constexpr int N_FWD_VARIANTS = 4;          // projector tile (rays x angles, unroll)
+constexpr int N_ADJ_VARIANTS = 3;          // adjoint voxels per thread and occupancy
+void project_variant_shape(int id, int *rays, int *angles);
+int backproject_variant_rows(int id);
+
+struct FwdVariant {
+    int id = 0;
+    const int *prefix = nullptr;   // device [n_slices + 1] work-item prefix sums
+    int total = 0;
+};
+struct AdjVariant {
+    int id = 0;
+    const int *prefix = nullptr;
+    int total = 0;
+};
 
 // Device-side view of a geometry, passed to kernels by value.
 struct DevGeom {
@@ -95,13 +94,11 @@ struct DevGeom {
     const AngleInfo *ang;        // [sum n_theta]
     const float *m_o;            // [sum n_theta]
     const float4 *pix;           // [sum n_dp]: (A, c, w, m_r)
-    const int *fwd_prefix;       // [n_slices + 1] work-item prefix sums
-    const int *ic_prefix;
-    const int *adj_prefix;
-    const int *prep_prefix;
-    const int *vec_prefix;
+    const int *ic_prefix;        // [n_slices + 1] work-item prefix sums (IC rows,
+    const int *prep_prefix;      // staging tiles, vector blocks; the projector's and
+    const int *vec_prefix;       // adjoint's belong to their variants)
     int n_slices;
-    int total_fwd, total_ic, total_adj, total_prep, total_vec;
+    int total_ic, total_prep, total_vec;
     int max_ndp, max_n_theta;
     ModelConsts mc;
 };
@@ -146,6 +143,18 @@ struct ei_geometry {
             meas_count = 0;
     int64_t workspace_bytes = 0;
     ei::Solver *solver = nullptr;      // allocated on first ei_reconstruct
+    // kernel variants (autotuner) and persistent launches
+    ei::FwdVariant fwd_variant;
+    ei::AdjVariant adj_variant;
+    const int *fwd_prefixes[ei::N_FWD_VARIANTS] = {};
+    int fwd_totals[ei::N_FWD_VARIANTS] = {};
+    const int *adj_prefixes[ei::N_ADJ_VARIANTS] = {};
+    int adj_totals[ei::N_ADJ_VARIANTS] = {};
+    bool persistent = false;
+    int num_sms = 0;
+    int *work_counter = nullptr;       // [2] work counters of the persistent kernels
+    // work per slice, for the autotuner's cache key
+    uint64_t shape_hash = 0;
     // tracing (ei_profile_enable): launch counter and event pairs per traced kernel
     bool prof_on = false;
     int64_t launches = 0;
@@ -193,6 +202,10 @@ cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double 
 
 int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_solve_opts *opts,
                 ei_solve_report *report, cudaStream_t st);
+// Remember the last CUDA error of this thread (reported by ei_last_error).
+void record_error(cudaError_t e);
+// Select kernel variants (ids in range) and the launch mode.
+void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent);
 void destroy_solver(ei_geometry *g);
 
 }  // namespace ei

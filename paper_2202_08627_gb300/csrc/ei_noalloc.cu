@@ -153,13 +153,17 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     {
         const double hn = 0.5 * (n - 1);
         const int cpad = (n + ADJ_TC - 1) / ADJ_TC * ADJ_TC;
-        const int rpad = (n + ADJ_TR - 1) / ADJ_TR * ADJ_TR;
+        const int rpad = (n + ADJ_MAX_TR - 1) / ADJ_MAX_TR * ADJ_MAX_TR;
         const double mdx = std::max(hn, cpad - 1 - hn), mdy = std::max(hn, rpad - 1 - hn);
         si.marg = std::max(2, (int)ceil(sqrt(mdx * mdx + mdy * mdy) - 0.5 * (nd - 1)) + 3);
     }
     si.gw = ndp + 2 * si.marg;
-    const int n_fwd = ((nth + FWD_ANGLES - 1) / FWD_ANGLES) * ((ndp + FWD_RAYS - 1) / FWD_RAYS);
-    const int n_adj = ((n + ADJ_TC - 1) / ADJ_TC) * ((n + ADJ_TR - 1) / ADJ_TR);
+    // default kernel variants (0): their work decompositions
+    int rays = 0, angles = 0;
+    project_variant_shape(0, &rays, &angles);
+    const int adj_rows = backproject_variant_rows(0);
+    const int n_fwd = ((nth + angles - 1) / angles) * ((ndp + rays - 1) / rays);
+    const int n_adj = ((n + ADJ_TC - 1) / ADJ_TC) * ((n + adj_rows - 1) / adj_rows);
     const int pt = (n + 1 + PREP_TILE - 1) / PREP_TILE;
     const int n_prep = pt * pt;
     const int n_vec = (int)(((int64_t)n * n + VEC_BLK - 1) / VEC_BLK);
@@ -248,15 +252,17 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     dg.ang = (const AngleInfo *)(base + o_ang);
     dg.m_o = (const float *)(base + o_mo);
     dg.pix = (const float4 *)(base + o_pix);
-    dg.fwd_prefix = pref + 0;
     dg.ic_prefix = pref + 2;
-    dg.adj_prefix = pref + 4;
     dg.prep_prefix = pref + 6;
     dg.vec_prefix = pref + 8;
     dg.n_slices = 1;
-    dg.total_fwd = n_fwd;
     dg.total_ic = nth;
-    dg.total_adj = n_adj;
+    g.fwd_variant.id = 0;
+    g.fwd_variant.prefix = pref + 0;
+    g.fwd_variant.total = n_fwd;
+    g.adj_variant.id = 0;
+    g.adj_variant.prefix = pref + 4;
+    g.adj_variant.total = n_adj;
     dg.total_prep = n_prep;
     dg.total_vec = n_vec;
     dg.max_ndp = ndp;

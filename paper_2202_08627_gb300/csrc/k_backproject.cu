@@ -24,11 +24,12 @@
 // Also fused: out = out_mult * R^T g + reg2 * v (the regulariser's gradient)
 // and per-tile FP64 partial sums of sum_c reg1_c v_c^2 (its value); v may be
 // null (no regulariser).
+#include <algorithm>
+
 #include "ei_internal.h"
 
 namespace ei {
 
-constexpr int ADJ_PASSES = EI_ADJ_PASSES;   // 8 rows per pass (8 warps: 4 columns x 2 rows of 8x4)
 constexpr int ADJ_CHUNK = 128;           // angles staged per shared-memory chunk
 
 __device__ __forceinline__ double block_sum_double_adj(double v, double *red)
@@ -45,31 +46,37 @@ __device__ __forceinline__ double block_sum_double_adj(double v, double *red)
     return t;
 }
 
-__global__ void __launch_bounds__(ADJ_THREADS, EI_ADJ_MINBLOCKS)
-k_backproject(DevGeom dg, const float4 *__restrict__ gA, const float2 *__restrict__ gB,
-              bool with_sino, const float4 *__restrict__ v, float4 *__restrict__ out,
-              float4 out_mult, float4 reg2, float4 reg1, double *__restrict__ part,
-              const int *__restrict__ active)
-{
-    __shared__ float4 s_cs[ADJ_CHUNK];   // cos, sin, pitch/(ch*ch), pitch/ch
-    __shared__ float4 s_jp[ADJ_CHUNK];   // J (int bits), phi, pitch/ch - pitch/(ch*ch), -
-    __shared__ double red[32];
+struct AdjShared {
+    float4 cs[ADJ_CHUNK];   // cos, sin, pitch/(ch*ch), pitch/ch
+    float4 jp[ADJ_CHUNK];   // J (int bits), phi, pitch/ch - pitch/(ch*ch), -
+    double red[32];
+};
 
-    const int item = blockIdx.x;
-    const int s = find_slice(dg.adj_prefix, dg.n_slices, item);
+// One work item: a 32-column x (8 PASSES)-row voxel tile, 8 x 4 voxel patch per
+// warp and pass, one voxel per thread and pass.  Angles are summed in order
+// whatever PASSES, so every variant gives bit-identical results.
+template <int PASSES>
+__device__ __forceinline__ void backproject_item(
+    const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
+    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
+    double *__restrict__ part, const int *__restrict__ active)
+{
+    constexpr int TR = 8 * PASSES;
+    const int s = find_slice(prefix, dg.n_slices, item);
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
     const int n = si.n;
     const int ntc = (n + ADJ_TC - 1) / ADJ_TC;
-    const int local = item - dg.adj_prefix[s];
-    const int r_t = (local / ntc) * ADJ_TR, c_t = (local % ntc) * ADJ_TC;
+    const int local = item - prefix[s];
+    const int r_t = (local / ntc) * TR, c_t = (local % ntc) * ADJ_TC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int dc = (warp & 3) * 8 + (lane & 7);        // column offset in the tile
     const int dr0 = (warp >> 2) * 4 + (lane >> 3);     // row offset of pass 0 (passes add 8)
 
-    float acc[ADJ_PASSES][3];
+    float acc[PASSES][3];
 #pragma unroll
-    for (int p = 0; p < ADJ_PASSES; ++p) acc[p][0] = acc[p][1] = acc[p][2] = 0.f;
+    for (int p = 0; p < PASSES; ++p) acc[p][0] = acc[p][1] = acc[p][2] = 0.f;
 
     if (with_sino) {
         const float4 *rowA0 = gA + si.gp_off + si.marg;
@@ -85,8 +92,8 @@ k_backproject(DevGeom dg, const float4 *__restrict__ gA, const float2 *__restric
                 const AngleInfo an = dg.ang[si.ang_off + a0 + threadIdx.x];
                 const long long U = (two_ct * an.cos_fx + two_rt * an.sin_fx + hd2) >> 1;
                 const float pi = an.pch * an.inv_ch;
-                s_cs[threadIdx.x] = make_float4(an.cosf, an.sinf, pi, an.pch);
-                s_jp[threadIdx.x] = make_float4(
+                sh.cs[threadIdx.x] = make_float4(an.cosf, an.sinf, pi, an.pch);
+                sh.jp[threadIdx.x] = make_float4(
                     __int_as_float((int)(U >> 32)),
                     (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f, an.pch - pi, 0.f);
             }
@@ -94,15 +101,15 @@ k_backproject(DevGeom dg, const float4 *__restrict__ gA, const float2 *__restric
             const float4 *rowA = rowA0 + (int64_t)a0 * si.gw;
             const float2 *rowB = rowB0 + (int64_t)a0 * si.gw;
             for (int k = 0; k < na; ++k) {
-                const float4 cs = s_cs[k];
-                const float4 jp = s_jp[k];
+                const float4 cs = sh.cs[k];
+                const float4 jp = sh.jp[k];
                 const int J = __float_as_int(jp.x);
                 const float v0 = fmaf(fx, cs.x, fmaf(-fy, cs.y, jp.y));
                 const float step = -8.f * cs.y;
                 const float4 *rA = rowA + J;
                 const float2 *rB = rowB + J;
 #pragma unroll
-                for (int p = 0; p < ADJ_PASSES; ++p) {
+                for (int p = 0; p < PASSES; ++p) {
                     const float vl = fmaf((float)p, step, v0);
                     const float fl = floorf(vl);
                     const int jj = (int)fl;
@@ -124,7 +131,7 @@ k_backproject(DevGeom dg, const float4 *__restrict__ gA, const float2 *__restric
     double regv = 0.0;
     const int c = c_t + dc;
 #pragma unroll
-    for (int p = 0; p < ADJ_PASSES; ++p) {
+    for (int p = 0; p < PASSES; ++p) {
         const int r = r_t + dr0 + 8 * p;
         if (r < n && c < n) {
             const int64_t idx = si.vol_off + (int64_t)r * n + c;
@@ -137,18 +144,86 @@ k_backproject(DevGeom dg, const float4 *__restrict__ gA, const float2 *__restric
                                        fmaf(out_mult.z, acc[p][2], reg2.z * x.z), 0.f);
         }
     }
-    const double tot = block_sum_double_adj(regv, red);
+    const double tot = block_sum_double_adj(regv, sh.red);
     if (threadIdx.x == 0) part[item] = tot;
+}
+
+template <int PASSES, int MINB>
+__global__ void __launch_bounds__(ADJ_THREADS, MINB)
+k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
+              const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
+              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
+              double *__restrict__ part, const int *__restrict__ active)
+{
+    __shared__ AdjShared sh;
+    backproject_item<PASSES>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out, out_mult,
+                             reg2, reg1, part, active);
+}
+
+// Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
+// launch) until the list is exhausted; no block waits on another.
+template <int PASSES, int MINB>
+__global__ void __launch_bounds__(ADJ_THREADS, MINB)
+k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
+                         const float4 *__restrict__ gA, const float2 *__restrict__ gB,
+                         bool with_sino, const float4 *__restrict__ v, float4 *__restrict__ out,
+                         float4 out_mult, float4 reg2, float4 reg1, double *__restrict__ part,
+                         const int *__restrict__ active)
+{
+    __shared__ AdjShared sh;
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) return;
+        backproject_item<PASSES>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
+                                 reg2, reg1, part, active);
+    }
+}
+
+template <int P, int M>
+static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const float4 *v,
+                                     float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                                     double *part, const int *active, cudaStream_t st)
+{
+    const AdjVariant &av = g->adj_variant;
+    if (av.total == 0) return cudaSuccess;
+    if (!g->persistent) {
+        k_backproject<P, M><<<av.total, ADJ_THREADS, 0, st>>>(g->dg, av.prefix, g->gA, g->gB,
+                                                              with_sino, v, out, out_mult, reg2,
+                                                              reg1, part, active);
+    } else {
+        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
+        if (per_sm == 0)
+            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_backproject_persistent<P, M>, ADJ_THREADS, 0));
+        const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
+        EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
+        k_backproject_persistent<P, M><<<grid, ADJ_THREADS, 0, st>>>(
+            g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
+            out_mult, reg2, reg1, part, active);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
                                float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                double *part, const int *active, cudaStream_t st)
 {
-    if (g->dg.total_adj == 0) return cudaSuccess;
-    k_backproject<<<g->dg.total_adj, ADJ_THREADS, 0, st>>>(g->dg, g->gA, g->gB, with_sino, v, out,
-                                                            out_mult, reg2, reg1, part, active);
-    return cudaGetLastError();
+    switch (g->adj_variant.id) {
+    case 0: return launch_bp_variant<8, 4>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 1: return launch_bp_variant<4, 1>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    default: return launch_bp_variant<16, 2>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    }
+}
+
+// Voxel rows per tile of adjoint variant `id` (see launch_backproject).
+int backproject_variant_rows(int id)
+{
+    static const int P[3] = {8, 4, 16};
+    return 8 * P[id];
 }
 
 // ----------------------------------------------------------------------------
@@ -183,7 +258,8 @@ cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStre
 // ----------------------------------------------------------------------------
 // S[s] = sum_rows part_ic + sum_tiles part_adj, one block per slice, fixed order.
 // ----------------------------------------------------------------------------
-__global__ void k_finalize_objective(DevGeom dg, const double *__restrict__ part_ic,
+__global__ void k_finalize_objective(DevGeom dg, const int *__restrict__ adj_prefix,
+                                     const double *__restrict__ part_ic,
                                      const double *__restrict__ part_adj, double *__restrict__ S,
                                      const int *__restrict__ active)
 {
@@ -193,7 +269,7 @@ __global__ void k_finalize_objective(DevGeom dg, const double *__restrict__ part
     double acc = 0.0;
     for (int i = dg.ic_prefix[s] + threadIdx.x; i < dg.ic_prefix[s + 1]; i += blockDim.x)
         acc += part_ic[i];
-    for (int i = dg.adj_prefix[s] + threadIdx.x; i < dg.adj_prefix[s + 1]; i += blockDim.x)
+    for (int i = adj_prefix[s] + threadIdx.x; i < adj_prefix[s + 1]; i += blockDim.x)
         acc += part_adj[i];
     const double tot = block_sum_double_adj(acc, red);
     if (threadIdx.x == 0) S[s] = tot;
@@ -203,7 +279,8 @@ cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_i
                                       const double *part_adj, double *S, const int *active,
                                       cudaStream_t st)
 {
-    k_finalize_objective<<<g->n_slices, 256, 0, st>>>(g->dg, part_ic, part_adj, S, active);
+    k_finalize_objective<<<g->n_slices, 256, 0, st>>>(g->dg, g->adj_variant.prefix, part_ic,
+                                                       part_adj, S, active);
     return cudaGetLastError();
 }
 

@@ -62,94 +62,134 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
                      float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
                      double *__restrict__ part, const int *__restrict__ active)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
     __shared__ double red[32];
     const int row = blockIdx.x;
     const int s = find_slice(dg.ic_prefix, dg.n_slices, row);
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
     const int a = row - dg.ic_prefix[s];
-    const int nd = si.n_det, ndp = si.n_dp;
+    const int nd = si.n_det, ndp = si.n_dp, ng = ndp >> 2;
     const int64_t plane = (int64_t)si.n_theta * ndp;
     const int64_t rbase = (int64_t)a * ndp;
-    const float *Pmu = proj + si.proj_off + rbase;
-    const float *Pde = Pmu + plane;
-    const float *Psg = Pde + plane;
-    const float *Sx = meas + si.meas_off + rbase;      // plane k at Sx + k * plane
+    // every row starts on a 16-byte boundary (n_dp is a multiple of 4)
+    const float4 *Pmu = reinterpret_cast<const float4 *>(proj + si.proj_off + rbase);
+    const float4 *Pde = reinterpret_cast<const float4 *>(proj + si.proj_off + plane + rbase);
+    const float4 *Psg = reinterpret_cast<const float4 *>(proj + si.proj_off + 2 * plane + rbase);
+    const int64_t plane4 = plane >> 2;
     const float4 *pix = dg.pix + si.pix_off;
     const float mo = dg.m_o[si.ang_off + a];
     const int n_m = dg.mc.n_m;
     const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
 
-    float *s_pd = sm;                  // R[delta] of the row
-    float *s_gsh = sm + dg.max_ndp;    // G_shift, G_mu, G_V of the row
-    float *s_gmu = s_gsh + dg.max_ndp;
-    float *s_gv = s_gmu + dg.max_ndp;
+    const int mq = dg.max_ndp >> 2;
+    float4 *s_pd4 = sm4;               // R[delta] of the row, later g_delta
+    float4 *s_gsh4 = sm4 + mq;         // G_shift, G_mu, G_V of the row
+    float4 *s_gmu4 = s_gsh4 + mq;
+    float4 *s_gv4 = s_gmu4 + mq;
+    const float *s_pd = reinterpret_cast<const float *>(s_pd4);
+    const float *s_gsh = reinterpret_cast<const float *>(s_gsh4);
 
-    for (int gi = threadIdx.x; gi < (ndp >> 2); gi += blockDim.x)
-        reinterpret_cast<float4 *>(s_pd)[gi] = __ldg(reinterpret_cast<const float4 *>(Pde) + gi);
+    for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) s_pd4[gi] = __ldg(Pde + gi);
     __syncthreads();
 
     double e2 = 0.0;
     bool out_of_domain = false;
-    for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
-        float gmu = 0.f, gsh = 0.f, gvv = 0.f;
-        if (j < nd) {
-            const float4 fl = __ldg(pix + j);     // A, c, w, m_r
-            const float shift = zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w;
-            const float V = fmaf(kappa, __ldg(Psg + j), fl.z * fl.z);
-            if (!(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
+    for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+        const float4 pm4 = __ldg(Pmu + gi), ps4 = __ldg(Psg + gi);
+        const float pmv[4] = {pm4.x, pm4.y, pm4.z, pm4.w};
+        const float psv[4] = {ps4.x, ps4.y, ps4.z, ps4.w};
+        float c[4], shift[4], iV[4], amp[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * gi + q;
+            ok[q] = j < nd;
+            const float4 fl = ok[q] ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
+            c[q] = fl.y;
+            shift[q] = ok[q] ? zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w : 0.f;
+            const float V = fmaf(kappa, psv[q], fl.z * fl.z);
+            if (ok[q] && !(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
             const float Vs = fmaxf(V, 1e-30f);
-            const float iV = 1.0f / Vs;
-            const float amp = fl.x * fl.z * rsqrtf(Vs);
-            const float pmu = __ldg(Pmu + j);
-            float st = 0.f, stq = 0.f, stq2 = 0.f, e2f = 0.f;
-            for (int k = 0; k < n_m; ++k) {
-                const float qd = dg.mc.m[k] - fl.y - shift;
-                const float sv = amp * expf(-pmu - 0.5f * qd * qd * iV);
-                if (MODE == IC_MODEL) {
-                    s_mod[si.meas_off + rbase + (int64_t)k * plane + j] = sv;
-                } else {
-                    const float e = sv - __ldcs(Sx + (int64_t)k * plane + j);
+            iV[q] = 1.0f / Vs;
+            amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
+        }
+        float st[4] = {0.f, 0.f, 0.f, 0.f}, stq[4] = {0.f, 0.f, 0.f, 0.f},
+              stq2[4] = {0.f, 0.f, 0.f, 0.f};
+        float e2f = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < n_m; ++k) {
+            const float mk = dg.mc.m[k];
+            float sv[4], qd[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                qd[q] = mk - c[q] - shift[q];
+                sv[q] = amp[q] * expf(-pmv[q] - 0.5f * qd[q] * qd[q] * iV[q]);
+            }
+            if (MODE == IC_MODEL) {
+                reinterpret_cast<float4 *>(s_mod + si.meas_off + rbase)[k * plane4 + gi] =
+                    make_float4(sv[0], sv[1], sv[2], sv[3]);
+            } else {
+                const float4 x4 = __ldcs(reinterpret_cast<const float4 *>(meas + si.meas_off + rbase) +
+                                         k * plane4 + gi);
+                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float e = ok[q] ? sv[q] - xv[q] : 0.f;
                     e2f = fmaf(e, e, e2f);
                     if (MODE == IC_OBJECTIVE_GRAD) {
-                        const float t = 2.f * e * sv;
-                        st += t;
-                        stq = fmaf(t, qd, stq);
-                        stq2 = fmaf(t * qd, qd, stq2);
+                        const float t = 2.f * e * sv[q];
+                        st[q] += t;
+                        stq[q] = fmaf(t, qd[q], stq[q]);
+                        stq2[q] = fmaf(t * qd[q], qd[q], stq2[q]);
                     }
                 }
             }
-            e2 += (double)e2f;
-            gmu = -st;
-            gsh = stq * iV;
-            gvv = 0.5f * iV * (stq2 * iV - st);
-        } else if (MODE == IC_MODEL) {
-            for (int k = 0; k < n_m; ++k) s_mod[si.meas_off + rbase + (int64_t)k * plane + j] = 0.f;
         }
+        if (MODE != IC_MODEL) e2 += (double)e2f;
         if (MODE == IC_OBJECTIVE_GRAD) {
-            s_gsh[j] = gsh;
-            s_gmu[j] = gmu;
-            s_gv[j] = gvv;
+            float gsh[4], gvv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                gsh[q] = stq[q] * iV[q];
+                gvv[q] = kappa * 0.5f * iV[q] * (stq2[q] * iV[q] - st[q]);
+            }
+            s_gsh4[gi] = make_float4(gsh[0], gsh[1], gsh[2], gsh[3]);
+            s_gmu4[gi] = make_float4(-st[0], -st[1], -st[2], -st[3]);
+            s_gv4[gi] = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
         }
     }
     if (MODE == IC_MODEL) return;
     if (MODE == IC_OBJECTIVE_GRAD) {
-        // g_delta = (z/period) D^T G_shift (into the R[delta] row, no longer needed) and
-        // g_sigma = kappa G_V; then the packed row: entry of pixel j holds g(j), g(j + 1)
+        // g_delta = (z/period) D^T G_shift into the R[delta] row (no longer needed); then
+        // the packed row: the entry of pixel j holds g(j) and g(j + 1)
         __syncthreads();
-        for (int j = threadIdx.x; j < nd; j += blockDim.x) {
-            s_pd[j] = zp * deriv_T_at(s_gsh, j, nd, si.inv_pitch);
-            s_gv[j] *= kappa;
+        for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+            float gd[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * gi + q;
+                gd[q] = j < nd ? zp * deriv_T_at(s_gsh, j, nd, si.inv_pitch) : 0.f;
+            }
+            s_pd4[gi] = make_float4(gd[0], gd[1], gd[2], gd[3]);
         }
         __syncthreads();
+        const float *gmu = reinterpret_cast<const float *>(s_gmu4);
+        const float *gdl = reinterpret_cast<const float *>(s_pd4);
+        const float *gsg = reinterpret_cast<const float *>(s_gv4);
         const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
-        for (int j = (int)threadIdx.x - 1; j < nd; j += blockDim.x) {
-            float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-            if (j >= 0) lx = s_gmu[j], ly = s_pd[j], lz = s_gv[j];
-            if (j + 1 < nd) hx = s_gmu[j + 1], hy = s_pd[j + 1], hz = s_gv[j + 1];
-            gA[dst + j] = make_float4(lx, ly, lz, hx);
-            gB[dst + j] = make_float2(hy, hz);
+        for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * gi + q;
+                const bool nx = j + 1 < ndp;
+                gA[dst + j] = make_float4(gmu[j], gdl[j], gsg[j], nx ? gmu[j + 1] : 0.f);
+                gB[dst + j] = make_float2(nx ? gdl[j + 1] : 0.f, nx ? gsg[j + 1] : 0.f);
+            }
+        }
+        if (threadIdx.x == 0) {                     // entry of pixel -1: (0, g(0))
+            gA[dst - 1] = make_float4(0.f, 0.f, 0.f, gmu[0]);
+            gB[dst - 1] = make_float2(gdl[0], gsg[0]);
         }
     }
     const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
@@ -161,8 +201,9 @@ cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas
                       double *part, IcMode mode, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
-    int threads = (g->dg.max_ndp + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
+    // one thread per 4 pixels of the widest row, at most 512 (then threads loop)
+    int threads = (g->dg.max_ndp / 4 + 31) / 32 * 32;
+    if (threads > 512) threads = 512;
     const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
     switch (mode) {
     case IC_MODEL:

@@ -21,6 +21,8 @@
 //  - the crossing position is carried in 32.32 fixed point (int64): one
 //    integer add per sample; the integer part is the voxel index and the low
 //    word the interpolation weight, exact to ~1e-7 voxel at any slice size.
+#include <algorithm>
+
 #include "ei_internal.h"
 
 namespace ei {
@@ -83,25 +85,28 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restri
 }
 
 // --------------------------------------------------------------------------
-// Projector: one thread per ray; a work item is FWD_ANGLES angles x FWD_RAYS
-// pixels of one slice; warp = 8 pixels x 4 angles.
+// Projector: one thread per ray; a work item is ANGLES angles x RAYS pixels of
+// one slice; warp = 8 pixels x 4 angles.  Templated on the tile shape and the
+// unroll so the autotuner can choose among instantiations.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(FWD_RAYS * FWD_ANGLES)
-k_project(DevGeom dg, const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
-          const float4 *__restrict__ xtA, const float2 *__restrict__ xtB, float *__restrict__ proj,
-          const int *__restrict__ active)
+template <int RAYS, int ANGLES, int UNROLL>
+__device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
+                                             const float4 *__restrict__ xpA,
+                                             const float2 *__restrict__ xpB,
+                                             const float4 *__restrict__ xtA,
+                                             const float2 *__restrict__ xtB,
+                                             float *__restrict__ proj, const int *__restrict__ active)
 {
-    const int item = blockIdx.x;
-    const int s = find_slice(dg.fwd_prefix, dg.n_slices, item);
+    const int s = find_slice(prefix, dg.n_slices, item);
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
-    const int nrb = (si.n_dp + FWD_RAYS - 1) / FWD_RAYS;
-    const int local = item - dg.fwd_prefix[s];
+    const int nrb = (si.n_dp + RAYS - 1) / RAYS;
+    const int local = item - prefix[s];
     const int ab = local / nrb, rb = local - ab * nrb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int WR = FWD_RAYS / 8;                   // warps along the rays
-    const int a = ab * FWD_ANGLES + (warp / WR) * 4 + (lane >> 3);
-    const int j = rb * FWD_RAYS + (warp % WR) * 8 + (lane & 7);
+    constexpr int WR = RAYS / 8;                       // warps along the rays
+    const int a = ab * ANGLES + (warp / WR) * 4 + (lane >> 3);
+    const int j = rb * RAYS + (warp % WR) * 8 + (lane & 7);
     if (a >= si.n_theta || j >= si.n_dp) return;
     const int64_t plane = (int64_t)si.n_theta * si.n_dp;
     float *out = proj + si.proj_off + (int64_t)a * si.n_dp + j;
@@ -147,14 +152,16 @@ k_project(DevGeom dg, const float4 *__restrict__ xpA, const float2 *__restrict__
     float ax = 0.f, ay = 0.f, az = 0.f;
     long long pos = base + (long long)o_lo * p1;
     const float inv32 = 2.3283064365386963e-10f;   // 2^-32
-    // EI_FWD_UNROLL samples per iteration, their loads independent of each other
+    // UNROLL samples per iteration, their loads independent of each other; the
+    // samples are summed in row order whatever the unroll, so every variant
+    // gives bit-identical projections
     int o = o_lo;
-    for (; o + EI_FWD_UNROLL - 1 <= o_hi; o += EI_FWD_UNROLL) {
-        float4 va[EI_FWD_UNROLL];
-        float2 vb[EI_FWD_UNROLL];
-        float f[EI_FWD_UNROLL];
+    for (; o + UNROLL - 1 <= o_hi; o += UNROLL) {
+        float4 va[UNROLL];
+        float2 vb[UNROLL];
+        float f[UNROLL];
 #pragma unroll
-        for (int u = 0; u < EI_FWD_UNROLL; ++u) {
+        for (int u = 0; u < UNROLL; ++u) {
             const long long q = pos + u * p1;
             const int i0 = (int)(q >> 32);                     // floor of the position
             f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
@@ -162,14 +169,14 @@ k_project(DevGeom dg, const float4 *__restrict__ xpA, const float2 *__restrict__
             vb[u] = __ldg(rowB + u * w + i0);
         }
 #pragma unroll
-        for (int u = 0; u < EI_FWD_UNROLL; ++u) {
+        for (int u = 0; u < UNROLL; ++u) {
             ax += fmaf(f[u], va[u].w - va[u].x, va[u].x);
             ay += fmaf(f[u], vb[u].x - va[u].y, va[u].y);
             az += fmaf(f[u], vb[u].y - va[u].z, va[u].z);
         }
-        pos += EI_FWD_UNROLL * p1;
-        rowA += EI_FWD_UNROLL * w;
-        rowB += EI_FWD_UNROLL * w;
+        pos += UNROLL * p1;
+        rowA += UNROLL * w;
+        rowB += UNROLL * w;
     }
     for (; o <= o_hi; ++o) {
         const int i0 = (int)(pos >> 32);
@@ -188,6 +195,60 @@ k_project(DevGeom dg, const float4 *__restrict__ xpA, const float2 *__restrict__
     out[2 * plane] = az * an.pch;
 }
 
+// One block per work item.
+template <int RAYS, int ANGLES, int UNROLL>
+__global__ void __launch_bounds__(RAYS * ANGLES)
+k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
+          const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
+          const float2 *__restrict__ xtB, float *__restrict__ proj, const int *__restrict__ active)
+{
+    project_item<RAYS, ANGLES, UNROLL>(dg, prefix, blockIdx.x, xpA, xpB, xtA, xtB, proj, active);
+}
+
+// Persistent: a GPU-sized grid whose blocks take work items from a counter
+// (set to 0 before the launch) until the list is exhausted; no block waits on
+// another.
+template <int RAYS, int ANGLES, int UNROLL>
+__global__ void __launch_bounds__(RAYS * ANGLES)
+k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
+                     const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
+                     const float4 *__restrict__ xtA, const float2 *__restrict__ xtB,
+                     float *__restrict__ proj, const int *__restrict__ active)
+{
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= total) return;
+        project_item<RAYS, ANGLES, UNROLL>(dg, prefix, item, xpA, xpB, xtA, xtB, proj, active);
+    }
+}
+
+template <int R, int A, int U>
+static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, const int *active,
+                                          cudaStream_t st)
+{
+    const FwdVariant &v = g->fwd_variant;
+    if (v.total == 0) return cudaSuccess;
+    if (!g->persistent) {
+        k_project<R, A, U><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB, g->xtA,
+                                                       g->xtB, proj, active);
+    } else {
+        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
+        if (per_sm == 0)
+            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_project_persistent<R, A, U>, R * A, 0));
+        const int grid = std::max(1, std::min(v.total, per_sm * g->num_sms));
+        EI_CUDA_TRY(cudaMemsetAsync(g->work_counter, 0, sizeof(int), st));
+        k_project_persistent<R, A, U><<<grid, R * A, 0, st>>>(g->dg, v.prefix, v.total,
+                                                             g->work_counter, g->xpA, g->xpB,
+                                                             g->xtA, g->xtB, proj, active);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, const int *active,
                         cudaStream_t st)
 {
@@ -199,10 +260,20 @@ cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, co
 
 cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st)
 {
-    if (g->dg.total_fwd == 0) return cudaSuccess;
-    k_project<<<g->dg.total_fwd, FWD_RAYS * FWD_ANGLES, 0, st>>>(g->dg, g->xpA, g->xpB, g->xtA,
-                                                                  g->xtB, proj, active);
-    return cudaGetLastError();
+    switch (g->fwd_variant.id) {
+    case 0: return launch_project_variant<16, 16, 4>(g, proj, active, st);
+    case 1: return launch_project_variant<32, 8, 4>(g, proj, active, st);
+    case 2: return launch_project_variant<32, 16, 4>(g, proj, active, st);
+    default: return launch_project_variant<16, 16, 2>(g, proj, active, st);
+    }
+}
+
+// Tile shape (rays, angles) of projector variant `id` (see launch_project).
+void project_variant_shape(int id, int *rays, int *angles)
+{
+    static const int R[4] = {16, 32, 32, 16}, A[4] = {16, 8, 16, 16};
+    *rays = R[id];
+    *angles = A[id];
 }
 
 }  // namespace ei

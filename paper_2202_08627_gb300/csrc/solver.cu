@@ -51,6 +51,7 @@ struct Solver {
     int *mask_dir = nullptr, *mask_ls = nullptr, *mask_acc = nullptr;
     int *summary = nullptr;                 // [2]: slices still running, slices in line search
     int *summary_h = nullptr;               // pinned host copy
+    cudaStream_t stream = nullptr;          // the solver's own stream (capturable)
     std::vector<void *> allocs;
 };
 
@@ -484,6 +485,7 @@ void destroy_solver(ei_geometry *g)
     if (!g->solver) return;
     for (void *p : g->solver->allocs) cudaFree(p);
     if (g->solver->summary_h) cudaFreeHost(g->solver->summary_h);
+    if (g->solver->stream) cudaStreamDestroy(g->solver->stream);
     delete g->solver;
     g->solver = nullptr;
 }
@@ -515,6 +517,7 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(salloc(s, &s->mask_acc, S));
     EI_CUDA_TRY(salloc(s, &s->summary, 2));
     EI_CUDA_TRY(cudaMallocHost(&s->summary_h, 2 * sizeof(int)));
+    EI_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     // pad lanes of every vector stay 0: start from zeroed memory
     EI_CUDA_TRY(cudaMemset(s->d, 0, V * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->Sr, 0, V * s->ring * sizeof(float4)));
@@ -555,9 +558,10 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     *evals = 1;
     EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     EI_CUDA_TRY(cudaStreamSynchronize(st));
-    const long long max_rounds = (long long)opts->max_iter * (opts->max_trials + 1) + 2;
-    for (long long round = 0; sv->summary_h[0] > 0 && round < max_rounds; ++round) {
-        // ---- direction (gated per slice on mask_dir)
+
+    // one round: direction for the slices that need one, a trial step and its
+    // evaluation for every slice in line search, Armijo, memory update, summary
+    auto round = [&]() -> cudaError_t {
         double *pa = sv->part[0], *pb = sv->part[1];
         k_tl_first<<<NB, T, 0, st>>>(dg, dv, pa);
         for (int i = 0; i < sv->m; ++i) {
@@ -572,7 +576,6 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         k_tl_end<<<NB, T, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
         k_ls_start<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
         k_reset_dir<<<NB, T, 0, st>>>(dg, dv);
-        // ---- trial step for every slice in line search
         k_trial<<<NB, T, 0, st>>>(dg, dv);
         EI_CUDA_TRY(cudaGetLastError());
         EI_CUDA_TRY(evaluate(g, sv->xt, meas, g->S_dev, sv->gt, true, sv->mask_ls, st));
@@ -584,11 +587,46 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         // armijo, accept, update (the evaluation counts its own launches)
         count_launches(g, 2 * sv->m + 5 + 4);
         EI_CUDA_TRY(cudaGetLastError());
-        *evals += 1;
-        EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int),
-                                    cudaMemcpyDeviceToHost, st));
-        EI_CUDA_TRY(cudaStreamSynchronize(st));
+        return cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    };
+
+    // CUDA graph: capture the round once, replay it every round.  While
+    // tracing is on, rounds run eagerly so that every traced launch is timed.
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_per_round = 0;
+    if (opts->use_graph && !g->prof_on) {
+        const int64_t l0 = g->launches;
+        cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        cudaGraph_t graph = nullptr;
+        if (ce == cudaSuccess) {
+            ce = round();
+            const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+            if (ce == cudaSuccess) ce = ee;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        launches_per_round = g->launches - l0;
+        g->launches = l0;
+        if (ce != cudaSuccess) {            // capture not possible here: run the rounds eagerly
+            cudaGetLastError();
+            exec = nullptr;
+        }
     }
+    cudaError_t err = cudaSuccess;
+    const long long max_rounds = (long long)opts->max_iter * (opts->max_trials + 1) + 2;
+    for (long long r = 0; sv->summary_h[0] > 0 && r < max_rounds; ++r) {
+        if (exec) {
+            err = cudaGraphLaunch(exec, st);
+            g->launches += launches_per_round;
+        } else {
+            err = round();
+        }
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) break;
+        *evals += 1;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (err != cudaSuccess) return err;
     k_from_scaled<<<NB, T, 0, st>>>(dg, sv->u, x_dev, sc);
     count_launches(g, 1);
     return cudaGetLastError();
@@ -600,12 +638,21 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
     const auto t0 = std::chrono::steady_clock::now();
     cudaError_t e = ensure_solver(g, opts->lbfgs_m);
     if (e != cudaSuccess) {
+        record_error(e);
         const bool oom = e == cudaErrorMemoryAllocation;
         cudaGetLastError();
         destroy_solver(g);
         return oom ? EI_ERR_ALLOC : EI_ERR_CUDA;
     }
     Solver *sv = g->solver;
+    // the call is synchronous: finish the caller's queued work, then run on the
+    // solver's own stream (a legacy default stream could not be captured)
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        record_error(e);
+        return EI_ERR_CUDA;
+    }
+    st = sv->stream;
     const bool meas_dev = is_device_ptr(s_exp), vol_dev = is_device_ptr(vol_inout);
     const float *meas = s_exp;
     float4 *x = (float4 *)vol_inout;
@@ -633,7 +680,10 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
         e = cudaMemcpyAsync(hs.data(), sv->st, sizeof(SliceState) * g->n_slices,
                             cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    if (e != cudaSuccess) {
+        record_error(e);
+        return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    }
     int first_err = EI_OK;
     for (int s = 0; s < g->n_slices; ++s) {
         int status = hs[s].status;

@@ -61,7 +61,7 @@ class ei_layout(ctypes.Structure):
 
 class ei_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("lbfgs_m", c_int), ("c1", c_double),
-                ("max_trials", c_int), ("curv_eps", c_double)]
+                ("max_trials", c_int), ("curv_eps", c_double), ("use_graph", c_int)]
 
 
 class ei_solve_report(ctypes.Structure):
@@ -81,7 +81,10 @@ class ei_profile(ctypes.Structure):
 EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get_slice_layout",
             "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
             "ei_reconstruct", "ei_default_solve_opts", "ei_status_string", "ei_profile_enable",
-            "ei_profile_read", "ei_objective_grad_noalloc"]
+            "ei_profile_read", "ei_objective_grad_noalloc", "ei_autotune", "ei_set_variant",
+            "ei_get_variant", "ei_last_error"]
+EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 4, 3
 
 _lib = None
 
@@ -124,6 +127,14 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_objective_grad_noalloc.argtypes = [P(ei_geometry_desc), c_void_p, c_void_p, c_void_p,
                                               c_void_p, c_void_p]
     lib.ei_objective_grad_noalloc.restype = c_int
+    lib.ei_autotune.argtypes = [c_void_p, c_int, c_void_p]
+    lib.ei_autotune.restype = c_int
+    lib.ei_set_variant.argtypes = [c_void_p, c_int, c_int, c_int]
+    lib.ei_set_variant.restype = c_int
+    lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
+    lib.ei_get_variant.restype = c_int
+    lib.ei_last_error.argtypes = []
+    lib.ei_last_error.restype = ctypes.c_char_p
     lib.ei_status_string.argtypes = [c_int]
     lib.ei_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -133,7 +144,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
 class EIError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        msg = load_library().ei_status_string(status).decode()
+        lib = load_library()
+        msg = lib.ei_status_string(status).decode()
+        if status in (EI_ERR_CUDA, EI_ERR_ALLOC):
+            msg += " (%s)" % lib.ei_last_error().decode()
         super().__init__("%s failed: %s" % (where, msg))
 
 
@@ -418,7 +432,7 @@ class SolveReport:
 
 
 def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbfgs_m=10,
-                   c1=1e-4, max_trials=20, curv_eps=1e-10, stream=None,
+                   c1=1e-4, max_trials=20, curv_eps=1e-10, use_graph=True, stream=None,
                    raise_on_error: bool = True) -> SolveReport:
     """Batched L-BFGS minimisation of S.  s_exp / vol_inout: CUDA tensors, or
     pinned/pageable CPU tensors (the library stages host arrays)."""
@@ -426,7 +440,7 @@ def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbf
     if s_exp.numel() < geom.meas_count or vol_inout.numel() < 4 * geom.vol_count:
         raise ValueError("s_exp / vol_inout smaller than the layout")
     o = ei_solve_opts(float(tol), int(max_iter), int(lbfgs_m), float(c1), int(max_trials),
-                      float(curv_eps))
+                      float(curv_eps), int(bool(use_graph)))
     S = geom.n_slices
     it = np.zeros(S, np.int32)
     st = np.zeros(S, np.int32)
@@ -504,3 +518,23 @@ def ei_objective_grad_noalloc(n: int, n_theta: int, n_det: int, pitch_cm: float,
     _check(load_library().ei_objective_grad_noalloc(
         ctypes.byref(d), _dptr(vol, "vol", torch.float32), _dptr(s_exp, "s_exp", torch.float32),
         _dptr(S_out, "S_out"), gp, _stream_ptr(stream)), "ei_objective_grad_noalloc")
+
+
+def ei_autotune(geom: Geometry, force: bool = False, write_cache: bool = True, stream=None):
+    """Time the projector/adjoint variants on this geometry, select the fastest
+    (cached on disk); returns (fwd_variant, adj_variant, persistent)."""
+    flags = (EI_TUNE_FORCE if force else 0) | (0 if write_cache else EI_TUNE_NO_CACHE_WRITE)
+    _check(load_library().ei_autotune(geom.handle, flags, _stream_ptr(stream)), "ei_autotune")
+    return ei_get_variant(geom)
+
+
+def ei_set_variant(geom: Geometry, fwd_variant: int, adj_variant: int, persistent: bool) -> None:
+    _check(load_library().ei_set_variant(geom.handle, int(fwd_variant), int(adj_variant),
+                                         int(bool(persistent))), "ei_set_variant")
+
+
+def ei_get_variant(geom: Geometry):
+    f, a, p = c_int(), c_int(), c_int()
+    _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
+                                         ctypes.byref(p)), "ei_get_variant")
+    return f.value, a.value, bool(p.value)
