@@ -386,3 +386,92 @@ def reconstruct(s_exp: np.ndarray, geom: Geometry, x0: Optional[np.ndarray] = No
 
     u, rep = lbfgs(fun, u0, opts)
     return u * scale, rep
+
+
+# --------------------------------------------------------------------------
+# Single-shot retrieval and filtered back-projection (the non-iterative
+# reconstruction of the paper's Eq. 3 + inverse Radon, generalised to three
+# channels through the moments of the IC): the warm-start input.
+# --------------------------------------------------------------------------
+def flat_at_masks(geom: Geometry) -> np.ndarray:
+    """f(t, m_k) of the Gaussian flat IC, [M][n_det]."""
+    m = np.asarray(geom.m, dtype=np.float64)[:, None]
+    return geom.flat_A[None, :] * np.exp(-(m - geom.flat_c[None, :]) ** 2 /
+                                         (2.0 * geom.flat_w[None, :] ** 2))
+
+
+def retrieve_moments(s_exp: np.ndarray, geom: Geometry):
+    """Per pixel, from the zeroth, first and second moments over m of the
+    measured IC and of the flat IC:
+      T     = sum s / sum f                      (transmission, exp(-R[mu]))
+      shift = mean_m(s) - mean_m(f) - m_o - m_r   (IC shift in periods)
+      dv    = max(0, var_m(s) - var_m(f))         (IC broadening)
+    Returns (P_mu = -ln T, shift, P_sigma = dv / kappa), each [n_theta][n_det].
+    With moments over a dense, wide set of m these are exact for the model
+    of ic_model; with a few positions over one period they are estimates."""
+    m = np.asarray(geom.m, dtype=np.float64)[:, None, None]
+    s = np.asarray(s_exp, dtype=np.float64)
+    f = flat_at_masks(geom)[:, None, :]
+    S0, S1, S2 = s.sum(0), (m * s).sum(0), (m * m * s).sum(0)
+    F0, F1, F2 = f.sum(0), (m * f).sum(0), (m * m * f).sum(0)
+    T = S0 / F0
+    cs = S1 / np.where(S0 != 0.0, S0, 1.0)
+    cf = F1 / F0
+    shift = cs - cf
+    if geom.m_o is not None:
+        shift = shift - np.asarray(geom.m_o, dtype=np.float64)[:, None]
+    if geom.m_r is not None:
+        shift = shift - np.asarray(geom.m_r, dtype=np.float64)[None, :]
+    vs = S2 / np.where(S0 != 0.0, S0, 1.0) - cs * cs
+    vf = F2 / F0 - cf * cf
+    dv = np.maximum(vs - vf, 0.0)
+    P_mu = -np.log(np.maximum(T, 1e-6))
+    P_sigma = dv / geom.kappa if geom.kappa > 0 else np.zeros_like(dv)
+    return P_mu, shift, P_sigma
+
+
+def integrate_shift(shift: np.ndarray, geom: Geometry) -> np.ndarray:
+    """R[delta] from its detector derivative: shift = (z/period) dR/dt, so
+    R(t_j) = (period/z) pitch sum_{j' <= j} shift_j' (running sum from the
+    first pixel), then the straight line through 0 before the first pixel and
+    the last running sum is removed, so that R vanishes outside the object at
+    both ends of every row."""
+    cum = np.cumsum(shift, axis=-1) * geom.pitch / geom.z_over_p
+    nd = shift.shape[-1]
+    ramp = (np.arange(nd) + 1.0) / nd
+    return cum - cum[..., -1:] * ramp
+
+
+def ramp_filter(p: np.ndarray, pitch: float) -> np.ndarray:
+    """Ram-Lak filtering along t (Kak & Slaney's spatial kernel for the inverse
+    Radon transform): q_j = pitch sum_k h(j - k) p_k with h(0) = 1/(4 pitch^2),
+    h(d) = -1/(pi^2 d^2 pitch^2) for odd d, 0 for even d != 0, over the row."""
+    p = np.asarray(p, dtype=np.float64)
+    nd = p.shape[-1]
+    d = np.arange(-(nd - 1), nd)
+    h = np.zeros(d.shape)
+    h[d == 0] = 0.25
+    odd = (d % 2) != 0
+    h[odd] = -1.0 / (np.pi ** 2 * d[odd].astype(np.float64) ** 2)
+    h = h / pitch ** 2
+    out = np.empty_like(p)
+    for idx in np.ndindex(*p.shape[:-1]):
+        out[idx] = pitch * np.convolve(p[idx], h, mode="full")[nd - 1:2 * nd - 1]
+    return out
+
+
+def fbp(P: np.ndarray, geom: Geometry) -> np.ndarray:
+    """Filtered back-projection of projections P [c][n_theta][n_det] over
+    180 degrees: x = (pi / n_theta) (1/pitch) R^T (ramp-filtered P), per channel
+    (R^T carries one pitch per angle, hence the 1/pitch)."""
+    scale = np.pi / geom.n_theta / geom.pitch
+    return np.stack([scale * backproject(ramp_filter(P[c], geom.pitch), geom)
+                     for c in range(P.shape[0])])
+
+
+def single_shot(s_exp: np.ndarray, geom: Geometry) -> np.ndarray:
+    """Non-iterative reconstruction [3][n][n] (physical units): moment
+    retrieval of the three projections, integration of the shift, FBP."""
+    P_mu, shift, P_sigma = retrieve_moments(s_exp, geom)
+    P = np.stack([P_mu, integrate_shift(shift, geom), P_sigma])
+    return fbp(P, geom)
