@@ -206,6 +206,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_to_tolerance(G, s_exp, wl, starts, tol, max_iter, warm_fn=None):
+    """Solve every slice to the relative-change tolerance from each start;
+    returns {start: {...}} with wall time (CUDA events around the start's
+    computation and the solve), per-1024^2-slice time and iteration counts."""
+    import torch
+    from paper_2202_08627_gb300 import ei
+    out = {}
+    for start in starts:
+        vol = G.empty("vol")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if start == "single_shot":
+            ei.ei_single_shot_fbp(G, s_exp, vol)
+        elif start == "cnn" and warm_fn is not None:
+            warm_fn(G, s_exp, vol)
+        rep = ei.ei_reconstruct(G, s_exp, vol, tol=tol, max_iter=max_iter, raise_on_error=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        it = rep.iterations
+        out[start] = {"seconds": t, "seconds_per_1024_slice": t / wl.voxel_equiv_1024(),
+                      "iterations_median": float(np.median(it)), "iterations_max": int(it.max()),
+                      "converged": int(rep.converged.sum()), "slices": int(len(it)),
+                      "f_final_sum": float(np.sum(rep.f_final))}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2202_08627_gb300 import build, ei, workloads
@@ -288,6 +316,12 @@ def run_ours(args, rank, world, local_rank):
         if prof["ic_ms"] else None
     clocks = clk.summary(float(peaks.get("sm_max_mhz", 2070.0)))
 
+    # time to tolerance from zero and from the single-shot start (optional)
+    ttt = None
+    if args.ttt:
+        ttt = time_to_tolerance(G, s_exp, wl, ["zero", "single_shot"], args.tol, args.ttt_max_iter)
+        ttt["tol"] = args.tol
+
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
@@ -337,6 +371,8 @@ def run_ours(args, rank, world, local_rank):
                            "persistent": G.variant[2], "solver_round": "CUDA graph"},
         "e2e": e2e,
     }
+    if ttt is not None:
+        line["time_to_tolerance"] = ttt
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         dt, nbytes, cores, desc = cpu_oracle_sample(wl, 1, evals=8)
         line["cpu_baseline"] = {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": cores,
@@ -355,6 +391,10 @@ def main():
     ap.add_argument("--workload", default="uneven1024")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt", action="store_true",
+                    help="also solve every slice to --tol from x0 = 0 and from the single-shot start")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--ttt-max-iter", type=int, default=400)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

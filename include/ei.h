@@ -173,6 +173,19 @@ int ei_backproject(const ei_geometry *g, const float *sino4, float *vol, void *s
  */
 int ei_ic_model(const ei_geometry *g, const float *proj, float *s_mod, void *stream);
 
+/*
+ * Non-iterative (single-shot) reconstruction, the warm-start input of the
+ * iteration: the paper's non-iterative baseline retrieves the projection from
+ * a single mask position (Eq. 3) and inverts it with a filtered
+ * back-projection.  Here, per pixel, the moments over m of s_exp against the
+ * flat IC give R[mu] = -ln(sum s / sum f), the IC shift (centroid difference,
+ * minus m_o and m_r), integrated along t into R[delta] with both row ends
+ * pinned to zero, and R[sigma] = max(0, var s - var f) / kappa; each channel
+ * is Ram-Lak filtered along t and back-projected (pi / n_theta / pitch R^T).
+ * s_exp: device, measurement layout; vol_out: device, vol layout (physical).
+ */
+int ei_single_shot_fbp(const ei_geometry *g, const float *s_exp, float *vol_out, void *stream);
+
 /* s_mod for a physical volume: ei_project followed by ei_ic_model. */
 int ei_forward(const ei_geometry *g, const float *vol, float *s_mod, void *stream);
 
@@ -278,6 +291,37 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
 int ei_autotune(ei_geometry *g, int flags, void *stream);
 int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persistent);
 int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent);
+
+/*
+ * Learned warm start (not in the paper; the task adds it): a U-Net that maps
+ * the single-shot reconstruction (ei_single_shot_fbp, in the solver's scaled
+ * units u = x / scale) to a start near the converged iteration, y = x + net(x).
+ * levels L (1..6), base width 32 or 64 (width of level l: base 2^l); per
+ * encoder level two 3x3 conv + ReLU (2x2 average pooling between levels), per
+ * decoder level a nearest 2x upsample, 3x3 conv + ReLU, 3x3 conv + ReLU over
+ * the concatenation with the skip tensor, 3x3 conv + ReLU; a 1x1 head.  BF16
+ * activations and tensor-core convolutions with FP32 accumulation, FP32
+ * master weights updated by Adam (0.9, 0.999, 1e-8).  height and width must
+ * be multiples of 2^(L-1); every batch is at most the `batch` of creation.
+ * Arrays: x, y, target are device FP32 NHWC [batch][height][width][3].
+ * Parameters (export order): each conv's W [tap][c_in][c_out] then b [c_out]
+ * in creation order (encoder levels 0..L-1: two convs each; decoder levels
+ * L-2..0: up-conv, concat-conv, conv), then head W [base][3], head b [3].
+ */
+typedef struct ei_unet ei_unet;
+int ei_unet_create(int levels, int base, int batch, int height, int width,
+                   unsigned long long seed, ei_unet **out);
+void ei_unet_destroy(ei_unet *net);
+int ei_unet_forward(ei_unet *net, const float *x, float *y, int batch, void *stream);
+/* one Adam step on the MSE loss mean((y - target)^2); *loss (host, may be NULL)
+ * receives the loss before the step (synchronises the stream when non-NULL) */
+int ei_unet_train_step(ei_unet *net, const float *x, const float *target, int batch, double lr,
+                       double *loss, void *stream);
+int64_t ei_unet_num_params(const ei_unet *net);
+/* host arrays of ei_unet_num_params floats (synchronous) */
+int ei_unet_get_params(const ei_unet *net, float *host);
+int ei_unet_set_params(ei_unet *net, const float *host);
+int ei_unet_get_grads(const ei_unet *net, float *host);
 
 /*
  * ei_objective_grad_noalloc — S and its gradient for ONE slice with no device

@@ -486,6 +486,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = cudaMemset(g->gA, 0, (size_t)g->gp_count * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(g->gB, 0, (size_t)g->gp_count * sizeof(float2));
     if (e == cudaSuccess) e = ic_set_smem_limit();
+    if (e == cudaSuccess) e = single_shot_set_smem_limit();
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;
         cudaGetLastError();
@@ -701,6 +702,20 @@ int ei_ic_model(const ei_geometry *gc, const float *proj, float *s_mod, void *st
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     return status_from(traced_ic(g, proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr,
                                  (cudaStream_t)stream));
+}
+
+int ei_single_shot_fbp(const ei_geometry *gc, const float *s_exp, float *vol_out, void *stream)
+{
+    if (!gc || !s_exp || !vol_out || !aligned16(s_exp) || !aligned16(vol_out)) return EI_ERR_ARG;
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    count_launches(g, 1);
+    cudaError_t e = launch_single_shot(g, s_exp, st);
+    if (e == cudaSuccess)
+        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, g->part_adj,
+                               nullptr, st);
+    return status_from(e);
 }
 
 int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stream)

@@ -182,6 +182,10 @@ cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active,
 // IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram.
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
                       double *part, IcMode mode, const int *active, cudaStream_t st);
+// Single-shot retrieval + ramp filter into the packed gradient sinogram
+// (the adjoint then gives the filtered back-projection).
+cudaError_t launch_single_shot(const ei_geometry *g, const float *meas, cudaStream_t st);
+cudaError_t single_shot_set_smem_limit();
 // Packed gradient sinogram from a user sino4 array.
 cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
 // out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial

@@ -1,0 +1,156 @@
+// Non-iterative (single-shot) reconstruction: the warm-start input.
+//
+// The paper's non-iterative baseline retrieves the projection from a single
+// mask position by Eq. 3 and inverts the Radon transform with a filtered
+// back-projection (scikit-image).  With M mask positions and three channels,
+// the retrieval here uses the moments of the measured IC over m against those
+// of the flat IC, per pixel:
+//   T = sum s / sum f               -> R[mu]    = -ln T
+//   shift = mean(s) - mean(f)       -> R[delta] = (period/z) pitch cumsum_t(shift),
+//                                      minus the line that makes both row ends 0
+//   dv = max(0, var(s) - var(f))    -> R[sigma] = dv / kappa
+// then every channel is ramp-filtered along t (the spatial Ram-Lak kernel:
+// 1/(4 pitch^2) at 0, -1/(pi^2 d^2 pitch^2) at odd offsets d) and
+// back-projected with the library's adjoint, scaled by pi / n_theta / pitch.
+//
+// One block per sinogram row; the row lives in shared memory: the moments,
+// a deterministic block scan for the running sum, the filter (a direct
+// convolution over the row, O(n_det^2 / 2) per row), and the packed write-out
+// that the adjoint kernel reads.
+#include "ei_internal.h"
+
+namespace ei {
+
+namespace {
+
+// Inclusive prefix sum of v[0..n) in place, fixed order, accumulated in FP64
+// (chunk per thread: its total, a scan of the totals, then the chunk's running
+// sums from its offset), each result rounded once to FP32.
+__device__ void block_inclusive_scan(float *v, int n, double *tot)
+{
+    const int T = blockDim.x, t = threadIdx.x;
+    const int chunk = (n + T - 1) / T;
+    const int b = t * chunk, e = min(n, b + chunk);
+    double acc = 0.0;
+    for (int i = b; i < e; ++i) acc += (double)v[i];
+    tot[t] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double run = 0.0;
+        for (int i = 0; i < T; ++i) {
+            const double x = tot[i];
+            tot[i] = run;        // exclusive offsets
+            run += x;
+        }
+    }
+    __syncthreads();
+    double run = tot[t];
+    for (int i = b; i < e; ++i) {
+        run += (double)v[i];
+        v[i] = (float)run;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+__global__ void k_single_shot(DevGeom dg, const float *__restrict__ meas, float4 *__restrict__ gA,
+                              float2 *__restrict__ gB)
+{
+    extern __shared__ float sm[];
+    const int row = blockIdx.x;
+    const int s = find_slice(dg.ic_prefix, dg.n_slices, row);
+    const SliceInfo si = dg.slices[s];
+    const int a = row - dg.ic_prefix[s];
+    const int nd = si.n_det, ndp = si.n_dp;
+    const int64_t plane = (int64_t)si.n_theta * ndp;
+    const float *Sx = meas + si.meas_off + (int64_t)a * ndp;
+    const float4 *pix = dg.pix + si.pix_off;
+    const float mo = dg.m_o[si.ang_off + a];
+    const int n_m = dg.mc.n_m;
+    const int mx = dg.max_ndp;
+    float *pm = sm, *pd = sm + mx, *ps = sm + 2 * mx, *w = sm + 3 * mx;
+    double *tot = reinterpret_cast<double *>(sm + 4 * mx);     // blockDim doubles
+
+    // ---- moments of the measured and of the flat IC, per pixel, in FP64 (the
+    // variance difference cancels)
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+        const float4 fl = __ldg(pix + j);            // A, c, w, m_r
+        double S0 = 0.0, S1 = 0.0, S2 = 0.0, F0 = 0.0, F1 = 0.0, F2 = 0.0;
+        for (int k = 0; k < n_m; ++k) {
+            const double mk = dg.mc.m[k];
+            const double sv = __ldg(Sx + (int64_t)k * plane + j);
+            const float dm = (dg.mc.m[k] - fl.y) / fl.z;
+            const double fv = (double)(fl.x * expf(-0.5f * dm * dm));
+            S0 += sv, S1 = fma(mk, sv, S1), S2 = fma(mk * mk, sv, S2);
+            F0 += fv, F1 = fma(mk, fv, F1), F2 = fma(mk * mk, fv, F2);
+        }
+        const double T = S0 / F0;
+        const double cs = S0 != 0.0 ? S1 / S0 : 0.0, cf = F1 / F0;
+        const double vs = S0 != 0.0 ? S2 / S0 - cs * cs : 0.0, vf = F2 / F0 - cf * cf;
+        pm[j] = (float)(-log(fmax(T, 1e-6)));
+        pd[j] = (float)(cs - cf) - mo - fl.w;
+        ps[j] = dg.mc.kappa > 0.f ? (float)(fmax(vs - vf, 0.0) / dg.mc.kappa) : 0.f;
+    }
+    // filter weights 1/(pi^2 d^2) for odd d
+    for (int d = threadIdx.x; d < nd; d += blockDim.x)
+        w[d] = (d & 1) ? 1.f / (9.8696044010893586f * (float)d * (float)d) : 0.f;
+    __syncthreads();
+
+    // ---- R[delta] = (period/z) pitch running sum of the shift, ends pinned to 0
+    block_inclusive_scan(pd, nd, tot);
+    {
+        const float k = si.pitch / dg.mc.z_over_p;
+        const float last = pd[nd - 1];
+        for (int j = threadIdx.x; j < nd; j += blockDim.x)
+            pd[j] = k * (pd[j] - last * (float)(j + 1) / (float)nd);
+    }
+    __syncthreads();
+
+    // ---- ramp filter and FBP scale: q = (pi / n_theta) / pitch^2 (p/4 - sum_odd p(j-d)/(pi^2 d^2)),
+    // written pair-packed for the adjoint (entry of pixel j holds q(j), q(j + 1))
+    const float K = 3.14159265358979f / (float)si.n_theta / (si.pitch * si.pitch);
+    float *qm = reinterpret_cast<float *>(tot + blockDim.x);   // filtered rows (3 x max_ndp)
+    float *qd = qm + mx, *qs = qd + mx;
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+        float am = 0.25f * pm[j], ad = 0.25f * pd[j], as = 0.25f * ps[j];
+        for (int d = 1; d < nd; d += 2) {
+            const float wd = w[d];
+            if (j - d >= 0) am -= wd * pm[j - d], ad -= wd * pd[j - d], as -= wd * ps[j - d];
+            if (j + d < nd) am -= wd * pm[j + d], ad -= wd * pd[j + d], as -= wd * ps[j + d];
+        }
+        qm[j] = K * am, qd[j] = K * ad, qs[j] = K * as;
+    }
+    __syncthreads();
+    const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
+    for (int j = (int)threadIdx.x - 1; j < nd; j += blockDim.x) {
+        float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+        if (j >= 0) lx = qm[j], ly = qd[j], lz = qs[j];
+        if (j + 1 < nd) hx = qm[j + 1], hy = qd[j + 1], hz = qs[j + 1];
+        gA[dst + j] = make_float4(lx, ly, lz, hx);
+        gB[dst + j] = make_float2(hy, hz);
+    }
+}
+
+static const int kSingleShotThreads = 256;
+
+size_t single_shot_smem(const ei_geometry *g)
+{
+    return (size_t)(7 * g->dg.max_ndp + 2 * kSingleShotThreads) * sizeof(float);
+}
+
+cudaError_t single_shot_set_smem_limit()
+{
+    const int bytes = (7 * EI_MAX_NDET + 2 * kSingleShotThreads) * (int)sizeof(float);
+    return cudaFuncSetAttribute(k_single_shot, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_single_shot(const ei_geometry *g, const float *meas, cudaStream_t st)
+{
+    if (g->dg.total_ic == 0) return cudaSuccess;
+    k_single_shot<<<g->dg.total_ic, kSingleShotThreads, single_shot_smem(g), st>>>(g->dg, meas,
+                                                                                  g->gA, g->gB);
+    return cudaGetLastError();
+}
+
+}  // namespace ei

@@ -82,7 +82,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
             "ei_reconstruct", "ei_default_solve_opts", "ei_status_string", "ei_profile_enable",
             "ei_profile_read", "ei_objective_grad_noalloc", "ei_autotune", "ei_set_variant",
-            "ei_get_variant", "ei_last_error"]
+            "ei_get_variant", "ei_last_error", "ei_single_shot_fbp"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 4, 3
 
@@ -109,7 +109,7 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_get_layout.restype = c_int
     lib.ei_get_slice_layout.argtypes = [c_void_p, c_int, P(ei_slice_layout)]
     lib.ei_get_slice_layout.restype = c_int
-    for name in ("ei_project", "ei_backproject", "ei_ic_model", "ei_forward"):
+    for name in ("ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_single_shot_fbp"):
         fn = getattr(lib, name)
         fn.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         fn.restype = c_int
@@ -393,6 +393,16 @@ def ei_forward(geom: Geometry, vol, s_mod, stream=None) -> None:
     _check(load_library().ei_forward(geom.handle, _dptr(vol, "vol", torch.float32),
                                      _dptr(s_mod, "s_mod", torch.float32), _stream_ptr(stream)),
            "ei_forward")
+
+
+def ei_single_shot_fbp(geom: Geometry, s_exp, vol_out, stream=None) -> None:
+    """Non-iterative reconstruction (moment retrieval + filtered back-projection)."""
+    import torch
+    _check_size(s_exp, geom.meas_count, "s_exp")
+    _check_size(vol_out, 4 * geom.vol_count, "vol_out")
+    _check(load_library().ei_single_shot_fbp(geom.handle, _dptr(s_exp, "s_exp", torch.float32),
+                                             _dptr(vol_out, "vol_out", torch.float32),
+                                             _stream_ptr(stream)), "ei_single_shot_fbp")
 
 
 def ei_objective_grad(geom: Geometry, vol, s_exp, S_out, grad=None, stream=None) -> None:
