@@ -82,7 +82,9 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_project", "ei_backproject", "ei_ic_model", "ei_forward", "ei_objective_grad",
             "ei_reconstruct", "ei_default_solve_opts", "ei_status_string", "ei_profile_enable",
             "ei_profile_read", "ei_objective_grad_noalloc", "ei_autotune", "ei_set_variant",
-            "ei_get_variant", "ei_last_error", "ei_single_shot_fbp"]
+            "ei_get_variant", "ei_last_error", "ei_single_shot_fbp", "ei_unet_create",
+            "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
+            "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 4, 3
 
@@ -133,6 +135,21 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_unet_create.argtypes = [c_int, c_int, c_int, c_int, c_int, ctypes.c_ulonglong,
+                                   P(c_void_p)]
+    lib.ei_unet_create.restype = c_int
+    lib.ei_unet_destroy.argtypes = [c_void_p]
+    lib.ei_unet_destroy.restype = None
+    lib.ei_unet_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+    lib.ei_unet_forward.restype = c_int
+    lib.ei_unet_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_double,
+                                       P(c_double), c_void_p]
+    lib.ei_unet_train_step.restype = c_int
+    lib.ei_unet_num_params.argtypes = [c_void_p]
+    lib.ei_unet_num_params.restype = c_int64
+    for name in ("ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads"):
+        getattr(lib, name).argtypes = [c_void_p, c_void_p]
+        getattr(lib, name).restype = c_int
     lib.ei_last_error.argtypes = []
     lib.ei_last_error.restype = ctypes.c_char_p
     lib.ei_status_string.argtypes = [c_int]
@@ -548,3 +565,70 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+class UNet:
+    """The learned warm start's network (see include/ei.h: ei_unet_*).
+    Arrays are FP32 CUDA tensors NHWC [batch][height][width][3]."""
+
+    def __init__(self, levels: int = 4, base: int = 32, batch: int = 16, height: int = 256,
+                 width: int = 256, seed: int = 0):
+        h = c_void_p()
+        _check(load_library().ei_unet_create(int(levels), int(base), int(batch), int(height),
+                                             int(width), int(seed), ctypes.byref(h)),
+               "ei_unet_create")
+        self.handle = h.value
+        self.levels, self.base, self.batch, self.height, self.width = levels, base, batch, height, width
+        self.num_params = int(load_library().ei_unet_num_params(self.handle))
+
+    def close(self):
+        if self.handle:
+            load_library().ei_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_io(self, t, name):
+        import torch
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 4 or t.shape[1:] != (
+                self.height, self.width, 3) or t.shape[0] > self.batch:
+            raise ValueError("%s must be a CUDA float32 tensor [<=%d][%d][%d][3]"
+                             % (name, self.batch, self.height, self.width))
+        return _dptr(t, name)
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(load_library().ei_unet_forward(self.handle, self._check_io(x, "x"),
+                                              self._check_io(y, "y"), int(x.shape[0]),
+                                              _stream_ptr(stream)), "ei_unet_forward")
+        return y
+
+    def train_step(self, x, target, lr: float, stream=None) -> float:
+        loss = c_double()
+        _check(load_library().ei_unet_train_step(self.handle, self._check_io(x, "x"),
+                                                 self._check_io(target, "target"), int(x.shape[0]),
+                                                 float(lr), ctypes.byref(loss), _stream_ptr(stream)),
+               "ei_unet_train_step")
+        return loss.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(load_library().ei_unet_get_params(self.handle, out.ctypes.data), "ei_unet_get_params")
+        return out
+
+    def set_params(self, flat) -> None:
+        arr = np.ascontiguousarray(flat, dtype=np.float32)
+        if arr.size != self.num_params:
+            raise ValueError("expected %d parameters" % self.num_params)
+        _check(load_library().ei_unet_set_params(self.handle, arr.ctypes.data), "ei_unet_set_params")
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(load_library().ei_unet_get_grads(self.handle, out.ctypes.data), "ei_unet_get_grads")
+        return out
