@@ -120,33 +120,12 @@ def _device_uuid():
 
 # ------------------------------------------------------------------ inputs
 def build_problem(wl, rank: int, device):
-    """Geometry + measured ICs on the device (seeded, per rank)."""
-    import torch
-    from paper_2202_08627_gb300 import ei, inputs
+    """Geometry + measured ICs on the device (seeded, per rank), kernel variants tuned."""
+    from paper_2202_08627_gb300 import ei, synth
     seeds = [wl.seed0 + 1000 * rank + s for s in range(wl.n_slices)]
-    fA, fc, fw, th = [], [], [], []
-    for s, (n, nth, nd) in enumerate(wl.slices):
-        A, c, w = inputs.flat_ic(seeds[s], nd)
-        fA.append(A), fc.append(c), fw.append(w), th.append(inputs.angles(nth))
-    G = ei.ei_setup_geometry(
-        n_m=wl.n_m, m=inputs.mask_positions(wl.n_m), z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM,
-        kappa_sigma=inputs.KAPPA, flat_A=np.concatenate(fA), flat_c=np.concatenate(fc),
-        flat_w=np.concatenate(fw), lam=(inputs.LAMBDA,) * 3, scale=inputs.SCALE,
-        per_slice=wl.per_slice(), theta=np.concatenate(th))
-    proj = G.empty("proj", device)
-    for s, (n, nth, nd) in enumerate(wl.slices):
-        sl = G.slices[s]
-        P = inputs.ellipse_line_integrals_torch(inputs.random_ellipses(seeds[s]), th[s], nd,
-                                                inputs.pitch_for(n), device)
-        proj[sl.proj_offset:sl.proj_offset + sl.proj_count].view(3, nth, sl.n_dp)[:, :, :nd] = P
-    clean = G.empty("meas", device)
-    ei.ei_ic_model(G, proj, clean)
-    del proj
+    G, s_exp = synth.build_problem(wl.slices, wl.n_m, seeds, device, wl.seed0 + 1000 * rank)
     # kernel variants for these slice sizes (timed once, then cached on disk)
     G.variant = ei.ei_autotune(G)
-    s_exp = inputs.poisson_noise_torch(clean, seed=wl.seed0 + 1000 * rank)
-    del clean
-    torch.cuda.synchronize()
     return G, s_exp
 
 

@@ -92,3 +92,19 @@ def single1024() -> Workload:
 
 WORKLOADS = {"small": small, "batch256": batch256, "check128": check128,
              "uneven1024": uneven1024, "single1024": single1024}
+
+
+def shard_slices(slices: List[Tuple[int, int, int]], world: int) -> List[List[int]]:
+    """Partition slice indices over `world` ranks, balancing the cost of one
+    evaluation (n^2 n_theta voxel-angles + n_theta n_det pixels): longest
+    first, each to the least-loaded rank (ties to the lower rank).  Slices are
+    independent problems, so the ranks never exchange data while solving."""
+    cost = [(n * n * nth + nth * nd, i) for i, (n, nth, nd) in enumerate(slices)]
+    cost.sort(key=lambda c: (-c[0], c[1]))
+    load = [0] * world
+    parts: List[List[int]] = [[] for _ in range(world)]
+    for c, i in cost:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += c
+    return [sorted(p) for p in parts]
