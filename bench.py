@@ -361,6 +361,35 @@ def run_ours(args, rank, world, local_rank):
     G.close()
 
 
+def run_profile_case(args):
+    """The command the ncu summaries are captured with: `--profile-evals N`
+    objective+gradient evaluations of the workload (variants as `ei_autotune`
+    picks them), after one untimed evaluation, inside a cudaProfilerStart/Stop
+    range (`ncu --profile-from-start off` captures only those).  Prints one
+    line with the objective; reports no performance number."""
+    import torch
+    from paper_2202_08627_gb300 import build, ei, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    wl = workloads.WORKLOADS[args.workload]()
+    device = torch.device("cuda", 0)
+    G, s_exp = build_problem(wl, 0, device)
+    vol = G.empty("vol", device)
+    ei.ei_single_shot_fbp(G, s_exp, vol)
+    grad = G.empty("vol", device)
+    S = torch.empty(G.n_slices, dtype=torch.float64, device=device)
+    ei.ei_objective_grad(G, vol, s_exp, S, grad)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.profile_evals):
+        ei.ei_objective_grad(G, vol, s_exp, S, grad)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_case": wl.name, "evaluations": args.profile_evals,
+                      "variant": list(G.variant), "S_sum": float(S.sum().item())}), flush=True)
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,7 +403,11 @@ def main():
                     help="also solve every slice to --tol from x0 = 0 and from the single-shot start")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--ttt-max-iter", type=int, default=400)
+    ap.add_argument("--profile-evals", type=int, default=0,
+                    help="run this many objective+gradient evaluations for ncu and exit")
     args = ap.parse_args()
+    if args.profile_evals > 0:
+        return run_profile_case(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

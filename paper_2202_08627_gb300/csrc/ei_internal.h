@@ -30,9 +30,12 @@ struct SliceInfo {
 // (mu, delta, sigma) triples; entry e of a packed row holds the triple at
 // e - 1 and the one at e as a float4 (mu0, delta0, sigma0, mu1) plus a float2
 // (delta1, sigma1), so one sample is 24 bytes in two loads.
-//   packed volume copy (projector input): row o, entry e = i + 1 holds voxels
-//     i and i + 1 of that row, i in [-1, n - 1] (zero outside the slice);
-//     xpA/xpB row-major (o = r, i = c), xtA/xtB transposed (o = c, i = r).
+//   packed volume copy (projector input): row o, entry e = i + 1 holds voxel
+//     i of that row and the difference voxel(i + 1) - voxel(i), as
+//     (mu0, delta0, sigma0, mu1 - mu0) + (delta1 - delta0, sigma1 - sigma0),
+//     i in [-1, n - 1] (voxels outside the slice are zero), so a sample is
+//     one FMA per channel; xpA/xpB row-major (o = r, i = c), xtA/xtB
+//     transposed (o = c, i = r).
 //   packed gradient sinogram (adjoint input): row a, entry e holds pixels
 //     j = e - marg and j + 1; pixels outside [0, n_det) are zero, and the
 //     margin covers every pixel a voxel of the slice can project to.

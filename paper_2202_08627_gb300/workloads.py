@@ -12,7 +12,10 @@ to the phantom's exact line integrals, plus Poisson noise at 1e4 counts.
                angles, detector pixels drawn per slice from {1024, 1152, 1280,
                1408, 1536}, M = 7 (about 16.5 GB of measured ICs)
   single1024   one 1024x1024 slice of that shape (1800 angles, 1536 pixels,
-               M = 7): the case the kernel profiles are captured on
+               M = 7)
+  batch8x1024  eight such slices: the case the kernel profiles are captured on
+               (134 MB volume, 620 MB of measured ICs: larger than L2, a few GB
+               on the device in all)
 """
 from __future__ import annotations
 
@@ -90,8 +93,13 @@ def single1024() -> Workload:
                     [(1024, 1800, 1536)], 7)
 
 
+def batch8x1024() -> Workload:
+    return Workload("batch8x1024", "8 slices of 1024x1024, 1800 angles, 1536 pixels, M=7",
+                    [(1024, 1800, 1536)] * 8, 7)
+
+
 WORKLOADS = {"small": small, "batch256": batch256, "check128": check128,
-             "uneven1024": uneven1024, "single1024": single1024}
+             "uneven1024": uneven1024, "single1024": single1024, "batch8x1024": batch8x1024}
 
 
 def shard_slices(slices: List[Tuple[int, int, int]], world: int) -> List[List[int]]:
