@@ -156,6 +156,37 @@ def cpu_oracle_sample(wl, angle_fraction: int, evals: int = 1):
     return dt, nbytes, oracle.num_threads(), desc
 
 
+def train_warm_start(args, wl, device):
+    """The learned warm start for this workload's slice shapes: --cnn-weights
+    if given, else trained here on --cnn-pairs pairs (seeds offset by 10^6 from
+    the benchmark's slices; shapes drawn like the workload's with another seed)
+    that the plain method generates.  Returns (network, training summary)."""
+    import torch
+    from paper_2202_08627_gb300 import warmstart
+    net = warmstart.WarmStartNet(levels=4, base=32, crop=256, batch=16)
+    if args.cnn_weights:
+        net.load(args.cnn_weights)
+        return net, {"weights": args.cnn_weights}
+    shapes = [wl.slices[i % wl.n_slices] for i in range(args.cnn_pairs)]
+    if wl.name == "uneven1024":
+        shapes = warmstart.shapes_for("uneven1024", args.cnn_pairs, 6)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pairs, it = warmstart.generate_pairs(shapes, wl.seed0 + 1_000_000, wl.n_m,
+                                         max_chunk_voxels=32 * 1024 * 1024, tol=args.tol,
+                                         max_iter=args.ttt_max_iter, device=device)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = warmstart.train(net, pairs, args.cnn_epochs, 1e-3, lr_final=5e-5, steps_per_epoch=256)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del pairs
+    return net, {"pairs": len(shapes), "pair_generation_s": t1 - t0, "training_s": t2 - t1,
+                 "epochs": args.cnn_epochs, "steps_per_epoch": 256, "batch": 16, "crop": 256,
+                 "pair_iterations_mean": float(it.mean()), "loss_first": hist[0],
+                 "loss_last": hist[-1]}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -183,34 +214,6 @@ def run_reference(args, rank, world):
         "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-def time_to_tolerance(G, s_exp, wl, starts, tol, max_iter, warm_fn=None):
-    """Solve every slice to the relative-change tolerance from each start;
-    returns {start: {...}} with wall time (CUDA events around the start's
-    computation and the solve), per-1024^2-slice time and iteration counts."""
-    import torch
-    from paper_2202_08627_gb300 import ei
-    out = {}
-    for start in starts:
-        vol = G.empty("vol")
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        if start == "single_shot":
-            ei.ei_single_shot_fbp(G, s_exp, vol)
-        elif start == "cnn" and warm_fn is not None:
-            warm_fn(G, s_exp, vol)
-        rep = ei.ei_reconstruct(G, s_exp, vol, tol=tol, max_iter=max_iter, raise_on_error=False)
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) * 1e-3
-        it = rep.iterations
-        out[start] = {"seconds": t, "seconds_per_1024_slice": t / wl.voxel_equiv_1024(),
-                      "iterations_median": float(np.median(it)), "iterations_max": int(it.max()),
-                      "converged": int(rep.converged.sum()), "slices": int(len(it)),
-                      "f_final_sum": float(np.sum(rep.f_final))}
-    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -298,8 +301,17 @@ def run_ours(args, rank, world, local_rank):
     # time to tolerance from zero and from the single-shot start (optional)
     ttt = None
     if args.ttt:
-        ttt = time_to_tolerance(G, s_exp, wl, ["zero", "single_shot"], args.tol, args.ttt_max_iter)
+        from paper_2202_08627_gb300 import warmstart
+        starts, net, training = ["zero", "single_shot"], None, None
+        if args.cnn:
+            net, training = train_warm_start(args, wl, device)
+            starts.append("cnn")
+        ttt = warmstart.time_to_tolerance(G, s_exp, starts, args.tol, args.ttt_max_iter, net)
         ttt["tol"] = args.tol
+        if training:
+            ttt["cnn_training"] = training
+        if net is not None:
+            net.close()
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -403,6 +415,11 @@ def main():
                     help="also solve every slice to --tol from x0 = 0 and from the single-shot start")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--ttt-max-iter", type=int, default=400)
+    ap.add_argument("--cnn", action="store_true",
+                    help="with --ttt: also solve from the learned warm start (trained first)")
+    ap.add_argument("--cnn-pairs", type=int, default=256)
+    ap.add_argument("--cnn-epochs", type=int, default=20)
+    ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="run this many objective+gradient evaluations for ncu and exit")
     args = ap.parse_args()

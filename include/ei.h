@@ -293,6 +293,24 @@ int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persist
 int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent);
 
 /*
+ * IC kernel variant (the fused Eq. 2 model, Eq. 5 residual and gradient).
+ *   0: one block per sinogram row; any row width and M.
+ *   1: persistent blocks (as many as fit on the GPU) that stream rows through
+ *      two shared-memory buffers filled by bulk asynchronous copies, so the
+ *      reads of the next row overlap the arithmetic of the current one.  Needs
+ *      (2 (3 + M) + 3) * 4 * max n_dp bytes of shared memory <= 220 KB
+ *      (e.g. rows up to 1536 pixels with M = 7); EI_ERR_ARG otherwise.
+ * ei_setup_geometry selects 1 when it fits, else 0.  The two agree to FP32
+ * rounding (variant 1 evaluates the exponential as 2^(log2(e) x) with the
+ * PTX ex2 instruction).  Variant 1's waits for its copies are bounded (2 s);
+ * a wait that runs out poisons the affected slices' objectives with NaN and
+ * sets a device status word, which the synchronous calls (ei_objective_grad
+ * with a host S_out, ei_reconstruct) return as EI_ERR_TIMEOUT.
+ */
+int ei_set_ic_variant(ei_geometry *g, int variant);
+int ei_get_ic_variant(const ei_geometry *g, int *variant);
+
+/*
  * Learned warm start (not in the paper; the task adds it): a U-Net that maps
  * the single-shot reconstruction (ei_single_shot_fbp, in the solver's scaled
  * units u = x / scale) to a start near the converged iteration, y = x + net(x).

@@ -1,6 +1,7 @@
 // C ABI of libei.so (declared in include/ei.h): geometry set-up, layouts and
 // the stream-ordered entry points.  All compute runs in the CUDA kernels of
 // this library; there is no CPU fallback.
+#include <cstdarg>
 #include <math.h>
 #include <string.h>
 
@@ -55,6 +56,28 @@ static thread_local char g_last_error[256] = "";
 void record_error(cudaError_t e)
 {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static void record_message(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+}
+
+// Read and clear the device-side status word that kernels with bounded waits
+// set; synchronises `st`.
+static int take_device_status(ei_geometry *g, cudaStream_t st)
+{
+    int h = 0;
+    if (cudaMemcpyAsync(&h, g->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EI_ERR_CUDA;
+    if (h == 0) return EI_OK;
+    cudaMemsetAsync(g->dev_status, 0, sizeof(int), st);
+    record_message("a kernel's bounded wait for its input rows ran out (status %d)", h);
+    return h;
 }
 
 void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent)
@@ -482,6 +505,8 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = dev_alloc(g, &g->work_counter, 2);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->dev_status, 1);
+    if (e == cudaSuccess) e = cudaMemset(g->dev_status, 0, sizeof(int));
     // the packed gradient sinogram's margins and padding pixels must read as zero
     if (e == cudaSuccess) e = cudaMemset(g->gA, 0, (size_t)g->gp_count * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(g->gB, 0, (size_t)g->gp_count * sizeof(float2));
@@ -501,7 +526,27 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     dg.prep_prefix = d_prep;
     dg.vec_prefix = d_vec;
     select_variants(g, 0, 0, false);
+    g->ic_variant = ic_pipe_fits(dg.max_ndp, dg.mc.n_m) ? 1 : 0;
     *out = g;
+    return EI_OK;
+}
+
+int ei_set_ic_variant(ei_geometry *g, int variant)
+{
+    if (!g || variant < 0 || variant > 1) return EI_ERR_ARG;
+    if (variant == 1 && !ic_pipe_fits(g->dg.max_ndp, g->dg.mc.n_m)) {
+        record_message("ei_set_ic_variant: rows of %d pixels with M = %d do not fit the "
+                     "bulk-copy variant's shared-memory buffers", g->dg.max_ndp, g->dg.mc.n_m);
+        return EI_ERR_ARG;
+    }
+    g->ic_variant = variant;
+    return EI_OK;
+}
+
+int ei_get_ic_variant(const ei_geometry *g, int *variant)
+{
+    if (!g || !variant) return EI_ERR_ARG;
+    *variant = g->ic_variant;
     return EI_OK;
 }
 
@@ -748,9 +793,10 @@ int ei_objective_grad(const ei_geometry *gc, const float *vol, const float *s_ex
         attr.type = cudaMemoryTypeUnregistered;
     }
     e = cudaMemcpyAsync(S_out, g->S_dev, sizeof(double) * g->n_slices, cudaMemcpyDefault, st);
-    if (e == cudaSuccess && attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
-        e = cudaStreamSynchronize(st);
-    return status_from(e);
+    if (e != cudaSuccess) return status_from(e);
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return take_device_status(g, st);        // synchronous call: report device errors too
+    return EI_OK;
 }
 
 int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
@@ -763,8 +809,10 @@ int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
     if (!(o.tol >= 0) || o.max_iter < 0 || o.lbfgs_m < 1 || o.lbfgs_m > 32 || !(o.c1 > 0) ||
         o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0))
         return EI_ERR_ARG;
-    return ei::reconstruct(const_cast<ei_geometry *>(gc), s_exp, vol_inout, &o, report,
-                           (cudaStream_t)stream);
+    ei_geometry *g = const_cast<ei_geometry *>(gc);
+    const int r = ei::reconstruct(g, s_exp, vol_inout, &o, report, (cudaStream_t)stream);
+    const int d = take_device_status(g, (cudaStream_t)stream);
+    return r != EI_OK ? r : d;
 }
 
 }  // extern "C"

@@ -154,6 +154,8 @@ struct ei_geometry {
     const int *adj_prefixes[ei::N_ADJ_VARIANTS] = {};
     int adj_totals[ei::N_ADJ_VARIANTS] = {};
     bool persistent = false;
+    int ic_variant = 0;                // 0: one block per row; 1: persistent, bulk-copy pipeline
+    int *dev_status = nullptr;         // [1] device-side error status (bounded waits)
     int num_sms = 0;
     int *work_counter = nullptr;       // [2] work counters of the persistent kernels
     // work per slice, for the autotuner's cache key
@@ -185,6 +187,8 @@ cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active,
 // IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram.
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
                       double *part, IcMode mode, const int *active, cudaStream_t st);
+// Whether the bulk-copy IC variant's two row buffers fit in shared memory.
+bool ic_pipe_fits(int max_ndp, int n_m);
 // Single-shot retrieval + ramp filter into the packed gradient sinogram
 // (the adjoint then gives the filtered back-projection).
 cudaError_t launch_single_shot(const ei_geometry *g, const float *meas, cudaStream_t st);

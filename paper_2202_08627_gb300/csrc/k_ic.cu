@@ -1,7 +1,9 @@
 // Illumination-curve (IC) model, residual and per-pixel gradient, fused
 // (Eq. 2 with the Eq. 4 offsets, the cost of Eq. 5 and its analytic gradient).
 //
-// One block per sinogram row (slice, angle).  Per pixel t of the row:
+// Work unit: one sinogram row (slice, angle); variant 0 runs one block per
+// row, variant 1 (below) persistent blocks that stream rows through shared
+// memory with bulk asynchronous copies.  Per pixel t of the row:
 //   shift = (z/period) D R[delta] + m_o(theta) + m_r(t)      (D: finite difference)
 //   V     = w^2 + kappa R[sigma]
 //   s_m   = A (w / sqrt(V)) exp(-R[mu] - (m - c - shift)^2 / (2 V))   for every m
@@ -16,6 +18,7 @@
 // Memory traffic per pixel (M = n_m): 12 B of projections + 4M B of s_exp
 // read, 24 B of packed g written; the per-pixel flat IC table is shared by all angles
 // and stays in L2.  The kernel is HBM-bound.
+#include "async_copy.h"
 #include "ei_internal.h"
 
 namespace ei {
@@ -197,13 +200,262 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
     if (threadIdx.x == 0) part[row] = bad ? __longlong_as_double(0x7ff0000000000000LL) : tot;
 }
 
+// ---------------------------------------------------------------------------
+// Variant 1: persistent blocks, rows staged by bulk asynchronous copies.
+//
+// Each block walks the rows blockIdx.x, blockIdx.x + gridDim.x, ... and keeps
+// two row buffers in shared memory: while it computes row r from one buffer,
+// the bulk copies of its next row (three projection rows and M measured rows,
+// one copy each) land in the other, so every SM keeps tens of KB of reads in
+// flight independently of its register budget.  The arithmetic per pixel is
+// the same as variant 0's, with the exponential taken as 2^(log2(e) x) by the
+// PTX ex2 instruction on a pre-scaled argument and the factor 2 of the
+// residual applied once per pixel; results agree with variant 0 to FP32
+// rounding.
+// ---------------------------------------------------------------------------
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr uint64_t kIcWaitNs = 2000000000ull;     // 2 s bound on one row's copies
+
+__device__ __forceinline__ int ic_next_row(const DevGeom &dg, const int *active, int r, int step)
+{
+    if (active)
+        while (r < dg.total_ic && !__ldg(active + find_slice(dg.ic_prefix, dg.n_slices, r))) r += step;
+    return r;
+}
+
+// Thread 0: arm `bar` and issue the copies of row r into the buffer `stage`
+// (slots of mx floats: P_mu, P_delta, P_sigma, then the M measured rows).
+__device__ __forceinline__ void ic_issue_row(const DevGeom &dg, int r, const float *proj,
+                                             const float *meas, float *stage, int mx, int n_in,
+                                             unsigned bar)
+{
+    const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
+    const SliceInfo &si = dg.slices[s];
+    const int a = r - dg.ic_prefix[s];
+    const unsigned bytes = (unsigned)si.n_dp * 4u;
+    const int64_t plane = (int64_t)si.n_theta * si.n_dp;
+    const int64_t rbase = (int64_t)a * si.n_dp;
+    mbar_arrive_expect_tx(bar, bytes * (unsigned)n_in);
+    for (int c = 0; c < 3; ++c)
+        bulk_copy_g2s(stage + c * mx, proj + si.proj_off + c * plane + rbase, bytes, bar);
+    for (int k = 0; k < n_in - 3; ++k)
+        bulk_copy_g2s(stage + (3 + k) * mx, meas + si.meas_off + k * plane + rbase, bytes, bar);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512)
+k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
+          float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
+          double *__restrict__ part, const int *__restrict__ active, int *__restrict__ status)
+{
+    extern __shared__ float4 sm4[];
+    __shared__ uint64_t bars[2];
+    __shared__ double red[32];
+    const int mx = dg.max_ndp;
+    const int n_m = dg.mc.n_m;
+    const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
+    float *const buf0 = reinterpret_cast<float *>(sm4);
+    float *const buf1 = buf0 + n_in * mx;
+    float *const g_sh = buf0 + 2 * n_in * mx;        // G_shift, G_mu, G_V of the row
+    float *const g_mu = g_sh + mx;
+    float *const g_v = g_mu + mx;
+    const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const int step = gridDim.x;
+    const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
+    int r = ic_next_row(dg, active, blockIdx.x, step);
+    if (threadIdx.x == 0 && r < dg.total_ic) ic_issue_row(dg, r, proj, meas, buf0, mx, n_in, bar0);
+    for (unsigned it = 0; r < dg.total_ic; ++it) {
+        const bool odd = it & 1u;
+        float *const stg = odd ? buf1 : buf0;
+        const int rn = ic_next_row(dg, active, r + step, step);
+        // the other buffer was released by the barrier that ended the previous row
+        if (threadIdx.x == 0 && rn < dg.total_ic)
+            ic_issue_row(dg, rn, proj, meas, odd ? buf0 : buf1, mx, n_in, odd ? bar0 : bar1);
+        const bool landed = mbar_wait_bounded(odd ? bar1 : bar0, (it >> 1) & 1u, kIcWaitNs);
+        if (__syncthreads_or(!landed)) {
+            // the row never arrived: report it, poison this block's remaining
+            // rows, and give the copy of the next row a bounded chance to land
+            // before the block's shared memory is released
+            if (threadIdx.x == 0) {
+                atomicExch(status, (int)EI_ERR_TIMEOUT);
+                if (MODE != IC_MODEL)
+                    for (int q = r; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
+                        part[q] = __longlong_as_double(0x7ff8000000000000LL);
+                if (rn < dg.total_ic)
+                    mbar_wait_bounded(odd ? bar0 : bar1, ((it + 1) >> 1) & 1u, kIcWaitNs);
+            }
+            return;
+        }
+
+        const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
+        const SliceInfo si = dg.slices[s];
+        const int a = r - dg.ic_prefix[s];
+        const int nd = si.n_det, ng = si.n_dp >> 2;
+        const int64_t plane4 = ((int64_t)si.n_theta * si.n_dp) >> 2;
+        const float *Pd = stg + mx;
+        const float4 *Pm4 = reinterpret_cast<const float4 *>(stg);
+        const float4 *Ps4 = reinterpret_cast<const float4 *>(stg + 2 * mx);
+        const float4 *pix = dg.pix + si.pix_off;
+        const float mo = dg.m_o[si.ang_off + a];
+
+        double e2 = 0.0;
+        bool out_of_domain = false;
+        for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+            const float4 pm4 = Pm4[gi], ps4 = Ps4[gi];
+            const float pmv[4] = {pm4.x, pm4.y, pm4.z, pm4.w};
+            const float psv[4] = {ps4.x, ps4.y, ps4.z, ps4.w};
+            float cs[4], iV[4], amp[4], a2[4], b2[4];
+            bool ok[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * gi + q;
+                ok[q] = j < nd;
+                const float4 fl = ok[q] ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
+                const float shift = ok[q] ? zp * deriv_at(Pd, j, nd, si.inv_pitch) + mo + fl.w : 0.f;
+                cs[q] = fl.y + shift;
+                const float V = fmaf(kappa, psv[q], fl.z * fl.z);
+                if (ok[q] && !(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
+                const float Vs = fmaxf(V, 1e-30f);
+                iV[q] = 1.0f / Vs;
+                amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
+                a2[q] = -kLog2e * pmv[q];
+                b2[q] = (0.5f * kLog2e) * iV[q];
+            }
+            float st[4] = {0.f, 0.f, 0.f, 0.f}, stq[4] = {0.f, 0.f, 0.f, 0.f},
+                  stq2[4] = {0.f, 0.f, 0.f, 0.f};
+            float e2f = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < n_m; ++k) {
+                const float mk = dg.mc.m[k];
+                float sv[4], qd[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    qd[q] = mk - cs[q];
+                    sv[q] = amp[q] * ex2_approx(fmaf(-b2[q], qd[q] * qd[q], a2[q]));
+                }
+                if (MODE == IC_MODEL) {
+                    reinterpret_cast<float4 *>(s_mod + si.meas_off)[k * plane4 + (int64_t)a * ng + gi] =
+                        make_float4(sv[0], sv[1], sv[2], sv[3]);
+                } else {
+                    const float4 x4 = reinterpret_cast<const float4 *>(stg + (3 + k) * mx)[gi];
+                    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float e = ok[q] ? sv[q] - xv[q] : 0.f;
+                        e2f = fmaf(e, e, e2f);
+                        if (MODE == IC_OBJECTIVE_GRAD) {
+                            const float t = e * sv[q];          // half of d(e^2)/d(s)
+                            const float tq = t * qd[q];
+                            st[q] += t;
+                            stq[q] += tq;
+                            stq2[q] = fmaf(tq, qd[q], stq2[q]);
+                        }
+                    }
+                }
+            }
+            if (MODE != IC_MODEL) e2 += (double)e2f;
+            if (MODE == IC_OBJECTIVE_GRAD) {
+                float gsh[4], gvv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    gsh[q] = 2.f * stq[q] * iV[q];
+                    gvv[q] = kappa * iV[q] * (stq2[q] * iV[q] - st[q]);
+                }
+                reinterpret_cast<float4 *>(g_sh)[gi] = make_float4(gsh[0], gsh[1], gsh[2], gsh[3]);
+                reinterpret_cast<float4 *>(g_mu)[gi] =
+                    make_float4(-2.f * st[0], -2.f * st[1], -2.f * st[2], -2.f * st[3]);
+                reinterpret_cast<float4 *>(g_v)[gi] = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
+            }
+        }
+        if (MODE == IC_OBJECTIVE_GRAD) {
+            // g_delta = (z/period) D^T G_shift into the P_delta slot (its last
+            // reader finished at this barrier), then the packed row
+            __syncthreads();
+            float *gdl = stg + mx;
+            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+                float gd[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * gi + q;
+                    gd[q] = j < nd ? zp * deriv_T_at(g_sh, j, nd, si.inv_pitch) : 0.f;
+                }
+                reinterpret_cast<float4 *>(gdl)[gi] = make_float4(gd[0], gd[1], gd[2], gd[3]);
+            }
+            __syncthreads();
+            const int ndp = si.n_dp;
+            const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
+            for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
+                const bool nx = j + 1 < ndp;
+                gA[dst + j] = make_float4(g_mu[j], gdl[j], g_v[j], nx ? g_mu[j + 1] : 0.f);
+                gB[dst + j] = make_float2(nx ? gdl[j + 1] : 0.f, nx ? g_v[j + 1] : 0.f);
+            }
+            if (threadIdx.x == 0) {                     // entry of pixel -1: (0, g(0))
+                gA[dst - 1] = make_float4(0.f, 0.f, 0.f, g_mu[0]);
+                gB[dst - 1] = make_float2(gdl[0], g_v[0]);
+            }
+        }
+        if (MODE != IC_MODEL) {
+            const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
+            const double tot = block_sum_double(e2, red);
+            if (threadIdx.x == 0) part[r] = bad ? __longlong_as_double(0x7ff0000000000000LL) : tot;
+        }
+        __syncthreads();            // this row's buffer and gradient rows are free again
+        r = rn;
+    }
+}
+
+static const int kIcPipeSmemLimit = 220 * 1024;
+
+static int ic_threads(const ei_geometry *g)
+{
+    // one thread per 4 pixels of the widest row, at most 512 (then threads loop)
+    int threads = (g->dg.max_ndp / 4 + 31) / 32 * 32;
+    return threads > 512 ? 512 : threads;
+}
+
+size_t ic_pipe_smem(int max_ndp, int n_m, IcMode mode)
+{
+    const int n_in = mode == IC_MODEL ? 3 : 3 + n_m;
+    return (size_t)(2 * n_in + 3) * max_ndp * sizeof(float);
+}
+
+bool ic_pipe_fits(int max_ndp, int n_m)
+{
+    return ic_pipe_smem(max_ndp, n_m, IC_OBJECTIVE_GRAD) <= (size_t)kIcPipeSmemLimit;
+}
+
+template <int MODE>
+static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
+                                  float *s_mod, double *part, const int *active, cudaStream_t st)
+{
+    const int threads = ic_threads(g);
+    const size_t smem = ic_pipe_smem(g->dg.max_ndp, g->dg.mc.n_m, (IcMode)MODE);
+    int per_sm = 0;
+    EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ic_pipe<MODE>, threads, smem));
+    const int grid = std::max(1, std::min(g->dg.total_ic, std::max(1, per_sm) * g->num_sms));
+    k_ic_pipe<MODE><<<grid, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA, g->gB, part,
+                                                 active, g->dev_status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
                       double *part, IcMode mode, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
-    // one thread per 4 pixels of the widest row, at most 512 (then threads loop)
-    int threads = (g->dg.max_ndp / 4 + 31) / 32 * 32;
-    if (threads > 512) threads = 512;
+    if (g->ic_variant == 1) {
+        switch (mode) {
+        case IC_MODEL: return launch_ic_pipe<IC_MODEL>(g, proj, meas, s_mod, part, active, st);
+        case IC_OBJECTIVE: return launch_ic_pipe<IC_OBJECTIVE>(g, proj, meas, s_mod, part, active, st);
+        default: return launch_ic_pipe<IC_OBJECTIVE_GRAD>(g, proj, meas, s_mod, part, active, st);
+        }
+    }
+    const int threads = ic_threads(g);
     const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
     switch (mode) {
     case IC_MODEL:
@@ -228,6 +480,12 @@ cudaError_t ic_set_smem_limit()
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kIcPipeSmemLimit));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_OBJECTIVE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kIcPipeSmemLimit));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_OBJECTIVE_GRAD>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kIcPipeSmemLimit));
     return cudaSuccess;
 }
 

@@ -84,7 +84,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_profile_read", "ei_objective_grad_noalloc", "ei_autotune", "ei_set_variant",
             "ei_get_variant", "ei_last_error", "ei_single_shot_fbp", "ei_unet_create",
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
-            "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads"]
+            "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
+            "ei_get_ic_variant"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 4, 3
 
@@ -135,6 +136,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_set_ic_variant.argtypes = [c_void_p, c_int]
+    lib.ei_set_ic_variant.restype = c_int
+    lib.ei_get_ic_variant.argtypes = [c_void_p, P(c_int)]
+    lib.ei_get_ic_variant.restype = c_int
     lib.ei_unet_create.argtypes = [c_int, c_int, c_int, c_int, c_int, ctypes.c_ulonglong,
                                    P(c_void_p)]
     lib.ei_unet_create.restype = c_int
@@ -565,6 +570,17 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+def ei_set_ic_variant(geom: Geometry, variant: int) -> None:
+    """IC kernel variant: 0 one block per row, 1 persistent bulk-copy pipeline."""
+    _check(load_library().ei_set_ic_variant(geom.handle, int(variant)), "ei_set_ic_variant")
+
+
+def ei_get_ic_variant(geom: Geometry) -> int:
+    v = c_int()
+    _check(load_library().ei_get_ic_variant(geom.handle, ctypes.byref(v)), "ei_get_ic_variant")
+    return v.value
 
 
 class UNet:
