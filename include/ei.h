@@ -270,8 +270,10 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
 /*
  * Kernel variants and autotuning (batched, serving-style launches).
  * The projector and the adjoint each come in several tile shapes
- * (projector: 16x16, 32x8, 32x16 rays x angles with a 4-sample unroll, and
- * 16x16 with a 2-sample unroll; adjoint: 8, 4 or 16 voxels per thread), and
+ * (projector, rays x angles per block / per warp and samples per loop
+ * iteration: 0 16x16/8x4/4, 1 32x8/8x4/4, 2 32x16/8x4/4, 3 16x16/8x4/2,
+ * 4 32x8/32x1/4, 5 16x16/16x2/4, 6 32x16/32x1/4; adjoint: 8, 4 or 16 voxels
+ * per thread), and
  * either as one block per work item or as a persistent GPU-sized grid whose
  * blocks take work items from a counter.  Projector variants compute every
  * ray identically (bit-identical projections); adjoint variants sum every
@@ -284,7 +286,7 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * cached in a text file (EI_TUNE_CACHE, default ~/.cache/ei_gb300_autotune.txt)
  * keyed by the GPU name and the slice sizes, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..3, adjoint 0..2).
+ * report a variant explicitly (ids: projector 0..6, adjoint 0..2).
  */
 #define EI_TUNE_FORCE 1
 #define EI_TUNE_NO_CACHE_WRITE 2
@@ -293,13 +295,31 @@ int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persist
 int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent);
 
 /*
+ * On-chip throughput of the current GPU, measured by microbenchmarks (each the
+ * best of three CUDA-event-timed runs after a warm-up; ~10 ms in all): the
+ * FP32 FMA rate (2 flops per FMA), the rate at which 16-byte global loads that
+ * hit L1 deliver bytes to registers, and the same for shared-memory loads.
+ * They are the denominators of the rooflines of kernels bound on chip rather
+ * than by HBM.  The paper has no counterpart.  Synchronises `stream`;
+ * allocates and frees 8 KB of device memory.
+ */
+typedef struct {
+    double fp32_tflops;
+    double l1_load_tbs;      /* TB/s, all SMs */
+    double smem_load_tbs;    /* TB/s, all SMs */
+    int num_sms;
+} ei_peaks;
+int ei_measure_peaks(ei_peaks *out, void *stream);
+
+/*
  * IC kernel variant (the fused Eq. 2 model, Eq. 5 residual and gradient).
  *   0: one block per sinogram row; any row width and M.
  *   1: persistent blocks (as many as fit on the GPU) that stream rows through
- *      two shared-memory buffers filled by bulk asynchronous copies, so the
- *      reads of the next row overlap the arithmetic of the current one.  Needs
- *      (2 (3 + M) + 3) * 4 * max n_dp bytes of shared memory <= 220 KB
- *      (e.g. rows up to 1536 pixels with M = 7); EI_ERR_ARG otherwise.
+ *      NST shared-memory buffers filled by bulk asynchronous copies, so the
+ *      reads of the next NST - 1 rows overlap the arithmetic of the current
+ *      one.  NST = 3 when (3 (3 + M) + 3) * 4 * max n_dp bytes <= 220 KB (rows
+ *      up to 1536 pixels with M = 7), else 2 when (2 (3 + M) + 3) * 4 * max n_dp
+ *      bytes fit; EI_ERR_ARG otherwise.
  * ei_setup_geometry selects 1 when it fits, else 0.  The two agree to FP32
  * rounding (variant 1 evaluates the exponential as 2^(log2(e) x) with the
  * PTX ex2 instruction).  Variant 1's waits for its copies are bounded (2 s);

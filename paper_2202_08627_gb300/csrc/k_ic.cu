@@ -204,17 +204,20 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
 // Variant 1: persistent blocks, rows staged by bulk asynchronous copies.
 //
 // Each block walks the rows blockIdx.x, blockIdx.x + gridDim.x, ... and keeps
-// two row buffers in shared memory: while it computes row r from one buffer,
-// the bulk copies of its next row (three projection rows and M measured rows,
-// one copy each) land in the other, so every SM keeps tens of KB of reads in
-// flight independently of its register budget.  The arithmetic per pixel is
-// the same as variant 0's, with the exponential taken as 2^(log2(e) x) by the
-// PTX ex2 instruction on a pre-scaled argument and the factor 2 of the
-// residual applied once per pixel; results agree with variant 0 to FP32
-// rounding.
+// NST (3, else 2) row buffers in shared memory: while it computes row r, the
+// bulk copies of its next NST - 1 rows (three projection rows and M measured
+// rows, one copy each) are in flight, so every SM keeps up to ~120 KB of reads
+// outstanding independently of its register budget.  Two pixels per thread;
+// per row two block barriers (before D^T, which reads neighbours' G_shift,
+// and the objective reduction, which also releases the row's buffer).  The
+// arithmetic per pixel is variant 0's, with the exponential taken as
+// 2^(log2(e) x) by the PTX ex2 instruction on a pre-scaled argument and the
+// factor 2 of the residual applied once per pixel; results agree with
+// variant 0 to FP32 rounding.
 // ---------------------------------------------------------------------------
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint64_t kIcWaitNs = 2000000000ull;     // 2 s bound on one row's copies
+constexpr int kIcPipeMaxStages = 3;
 
 __device__ __forceinline__ int ic_next_row(const DevGeom &dg, const int *active, int r, int step)
 {
@@ -243,110 +246,106 @@ __device__ __forceinline__ void ic_issue_row(const DevGeom &dg, int r, const flo
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
           float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
-          double *__restrict__ part, const int *__restrict__ active, int *__restrict__ status)
+          double *__restrict__ part, const int *__restrict__ active, int *__restrict__ status,
+          int nst)
 {
     extern __shared__ float4 sm4[];
-    __shared__ uint64_t bars[2];
-    __shared__ double red[32];
+    __shared__ uint64_t bars[kIcPipeMaxStages];
+    __shared__ double red[2][32];        // alternate rows: no barrier between one
+    __shared__ int s_abort;              // row's final read and the next row's writes
     const int mx = dg.max_ndp;
     const int n_m = dg.mc.n_m;
     const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
-    float *const buf0 = reinterpret_cast<float *>(sm4);
-    float *const buf1 = buf0 + n_in * mx;
-    float *const g_sh = buf0 + 2 * n_in * mx;        // G_shift, G_mu, G_V of the row
+    float *const bufs = reinterpret_cast<float *>(sm4);           // nst buffers of n_in * mx
+    float *const g_sh = bufs + nst * n_in * mx;                   // G_shift, G_mu, G_V of the row
     float *const g_mu = g_sh + mx;
     float *const g_v = g_mu + mx;
-    const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
     if (threadIdx.x == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+        for (int i = 0; i < nst; ++i) mbar_init(smem_addr(&bars[i]), 1);
         mbar_init_fence();
+        s_abort = 0;
     }
     __syncthreads();
     const int step = gridDim.x;
     const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
     int r = ic_next_row(dg, active, blockIdx.x, step);
-    if (threadIdx.x == 0 && r < dg.total_ic) ic_issue_row(dg, r, proj, meas, buf0, mx, n_in, bar0);
-    for (unsigned it = 0; r < dg.total_ic; ++it) {
-        const bool odd = it & 1u;
-        float *const stg = odd ? buf1 : buf0;
-        const int rn = ic_next_row(dg, active, r + step, step);
-        // the other buffer was released by the barrier that ended the previous row
-        if (threadIdx.x == 0 && rn < dg.total_ic)
-            ic_issue_row(dg, rn, proj, meas, odd ? buf0 : buf1, mx, n_in, odd ? bar0 : bar1);
-        const bool landed = mbar_wait_bounded(odd ? bar1 : bar0, (it >> 1) & 1u, kIcWaitNs);
-        if (__syncthreads_or(!landed)) {
-            // the row never arrived: report it, poison this block's remaining
-            // rows, and give the copy of the next row a bounded chance to land
-            // before the block's shared memory is released
-            if (threadIdx.x == 0) {
-                atomicExch(status, (int)EI_ERR_TIMEOUT);
-                if (MODE != IC_MODEL)
-                    for (int q = r; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
-                        part[q] = __longlong_as_double(0x7ff8000000000000LL);
-                if (rn < dg.total_ic)
-                    mbar_wait_bounded(odd ? bar0 : bar1, ((it + 1) >> 1) & 1u, kIcWaitNs);
-            }
-            return;
+    // thread 0 runs ahead: r_issue is the row of iteration `issued`
+    int r_issue = r;
+    unsigned issued = 0;
+    if (threadIdx.x == 0) {
+        while (issued < (unsigned)nst - 1 && r_issue < dg.total_ic) {
+            ic_issue_row(dg, r_issue, proj, meas, bufs + issued * n_in * mx, mx, n_in,
+                         smem_addr(&bars[issued]));
+            r_issue = ic_next_row(dg, active, r_issue + step, step);
+            ++issued;
         }
+    }
+    for (unsigned it = 0; r < dg.total_ic; ++it) {
+        const unsigned slot = it % nst;
+        float *const stg = bufs + slot * n_in * mx;
+        // the buffer of iteration it - 1 was released by that row's last barrier
+        if (threadIdx.x == 0 && r_issue < dg.total_ic) {
+            const unsigned sl = issued % nst;
+            ic_issue_row(dg, r_issue, proj, meas, bufs + sl * n_in * mx, mx, n_in, smem_addr(&bars[sl]));
+            r_issue = ic_next_row(dg, active, r_issue + step, step);
+            ++issued;
+        }
+        const bool landed = mbar_wait_bounded(smem_addr(&bars[slot]), (it / nst) & 1u, kIcWaitNs);
+        if (!landed) s_abort = 1;        // finish the row on whatever is there; reported below
 
         const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
         const SliceInfo si = dg.slices[s];
         const int a = r - dg.ic_prefix[s];
-        const int nd = si.n_det, ng = si.n_dp >> 2;
-        const int64_t plane4 = ((int64_t)si.n_theta * si.n_dp) >> 2;
+        const int nd = si.n_det, ndp = si.n_dp, nh = ndp >> 1;
         const float *Pd = stg + mx;
-        const float4 *Pm4 = reinterpret_cast<const float4 *>(stg);
-        const float4 *Ps4 = reinterpret_cast<const float4 *>(stg + 2 * mx);
+        const float2 *Pm2 = reinterpret_cast<const float2 *>(stg);
+        const float2 *Ps2 = reinterpret_cast<const float2 *>(stg + 2 * mx);
         const float4 *pix = dg.pix + si.pix_off;
         const float mo = dg.m_o[si.ang_off + a];
 
-        double e2 = 0.0;
-        bool out_of_domain = false;
-        for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
-            const float4 pm4 = Pm4[gi], ps4 = Ps4[gi];
-            const float pmv[4] = {pm4.x, pm4.y, pm4.z, pm4.w};
-            const float psv[4] = {ps4.x, ps4.y, ps4.z, ps4.w};
-            float cs[4], iV[4], amp[4], a2[4], b2[4];
-            bool ok[4];
+        double e2 = landed ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
+        for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+            const float2 pm = Pm2[h], ps = Ps2[h];
+            const float pmv[2] = {pm.x, pm.y}, psv[2] = {ps.x, ps.y};
+            float cs[2], iV[2], amp[2], a2[2], b2[2];
+            bool ok[2];
+            float e2f = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * gi + q;
+            for (int q = 0; q < 2; ++q) {
+                const int j = 2 * h + q;
                 ok[q] = j < nd;
                 const float4 fl = ok[q] ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
                 const float shift = ok[q] ? zp * deriv_at(Pd, j, nd, si.inv_pitch) + mo + fl.w : 0.f;
                 cs[q] = fl.y + shift;
                 const float V = fmaf(kappa, psv[q], fl.z * fl.z);
-                if (ok[q] && !(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
+                if (ok[q] && !(V > 0.01f * fl.z * fl.z)) e2f = __int_as_float(0x7f800000);
                 const float Vs = fmaxf(V, 1e-30f);
                 iV[q] = 1.0f / Vs;
                 amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
                 a2[q] = -kLog2e * pmv[q];
                 b2[q] = (0.5f * kLog2e) * iV[q];
             }
-            float st[4] = {0.f, 0.f, 0.f, 0.f}, stq[4] = {0.f, 0.f, 0.f, 0.f},
-                  stq2[4] = {0.f, 0.f, 0.f, 0.f};
-            float e2f = 0.f;
+            float st[2] = {0.f, 0.f}, stq[2] = {0.f, 0.f}, stq2[2] = {0.f, 0.f};
 #pragma unroll 4
             for (int k = 0; k < n_m; ++k) {
                 const float mk = dg.mc.m[k];
-                float sv[4], qd[4];
+                float sv[2], qd[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 2; ++q) {
                     qd[q] = mk - cs[q];
                     sv[q] = amp[q] * ex2_approx(fmaf(-b2[q], qd[q] * qd[q], a2[q]));
                 }
                 if (MODE == IC_MODEL) {
-                    reinterpret_cast<float4 *>(s_mod + si.meas_off)[k * plane4 + (int64_t)a * ng + gi] =
-                        make_float4(sv[0], sv[1], sv[2], sv[3]);
+                    reinterpret_cast<float2 *>(s_mod + si.meas_off)[(k * (int64_t)si.n_theta + a) * nh + h] =
+                        make_float2(sv[0], sv[1]);
                 } else {
-                    const float4 x4 = reinterpret_cast<const float4 *>(stg + (3 + k) * mx)[gi];
-                    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+                    const float2 x2 = reinterpret_cast<const float2 *>(stg + (3 + k) * mx)[h];
+                    const float xv[2] = {x2.x, x2.y};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < 2; ++q) {
                         const float e = ok[q] ? sv[q] - xv[q] : 0.f;
                         e2f = fmaf(e, e, e2f);
                         if (MODE == IC_OBJECTIVE_GRAD) {
@@ -361,86 +360,91 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             }
             if (MODE != IC_MODEL) e2 += (double)e2f;
             if (MODE == IC_OBJECTIVE_GRAD) {
-                float gsh[4], gvv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    gsh[q] = 2.f * stq[q] * iV[q];
-                    gvv[q] = kappa * iV[q] * (stq2[q] * iV[q] - st[q]);
-                }
-                reinterpret_cast<float4 *>(g_sh)[gi] = make_float4(gsh[0], gsh[1], gsh[2], gsh[3]);
-                reinterpret_cast<float4 *>(g_mu)[gi] =
-                    make_float4(-2.f * st[0], -2.f * st[1], -2.f * st[2], -2.f * st[3]);
-                reinterpret_cast<float4 *>(g_v)[gi] = make_float4(gvv[0], gvv[1], gvv[2], gvv[3]);
+                reinterpret_cast<float2 *>(g_sh)[h] =
+                    make_float2(2.f * stq[0] * iV[0], 2.f * stq[1] * iV[1]);
+                reinterpret_cast<float2 *>(g_mu)[h] = make_float2(-2.f * st[0], -2.f * st[1]);
+                reinterpret_cast<float2 *>(g_v)[h] =
+                    make_float2(kappa * iV[0] * (stq2[0] * iV[0] - st[0]),
+                                kappa * iV[1] * (stq2[1] * iV[1] - st[1]));
             }
         }
         if (MODE == IC_OBJECTIVE_GRAD) {
-            // g_delta = (z/period) D^T G_shift into the P_delta slot (its last
-            // reader finished at this barrier), then the packed row
-            __syncthreads();
-            float *gdl = stg + mx;
-            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
-                float gd[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = 4 * gi + q;
-                    gd[q] = j < nd ? zp * deriv_T_at(g_sh, j, nd, si.inv_pitch) : 0.f;
-                }
-                reinterpret_cast<float4 *>(gdl)[gi] = make_float4(gd[0], gd[1], gd[2], gd[3]);
-            }
-            __syncthreads();
-            const int ndp = si.n_dp;
+            __syncthreads();                       // every G_shift of the row is in place
+            // packed row: the entry of pixel j holds g(j) and g(j + 1), with
+            // g_delta = (z/period) D^T G_shift evaluated where it is needed
             const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
-            for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
-                const bool nx = j + 1 < ndp;
-                gA[dst + j] = make_float4(g_mu[j], gdl[j], g_v[j], nx ? g_mu[j + 1] : 0.f);
-                gB[dst + j] = make_float2(nx ? gdl[j + 1] : 0.f, nx ? g_v[j + 1] : 0.f);
-            }
-            if (threadIdx.x == 0) {                     // entry of pixel -1: (0, g(0))
-                gA[dst - 1] = make_float4(0.f, 0.f, 0.f, g_mu[0]);
-                gB[dst - 1] = make_float2(gdl[0], g_v[0]);
+            for (int j = threadIdx.x - 1; j < ndp; j += blockDim.x) {
+                const bool cur = j >= 0, nx = j + 1 < ndp;
+                const float d0 = cur && j < nd ? zp * deriv_T_at(g_sh, j, nd, si.inv_pitch) : 0.f;
+                const float d1 = nx && j + 1 < nd ? zp * deriv_T_at(g_sh, j + 1, nd, si.inv_pitch) : 0.f;
+                gA[dst + j] = make_float4(cur ? g_mu[j] : 0.f, d0, cur ? g_v[j] : 0.f,
+                                          nx ? g_mu[j + 1] : 0.f);
+                gB[dst + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
             }
         }
         if (MODE != IC_MODEL) {
-            const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
-            const double tot = block_sum_double(e2, red);
-            if (threadIdx.x == 0) part[r] = bad ? __longlong_as_double(0x7ff0000000000000LL) : tot;
+            const double tot = block_sum_double(e2, red[it & 1u]);  // its barrier releases the row
+            if (threadIdx.x == 0) part[r] = tot;
+        } else {
+            __syncthreads();
         }
-        __syncthreads();            // this row's buffer and gradient rows are free again
-        r = rn;
+        if (s_abort) {
+            // a row never arrived: report it, poison this block's remaining rows,
+            // and give the copies still in flight a bounded chance to land before
+            // the block's shared memory is released
+            if (threadIdx.x == 0) {
+                atomicExch(status, (int)EI_ERR_TIMEOUT);
+                if (MODE != IC_MODEL)
+                    for (int q = r; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
+                        part[q] = __longlong_as_double(0x7ff8000000000000LL);
+                for (unsigned i = it; i < issued; ++i)
+                    mbar_wait_bounded(smem_addr(&bars[i % nst]), (i / nst) & 1u, kIcWaitNs);
+            }
+            return;
+        }
+        r = ic_next_row(dg, active, r + step, step);
     }
 }
 
 static const int kIcPipeSmemLimit = 220 * 1024;
 
-static int ic_threads(const ei_geometry *g)
+// Threads for the row kernels: one per 4 (variant 0) or 2 (variant 1) pixels
+// of the widest row, capped (threads then loop over the row).
+static int ic_threads(const ei_geometry *g, int px, int cap)
 {
-    // one thread per 4 pixels of the widest row, at most 512 (then threads loop)
-    int threads = (g->dg.max_ndp / 4 + 31) / 32 * 32;
-    return threads > 512 ? 512 : threads;
+    const int threads = (g->dg.max_ndp / px + 31) / 32 * 32;
+    return threads > cap ? cap : threads;
 }
 
-size_t ic_pipe_smem(int max_ndp, int n_m, IcMode mode)
+static size_t ic_pipe_smem_stages(int max_ndp, int n_m, IcMode mode, int nst)
 {
     const int n_in = mode == IC_MODEL ? 3 : 3 + n_m;
-    return (size_t)(2 * n_in + 3) * max_ndp * sizeof(float);
+    return (size_t)(nst * n_in + 3) * max_ndp * sizeof(float);
 }
 
-bool ic_pipe_fits(int max_ndp, int n_m)
+// Row buffers of the bulk-copy variant: 3 when they fit, else 2, else 0.
+static int ic_pipe_stages(int max_ndp, int n_m)
 {
-    return ic_pipe_smem(max_ndp, n_m, IC_OBJECTIVE_GRAD) <= (size_t)kIcPipeSmemLimit;
+    for (int nst = kIcPipeMaxStages; nst >= 2; --nst)
+        if (ic_pipe_smem_stages(max_ndp, n_m, IC_OBJECTIVE_GRAD, nst) <= (size_t)kIcPipeSmemLimit)
+            return nst;
+    return 0;
 }
+
+bool ic_pipe_fits(int max_ndp, int n_m) { return ic_pipe_stages(max_ndp, n_m) > 0; }
 
 template <int MODE>
 static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
                                   float *s_mod, double *part, const int *active, cudaStream_t st)
 {
-    const int threads = ic_threads(g);
-    const size_t smem = ic_pipe_smem(g->dg.max_ndp, g->dg.mc.n_m, (IcMode)MODE);
+    const int threads = ic_threads(g, 2, 1024);
+    const int nst = ic_pipe_stages(g->dg.max_ndp, g->dg.mc.n_m);
+    const size_t smem = ic_pipe_smem_stages(g->dg.max_ndp, g->dg.mc.n_m, (IcMode)MODE, nst);
     int per_sm = 0;
     EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ic_pipe<MODE>, threads, smem));
     const int grid = std::max(1, std::min(g->dg.total_ic, std::max(1, per_sm) * g->num_sms));
     k_ic_pipe<MODE><<<grid, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA, g->gB, part,
-                                                 active, g->dev_status);
+                                                 active, g->dev_status, nst);
     return cudaGetLastError();
 }
 
@@ -455,7 +459,7 @@ cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas
         default: return launch_ic_pipe<IC_OBJECTIVE_GRAD>(g, proj, meas, s_mod, part, active, st);
         }
     }
-    const int threads = ic_threads(g);
+    const int threads = ic_threads(g, 4, 512);
     const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
     switch (mode) {
     case IC_MODEL:

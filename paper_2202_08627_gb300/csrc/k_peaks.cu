@@ -1,0 +1,143 @@
+// On-chip throughput microbenchmarks: the denominators of the rooflines of
+// the kernels that are bound on chip rather than by HBM (the projector and
+// the adjoint move ~50 B per voxel-angle from L1 into registers; the IC
+// kernel's arithmetic is FP32).
+//
+//   FP32 FMA rate      every thread runs 8 independent FMA chains
+//   L1 load bandwidth  every block re-reads one 8 KB region with lane-contiguous
+//                      16-byte loads (after the first pass every load hits L1)
+//   shared memory      the same pattern on an 8 KB shared-memory copy
+//
+// Each is timed with CUDA events after a warm-up launch; the best of three
+// runs is reported.  Work sizes are fixed and the loops have constant trip
+// counts, so every launch ends.
+#include <algorithm>
+
+#include "ei_internal.h"
+
+namespace ei {
+
+namespace {
+
+constexpr int kPeakThreads = 256;
+constexpr int kSpan4 = 512;                 // float4 per block region: 8 KB
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_fma(float *out, int iters)
+{
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 1.0f + 1e-3f * (float)(threadIdx.x + i);
+    const float b = 0.9999999f, c = 1e-7f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], b, c);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == 12345.0f) out[blockIdx.x] = s;     // keeps the chains live; never true
+}
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_l1(const float4 *__restrict__ src, float *out,
+                                                          int iters)
+{
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = threadIdx.x; k < kSpan4; k += kPeakThreads) {
+            // the offset moves with the iteration so no load is loop-invariant
+            const float4 v = __ldg(src + ((k + it * 32) & (kSpan4 - 1)));
+            acc.x += v.x, acc.y += v.y, acc.z += v.z, acc.w += v.w;
+        }
+    }
+    const float s = acc.x + acc.y + acc.z + acc.w;
+    if (s == 12345.0f) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_smem(const float4 *__restrict__ src, float *out,
+                                                            int iters)
+{
+    __shared__ float4 buf[kSpan4];
+    for (int k = threadIdx.x; k < kSpan4; k += kPeakThreads) buf[k] = src[k];
+    __syncthreads();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = threadIdx.x; k < kSpan4; k += kPeakThreads) {
+            const float4 v = buf[(k + it * 32) & (kSpan4 - 1)];
+            acc.x += v.x, acc.y += v.y, acc.z += v.z, acc.w += v.w;
+        }
+    }
+    const float s = acc.x + acc.y + acc.z + acc.w;
+    if (s == 12345.0f) out[blockIdx.x] = s;
+}
+
+template <typename F>
+cudaError_t best_ms(F launch, cudaStream_t st, float *ms)
+{
+    cudaEvent_t e0, e1;
+    EI_CUDA_TRY(cudaEventCreate(&e0));
+    EI_CUDA_TRY(cudaEventCreate(&e1));
+    launch();                                           // warm-up
+    float best = 1e30f;
+    cudaError_t e = cudaGetLastError();
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, st);
+        launch();
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return e;
+}
+
+}  // namespace
+
+}  // namespace ei
+
+using namespace ei;
+
+extern "C" int ei_measure_peaks(ei_peaks *out, void *stream)
+{
+    if (!out) return EI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return EI_ERR_CUDA;
+    float4 *src = nullptr;
+    float *sink = nullptr;
+    const int grid = sms * 8;                 // 2048 threads per SM
+    cudaError_t e = cudaMalloc(&src, kSpan4 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&sink, grid * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(src, 0, kSpan4 * sizeof(float4), st);
+    const int fma_iters = 4096, mem_iters = 2048;
+    float t_fma = 0.f, t_l1 = 0.f, t_sm = 0.f;
+    if (e == cudaSuccess)
+        e = best_ms([&] { k_peak_fma<<<grid, kPeakThreads, 0, st>>>(sink, fma_iters); }, st, &t_fma);
+    if (e == cudaSuccess)
+        e = best_ms([&] { k_peak_l1<<<grid, kPeakThreads, 0, st>>>(src, sink, mem_iters); }, st, &t_l1);
+    if (e == cudaSuccess)
+        e = best_ms([&] { k_peak_smem<<<grid, kPeakThreads, 0, st>>>(src, sink, mem_iters); }, st, &t_sm);
+    cudaFree(src);
+    cudaFree(sink);
+    if (e != cudaSuccess) {
+        record_error(e);
+        return EI_ERR_CUDA;
+    }
+    const double threads = (double)grid * kPeakThreads;
+    out->fp32_tflops = threads * fma_iters * 16 * 8 * 2 / (t_fma * 1e-3) / 1e12;
+    const double bytes = (double)grid * mem_iters * kSpan4 * sizeof(float4);
+    out->l1_load_tbs = bytes / (t_l1 * 1e-3) / 1e12;
+    out->smem_load_tbs = bytes / (t_sm * 1e-3) / 1e12;
+    out->num_sms = sms;
+    return EI_OK;
+}

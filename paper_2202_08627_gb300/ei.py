@@ -72,6 +72,11 @@ class ei_solve_report(ctypes.Structure):
                 ("seconds", c_double)]
 
 
+class ei_peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", c_double), ("l1_load_tbs", c_double),
+                ("smem_load_tbs", c_double), ("num_sms", c_int)]
+
+
 class ei_profile(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("project_launches", c_int64), ("ic_launches", c_int64),
                 ("backproject_launches", c_int64), ("project_ms", c_double), ("ic_ms", c_double),
@@ -85,9 +90,9 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_get_variant", "ei_last_error", "ei_single_shot_fbp", "ei_unet_create",
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
-            "ei_get_ic_variant"]
+            "ei_get_ic_variant", "ei_measure_peaks"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 4, 3
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 7, 3
 
 _lib = None
 
@@ -136,6 +141,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_measure_peaks.argtypes = [P(ei_peaks), c_void_p]
+    lib.ei_measure_peaks.restype = c_int
     lib.ei_set_ic_variant.argtypes = [c_void_p, c_int]
     lib.ei_set_ic_variant.restype = c_int
     lib.ei_get_ic_variant.argtypes = [c_void_p, P(c_int)]
@@ -570,6 +577,14 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+def ei_measure_peaks(stream=None) -> dict:
+    """On-chip throughput of the current GPU (FP32 FMA TFLOP/s, L1 and shared
+    memory load TB/s), measured by microbenchmarks."""
+    p = ei_peaks()
+    _check(load_library().ei_measure_peaks(ctypes.byref(p), _stream_ptr(stream)), "ei_measure_peaks")
+    return {f: getattr(p, f) for f, _ in p._fields_}
 
 
 def ei_set_ic_variant(geom: Geometry, variant: int) -> None:
