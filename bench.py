@@ -223,6 +223,53 @@ def train_warm_start(args, wl, device):
                  "loss_last": hist[-1]}
 
 
+def run_oracle_timing(args):
+    """The FP64 oracle on this machine's host cores, as it stands: time to
+    tolerance of a 64x64 slice (90 angles, 96 pixels, M=7, at most 20
+    iterations) and of one 256x256 slice (720 angles, 384 pixels, M=7, relative
+    change 1e-6), and the time per L-BFGS iteration (3 iterations) of one
+    512x512 and one 1024x1024 slice with 1800 angles; with all cores
+    (os.cpu_count()), 3 threads and (except the 1024x1024 slice) 1 thread.
+    Prints one JSON line."""
+    import oracle
+    from paper_2202_08627_gb300 import inputs
+
+    def problem(seed, n, nth, nd, n_m=7):
+        spec = inputs.make_slice(seed, n, nth, nd, n_m)
+        geom = oracle.Geometry(n=n, n_theta=nth, n_det=nd, pitch=spec.pitch, theta=spec.theta,
+                               m=spec.m, z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM,
+                               kappa=inputs.KAPPA, flat_A=spec.flat_A, flat_c=spec.flat_c,
+                               flat_w=spec.flat_w)
+        return geom, inputs.poisson_noise(oracle.ic_model(spec.P_exact, geom), spec.seed)
+
+    nproc = os.cpu_count() or 1
+    runs = []
+    # (case, slice shape, tol, [(threads, max_iter)]): single-threaded runs of
+    # the large slices are shortened to one iteration to bound the wall time
+    cases = [("64x64, 90 angles, 96 pixels, M=7, tol 1e-6, at most 20 iterations", (64, 90, 96),
+              1e-6, [(nproc, 20), (3, 20), (1, 20)]),
+             ("256x256, 720 angles, 384 pixels, M=7, tol 1e-6", (256, 720, 384), 1e-6,
+              [(nproc, 400), (3, 400)]),
+             ("512x512, 1800 angles, 1280 pixels, M=7, fixed iterations", (512, 1800, 1280), 0.0,
+              [(nproc, 3), (3, 3), (1, 1)]),
+             ("1024x1024, 1800 angles, 1536 pixels, M=7, fixed iterations", (1024, 1800, 1536), 0.0,
+              [(nproc, 3), (3, 1)])]
+    for name, (n, nth, nd), tol, plan in cases:
+        geom, s_exp = problem(7, n, nth, nd)
+        for t, max_iter in plan:
+            oracle.set_num_threads(t)
+            t0 = time.perf_counter()
+            _, rep = oracle.reconstruct(s_exp, geom, opts=oracle.SolveOptions(tol=tol, max_iter=max_iter))
+            dt = time.perf_counter() - t0
+            runs.append({"case": name, "threads": t, "seconds": dt, "iterations": rep.iterations,
+                         "evaluations": rep.evaluations, "status": rep.status,
+                         "seconds_per_iteration": dt / max(1, rep.iterations)})
+            print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
+    oracle.set_num_threads(nproc)
+    print(json.dumps({"impl": "oracle-timing", "kind": "FP64 oracle, host cores", "nproc": nproc,
+                      "runs": runs}), flush=True)
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -489,11 +536,15 @@ def main():
     ap.add_argument("--cnn-pairs", type=int, default=256)
     ap.add_argument("--cnn-epochs", type=int, default=20)
     ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="run this many objective+gradient evaluations for ncu and exit")
     args = ap.parse_args()
     if args.profile_evals > 0:
         return run_profile_case(args)
+    if args.oracle_timing:
+        return run_oracle_timing(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -76,6 +76,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
         : "memory");
 }
 
+// Orders this thread's earlier generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) accesses to the same locations.
+__device__ __forceinline__ void proxy_fence_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // 2^x, the PTX approximate base-2 exponential (relative error about 2^-22;
 // results below the normal range flush to zero).
 __device__ __forceinline__ float ex2_approx(float x)

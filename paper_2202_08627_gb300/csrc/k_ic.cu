@@ -207,17 +207,29 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
 // NST (3, else 2) row buffers in shared memory: while it computes row r, the
 // bulk copies of its next NST - 1 rows (three projection rows and M measured
 // rows, one copy each) are in flight, so every SM keeps up to ~120 KB of reads
-// outstanding independently of its register budget.  Two pixels per thread;
-// per row two block barriers (before D^T, which reads neighbours' G_shift,
-// and the objective reduction, which also releases the row's buffer).  The
-// arithmetic per pixel is variant 0's, with the exponential taken as
-// 2^(log2(e) x) by the PTX ex2 instruction on a pre-scaled argument and the
-// factor 2 of the residual applied once per pixel; results agree with
-// variant 0 to FP32 rounding.
+// outstanding independently of its register budget.  Thread 0 issues the
+// copies and publishes each row's slice constants in shared memory.  Two
+// pixels per thread; two block barriers per row (before D^T, which reads
+// neighbours' G_shift, and the objective reduction, which also releases the
+// row's buffer).  Per pixel the arithmetic is variant 0's, arranged to issue
+// fewer instructions: 1/V as rsqrt(V)^2, the exponential as 2^(log2(e) x) by
+// the PTX ex2 instruction on a pre-scaled argument, D and D^T without
+// branches (D^T from G_shift pre-weighted by its row of D), padding pixels'
+// measured values zeroed once per row, the factor 2 of the residual applied
+// once per pixel.  Results agree with variant 0 to FP32 rounding.
 // ---------------------------------------------------------------------------
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint64_t kIcWaitNs = 2000000000ull;     // 2 s bound on one row's copies
 constexpr int kIcPipeMaxStages = 3;
+
+// A row's constants, written by the issuing thread next to its buffer.
+struct IcRow {
+    int row;                 // -1: the block has no further row
+    int a, nd, ndp;
+    int pix_off, pad_;
+    float inv_pitch, mo;
+    int64_t meas_off, gp_off, plane;
+};
 
 __device__ __forceinline__ int ic_next_row(const DevGeom &dg, const int *active, int r, int step)
 {
@@ -226,17 +238,31 @@ __device__ __forceinline__ int ic_next_row(const DevGeom &dg, const int *active,
     return r;
 }
 
-// Thread 0: arm `bar` and issue the copies of row r into the buffer `stage`
-// (slots of mx floats: P_mu, P_delta, P_sigma, then the M measured rows).
+// Thread 0: publish row r's constants in *meta (row = -1 when r is past the
+// end) and, for a real row, arm `bar` and issue the copies of the row into
+// the buffer `stage` (slots of mx floats: P_mu, P_delta, P_sigma, then the M
+// measured rows).
 __device__ __forceinline__ void ic_issue_row(const DevGeom &dg, int r, const float *proj,
                                              const float *meas, float *stage, int mx, int n_in,
-                                             unsigned bar)
+                                             unsigned bar, IcRow *meta)
 {
+    if (r >= dg.total_ic) {
+        meta->row = -1;
+        return;
+    }
     const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
     const SliceInfo &si = dg.slices[s];
     const int a = r - dg.ic_prefix[s];
-    const unsigned bytes = (unsigned)si.n_dp * 4u;
+    IcRow m;
+    m.row = r, m.a = a, m.nd = si.n_det, m.ndp = si.n_dp;
+    m.pix_off = si.pix_off, m.pad_ = 0;
+    m.inv_pitch = si.inv_pitch, m.mo = dg.m_o[si.ang_off + a];
+    m.meas_off = si.meas_off + (int64_t)a * si.n_dp;                 // row start, plane m = 0
+    m.gp_off = si.gp_off + (int64_t)a * si.gw + si.marg;             // entry of pixel 0
     const int64_t plane = (int64_t)si.n_theta * si.n_dp;
+    m.plane = plane;
+    *meta = m;
+    const unsigned bytes = (unsigned)si.n_dp * 4u;
     const int64_t rbase = (int64_t)a * si.n_dp;
     mbar_arrive_expect_tx(bar, bytes * (unsigned)n_in);
     for (int c = 0; c < 3; ++c)
@@ -254,79 +280,86 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
 {
     extern __shared__ float4 sm4[];
     __shared__ uint64_t bars[kIcPipeMaxStages];
+    __shared__ IcRow metas[kIcPipeMaxStages];
     __shared__ double red[2][32];        // alternate rows: no barrier between one
     __shared__ int s_abort;              // row's final read and the next row's writes
     const int mx = dg.max_ndp;
     const int n_m = dg.mc.n_m;
     const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
     float *const bufs = reinterpret_cast<float *>(sm4);           // nst buffers of n_in * mx
-    float *const g_sh = bufs + nst * n_in * mx;                   // G_shift, G_mu, G_V of the row
-    float *const g_mu = g_sh + mx;
+    // G_shift weighted by its row of D (one zero entry in front), G_mu, G_V
+    float *const g_sw = bufs + nst * n_in * mx + 4;
+    float *const g_mu = g_sw + mx + 4;
     float *const g_v = g_mu + mx;
+    const int step = gridDim.x;
+    const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
+    // thread 0 runs ahead: r_issue is the row of iteration `issued`
+    int r_issue = ic_next_row(dg, active, blockIdx.x, step);
+    unsigned issued = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < nst; ++i) mbar_init(smem_addr(&bars[i]), 1);
         mbar_init_fence();
         s_abort = 0;
-    }
-    __syncthreads();
-    const int step = gridDim.x;
-    const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
-    int r = ic_next_row(dg, active, blockIdx.x, step);
-    // thread 0 runs ahead: r_issue is the row of iteration `issued`
-    int r_issue = r;
-    unsigned issued = 0;
-    if (threadIdx.x == 0) {
-        while (issued < (unsigned)nst - 1 && r_issue < dg.total_ic) {
+        g_sw[-1] = 0.f;
+        while (issued < (unsigned)nst - 1) {
             ic_issue_row(dg, r_issue, proj, meas, bufs + issued * n_in * mx, mx, n_in,
-                         smem_addr(&bars[issued]));
-            r_issue = ic_next_row(dg, active, r_issue + step, step);
+                         smem_addr(&bars[issued]), &metas[issued]);
+            if (r_issue < dg.total_ic) r_issue = ic_next_row(dg, active, r_issue + step, step);
             ++issued;
         }
     }
-    for (unsigned it = 0; r < dg.total_ic; ++it) {
+    __syncthreads();
+    for (unsigned it = 0;; ++it) {
         const unsigned slot = it % nst;
+        const IcRow m = metas[slot];
+        if (m.row < 0) break;
         float *const stg = bufs + slot * n_in * mx;
         // the buffer of iteration it - 1 was released by that row's last barrier
-        if (threadIdx.x == 0 && r_issue < dg.total_ic) {
+        if (threadIdx.x == 0) {
             const unsigned sl = issued % nst;
-            ic_issue_row(dg, r_issue, proj, meas, bufs + sl * n_in * mx, mx, n_in, smem_addr(&bars[sl]));
-            r_issue = ic_next_row(dg, active, r_issue + step, step);
+            ic_issue_row(dg, r_issue, proj, meas, bufs + sl * n_in * mx, mx, n_in,
+                         smem_addr(&bars[sl]), &metas[sl]);
+            if (r_issue < dg.total_ic) r_issue = ic_next_row(dg, active, r_issue + step, step);
             ++issued;
         }
         const bool landed = mbar_wait_bounded(smem_addr(&bars[slot]), (it / nst) & 1u, kIcWaitNs);
         if (!landed) s_abort = 1;        // finish the row on whatever is there; reported below
 
-        const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
-        const SliceInfo si = dg.slices[s];
-        const int a = r - dg.ic_prefix[s];
-        const int nd = si.n_det, ndp = si.n_dp, nh = ndp >> 1;
+        const int nd = m.nd, ndp = m.ndp, nh = ndp >> 1;
         const float *Pd = stg + mx;
         const float2 *Pm2 = reinterpret_cast<const float2 *>(stg);
         const float2 *Ps2 = reinterpret_cast<const float2 *>(stg + 2 * mx);
-        const float4 *pix = dg.pix + si.pix_off;
-        const float mo = dg.m_o[si.ang_off + a];
-
+        const float4 *pix = dg.pix + m.pix_off;
+        const float h_in = zp * m.inv_pitch;                 // (z/period) / pitch
         double e2 = landed ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
         for (int h = threadIdx.x; h < nh; h += blockDim.x) {
             const float2 pm = Pm2[h], ps = Ps2[h];
             const float pmv[2] = {pm.x, pm.y}, psv[2] = {ps.x, ps.y};
-            float cs[2], iV[2], amp[2], a2[2], b2[2];
-            bool ok[2];
+            float cs[2], r2[2], amp[2], a2[2], b2[2];
             float e2f = 0.f;
+            if (MODE != IC_MODEL && 2 * h + 1 >= nd) {
+                // padding pixels of this pair: their measured values count as 0
+                for (int q = 0; q < 2; ++q)
+                    if (2 * h + q >= nd)
+                        for (int k = 0; k < n_m; ++k) stg[(3 + k) * mx + 2 * h + q] = 0.f;
+                proxy_fence_async();             // ordered before the buffer's next bulk copy
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int j = 2 * h + q;
-                ok[q] = j < nd;
-                const float4 fl = ok[q] ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
-                const float shift = ok[q] ? zp * deriv_at(Pd, j, nd, si.inv_pitch) + mo + fl.w : 0.f;
-                cs[q] = fl.y + shift;
+                const bool ok = j < nd;
+                const float4 fl = ok ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
+                // D R[delta]: central difference, one-sided at the row ends
+                const int jl = max(j - 1, 0), jr = min(j + 1, nd - 1);
+                const float dd = (Pd[jr] - Pd[jl]) * (jr - jl == 2 ? 0.5f : 1.0f);
+                cs[q] = fl.y + (ok ? fmaf(h_in, dd, m.mo + fl.w) : 0.f);
                 const float V = fmaf(kappa, psv[q], fl.z * fl.z);
-                if (ok[q] && !(V > 0.01f * fl.z * fl.z)) e2f = __int_as_float(0x7f800000);
-                const float Vs = fmaxf(V, 1e-30f);
-                iV[q] = 1.0f / Vs;
-                amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
+                if (ok && !(V > 0.01f * fl.z * fl.z)) e2f = __int_as_float(0x7f800000);
+                const float rs = rsqrtf(fmaxf(V, 1e-30f));
+                r2[q] = rs * rs;                                  // 1 / V
+                amp[q] = ok ? fl.x * fl.z * rs : 0.f;
                 a2[q] = -kLog2e * pmv[q];
-                b2[q] = (0.5f * kLog2e) * iV[q];
+                b2[q] = (0.5f * kLog2e) * r2[q];
             }
             float st[2] = {0.f, 0.f}, stq[2] = {0.f, 0.f}, stq2[2] = {0.f, 0.f};
 #pragma unroll 4
@@ -339,14 +372,14 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                     sv[q] = amp[q] * ex2_approx(fmaf(-b2[q], qd[q] * qd[q], a2[q]));
                 }
                 if (MODE == IC_MODEL) {
-                    reinterpret_cast<float2 *>(s_mod + si.meas_off)[(k * (int64_t)si.n_theta + a) * nh + h] =
+                    reinterpret_cast<float2 *>(s_mod + m.meas_off + k * m.plane)[h] =
                         make_float2(sv[0], sv[1]);
                 } else {
                     const float2 x2 = reinterpret_cast<const float2 *>(stg + (3 + k) * mx)[h];
                     const float xv[2] = {x2.x, x2.y};
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float e = ok[q] ? sv[q] - xv[q] : 0.f;
+                        const float e = sv[q] - xv[q];
                         e2f = fmaf(e, e, e2f);
                         if (MODE == IC_OBJECTIVE_GRAD) {
                             const float t = e * sv[q];          // half of d(e^2)/d(s)
@@ -360,31 +393,44 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             }
             if (MODE != IC_MODEL) e2 += (double)e2f;
             if (MODE == IC_OBJECTIVE_GRAD) {
-                reinterpret_cast<float2 *>(g_sh)[h] =
-                    make_float2(2.f * stq[0] * iV[0], 2.f * stq[1] * iV[1]);
+                float gsw[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int j = 2 * h + q;
+                    // weight of G_shift(j) in its row of D: 1/pitch at the ends, 1/(2 pitch) inside
+                    const float wd = nd == 1 || j >= nd ? 0.f : (j == 0 || j == nd - 1 ? 2.f : 1.f);
+                    gsw[q] = wd * (2.f * stq[q] * r2[q]);    // row weight x 2 pitch x G_shift
+                }
+                reinterpret_cast<float2 *>(g_sw)[h] = make_float2(gsw[0], gsw[1]);
                 reinterpret_cast<float2 *>(g_mu)[h] = make_float2(-2.f * st[0], -2.f * st[1]);
                 reinterpret_cast<float2 *>(g_v)[h] =
-                    make_float2(kappa * iV[0] * (stq2[0] * iV[0] - st[0]),
-                                kappa * iV[1] * (stq2[1] * iV[1] - st[1]));
+                    make_float2(kappa * r2[0] * (stq2[0] * r2[0] - st[0]),
+                                kappa * r2[1] * (stq2[1] * r2[1] - st[1]));
             }
         }
         if (MODE == IC_OBJECTIVE_GRAD) {
+            if (threadIdx.x == 0) g_sw[ndp] = g_sw[ndp + 1] = 0.f;   // D^T reads past the row
             __syncthreads();                       // every G_shift of the row is in place
             // packed row: the entry of pixel j holds g(j) and g(j + 1), with
-            // g_delta = (z/period) D^T G_shift evaluated where it is needed
-            const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
-            for (int j = threadIdx.x - 1; j < ndp; j += blockDim.x) {
+            // g_delta(j) = (z/period) (D^T G_shift)(j)
+            //            = (z/period)/(2 pitch) (gsw(j-1) - gsw(j+1) + e(j) gsw(j)),
+            // e(j) = +1 at j = nd - 1, -1 at j = 0 (gsw(-1) = gsw(nd) = 0)
+            const float kdt = 0.5f * h_in;
+            for (int j = (int)threadIdx.x - 1; j < ndp; j += blockDim.x) {
+                const float gm1 = g_sw[j - 1], g0 = g_sw[j], g1 = g_sw[j + 1], g2 = g_sw[j + 2];
+                const float e0 = (j == nd - 1 ? 1.f : 0.f) - (j == 0 ? 1.f : 0.f);
+                const float e1 = (j + 1 == nd - 1 ? 1.f : 0.f) - (j + 1 == 0 ? 1.f : 0.f);
+                const float d0 = j >= 0 && j < nd ? kdt * fmaf(e0, g0, gm1 - g1) : 0.f;
+                const float d1 = j + 1 < nd ? kdt * fmaf(e1, g1, g0 - g2) : 0.f;
                 const bool cur = j >= 0, nx = j + 1 < ndp;
-                const float d0 = cur && j < nd ? zp * deriv_T_at(g_sh, j, nd, si.inv_pitch) : 0.f;
-                const float d1 = nx && j + 1 < nd ? zp * deriv_T_at(g_sh, j + 1, nd, si.inv_pitch) : 0.f;
-                gA[dst + j] = make_float4(cur ? g_mu[j] : 0.f, d0, cur ? g_v[j] : 0.f,
-                                          nx ? g_mu[j + 1] : 0.f);
-                gB[dst + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
+                gA[m.gp_off + j] = make_float4(cur ? g_mu[j] : 0.f, d0, cur ? g_v[j] : 0.f,
+                                               nx ? g_mu[j + 1] : 0.f);
+                gB[m.gp_off + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
             }
         }
         if (MODE != IC_MODEL) {
             const double tot = block_sum_double(e2, red[it & 1u]);  // its barrier releases the row
-            if (threadIdx.x == 0) part[r] = tot;
+            if (threadIdx.x == 0) part[m.row] = tot;
         } else {
             __syncthreads();
         }
@@ -395,14 +441,14 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             if (threadIdx.x == 0) {
                 atomicExch(status, (int)EI_ERR_TIMEOUT);
                 if (MODE != IC_MODEL)
-                    for (int q = r; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
+                    for (int q = m.row; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
                         part[q] = __longlong_as_double(0x7ff8000000000000LL);
                 for (unsigned i = it; i < issued; ++i)
-                    mbar_wait_bounded(smem_addr(&bars[i % nst]), (i / nst) & 1u, kIcWaitNs);
+                    if (metas[i % nst].row >= 0)
+                        mbar_wait_bounded(smem_addr(&bars[i % nst]), (i / nst) & 1u, kIcWaitNs);
             }
             return;
         }
-        r = ic_next_row(dg, active, r + step, step);
     }
 }
 
@@ -419,7 +465,7 @@ static int ic_threads(const ei_geometry *g, int px, int cap)
 static size_t ic_pipe_smem_stages(int max_ndp, int n_m, IcMode mode, int nst)
 {
     const int n_in = mode == IC_MODEL ? 3 : 3 + n_m;
-    return (size_t)(nst * n_in + 3) * max_ndp * sizeof(float);
+    return ((size_t)(nst * n_in + 3) * max_ndp + 16) * sizeof(float);
 }
 
 // Row buffers of the bulk-copy variant: 3 when they fit, else 2, else 0.
