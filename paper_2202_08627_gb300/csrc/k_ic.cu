@@ -207,9 +207,10 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
 // NST (3, else 2) row buffers in shared memory: while it computes row r, the
 // bulk copies of its next NST - 1 rows (three projection rows and M measured
 // rows, one copy each) are in flight, so every SM keeps up to ~120 KB of reads
-// outstanding independently of its register budget.  Thread 0 issues the
-// copies and publishes each row's slice constants in shared memory.  Two
-// pixels per thread; two block barriers per row (before D^T, which reads
+// outstanding independently of its register budget.  One thread issues the
+// copies and publishes each row's slice constants in shared memory from a
+// warp of its own, so its latency stays off the consumers' path.  Two
+// pixels per consumer thread; two block barriers per row (before D^T, which reads
 // neighbours' G_shift, and the objective reduction, which also releases the
 // row's buffer).  Per pixel the arithmetic is variant 0's, arranged to issue
 // fewer instructions: 1/V as rsqrt(V)^2, the exponential as 2^(log2(e) x) by
@@ -238,19 +239,55 @@ __device__ __forceinline__ int ic_next_row(const DevGeom &dg, const int *active,
     return r;
 }
 
-// Thread 0: publish row r's constants in *meta (row = -1 when r is past the
-// end) and, for a real row, arm `bar` and issue the copies of the row into
-// the buffer `stage` (slots of mx floats: P_mu, P_delta, P_sigma, then the M
+// The producer's walk over its block's rows r0, r0 + step, ...: rows only
+// increase, so the owning slice is tracked incrementally (a load per slice
+// boundary instead of a binary search per row).
+struct IcRowWalker {
+    int r, s, s_end, step;
+
+    __device__ void start(const DevGeom &dg, const int *active, int r0, int stride)
+    {
+        r = r0, step = stride, s = 0, s_end = __ldg(dg.ic_prefix + 1);
+        skip_inactive(dg, active);
+    }
+    // advance s to the slice owning r (r < total_ic)
+    __device__ void seek(const DevGeom &dg)
+    {
+        while (r >= s_end) {
+            ++s;
+            s_end = __ldg(dg.ic_prefix + s + 1);
+        }
+    }
+    // move r to the first row >= r (same residue) of an active slice
+    __device__ void skip_inactive(const DevGeom &dg, const int *active)
+    {
+        while (r < dg.total_ic) {
+            seek(dg);
+            if (!active || __ldg(active + s)) return;
+            r += (s_end - r + step - 1) / step * step;
+        }
+    }
+    __device__ void next(const DevGeom &dg, const int *active)
+    {
+        r += step;
+        skip_inactive(dg, active);
+    }
+};
+
+// Producer: publish row w.r's constants in *meta (row = -1 when past the end)
+// and, for a real row, arm `bar` and issue the copies of the row into the
+// buffer `stage` (slots of mx floats: P_mu, P_delta, P_sigma, then the M
 // measured rows).
-__device__ __forceinline__ void ic_issue_row(const DevGeom &dg, int r, const float *proj,
-                                             const float *meas, float *stage, int mx, int n_in,
-                                             unsigned bar, IcRow *meta)
+__device__ __forceinline__ void ic_issue_row(const DevGeom &dg, const IcRowWalker &w,
+                                             const float *proj, const float *meas, float *stage,
+                                             int mx, int n_in, unsigned bar, IcRow *meta)
 {
+    const int r = w.r;
     if (r >= dg.total_ic) {
         meta->row = -1;
         return;
     }
-    const int s = find_slice(dg.ic_prefix, dg.n_slices, r);
+    const int s = w.s;
     const SliceInfo &si = dg.slices[s];
     const int a = r - dg.ic_prefix[s];
     IcRow m;
@@ -293,18 +330,22 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
     float *const g_v = g_mu + mx;
     const int step = gridDim.x;
     const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
-    // thread 0 runs ahead: r_issue is the row of iteration `issued`
-    int r_issue = ic_next_row(dg, active, blockIdx.x, step);
-    unsigned issued = 0;
-    if (threadIdx.x == 0) {
+    // the last warp produces (its lane 0 issues the copies and runs ahead over
+    // the rows); the others consume, two pixels per thread
+    const int n_cons = (int)blockDim.x - 32;
+    const bool producer = threadIdx.x == (unsigned)n_cons;
+    IcRowWalker walk;
+    unsigned issued = 0;                 // iterations whose row the producer has published
+    if (producer) {
         for (int i = 0; i < nst; ++i) mbar_init(smem_addr(&bars[i]), 1);
         mbar_init_fence();
         s_abort = 0;
         g_sw[-1] = 0.f;
+        walk.start(dg, active, blockIdx.x, step);
         while (issued < (unsigned)nst - 1) {
-            ic_issue_row(dg, r_issue, proj, meas, bufs + issued * n_in * mx, mx, n_in,
+            ic_issue_row(dg, walk, proj, meas, bufs + issued * n_in * mx, mx, n_in,
                          smem_addr(&bars[issued]), &metas[issued]);
-            if (r_issue < dg.total_ic) r_issue = ic_next_row(dg, active, r_issue + step, step);
+            if (walk.r < dg.total_ic) walk.next(dg, active);
             ++issued;
         }
     }
@@ -315,11 +356,11 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         if (m.row < 0) break;
         float *const stg = bufs + slot * n_in * mx;
         // the buffer of iteration it - 1 was released by that row's last barrier
-        if (threadIdx.x == 0) {
+        if (producer) {
             const unsigned sl = issued % nst;
-            ic_issue_row(dg, r_issue, proj, meas, bufs + sl * n_in * mx, mx, n_in,
+            ic_issue_row(dg, walk, proj, meas, bufs + sl * n_in * mx, mx, n_in,
                          smem_addr(&bars[sl]), &metas[sl]);
-            if (r_issue < dg.total_ic) r_issue = ic_next_row(dg, active, r_issue + step, step);
+            if (walk.r < dg.total_ic) walk.next(dg, active);
             ++issued;
         }
         const bool landed = mbar_wait_bounded(smem_addr(&bars[slot]), (it / nst) & 1u, kIcWaitNs);
@@ -332,7 +373,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         const float4 *pix = dg.pix + m.pix_off;
         const float h_in = zp * m.inv_pitch;                 // (z/period) / pitch
         double e2 = landed ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
-        for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        for (int h = threadIdx.x; h < nh && (int)threadIdx.x < n_cons; h += n_cons) {
             const float2 pm = Pm2[h], ps = Ps2[h];
             const float pmv[2] = {pm.x, pm.y}, psv[2] = {ps.x, ps.y};
             float cs[2], r2[2], amp[2], a2[2], b2[2];
@@ -416,7 +457,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             //            = (z/period)/(2 pitch) (gsw(j-1) - gsw(j+1) + e(j) gsw(j)),
             // e(j) = +1 at j = nd - 1, -1 at j = 0 (gsw(-1) = gsw(nd) = 0)
             const float kdt = 0.5f * h_in;
-            for (int j = (int)threadIdx.x - 1; j < ndp; j += blockDim.x) {
+            for (int j = (int)threadIdx.x - 1; j < ndp && (int)threadIdx.x < n_cons; j += n_cons) {
                 const float gm1 = g_sw[j - 1], g0 = g_sw[j], g1 = g_sw[j + 1], g2 = g_sw[j + 2];
                 const float e0 = (j == nd - 1 ? 1.f : 0.f) - (j == 0 ? 1.f : 0.f);
                 const float e1 = (j + 1 == nd - 1 ? 1.f : 0.f) - (j + 1 == 0 ? 1.f : 0.f);
@@ -438,7 +479,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             // a row never arrived: report it, poison this block's remaining rows,
             // and give the copies still in flight a bounded chance to land before
             // the block's shared memory is released
-            if (threadIdx.x == 0) {
+            if (producer) {
                 atomicExch(status, (int)EI_ERR_TIMEOUT);
                 if (MODE != IC_MODEL)
                     for (int q = m.row; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
@@ -483,7 +524,7 @@ template <int MODE>
 static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
                                   float *s_mod, double *part, const int *active, cudaStream_t st)
 {
-    const int threads = ic_threads(g, 2, 1024);
+    const int threads = ic_threads(g, 2, 1024 - 32) + 32;      // consumers + one producer warp
     const int nst = ic_pipe_stages(g->dg.max_ndp, g->dg.mc.n_m);
     const size_t smem = ic_pipe_smem_stages(g->dg.max_ndp, g->dg.mc.n_m, (IcMode)MODE, nst);
     int per_sm = 0;
