@@ -34,16 +34,28 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned byt
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+// One bounded try: the thread may be suspended until the phase completes or
+// about `hint_ns` nanoseconds pass (a hint; the hardware may wake it earlier).
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity, unsigned hint_ns = 0)
 {
     unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
+    if (hint_ns == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(hint_ns)
+            : "memory");
+    }
     return ok != 0;
 }
 
@@ -61,8 +73,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (unsigned i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
+        if (mbar_try_wait(bar, parity, 20000u)) return true;      // sleep up to ~20 us a try
+        if ((i & 15u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
 

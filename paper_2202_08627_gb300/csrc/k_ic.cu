@@ -308,7 +308,7 @@ __device__ __forceinline__ void ic_issue_row(const DevGeom &dg, const IcRowWalke
         bulk_copy_g2s(stage + (3 + k) * mx, meas + si.meas_off + k * plane + rbase, bytes, bar);
 }
 
-template <int MODE>
+template <int MODE, int NM>
 __global__ void __launch_bounds__(1024)
 k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
           float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
@@ -321,7 +321,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
     __shared__ double red[2][32];        // alternate rows: no barrier between one
     __shared__ int s_abort;              // row's final read and the next row's writes
     const int mx = dg.max_ndp;
-    const int n_m = dg.mc.n_m;
+    const int n_m = NM > 0 ? NM : dg.mc.n_m;     // NM > 0: M known at compile time
     const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
     float *const bufs = reinterpret_cast<float *>(sm4);           // nst buffers of n_in * mx
     // G_shift weighted by its row of D (one zero entry in front), G_mu, G_V
@@ -403,7 +403,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                 b2[q] = (0.5f * kLog2e) * r2[q];
             }
             float st[2] = {0.f, 0.f}, stq[2] = {0.f, 0.f}, stq2[2] = {0.f, 0.f};
-#pragma unroll 4
+#pragma unroll(NM > 0 ? NM : 4)
             for (int k = 0; k < n_m; ++k) {
                 const float mk = dg.mc.m[k];
                 float sv[2], qd[2];
@@ -520,19 +520,43 @@ static int ic_pipe_stages(int max_ndp, int n_m)
 
 bool ic_pipe_fits(int max_ndp, int n_m) { return ic_pipe_stages(max_ndp, n_m) > 0; }
 
-template <int MODE>
-static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
-                                  float *s_mod, double *part, const int *active, cudaStream_t st)
+template <int MODE, int NM>
+static cudaError_t launch_ic_pipe_nm(const ei_geometry *g, const float *proj, const float *meas,
+                                     float *s_mod, double *part, const int *active, cudaStream_t st)
 {
     const int threads = ic_threads(g, 2, 1024 - 32) + 32;      // consumers + one producer warp
     const int nst = ic_pipe_stages(g->dg.max_ndp, g->dg.mc.n_m);
     const size_t smem = ic_pipe_smem_stages(g->dg.max_ndp, g->dg.mc.n_m, (IcMode)MODE, nst);
     int per_sm = 0;
-    EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ic_pipe<MODE>, threads, smem));
+    EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ic_pipe<MODE, NM>, threads, smem));
     const int grid = std::max(1, std::min(g->dg.total_ic, std::max(1, per_sm) * g->num_sms));
-    k_ic_pipe<MODE><<<grid, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA, g->gB, part,
-                                                 active, g->dev_status, nst);
+    k_ic_pipe<MODE, NM><<<grid, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA, g->gB, part,
+                                                     active, g->dev_status, nst);
     return cudaGetLastError();
+}
+
+// M = 7 (the paper's scans) and M = 5 get fully unrolled loops over m.
+template <int MODE>
+static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
+                                  float *s_mod, double *part, const int *active, cudaStream_t st)
+{
+    switch (g->dg.mc.n_m) {
+    case 7: return launch_ic_pipe_nm<MODE, 7>(g, proj, meas, s_mod, part, active, st);
+    case 5: return launch_ic_pipe_nm<MODE, 5>(g, proj, meas, s_mod, part, active, st);
+    default: return launch_ic_pipe_nm<MODE, 0>(g, proj, meas, s_mod, part, active, st);
+    }
+}
+
+template <int MODE>
+static cudaError_t ic_pipe_set_smem_limit()
+{
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kIcPipeSmemLimit));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<MODE, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kIcPipeSmemLimit));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<MODE, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kIcPipeSmemLimit));
+    return cudaSuccess;
 }
 
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
@@ -571,12 +595,9 @@ cudaError_t ic_set_smem_limit()
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kIcPipeSmemLimit));
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_OBJECTIVE>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kIcPipeSmemLimit));
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic_pipe<IC_OBJECTIVE_GRAD>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kIcPipeSmemLimit));
+    EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_MODEL>());
+    EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_OBJECTIVE>());
+    EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_OBJECTIVE_GRAD>());
     return cudaSuccess;
 }
 
