@@ -271,9 +271,11 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * Kernel variants and autotuning (batched, serving-style launches).
  * The projector and the adjoint each come in several tile shapes
  * (projector, rays x angles per block / per warp and samples per loop
- * iteration: 0 16x16/8x4/4, 1 32x8/8x4/4, 2 32x16/8x4/4, 3 16x16/8x4/2,
- * 4 32x8/32x1/4, 5 16x16/16x2/4, 6 32x16/32x1/4; adjoint: 8, 4 or 16 voxels
- * per thread), and
+ * iteration, lanes ray-major: 0 16x16/8x4/4, 1 32x8/8x4/4, 2 32x16/8x4/4,
+ * 3 16x16/8x4/2, 4 32x8/32x1/4, 5 16x16/16x2/4, 6 32x16/32x1/4; lanes
+ * angle-major: 7 16x16/4x8/4, 8 8x32/4x8/4, 9 32x8/4x8/4, 10 16x16/2x16/4;
+ * adjoint: 0 8, 1 4, 2 16 voxels per thread with lanes along rows of 8 voxels,
+ * 3 8 and 4 16 voxels per thread with 8-lane groups on 2 x 4 sub-patches), and
  * either as one block per work item or as a persistent GPU-sized grid whose
  * blocks take work items from a counter.  Projector variants compute every
  * ray identically (bit-identical projections); adjoint variants sum every
@@ -286,7 +288,7 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * cached in a text file (EI_TUNE_CACHE, default ~/.cache/ei_gb300_autotune.txt)
  * keyed by the GPU name and the slice sizes, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..6, adjoint 0..2).
+ * report a variant explicitly (ids: projector 0..10, adjoint 0..4).
  */
 #define EI_TUNE_FORCE 1
 #define EI_TUNE_NO_CACHE_WRITE 2

@@ -53,9 +53,13 @@ struct AdjShared {
 };
 
 // One work item: a 32-column x (8 PASSES)-row voxel tile, 8 x 4 voxel patch per
-// warp and pass, one voxel per thread and pass.  Angles are summed in order
-// whatever PASSES, so every variant gives bit-identical results.
-template <int PASSES>
+// warp and pass, one voxel per thread and pass.  Lanes run along the patch's
+// rows of 8 voxels, or (QUAD) each group of 8 consecutive lanes covers a 2 x 4
+// sub-patch, whose detector positions lie closer together (L1 serves the
+// group's 16-byte loads in one pass when they share a 128-byte line).  A
+// voxel's computation does not depend on the lane order, and angles are
+// summed in order whatever PASSES.
+template <int PASSES, bool QUAD>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -71,8 +75,9 @@ __device__ __forceinline__ void backproject_item(
     const int local = item - prefix[s];
     const int r_t = (local / ntc) * TR, c_t = (local % ntc) * ADJ_TC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int dc = (warp & 3) * 8 + (lane & 7);        // column offset in the tile
-    const int dr0 = (warp >> 2) * 4 + (lane >> 3);     // row offset of pass 0 (passes add 8)
+    // column offset in the tile, row offset of pass 0 (passes add 8)
+    const int dc = (warp & 3) * 8 + (QUAD ? 2 * (lane >> 3) + (lane & 1) : lane & 7);
+    const int dr0 = (warp >> 2) * 4 + (QUAD ? (lane >> 1) & 3 : lane >> 3);
 
     float acc[PASSES][3];
 #pragma unroll
@@ -148,7 +153,7 @@ __device__ __forceinline__ void backproject_item(
     if (threadIdx.x == 0) part[item] = tot;
 }
 
-template <int PASSES, int MINB>
+template <int PASSES, int MINB, bool QUAD>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
               const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -156,13 +161,13 @@ k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restri
               double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
-    backproject_item<PASSES>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out, out_mult,
-                             reg2, reg1, part, active);
+    backproject_item<PASSES, QUAD>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
+                                   out_mult, reg2, reg1, part, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
 // launch) until the list is exhausted; no block waits on another.
-template <int PASSES, int MINB>
+template <int PASSES, int MINB, bool QUAD>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
@@ -178,12 +183,12 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        backproject_item<PASSES>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
-                                 reg2, reg1, part, active);
+        backproject_item<PASSES, QUAD>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
+                                       reg2, reg1, part, active);
     }
 }
 
-template <int P, int M>
+template <int P, int M, bool Q>
 static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const float4 *v,
                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                      double *part, const int *active, cudaStream_t st)
@@ -191,17 +196,17 @@ static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const
     const AdjVariant &av = g->adj_variant;
     if (av.total == 0) return cudaSuccess;
     if (!g->persistent) {
-        k_backproject<P, M><<<av.total, ADJ_THREADS, 0, st>>>(g->dg, av.prefix, g->gA, g->gB,
+        k_backproject<P, M, Q><<<av.total, ADJ_THREADS, 0, st>>>(g->dg, av.prefix, g->gA, g->gB,
                                                               with_sino, v, out, out_mult, reg2,
                                                               reg1, part, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
             EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_backproject_persistent<P, M>, ADJ_THREADS, 0));
+                &per_sm, k_backproject_persistent<P, M, Q>, ADJ_THREADS, 0));
         const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
-        k_backproject_persistent<P, M><<<grid, ADJ_THREADS, 0, st>>>(
+        k_backproject_persistent<P, M, Q><<<grid, ADJ_THREADS, 0, st>>>(
             g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
             out_mult, reg2, reg1, part, active);
     }
@@ -213,16 +218,18 @@ cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float
                                double *part, const int *active, cudaStream_t st)
 {
     switch (g->adj_variant.id) {
-    case 0: return launch_bp_variant<8, 4>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    case 1: return launch_bp_variant<4, 1>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    default: return launch_bp_variant<16, 2>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 0: return launch_bp_variant<8, 4, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 1: return launch_bp_variant<4, 1, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 2: return launch_bp_variant<16, 2, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 3: return launch_bp_variant<8, 4, true>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    default: return launch_bp_variant<16, 2, true>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
     }
 }
 
 // Voxel rows per tile of adjoint variant `id` (see launch_backproject).
 int backproject_variant_rows(int id)
 {
-    static const int P[3] = {8, 4, 16};
+    static const int P[N_ADJ_VARIANTS] = {8, 4, 16, 8, 16};
     return 8 * P[id];
 }
 

@@ -89,10 +89,15 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restri
 // --------------------------------------------------------------------------
 // Projector: one thread per ray; a work item is ANGLES angles x RAYS pixels of
 // one slice; a warp covers WRAYS neighbouring pixels x 32 / WRAYS neighbouring
-// angles.  Templated on the tile shape, the warp shape and the unroll so the
-// autotuner can choose among instantiations.
+// angles, with consecutive lanes on neighbouring pixels or (AFAST) on
+// neighbouring angles.  The order matters because L1 serves a 16-byte load of
+// 8 consecutive lanes in one pass only when their addresses share a 128-byte
+// line: neighbouring angles of one ray sample nearly the same voxels, while
+// neighbouring rays sample voxels 1 to 1.4 entries apart.  Templated on the
+// tile shape, the warp shape and the unroll so the autotuner can choose among
+// instantiations.
 // --------------------------------------------------------------------------
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
 __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
                                              const float4 *__restrict__ xpA,
                                              const float2 *__restrict__ xpB,
@@ -111,8 +116,8 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int WR = RAYS / WRAYS;                   // warps along the rays
     constexpr int WA = 32 / WRAYS;                     // angles per warp
-    const int a = ab * ANGLES + (warp / WR) * WA + lane / WRAYS;
-    const int j = rb * RAYS + (warp % WR) * WRAYS + lane % WRAYS;
+    const int a = ab * ANGLES + (warp / WR) * WA + (AFAST ? lane % WA : lane / WRAYS);
+    const int j = rb * RAYS + (warp % WR) * WRAYS + (AFAST ? lane / WA : lane % WRAYS);
     if (a >= si.n_theta || j >= si.n_dp) return;
     const int64_t plane = (int64_t)si.n_theta * si.n_dp;
     float *out = proj + si.proj_off + (int64_t)a * si.n_dp + j;
@@ -202,20 +207,20 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
 }
 
 // One block per work item.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
           const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
           const float2 *__restrict__ xtB, float *__restrict__ proj, const int *__restrict__ active)
 {
-    project_item<RAYS, ANGLES, UNROLL, WRAYS>(dg, prefix, blockIdx.x, xpA, xpB, xtA, xtB, proj,
-                                              active);
+    project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST>(dg, prefix, blockIdx.x, xpA, xpB, xtA, xtB,
+                                                     proj, active);
 }
 
 // Persistent: a GPU-sized grid whose blocks take work items from a counter
 // (set to 0 before the launch) until the list is exhausted; no block waits on
 // another.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                      const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
@@ -229,27 +234,28 @@ k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int 
         const int item = s_item;
         __syncthreads();
         if (item >= total) return;
-        project_item<RAYS, ANGLES, UNROLL, WRAYS>(dg, prefix, item, xpA, xpB, xtA, xtB, proj, active);
+        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST>(dg, prefix, item, xpA, xpB, xtA, xtB, proj,
+                                                         active);
     }
 }
 
-template <int R, int A, int U, int W>
+template <int R, int A, int U, int W, bool F>
 static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, const int *active,
                                           cudaStream_t st)
 {
     const FwdVariant &v = g->fwd_variant;
     if (v.total == 0) return cudaSuccess;
     if (!g->persistent) {
-        k_project<R, A, U, W><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB, g->xtA,
+        k_project<R, A, U, W, F><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB, g->xtA,
                                                        g->xtB, proj, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
             EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_project_persistent<R, A, U, W>, R * A, 0));
+                &per_sm, k_project_persistent<R, A, U, W, F>, R * A, 0));
         const int grid = std::max(1, std::min(v.total, per_sm * g->num_sms));
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter, 0, sizeof(int), st));
-        k_project_persistent<R, A, U, W><<<grid, R * A, 0, st>>>(g->dg, v.prefix, v.total,
+        k_project_persistent<R, A, U, W, F><<<grid, R * A, 0, st>>>(g->dg, v.prefix, v.total,
                                                              g->work_counter, g->xpA, g->xpB,
                                                              g->xtA, g->xtB, proj, active);
     }
@@ -268,21 +274,25 @@ cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, co
 cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st)
 {
     switch (g->fwd_variant.id) {
-    case 0: return launch_project_variant<16, 16, 4, 8>(g, proj, active, st);
-    case 1: return launch_project_variant<32, 8, 4, 8>(g, proj, active, st);
-    case 2: return launch_project_variant<32, 16, 4, 8>(g, proj, active, st);
-    case 3: return launch_project_variant<16, 16, 2, 8>(g, proj, active, st);
-    case 4: return launch_project_variant<32, 8, 4, 32>(g, proj, active, st);
-    case 5: return launch_project_variant<16, 16, 4, 16>(g, proj, active, st);
-    default: return launch_project_variant<32, 16, 4, 32>(g, proj, active, st);
+    case 0: return launch_project_variant<16, 16, 4, 8, false>(g, proj, active, st);
+    case 1: return launch_project_variant<32, 8, 4, 8, false>(g, proj, active, st);
+    case 2: return launch_project_variant<32, 16, 4, 8, false>(g, proj, active, st);
+    case 3: return launch_project_variant<16, 16, 2, 8, false>(g, proj, active, st);
+    case 4: return launch_project_variant<32, 8, 4, 32, false>(g, proj, active, st);
+    case 5: return launch_project_variant<16, 16, 4, 16, false>(g, proj, active, st);
+    case 6: return launch_project_variant<32, 16, 4, 32, false>(g, proj, active, st);
+    case 7: return launch_project_variant<16, 16, 4, 4, true>(g, proj, active, st);
+    case 8: return launch_project_variant<8, 32, 4, 4, true>(g, proj, active, st);
+    case 9: return launch_project_variant<32, 8, 4, 4, true>(g, proj, active, st);
+    default: return launch_project_variant<16, 16, 4, 2, true>(g, proj, active, st);
     }
 }
 
 // Tile shape (rays, angles) of projector variant `id` (see launch_project).
 void project_variant_shape(int id, int *rays, int *angles)
 {
-    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32},
-                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16};
+    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16},
+                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16};
     *rays = R[id];
     *angles = A[id];
 }

@@ -92,7 +92,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 7, 3
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
 
 _lib = None
 
