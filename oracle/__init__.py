@@ -23,6 +23,10 @@ What it computes, in the paper's order and notation:
   variance kappa R[sigma], which keeps its area.
 * ``objective_grad`` — the cost S of Eq. 5 (sum of squared residuals plus an
   L2 regulariser) and its analytic gradient.
+* ``objective_grad_linked`` — the same cost for the single unknown h of Eq. 4
+  (mu = h, delta = gamma h, no scatter) and its gradient with respect to h.
+* ``offset_grads`` — the gradient of S with respect to the drift m_o(theta)
+  and the ring term m_r(t) of Eq. 4.
 * ``lbfgs`` / ``reconstruct`` — the L-BFGS minimisation the paper uses
   ("Theoretical basis" section, [Byrd 1995] via SciPy), written out.
 
@@ -233,6 +237,60 @@ def ic_objective_grad(P: np.ndarray, s_exp: np.ndarray, geom: Geometry,
     g[1] = geom.z_over_p * deriv_T(G_shift, geom.pitch)
     g[2] = geom.kappa * G_V
     return S, g
+
+
+def shift_gradient(P: np.ndarray, s_exp: np.ndarray, geom: Geometry) -> np.ndarray:
+    """dS/d(shift) per pixel, [n_theta][n_det]: sum_m 2 e s q / V (the shift
+    enters the model only through q = m - c - shift).  Zero where the model
+    leaves its domain."""
+    P_mu, P_delta, P_sigma = P
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
+    shift = _shift_terms(geom, P_delta)
+    V = w * w + geom.kappa * P_sigma
+    if np.any(V <= 0.01 * w * w):
+        return np.zeros_like(P_mu)
+    G = np.zeros_like(P_mu)
+    for k, mk in enumerate(geom.m):
+        q = mk - c - shift
+        s = np.exp(-P_mu) * A * (w / np.sqrt(V)) * np.exp(-q * q / (2.0 * V))
+        G += 2.0 * (s - s_exp[k]) * s * q / V
+    return G
+
+
+def offset_grads(x: np.ndarray, s_exp: np.ndarray, geom: Geometry):
+    """Gradients of S with respect to the drift m_o(theta) and the ring term
+    m_r(t) of Eq. 4, for a physical volume x [3][n][n].  Both enter only the
+    shift of pixel (theta, t), with coefficient 1, so
+      dS/dm_o(theta) = sum_t dS/dshift(theta, t),
+      dS/dm_r(t)     = sum_theta dS/dshift(theta, t)."""
+    P = np.stack([project(np.asarray(x[ch], dtype=np.float64), geom) for ch in range(3)])
+    G = shift_gradient(P, s_exp, geom)
+    return G.sum(axis=1), G.sum(axis=0)
+
+
+def objective_grad_linked(h: np.ndarray, s_exp: np.ndarray, geom: Geometry, gamma: float,
+                          want_grad: bool = True, scaled: bool = False):
+    """S of Eq. 5 for the single unknown of Eq. 4: mu = h, delta = gamma h,
+    sigma = 0, with the regulariser lam_mu ||h / scale_mu||^2 (the paper's
+    lambda ||h||^2).  h [n][n] physical (scaled=False) or h / scale_mu
+    (scaled=True); the gradient is with respect to the same variable.
+    Chain rule through the linear R:
+      dS/dh = R^T (dS/dR[mu] + gamma dS/dR[delta]) + regulariser."""
+    s_mu = float(np.asarray(geom.scale, dtype=np.float64)[0])
+    lam = float(np.asarray(geom.lam, dtype=np.float64)[0])
+    h = np.asarray(h, dtype=np.float64)
+    u = h if scaled else h / s_mu
+    hp = u * s_mu
+    Ph = project(hp, geom)
+    P = np.stack([Ph, gamma * Ph, np.zeros_like(Ph)])
+    S_data, gP = ic_objective_grad(P, s_exp, geom, want_grad)
+    S = S_data + lam * float(np.sum(u * u))
+    if not want_grad:
+        return S, None
+    gh = backproject(gP[0] + gamma * gP[1], geom)
+    if scaled:
+        return S, s_mu * gh + 2.0 * lam * u
+    return S, gh + 2.0 * lam * u / s_mu
 
 
 def forward(x: np.ndarray, geom: Geometry) -> np.ndarray:
