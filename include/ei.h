@@ -297,6 +297,37 @@ int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persist
 int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int *persistent);
 
 /*
+ * Linked single unknown of Eq. 4.  With gamma > 0 the geometry models
+ * mu = h, delta = gamma h, sigma = 0 (the paper's homogeneous-sample
+ * assumption): ei_forward, ei_objective_grad, ei_offset_grad and
+ * ei_reconstruct read h from the mu lane of the volume (the other lanes are
+ * ignored), gradients come back as (dS/dh, 0, 0, 0), ei_reconstruct returns
+ * (h, 0, 0, 0), and the regulariser is lambda[0] ||h / scale[0]||^2 (the
+ * paper's lambda ||h||^2).  gamma is delta / mu in cm (the paper's gamma = 5 is
+ * in units it does not state).  gamma = 0 restores three independent channels.
+ * ei_project and ei_backproject stay the plain linear operators.  EI_ERR_ARG
+ * for a negative or non-finite gamma.
+ */
+int ei_set_linked(ei_geometry *g, double gamma);
+
+/*
+ * Gradient of S (Eq. 5) with respect to the drift m_o(theta) and the ring
+ * term m_r(t) of Eq. 4, at the physical volume vol (layout of ei_forward).
+ * Both terms enter only the shift of pixel (theta, t), with coefficient 1:
+ *   dS/dm_o(theta) = sum_t dS/dshift,   dS/dm_r(t) = sum_theta dS/dshift,
+ *   dS/dshift = sum_m 2 (s_mod - s_exp) s_mod q / V    (q = m - c - shift),
+ * each sum accumulated in FP64 in a fixed order.  g_mo: device [sum n_theta],
+ * g_mr: device [sum n_det], per slice in slice order (for a uniform batch whose
+ * m_o / m_r are shared by every slice, the gradient of the shared array is the
+ * sum over slices); either may be NULL.  Values are unspecified where S is
+ * +inf.  The first call allocates one float per sinogram pixel of scratch;
+ * stream-ordered otherwise.  Not part of the paper's solver here (m_o and m_r
+ * stay fixed during ei_reconstruct).
+ */
+int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *g_mo, float *g_mr,
+                   void *stream);
+
+/*
  * On-chip throughput of the current GPU, measured by microbenchmarks (each the
  * best of three CUDA-event-timed runs after a warm-up; ~10 ms in all): the
  * FP32 FMA rate (2 flops per FMA), the rate at which 16-byte global loads that

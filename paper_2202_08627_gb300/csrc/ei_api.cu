@@ -135,46 +135,62 @@ static cudaError_t traced_ic(ei_geometry *g, const float *proj, const float *mea
 
 static cudaError_t traced_backproject(ei_geometry *g, bool with_sino, const float4 *v,
                                       float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                      double *part, const int *active, cudaStream_t st)
+                                      float link, double *part, const int *active, cudaStream_t st)
 {
     cudaEvent_t b = with_sino ? trace_begin(g, st) : nullptr;
-    cudaError_t e = launch_backproject(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    cudaError_t e = launch_backproject(g, with_sino, v, out, out_mult, reg2, reg1, link, part,
+                                       active, st);
     if (with_sino) trace_end(g, TK_BACKPROJECT, b, st);
     count_launches(g, 1);
     return e;
 }
 
-static cudaError_t counted_prep(ei_geometry *g, const float4 *vol, float4 mult, const int *active,
-                                cudaStream_t st)
+static cudaError_t counted_prep(ei_geometry *g, const float4 *vol, float4 mult, bool linked,
+                                const int *active, cudaStream_t st)
 {
     count_launches(g, 1);
-    return launch_prep(g, vol, mult, active, st);
+    return launch_prep(g, vol, mult, linked, active, st);
+}
+
+// Staging multipliers of a physical volume for the model: (1, 1, 1), or in
+// linked mode (1, gamma, 0) applied to the mu lane's h.
+static float4 physical_mult(const ei_geometry *g)
+{
+    return g->link_gamma > 0.f ? make_float4(1.f, g->link_gamma, 0.f, 0.f)
+                               : make_float4(1.f, 1.f, 1.f, 0.f);
 }
 
 cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
                      float4 *grad, bool scaled, const int *active, cudaStream_t st)
 {
+    // linked mode: the unknown is h in the mu lane, mu = h, delta = gamma h,
+    // sigma = 0, regularised by lambda_mu only (Eq. 4, Eq. 5)
+    const bool linked = g->link_gamma > 0.f;
+    const float gam = g->link_gamma;
+    const float on1 = linked ? 0.f : 1.f;
     float4 mult, out_mult, reg2, reg1;
     if (scaled) {
-        mult = make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
-        out_mult = mult;
-        reg2 = make_float4(2.f * g->lambda[0], 2.f * g->lambda[1], 2.f * g->lambda[2], 0.f);
-        reg1 = make_float4(g->lambda[0], g->lambda[1], g->lambda[2], 0.f);
+        mult = linked ? make_float4(g->scale[0], gam * g->scale[0], 0.f, 0.f)
+                      : make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
+        out_mult = make_float4(g->scale[0], on1 * g->scale[1], on1 * g->scale[2], 0.f);
+        reg2 = make_float4(2.f * g->lambda[0], on1 * 2.f * g->lambda[1], on1 * 2.f * g->lambda[2], 0.f);
+        reg1 = make_float4(g->lambda[0], on1 * g->lambda[1], on1 * g->lambda[2], 0.f);
     } else {
-        mult = make_float4(1.f, 1.f, 1.f, 0.f);
-        out_mult = mult;
+        mult = physical_mult(g);
+        out_mult = make_float4(1.f, on1, on1, 0.f);
         float k[3];
         for (int c = 0; c < 3; ++c) k[c] = (float)(1.0 / ((double)g->scale[c] * g->scale[c]));
-        reg2 = make_float4(2.f * g->lambda[0] * k[0], 2.f * g->lambda[1] * k[1],
-                           2.f * g->lambda[2] * k[2], 0.f);
-        reg1 = make_float4(g->lambda[0] * k[0], g->lambda[1] * k[1], g->lambda[2] * k[2], 0.f);
+        reg2 = make_float4(2.f * g->lambda[0] * k[0], on1 * 2.f * g->lambda[1] * k[1],
+                           on1 * 2.f * g->lambda[2] * k[2], 0.f);
+        reg1 = make_float4(g->lambda[0] * k[0], on1 * g->lambda[1] * k[1],
+                           on1 * g->lambda[2] * k[2], 0.f);
     }
-    EI_CUDA_TRY(counted_prep(g, v, mult, active, st));
+    EI_CUDA_TRY(counted_prep(g, v, mult, linked, active, st));
     EI_CUDA_TRY(traced_project(g, g->proj, active, st));
     EI_CUDA_TRY(traced_ic(g, g->proj, meas, nullptr, g->part_ic,
                           grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, active, st));
     EI_CUDA_TRY(traced_backproject(g, grad != nullptr, v, grad, out_mult, reg2, reg1,
-                                   g->part_adj, active, st));
+                                   linked ? gam : 0.f, g->part_adj, active, st));
     count_launches(g, 1);
     EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, g->part_adj, S_dev, active, st));
     return cudaSuccess;
@@ -356,6 +372,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         si.inv_pitch = (float)(1.0 / q.pitch_cm);
         si.ang_off = ang_off;
         si.pix_off = pix_off;
+        si.det_off = (int)pix_in_off;
         // zero margin of the packed gradient-sinogram rows: every voxel of the adjoint's
         // (padded) tile grid projects within [hd - R, hd + R] pixels
         {
@@ -601,7 +618,7 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
     const int reps_ = reps;
     (void)reps_;
     auto launch = [&]() {
-        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero,
+        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero, 0.f,
                                             g->part_adj, nullptr, st)
                        : launch_project(g, g->proj, nullptr, st);
     };
@@ -722,7 +739,8 @@ int ei_project(const ei_geometry *gc, const float *vol, float *proj, void *strea
     if (!gc || !vol || !proj || !aligned16(vol) || !aligned16(proj)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), nullptr, st);
+    cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), false,
+                                 nullptr, st);
     if (e == cudaSuccess) e = traced_project(g, proj, nullptr, st);
     return status_from(e);
 }
@@ -736,7 +754,7 @@ int ei_backproject(const ei_geometry *gc, const float *sino4, float *vol, void *
     count_launches(g, 1);
     cudaError_t e = launch_pack_sino(g, (const float4 *)sino4, st);
     if (e == cudaSuccess)
-        e = traced_backproject(g, true, nullptr, (float4 *)vol, one, zero, zero, g->part_adj,
+        e = traced_backproject(g, true, nullptr, (float4 *)vol, one, zero, zero, 0.f, g->part_adj,
                                nullptr, st);
     return status_from(e);
 }
@@ -758,8 +776,8 @@ int ei_single_shot_fbp(const ei_geometry *gc, const float *s_exp, float *vol_out
     count_launches(g, 1);
     cudaError_t e = launch_single_shot(g, s_exp, st);
     if (e == cudaSuccess)
-        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, g->part_adj,
-                               nullptr, st);
+        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, 0.f,
+                               g->part_adj, nullptr, st);
     return status_from(e);
 }
 
@@ -768,10 +786,43 @@ int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stre
     if (!gc || !vol || !s_mod || !aligned16(vol) || !aligned16(s_mod)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), nullptr, st);
+    cudaError_t e = counted_prep(g, (const float4 *)vol, physical_mult(g), g->link_gamma > 0.f,
+                                 nullptr, st);
     if (e == cudaSuccess) e = traced_project(g, g->proj, nullptr, st);
     if (e == cudaSuccess)
         e = traced_ic(g, g->proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr, st);
+    return status_from(e);
+}
+
+int ei_set_linked(ei_geometry *g, double gamma)
+{
+    if (!g || !(gamma >= 0.0) || !isfinite(gamma)) return EI_ERR_ARG;
+    g->link_gamma = (float)gamma;
+    return EI_OK;
+}
+
+int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *g_mo, float *g_mr,
+                   void *stream)
+{
+    if (!g || !vol || !s_exp || !aligned16(vol) || !aligned16(s_exp)) return EI_ERR_ARG;
+    if (!g_mo && !g_mr) return EI_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!g->shift_scratch) {
+        e = dev_alloc(g, &g->shift_scratch, (size_t)g->sino4_count);
+        if (e == cudaSuccess) e = dev_alloc(g, &g->row_sums, (size_t)std::max(1, g->dg.total_ic));
+        if (e != cudaSuccess) {
+            record_error(e);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+        }
+    }
+    e = counted_prep(g, (const float4 *)vol, physical_mult(g), g->link_gamma > 0.f, nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, g->proj, nullptr, st);
+    if (e == cudaSuccess) {
+        count_launches(g, 2);
+        e = launch_offset_grads(g, g->proj, s_exp, g->shift_scratch, g->row_sums, g_mo, g_mr, st);
+    }
     return status_from(e);
 }
 

@@ -18,6 +18,7 @@ struct SliceInfo {
     int pix_off;             // first pixel of the slice in the pixel table (n_dp stride)
     int marg;                // zero entries on each side of a packed gradient-sinogram row
     int gw;                  // packed gradient-sinogram row width: n_dp + 2 marg entries
+    int det_off;             // first pixel of the slice in per-pixel user arrays (n_det stride)
     int64_t vol_off;         // float4 elements (vol layout)
     int64_t pp_off;          // entries of the packed volume copies: n rows of n + 1
     int64_t gp_off;          // entries of the packed gradient sinogram: n_theta rows of gw
@@ -155,6 +156,9 @@ struct ei_geometry {
     int adj_totals[ei::N_ADJ_VARIANTS] = {};
     bool persistent = false;
     int ic_variant = 0;                // 0: one block per row; 1: persistent, bulk-copy pipeline
+    float link_gamma = 0.f;            // > 0: linked unknown h (mu = h, delta = gamma h, sigma = 0)
+    float *shift_scratch = nullptr;    // [sino4_count] dS/dshift (ei_offset_grad, allocated on use)
+    double *row_sums = nullptr;        // [total_ic]
     int *dev_status = nullptr;         // [1] device-side error status (bounded waits)
     int num_sms = 0;
     int *work_counter = nullptr;       // [2] work counters of the persistent kernels
@@ -180,8 +184,8 @@ void trace_end(ei_geometry *g, TracedKernel k, cudaEvent_t begin, cudaStream_t s
 
 // Kernel launchers (each returns cudaGetLastError()).
 // Packed volume copies of mult * vol (row-major and transposed) in the workspace.
-cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, const int *active,
-                        cudaStream_t st);
+cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bool linked,
+                        const int *active, cudaStream_t st);
 // proj = R[x] from the packed copies.
 cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st);
 // IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram.
@@ -197,9 +201,17 @@ cudaError_t single_shot_set_smem_limit();
 cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
 // out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial
 // sums of sum_c reg1_c v_c^2.  with_sino == false: only the regulariser (out not written).
+// link > 0 (the linked unknown h of Eq. 4): out = (out_mult.x (R^T g_mu + link R^T g_delta)
+// + reg2.x v.x, 0, 0, 0) and the partial sums take the mu lane only.
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
-                               float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                               float4 *out, float4 out_mult, float4 reg2, float4 reg1, float link,
                                double *part, const int *active, cudaStream_t st);
+// dS/dshift per sinogram pixel into shift (sino layout, one float per pixel) and its
+// FP64 sum over each row into row_sum; then per slice dS/dm_o (the row sums) into
+// g_mo [sum n_theta] and dS/dm_r (FP64 sums over angles) into g_mr [sum n_det].
+cudaError_t launch_offset_grads(const ei_geometry *g, const float *proj, const float *meas,
+                                float *shift, double *row_sum, float *g_mo, float *g_mr,
+                                cudaStream_t st);
 // S[s] = sum of part_ic over the slice's rows + sum of part_adj over its tiles.
 cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_ic,
                                       const double *part_adj, double *S, const int *active,

@@ -63,7 +63,7 @@ template <int PASSES, bool QUAD>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
     double *__restrict__ part, const int *__restrict__ active)
 {
     constexpr int TR = 8 * PASSES;
@@ -141,12 +141,20 @@ __device__ __forceinline__ void backproject_item(
         if (r < n && c < n) {
             const int64_t idx = si.vol_off + (int64_t)r * n + c;
             const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-            regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
-                    (double)(reg1.z * x.z * x.z);
-            if (with_sino && out != nullptr)
-                out[idx] = make_float4(fmaf(out_mult.x, acc[p][0], reg2.x * x.x),
-                                       fmaf(out_mult.y, acc[p][1], reg2.y * x.y),
-                                       fmaf(out_mult.z, acc[p][2], reg2.z * x.z), 0.f);
+            if (link > 0.f) {
+                // linked unknown h in the mu lane: dS/dh = R^T g_mu + link R^T g_delta
+                regv += (double)(reg1.x * x.x * x.x);
+                if (with_sino && out != nullptr)
+                    out[idx] = make_float4(fmaf(out_mult.x, fmaf(link, acc[p][1], acc[p][0]),
+                                                reg2.x * x.x), 0.f, 0.f, 0.f);
+            } else {
+                regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
+                        (double)(reg1.z * x.z * x.z);
+                if (with_sino && out != nullptr)
+                    out[idx] = make_float4(fmaf(out_mult.x, acc[p][0], reg2.x * x.x),
+                                           fmaf(out_mult.y, acc[p][1], reg2.y * x.y),
+                                           fmaf(out_mult.z, acc[p][2], reg2.z * x.z), 0.f);
+            }
         }
     }
     const double tot = block_sum_double_adj(regv, sh.red);
@@ -157,12 +165,12 @@ template <int PASSES, int MINB, bool QUAD>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
               const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
+              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
               double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
     backproject_item<PASSES, QUAD>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
-                                   out_mult, reg2, reg1, part, active);
+                                   out_mult, reg2, reg1, link, part, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
@@ -172,8 +180,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
                          bool with_sino, const float4 *__restrict__ v, float4 *__restrict__ out,
-                         float4 out_mult, float4 reg2, float4 reg1, double *__restrict__ part,
-                         const int *__restrict__ active)
+                         float4 out_mult, float4 reg2, float4 reg1, float link,
+                         double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
     __shared__ int s_item;
@@ -184,21 +192,21 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         const int item = s_item;
         if (item >= total) return;
         backproject_item<PASSES, QUAD>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
-                                       reg2, reg1, part, active);
+                                       reg2, reg1, link, part, active);
     }
 }
 
 template <int P, int M, bool Q>
 static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const float4 *v,
                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                     double *part, const int *active, cudaStream_t st)
+                                     float link, double *part, const int *active, cudaStream_t st)
 {
     const AdjVariant &av = g->adj_variant;
     if (av.total == 0) return cudaSuccess;
     if (!g->persistent) {
         k_backproject<P, M, Q><<<av.total, ADJ_THREADS, 0, st>>>(g->dg, av.prefix, g->gA, g->gB,
                                                               with_sino, v, out, out_mult, reg2,
-                                                              reg1, part, active);
+                                                              reg1, link, part, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
@@ -208,21 +216,21 @@ static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
         k_backproject_persistent<P, M, Q><<<grid, ADJ_THREADS, 0, st>>>(
             g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
-            out_mult, reg2, reg1, part, active);
+            out_mult, reg2, reg1, link, part, active);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
-                               float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                               float4 *out, float4 out_mult, float4 reg2, float4 reg1, float link,
                                double *part, const int *active, cudaStream_t st)
 {
     switch (g->adj_variant.id) {
-    case 0: return launch_bp_variant<8, 4, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    case 1: return launch_bp_variant<4, 1, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    case 2: return launch_bp_variant<16, 2, false>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    case 3: return launch_bp_variant<8, 4, true>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
-    default: return launch_bp_variant<16, 2, true>(g, with_sino, v, out, out_mult, reg2, reg1, part, active, st);
+    case 0: return launch_bp_variant<8, 4, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 1: return launch_bp_variant<4, 1, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 2: return launch_bp_variant<16, 2, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 3: return launch_bp_variant<8, 4, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    default: return launch_bp_variant<16, 2, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
     }
 }
 

@@ -559,6 +559,89 @@ static cudaError_t ic_pipe_set_smem_limit()
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Gradient with respect to Eq. 4's drift m_o(theta) and ring term m_r(t).
+// Both add to the shift of pixel (theta, t) with coefficient 1, so the
+// gradients are sums of dS/dshift = sum_m 2 e s q / V over t (m_o) and over
+// theta (m_r).  k_shift_grad: one block per row, dS/dshift of every pixel
+// into `shift` (sino layout) and the row's FP64 sum into row_sum;
+// k_offset_sums: one block per slice, FP64 sums over the slice's angles in
+// angle order.  Deterministic; not on the solver's path.
+// ---------------------------------------------------------------------------
+__global__ void k_shift_grad(DevGeom dg, const float *__restrict__ proj,
+                             const float *__restrict__ meas, float *__restrict__ shift,
+                             double *__restrict__ row_sum)
+{
+    extern __shared__ float s_pd[];                   // R[delta] of the row
+    __shared__ double red[32];
+    const int row = blockIdx.x;
+    const int s = find_slice(dg.ic_prefix, dg.n_slices, row);
+    const SliceInfo si = dg.slices[s];
+    const int a = row - dg.ic_prefix[s];
+    const int nd = si.n_det, ndp = si.n_dp;
+    const int64_t plane = (int64_t)si.n_theta * ndp, rbase = (int64_t)a * ndp;
+    const float *Pm = proj + si.proj_off + rbase;
+    const float *Ps = Pm + 2 * plane;
+    const float *Sx = meas + si.meas_off + rbase;
+    for (int j = threadIdx.x; j < ndp; j += blockDim.x) s_pd[j] = Pm[plane + j];
+    __syncthreads();
+    const float4 *pix = dg.pix + si.pix_off;
+    const float mo = dg.m_o[si.ang_off + a];
+    const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < ndp; j += blockDim.x) {
+        float g = 0.f;
+        if (j < nd) {
+            const float4 fl = __ldg(pix + j);           // A, c, w, m_r
+            const float cs = fl.y + zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w;
+            const float Vs = fmaxf(fmaf(kappa, Ps[j], fl.z * fl.z), 1e-30f);
+            const float iV = 1.0f / Vs;
+            const float amp = fl.x * fl.z * rsqrtf(Vs);
+            const float pm = Pm[j];
+            float stq = 0.f;
+            for (int k = 0; k < dg.mc.n_m; ++k) {
+                const float q = dg.mc.m[k] - cs;
+                const float sv = amp * expf(-pm - 0.5f * q * q * iV);
+                stq = fmaf((sv - Sx[k * plane + j]) * sv, q, stq);
+            }
+            g = 2.f * stq * iV;
+        }
+        shift[si.sino_off + rbase + j] = g;
+        acc += (double)g;
+    }
+    const double tot = block_sum_double(acc, red);
+    if (threadIdx.x == 0) row_sum[row] = tot;
+}
+
+__global__ void k_offset_sums(DevGeom dg, const float *__restrict__ shift,
+                              const double *__restrict__ row_sum, float *__restrict__ g_mo,
+                              float *__restrict__ g_mr)
+{
+    const SliceInfo si = dg.slices[blockIdx.x];
+    const int r0 = dg.ic_prefix[blockIdx.x];
+    if (g_mo)
+        for (int a = threadIdx.x; a < si.n_theta; a += blockDim.x)
+            g_mo[si.ang_off + a] = (float)row_sum[r0 + a];
+    if (g_mr)
+        for (int j = threadIdx.x; j < si.n_det; j += blockDim.x) {
+            double acc = 0.0;
+            for (int a = 0; a < si.n_theta; ++a) acc += (double)shift[si.sino_off + (int64_t)a * si.n_dp + j];
+            g_mr[si.det_off + j] = (float)acc;
+        }
+}
+
+cudaError_t launch_offset_grads(const ei_geometry *g, const float *proj, const float *meas,
+                                float *shift, double *row_sum, float *g_mo, float *g_mr,
+                                cudaStream_t st)
+{
+    if (g->dg.total_ic == 0) return cudaSuccess;
+    k_shift_grad<<<g->dg.total_ic, 256, (size_t)g->dg.max_ndp * sizeof(float), st>>>(
+        g->dg, proj, meas, shift, row_sum);
+    EI_CUDA_TRY(cudaGetLastError());
+    k_offset_sums<<<g->n_slices, 256, 0, st>>>(g->dg, shift, row_sum, g_mo, g_mr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
                       double *part, IcMode mode, const int *active, cudaStream_t st)
 {

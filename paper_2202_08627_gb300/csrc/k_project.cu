@@ -30,12 +30,14 @@
 namespace ei {
 
 // --------------------------------------------------------------------------
-// Staging: packed row-major and transposed copies of mult * vol.
-// One block per 32 x 32 tile of entries; the tile loads the voxels it needs
-// (with a one-voxel halo above and to the left) into shared memory.
+// Staging: packed row-major and transposed copies of mult * vol, or with
+// `linked` (the single unknown h of Eq. 4 in the mu lane) of
+// (mult.x h, mult.y h, 0).  One block per 32 x 32 tile of entries; the tile
+// loads the voxels it needs (with a one-voxel halo above and to the left)
+// into shared memory.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(PREP_TILE * 8)
-k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restrict__ xpA,
+k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, bool linked, float4 *__restrict__ xpA,
        float2 *__restrict__ xpB, float4 *__restrict__ xtA, float2 *__restrict__ xtB,
        const int *__restrict__ active)
 {
@@ -57,7 +59,8 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, float4 *__restri
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r >= 0 && r < n && c >= 0 && c < n) {
                 const float4 q = v[(int64_t)r * n + c];
-                val = make_float4(q.x * mult.x, q.y * mult.y, q.z * mult.z, 0.f);
+                val = linked ? make_float4(q.x * mult.x, q.x * mult.y, 0.f, 0.f)
+                             : make_float4(q.x * mult.x, q.y * mult.y, q.z * mult.z, 0.f);
             }
             T[y][x] = val;
         }
@@ -262,11 +265,11 @@ static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, const int *active,
-                        cudaStream_t st)
+cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bool linked,
+                        const int *active, cudaStream_t st)
 {
     if (g->dg.total_prep == 0) return cudaSuccess;
-    k_prep<<<g->dg.total_prep, dim3(PREP_TILE, 8), 0, st>>>(g->dg, vol, mult, g->xpA, g->xpB,
+    k_prep<<<g->dg.total_prep, dim3(PREP_TILE, 8), 0, st>>>(g->dg, vol, mult, linked, g->xpA, g->xpB,
                                                              g->xtA, g->xtB, active);
     return cudaGetLastError();
 }

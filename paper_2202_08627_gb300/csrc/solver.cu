@@ -140,7 +140,8 @@ __global__ void k_to_scaled(DevGeom dg, const float4 *__restrict__ x0, float4 *_
     const VecBlock b = vec_block(dg);
     for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
         const float4 x = x0[i];
-        u[i] = f4(x.x * inv.x, x.y * inv.y, x.z * inv.z);
+        // a zero factor clears its lane (linked mode ignores the delta and sigma lanes)
+        u[i] = f4(x.x * inv.x, inv.y != 0.f ? x.y * inv.y : 0.f, inv.z != 0.f ? x.z * inv.z : 0.f);
     }
 }
 
@@ -543,8 +544,10 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     const DevGeom &dg = g->dg;
     const int NB = dg.total_vec;
     const int T = VEC_THREADS;
-    const float4 inv = make_float4(1.f / g->scale[0], 1.f / g->scale[1], 1.f / g->scale[2], 0.f);
-    const float4 sc = make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
+    // linked mode iterates on h alone: the other lanes of u start and stay at 0
+    const float on1 = g->link_gamma > 0.f ? 0.f : 1.f;
+    const float4 inv = make_float4(1.f / g->scale[0], on1 / g->scale[1], on1 / g->scale[2], 0.f);
+    const float4 sc = make_float4(g->scale[0], on1 * g->scale[1], on1 * g->scale[2], 0.f);
     Opts o{opts->tol, opts->c1, opts->curv_eps, opts->max_iter, opts->max_trials};
     const int scalar_threads = 256;
 

@@ -90,7 +90,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_get_variant", "ei_last_error", "ei_single_shot_fbp", "ei_unet_create",
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
-            "ei_get_ic_variant", "ei_measure_peaks"]
+            "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad"]
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
 
@@ -141,6 +141,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_set_linked.argtypes = [c_void_p, c_double]
+    lib.ei_set_linked.restype = c_int
+    lib.ei_offset_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.ei_offset_grad.restype = c_int
     lib.ei_measure_peaks.argtypes = [P(ei_peaks), c_void_p]
     lib.ei_measure_peaks.restype = c_int
     lib.ei_set_ic_variant.argtypes = [c_void_p, c_int]
@@ -577,6 +581,32 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+def ei_set_linked(geom: Geometry, gamma: float) -> None:
+    """Linked single unknown of Eq. 4 (mu = h, delta = gamma h, sigma = 0); 0 = off."""
+    _check(load_library().ei_set_linked(geom.handle, float(gamma)), "ei_set_linked")
+
+
+def ei_offset_grad(geom: Geometry, vol, s_exp, g_mo=None, g_mr=None, stream=None):
+    """dS/dm_o [sum n_theta] and dS/dm_r [sum n_det] (float32 device tensors,
+    allocated when not given); returns (g_mo, g_mr)."""
+    import torch
+    n_th = sum(sl.n_theta for sl in geom.slices)
+    n_px = sum(sl.n_det for sl in geom.slices)
+    dev = vol.device
+    if g_mo is None:
+        g_mo = torch.empty(n_th, dtype=torch.float32, device=dev)
+    if g_mr is None:
+        g_mr = torch.empty(n_px, dtype=torch.float32, device=dev)
+    _check_size(vol, geom.vol_count * 4, "vol")
+    _check_size(s_exp, geom.meas_count, "s_exp")
+    _check_size(g_mo, n_th, "g_mo")
+    _check_size(g_mr, n_px, "g_mr")
+    _check(load_library().ei_offset_grad(geom.handle, _dptr(vol, "vol"), _dptr(s_exp, "s_exp"),
+                                         _dptr(g_mo, "g_mo"), _dptr(g_mr, "g_mr"),
+                                         _stream_ptr(stream)), "ei_offset_grad")
+    return g_mo, g_mr
 
 
 def ei_measure_peaks(stream=None) -> dict:

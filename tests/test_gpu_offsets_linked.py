@@ -1,0 +1,155 @@
+"""The terms of Eq. 4 beyond the three-channel model on the GPU, against the
+FP64 oracle: the gradient with respect to the drift m_o(theta) and the ring
+term m_r(t) (ei_offset_grad), the gauge ambiguity the paper points out for
+them, and the linked single unknown h (mu = h, delta = gamma h, sigma = 0;
+ei_set_linked) through ei_forward, ei_objective_grad and ei_reconstruct."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_08627_gb300 import inputs
+from tests.problems import gpu_geometry, measured, oracle_geometry, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GAMMA = 5e-7          # delta / mu in cm: mu in [0, 2] / cm gives delta in [0, 1e-6]
+SHAPES = [(64, 90, 96, 5), (37, 23, 61, 5), (128, 180, 192, 5), (20, 7, 131, 5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2202_08627_gb300 import build
+    build.build()
+
+
+def _with_offsets(shapes, seed0, shift=0.0):
+    probs = []
+    for i, sh in enumerate(shapes):
+        spec = inputs.make_slice(seed0 + i, *sh)
+        m_o = inputs.uniform_noise(spec.n_theta, seed0 + 100 + i, -0.04, 0.04) + shift
+        m_r = inputs.uniform_noise(spec.n_det, seed0 + 200 + i, -0.04, 0.04) - shift
+        geom = oracle_geometry(spec, m_o=m_o, m_r=m_r)
+        probs.append((spec, geom, measured(spec, geom)))
+    return probs
+
+
+def test_offset_gradients_match_oracle():
+    from paper_2202_08627_gb300 import ei
+    probs = _with_offsets(SHAPES, 300)
+    specs, geoms, meas = zip(*probs)
+    G = gpu_geometry(list(specs), list(geoms))
+    xs = [sp.truth * 0.9 for sp in specs]
+    g_mo, g_mr = ei.ei_offset_grad(G, G.pack_volume(xs), G.pack_meas(meas))
+    g_mo, g_mr = g_mo.cpu().numpy(), g_mr.cpu().numpy()
+    o_th = o_px = 0
+    for (spec, geom, s_exp), x in zip(probs, xs):
+        r_mo, r_mr = oracle.offset_grads(x, s_exp, geom)
+        assert rel_l2(g_mo[o_th:o_th + spec.n_theta], r_mo) <= 1e-4, (spec.n, "m_o")
+        assert rel_l2(g_mr[o_px:o_px + spec.n_det], r_mr) <= 1e-4, (spec.n, "m_r")
+        o_th += spec.n_theta
+        o_px += spec.n_det
+
+
+def test_gauge_ambiguity_on_the_gpu():
+    """(m_o + a, m_r - a) leaves S unchanged, and the two gradients have the
+    same sum (the derivative of that invariance)."""
+    from paper_2202_08627_gb300 import ei
+    a, b = _with_offsets(SHAPES[:2], 400), _with_offsets(SHAPES[:2], 400, shift=0.0371)
+    Ga = gpu_geometry([p[0] for p in a], [p[1] for p in a])
+    Gb = gpu_geometry([p[0] for p in b], [p[1] for p in b])
+    xs = [p[0].truth * 1.05 for p in a]
+    meas = [p[2] for p in a]                     # the same measured data for both
+    S = torch.zeros(2, 2, dtype=torch.float64, device="cuda")
+    ei.ei_objective_grad(Ga, Ga.pack_volume(xs), Ga.pack_meas(meas), S[0], None)
+    ei.ei_objective_grad(Gb, Gb.pack_volume(xs), Gb.pack_meas(meas), S[1], None)
+    S = S.cpu().numpy()
+    np.testing.assert_allclose(S[1], S[0], rtol=1e-6)
+    g_mo, g_mr = ei.ei_offset_grad(Ga, Ga.pack_volume(xs), Ga.pack_meas(meas))
+    g_mo, g_mr = g_mo.cpu().numpy().astype(np.float64), g_mr.cpu().numpy().astype(np.float64)
+    o_th = o_px = 0
+    for spec, _, _ in a:
+        s_mo, s_mr = g_mo[o_th:o_th + spec.n_theta].sum(), g_mr[o_px:o_px + spec.n_det].sum()
+        assert abs(s_mo - s_mr) <= 1e-4 * np.abs(g_mo[o_th:o_th + spec.n_theta]).sum()
+        o_th += spec.n_theta
+        o_px += spec.n_det
+
+
+def _linked_problems(shapes, seed0):
+    """Measured ICs of a linked phantom: P = (R h, gamma R h, 0) from the exact
+    line integrals of the attenuation phantom h."""
+    probs = []
+    for i, sh in enumerate(shapes):
+        spec = inputs.make_slice(seed0 + i, *sh)
+        geom = oracle_geometry(spec, m_o=inputs.uniform_noise(spec.n_theta, seed0 + 7 + i, -0.02, 0.02))
+        Ph = spec.P_exact[0]
+        P = np.stack([Ph, GAMMA * Ph, np.zeros_like(Ph)])
+        s_exp = inputs.poisson_noise(oracle.ic_model(P, geom), spec.seed)
+        probs.append((spec, geom, s_exp))
+    return probs
+
+
+def test_linked_objective_gradient_and_forward_match_oracle():
+    from paper_2202_08627_gb300 import ei
+    probs = _linked_problems(SHAPES, 500)
+    specs, geoms, meas = zip(*probs)
+    G = gpu_geometry(list(specs), list(geoms))
+    ei.ei_set_linked(G, GAMMA)
+    hs = [sp.truth[0] * 0.9 for sp in specs]
+    # the delta and sigma lanes are ignored in linked mode
+    vols = [np.stack([h, np.full_like(h, 123.0), np.full_like(h, -7.0)]) for h in hs]
+    vol = G.pack_volume(vols)
+    S = torch.zeros(G.n_slices, dtype=torch.float64, device="cuda")
+    grad = G.empty("vol")
+    ei.ei_objective_grad(G, vol, G.pack_meas(meas), S, grad)
+    s_mod = G.empty("meas")
+    ei.ei_forward(G, vol, s_mod)
+    torch.cuda.synchronize()
+    gv = grad.cpu().numpy()
+    gs = G.unpack_volume(grad)
+    sm = G.unpack_meas(s_mod)
+    for i, ((spec, geom, s_exp), h) in enumerate(zip(probs, hs)):
+        S_ref, g_ref = oracle.objective_grad_linked(h, s_exp, geom, GAMMA)
+        assert abs(S[i].item() - S_ref) <= 1e-5 * abs(S_ref), (i, S[i].item(), S_ref)
+        assert rel_l2(gs[i][0], g_ref) <= 1e-4, (i, rel_l2(gs[i][0], g_ref))
+        assert not np.any(gs[i][1:]), i
+        x = np.stack([h, GAMMA * h, np.zeros_like(h)])
+        assert rel_l2(sm[i], oracle.forward(x, geom)) <= 1e-5
+    assert not np.any(gv[:, 3])
+
+
+def test_linked_reconstruct_matches_oracle_trajectory():
+    """20 L-BFGS iterations on the linked unknown from h = 0: the final
+    objective agrees with the FP64 oracle's within 1e-4 relative, and the
+    solution keeps the delta and sigma lanes at zero."""
+    from paper_2202_08627_gb300 import ei
+    (spec, geom, s_exp), = _linked_problems([(64, 90, 96, 7)], 600)
+    G = gpu_geometry([spec], [geom])
+    ei.ei_set_linked(G, GAMMA)
+    vol = G.pack_volume([np.stack([np.zeros((64, 64)), np.full((64, 64), 5.0), np.ones((64, 64))])])
+    rep = ei.ei_reconstruct(G, G.pack_meas([s_exp]), vol, tol=0.0, max_iter=20)
+
+    def fun(u):
+        return oracle.objective_grad_linked(u, s_exp, geom, GAMMA, scaled=True)
+
+    u_ref, rep_ref = oracle.lbfgs(fun, np.zeros((64, 64)), oracle.SolveOptions(tol=0.0, max_iter=20))
+    assert rep.iterations[0] == rep_ref.iterations == 20
+    assert abs(rep.f_initial[0] - rep_ref.f_history[0]) <= 1e-5 * rep_ref.f_history[0]
+    assert abs(rep.f_final[0] - rep_ref.f_history[-1]) <= 1e-4 * rep_ref.f_history[-1], \
+        (rep.f_final[0], rep_ref.f_history[-1])
+    out = G.unpack_volume(vol)[0]
+    assert not np.any(out[1:])
+    assert rep.f_final[0] < rep.f_initial[0]
+
+
+def test_set_linked_rejects_bad_gamma():
+    from paper_2202_08627_gb300 import ei
+    (spec, geom, _), = _linked_problems([(16, 8, 24, 3)], 700)
+    G = gpu_geometry([spec], [geom])
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(ei.EIError):
+            ei.ei_set_linked(G, bad)
+    ei.ei_set_linked(G, 0.0)
