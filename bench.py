@@ -205,7 +205,7 @@ def train_warm_start(args, wl, device):
         net.load(args.cnn_weights)
         return net, {"weights": args.cnn_weights}
     shapes = [wl.slices[i % wl.n_slices] for i in range(args.cnn_pairs)]
-    if wl.name == "uneven1024":
+    if wl.name in ("uneven1024", "pure1024"):
         shapes = warmstart.shapes_for("uneven1024", args.cnn_pairs, 6)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -218,6 +218,8 @@ def train_warm_start(args, wl, device):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     del pairs
+    if args.cnn_save:
+        net.save(args.cnn_save)
     return net, {"pairs": len(shapes), "pair_generation_s": t1 - t0, "training_s": t2 - t1,
                  "epochs": args.cnn_epochs, "steps_per_epoch": 256, "batch": 16, "crop": 256,
                  "pair_iterations_mean": float(it.mean()), "loss_first": hist[0],
@@ -537,6 +539,7 @@ def main():
     ap.add_argument("--cnn-pairs", type=int, default=256)
     ap.add_argument("--cnn-epochs", type=int, default=20)
     ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")
+    ap.add_argument("--cnn-save", default=None, help="write the trained parameters (.npy)")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
     ap.add_argument("--profile-evals", type=int, default=0,

@@ -11,6 +11,7 @@ to the phantom's exact line integrals, plus Poisson noise at 1e4 counts.
   uneven1024   256 slices, half 1024x1024 and half 512x512 (interleaved), 1800
                angles, detector pixels drawn per slice from {1024, 1152, 1280,
                1408, 1536}, M = 7 (about 16.5 GB of measured ICs)
+  pure1024     the 128 slices of 1024x1024 of uneven1024
   single1024   one 1024x1024 slice of that shape (1800 angles, 1536 pixels,
                M = 7)
   batch8x1024  eight such slices: the case the kernel profiles are captured on
@@ -88,6 +89,13 @@ def uneven1024(seed: int = 5) -> Workload:
                     "1024-1536 detector pixels per slice, M=7", slices, 7)
 
 
+def pure1024(seed: int = 5) -> Workload:
+    """The 1024x1024 half of uneven1024 (same seeds for the detector widths)."""
+    sl = [s for s in uneven1024(seed).slices if s[0] == 1024]
+    return Workload("pure1024", "the 128 slices of 1024x1024 of the uneven batch, 1800 angles, "
+                    "1024-1536 detector pixels per slice, M=7", sl, 7)
+
+
 def single1024() -> Workload:
     return Workload("single1024", "one 1024x1024 slice, 1800 angles, 1536 pixels, M=7",
                     [(1024, 1800, 1536)], 7)
@@ -99,7 +107,8 @@ def batch8x1024() -> Workload:
 
 
 WORKLOADS = {"small": small, "batch256": batch256, "check128": check128,
-             "uneven1024": uneven1024, "single1024": single1024, "batch8x1024": batch8x1024}
+             "uneven1024": uneven1024, "pure1024": pure1024, "single1024": single1024,
+             "batch8x1024": batch8x1024}
 
 
 def shard_slices(slices: List[Tuple[int, int, int]], world: int) -> List[List[int]]:
