@@ -328,6 +328,27 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
                    void *stream);
 
 /*
+ * Eq. 4's offsets as unknowns of ei_reconstruct (the paper minimises S over
+ * h, m_o and m_r together).  which = EI_OFFSET_MO | EI_OFFSET_MR selects the
+ * drift m_o(theta) and / or the ring term m_r(t) of every slice; the solver
+ * iterates on m / scale (scale > 0, in IC periods) starting from the
+ * geometry's current values (ei_setup_geometry's m_o / m_r, per slice), and
+ * leaves the solution's offsets in the geometry, where every later call uses
+ * them and ei_get_offsets reads them.  When both are unknowns, the gauge
+ * (m_o + a, m_r - a), which leaves S unchanged, is fixed by keeping the mean
+ * of m_r over each slice's pixels at its starting value (its gradient is
+ * projected onto zero mean).  which = 0 restores fixed offsets.  Each solver
+ * evaluation then also computes dS/dshift per pixel (one more pass over the
+ * projections and measured ICs).
+ */
+#define EI_OFFSET_MO 1
+#define EI_OFFSET_MR 2
+int ei_set_offset_unknowns(ei_geometry *g, int which, double scale);
+/* The geometry's current m_o [sum n_theta] and m_r [sum n_det], per slice in
+ * slice order, into host or device arrays (either may be NULL).  Synchronous. */
+int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r);
+
+/*
  * On-chip throughput of the current GPU, measured by microbenchmarks (each the
  * best of three CUDA-event-timed runs after a warm-up; ~10 ms in all): the
  * FP32 FMA rate (2 flops per FMA), the rate at which 16-byte global loads that

@@ -807,6 +807,38 @@ int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stre
     return status_from(e);
 }
 
+int ei_set_offset_unknowns(ei_geometry *g, int which, double scale)
+{
+    if (!g || (which & ~(EI_OFFSET_MO | EI_OFFSET_MR)) || !(scale > 0.0) || !isfinite(scale))
+        return EI_ERR_ARG;
+    g->off_which = which;
+    g->off_scale = (float)scale;
+    return EI_OK;
+}
+
+int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r)
+{
+    if (!g) return EI_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    int n_th = 0;
+    for (const SliceInfo &si : g->h_slices) n_th += si.n_theta;
+    if (m_o) e = cudaMemcpy(m_o, g->dg.m_o, (size_t)n_th * sizeof(float), cudaMemcpyDefault);
+    if (m_r)
+        for (const SliceInfo &si : g->h_slices) {
+            if (e != cudaSuccess) break;
+            // the w lane of the slice's pixel table entries
+            e = cudaMemcpy2D(m_r + si.det_off, sizeof(float),
+                             reinterpret_cast<const char *>(g->dg.pix + si.pix_off) + 3 * sizeof(float),
+                             sizeof(float4), sizeof(float), (size_t)si.n_det, cudaMemcpyDefault);
+        }
+    if (e != cudaSuccess) {
+        record_error(e);
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    return EI_OK;
+}
+
 int ei_set_linked(ei_geometry *g, double gamma)
 {
     if (!g || !(gamma >= 0.0) || !isfinite(gamma)) return EI_ERR_ARG;

@@ -105,6 +105,12 @@ struct DevGeom {
     int total_ic, total_prep, total_vec;
     int max_ndp, max_n_theta;
     ModelConsts mc;
+    // solver view with Eq. 4's offsets among the unknowns (null otherwise): per
+    // slice vec_nvb[s] volume blocks then the blocks of an offsets segment of
+    // off_len[s] float4 starting at element off_start[s] of the solver vectors
+    const int *vec_nvb = nullptr;
+    const int64_t *off_start = nullptr;
+    const int *off_len = nullptr;
 };
 
 #ifdef __CUDACC__
@@ -157,6 +163,8 @@ struct ei_geometry {
     bool persistent = false;
     int ic_variant = 0;                // 0: one block per row; 1: persistent, bulk-copy pipeline
     float link_gamma = 0.f;            // > 0: linked unknown h (mu = h, delta = gamma h, sigma = 0)
+    int off_which = 0;                 // Eq. 4 offsets among the solver's unknowns (EI_OFFSET_*)
+    float off_scale = 1.f;             // their solver scaling u = m / off_scale
     float *shift_scratch = nullptr;    // [sino4_count] dS/dshift (ei_offset_grad, allocated on use)
     double *row_sums = nullptr;        // [total_ic]
     int *dev_status = nullptr;         // [1] device-side error status (bounded waits)
@@ -212,6 +220,10 @@ cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float
 cudaError_t launch_offset_grads(const ei_geometry *g, const float *proj, const float *meas,
                                 float *shift, double *row_sum, float *g_mo, float *g_mr,
                                 cudaStream_t st);
+// First half of the above for the slices with active[s] (all when null):
+// dS/dshift into shift, its row sums into row_sum.
+cudaError_t launch_shift_grad(const ei_geometry *g, const float *proj, const float *meas,
+                              float *shift, double *row_sum, const int *active, cudaStream_t st);
 // S[s] = sum of part_ic over the slice's rows + sum of part_adj over its tiles.
 cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_ic,
                                       const double *part_adj, double *S, const int *active,

@@ -570,12 +570,13 @@ static cudaError_t ic_pipe_set_smem_limit()
 // ---------------------------------------------------------------------------
 __global__ void k_shift_grad(DevGeom dg, const float *__restrict__ proj,
                              const float *__restrict__ meas, float *__restrict__ shift,
-                             double *__restrict__ row_sum)
+                             double *__restrict__ row_sum, const int *__restrict__ active)
 {
     extern __shared__ float s_pd[];                   // R[delta] of the row
     __shared__ double red[32];
     const int row = blockIdx.x;
     const int s = find_slice(dg.ic_prefix, dg.n_slices, row);
+    if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
     const int a = row - dg.ic_prefix[s];
     const int nd = si.n_det, ndp = si.n_dp;
@@ -635,10 +636,17 @@ cudaError_t launch_offset_grads(const ei_geometry *g, const float *proj, const f
                                 cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
-    k_shift_grad<<<g->dg.total_ic, 256, (size_t)g->dg.max_ndp * sizeof(float), st>>>(
-        g->dg, proj, meas, shift, row_sum);
-    EI_CUDA_TRY(cudaGetLastError());
+    EI_CUDA_TRY(launch_shift_grad(g, proj, meas, shift, row_sum, nullptr, st));
     k_offset_sums<<<g->n_slices, 256, 0, st>>>(g->dg, shift, row_sum, g_mo, g_mr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_grad(const ei_geometry *g, const float *proj, const float *meas,
+                              float *shift, double *row_sum, const int *active, cudaStream_t st)
+{
+    if (g->dg.total_ic == 0) return cudaSuccess;
+    k_shift_grad<<<g->dg.total_ic, 256, (size_t)g->dg.max_ndp * sizeof(float), st>>>(
+        g->dg, proj, meas, shift, row_sum, active);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,10 @@
 //
 // Vectors are the batched vol layout (float4 per voxel, pad lane kept at 0);
 // vector kernels work on VEC_BLK-element blocks that each belong to one slice
-// and write one FP64 partial dot product per block.  A consumer block sums its
+// and write one FP64 partial dot product per block.  With Eq. 4's offsets
+// among the unknowns, every vector continues after the volumes with one
+// offsets segment per slice (m_o(theta) then m_r(t), scaled by 1/off_scale,
+// three values per float4), whose blocks belong to their slice too.  A consumer block sums its
 // slice's partials itself in a fixed order (deterministic, no atomics); the
 // partial buffers alternate between launches so no kernel reads what it writes.
 #include <math.h>
@@ -39,7 +42,11 @@ struct SliceState {
 
 struct Solver {
     int m = 0, ring = 0;
-    int64_t vol_count = 0;
+    int64_t vol_count = 0;              // vector length in float4 (volumes + offsets)
+    int off_which = 0;                  // offsets among the unknowns (EI_OFFSET_* bits)
+    DevGeom dgx{};                      // solver view of the geometry (extended blocks)
+    float *shift = nullptr;             // [sino pixels] dS/dshift (offsets mode)
+    double *row_sum = nullptr;          // [rows]
     float4 *u = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
     float4 *Sr = nullptr, *Yr = nullptr;    // rings of `ring` slots
     float *meas_stage = nullptr;            // device copy of host s_exp
@@ -86,7 +93,13 @@ __device__ __forceinline__ VecBlock vec_block(const DevGeom &dg)
     b.s = find_slice(dg.vec_prefix, dg.n_slices, blockIdx.x);
     const SliceInfo &si = dg.slices[b.s];
     const int64_t nvox = (int64_t)si.n * si.n;
-    const int64_t lb = blockIdx.x - dg.vec_prefix[b.s];
+    int64_t lb = blockIdx.x - dg.vec_prefix[b.s];
+    if (dg.vec_nvb && lb >= dg.vec_nvb[b.s]) {        // a block of the slice's offsets segment
+        lb -= dg.vec_nvb[b.s];
+        b.begin = dg.off_start[b.s] + lb * VEC_BLK;
+        b.end = dg.off_start[b.s] + min((int64_t)dg.off_len[b.s], (lb + 1) * (int64_t)VEC_BLK);
+        return b;
+    }
     b.begin = si.vol_off + lb * VEC_BLK;
     b.end = si.vol_off + min(nvox, (lb + 1) * (int64_t)VEC_BLK);
     return b;
@@ -152,6 +165,95 @@ __global__ void k_from_scaled(DevGeom dg, const float4 *__restrict__ u, float4 *
     for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
         const float4 v = u[i];
         x[i] = f4(v.x * sc.x, v.y * sc.y, v.z * sc.z);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Eq. 4's offsets among the unknowns.  Offsets segment of slice s: element k
+// (k < n_mo: m_o of angle k; then m_r of pixel k - n_mo) is lane k % 3 of
+// float4 k / 3 from off_start[s].  One block per slice.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float &off_elem(float4 *v, int64_t start, int k)
+{
+    return reinterpret_cast<float *>(v + start + k / 3)[k % 3];
+}
+
+// u's offsets segments from the geometry's current m_o / m_r tables
+__global__ void k_offsets_to_u(DevGeom dg, int which, float inv_scale, float4 *__restrict__ u)
+{
+    const int s = blockIdx.x;
+    const SliceInfo si = dg.slices[s];
+    const int n_mo = (which & EI_OFFSET_MO) ? si.n_theta : 0;
+    const int n_mr = (which & EI_OFFSET_MR) ? si.n_det : 0;
+    const int64_t st = dg.off_start[s];
+    for (int i = threadIdx.x; i < dg.off_len[s]; i += blockDim.x) u[st + i] = f4(0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_mo + n_mr; k += blockDim.x)
+        off_elem(u, st, k) = (k < n_mo ? dg.m_o[si.ang_off + k] : dg.pix[si.pix_off + k - n_mo].w) *
+                             inv_scale;
+}
+
+// the geometry's m_o / m_r tables from the offsets segments of v (slices with
+// active[s], all when null): the model then evaluates at v's offsets
+__global__ void k_offsets_apply(DevGeom dg, int which, float scale, const float4 *__restrict__ v,
+                                const int *__restrict__ active)
+{
+    const int s = blockIdx.x;
+    if (active && !active[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int n_mo = (which & EI_OFFSET_MO) ? si.n_theta : 0;
+    const int n_mr = (which & EI_OFFSET_MR) ? si.n_det : 0;
+    float *m_o = const_cast<float *>(dg.m_o);
+    float4 *pix = const_cast<float4 *>(dg.pix);
+    float4 *vv = const_cast<float4 *>(v);
+    for (int k = threadIdx.x; k < n_mo + n_mr; k += blockDim.x) {
+        const float val = off_elem(vv, dg.off_start[s], k) * scale;
+        if (k < n_mo) m_o[si.ang_off + k] = val;
+        else pix[si.pix_off + k - n_mo].w = val;
+    }
+}
+
+// the offsets segments of the gradient gv: scale * dS/dm_o (row sums of
+// dS/dshift) and scale * dS/dm_r (FP64 sums over the slice's angles in
+// order), the latter minus its mean over the slice when both offsets are
+// unknowns (the gauge (m_o + a, m_r - a) leaves S unchanged, so the iteration
+// keeps the mean of m_r fixed)
+__global__ void k_offsets_grad(DevGeom dg, int which, float scale, const float *__restrict__ shift,
+                               const double *__restrict__ row_sum, float4 *__restrict__ gv,
+                               const int *__restrict__ active)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    if (active && !active[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int n_mo = (which & EI_OFFSET_MO) ? si.n_theta : 0;
+    const int n_mr = (which & EI_OFFSET_MR) ? si.n_det : 0;
+    const int64_t st = dg.off_start[s];
+    const int r0 = dg.ic_prefix[s];
+    for (int a = threadIdx.x; a < n_mo; a += blockDim.x)
+        off_elem(gv, st, a) = (float)(row_sum[r0 + a] * scale);
+    if (n_mr == 0) return;
+    double part = 0.0;
+    for (int j = threadIdx.x; j < n_mr; j += blockDim.x) {
+        double acc = 0.0;
+        for (int a = 0; a < si.n_theta; ++a) acc += (double)shift[si.sino_off + (int64_t)a * si.n_dp + j];
+        off_elem(gv, st, n_mo + j) = (float)acc;     // unscaled for now
+        part += acc;
+    }
+    // fixed-order block reduction of the column sums
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[0] = t;
+    }
+    __syncthreads();
+    const double mean = n_mo > 0 ? red[0] / n_mr : 0.0;
+    for (int j = threadIdx.x; j < n_mr; j += blockDim.x) {
+        float &e = off_elem(gv, st, n_mo + j);
+        e = (float)(((double)e - mean) * scale);
     }
 }
 
@@ -493,15 +595,52 @@ void destroy_solver(ei_geometry *g)
 
 static cudaError_t ensure_solver(ei_geometry *g, int m)
 {
-    if (g->solver && g->solver->m == m) return cudaSuccess;
+    if (g->solver && g->solver->m == m && g->solver->off_which == g->off_which) return cudaSuccess;
     destroy_solver(g);
     Solver *s = new Solver();
     g->solver = s;
     s->m = m;
     s->ring = m + 1;
-    s->vol_count = g->vol_count;
-    const size_t V = (size_t)g->vol_count, S = (size_t)g->n_slices;
-    const size_t NB = (size_t)g->dg.total_vec;
+    s->off_which = g->off_which;
+    s->dgx = g->dg;
+    int64_t ext = g->vol_count;
+    if (g->off_which) {
+        // the offsets segments after the volumes, and the solver's block table
+        std::vector<int> prefix(1, 0), nvb, len;
+        std::vector<int64_t> start;
+        for (int k = 0; k < g->n_slices; ++k) {
+            const SliceInfo &si = g->h_slices[k];
+            const int nv = g->h_vec_prefix[k + 1] - g->h_vec_prefix[k];
+            const int K = ((g->off_which & EI_OFFSET_MO) ? si.n_theta : 0) +
+                          ((g->off_which & EI_OFFSET_MR) ? si.n_det : 0);
+            const int L = (K + 2) / 3;
+            nvb.push_back(nv);
+            len.push_back(L);
+            start.push_back(ext);
+            ext += L;
+            prefix.push_back(prefix.back() + nv + (L + VEC_BLK - 1) / VEC_BLK);
+        }
+        int *d_prefix = nullptr, *d_nvb = nullptr, *d_len = nullptr;
+        int64_t *d_start = nullptr;
+        EI_CUDA_TRY(salloc(s, &d_prefix, prefix.size()));
+        EI_CUDA_TRY(salloc(s, &d_nvb, nvb.size()));
+        EI_CUDA_TRY(salloc(s, &d_len, len.size()));
+        EI_CUDA_TRY(salloc(s, &d_start, start.size()));
+        EI_CUDA_TRY(cudaMemcpy(d_prefix, prefix.data(), prefix.size() * sizeof(int), cudaMemcpyHostToDevice));
+        EI_CUDA_TRY(cudaMemcpy(d_nvb, nvb.data(), nvb.size() * sizeof(int), cudaMemcpyHostToDevice));
+        EI_CUDA_TRY(cudaMemcpy(d_len, len.data(), len.size() * sizeof(int), cudaMemcpyHostToDevice));
+        EI_CUDA_TRY(cudaMemcpy(d_start, start.data(), start.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        s->dgx.vec_prefix = d_prefix;
+        s->dgx.total_vec = prefix.back();
+        s->dgx.vec_nvb = d_nvb;
+        s->dgx.off_len = d_len;
+        s->dgx.off_start = d_start;
+        EI_CUDA_TRY(salloc(s, &s->shift, (size_t)g->sino4_count));
+        EI_CUDA_TRY(salloc(s, &s->row_sum, (size_t)std::max(1, g->dg.total_ic)));
+    }
+    s->vol_count = ext;
+    const size_t V = (size_t)ext, S = (size_t)g->n_slices;
+    const size_t NB = (size_t)s->dgx.total_vec;
     EI_CUDA_TRY(salloc(s, &s->u, V));
     EI_CUDA_TRY(salloc(s, &s->g, V));
     EI_CUDA_TRY(salloc(s, &s->d, V));
@@ -520,6 +659,10 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(cudaMallocHost(&s->summary_h, 2 * sizeof(int)));
     EI_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     // pad lanes of every vector stay 0: start from zeroed memory
+    EI_CUDA_TRY(cudaMemset(s->u, 0, V * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->g, 0, V * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->xt, 0, V * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->gt, 0, V * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->d, 0, V * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->Sr, 0, V * s->ring * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->Yr, 0, V * s->ring * sizeof(float4)));
@@ -541,9 +684,27 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
 {
     Solver *sv = g->solver;
     const SolverDev dv = dev_view(sv);
-    const DevGeom &dg = g->dg;
+    const DevGeom &dg = sv->dgx;              // the solver's blocks (with offsets segments)
     const int NB = dg.total_vec;
+    const int NBv = g->dg.total_vec;          // the volumes' blocks only
     const int T = VEC_THREADS;
+    const int ow = sv->off_which;
+    const float os = g->off_scale;
+    // one evaluation at vector v (gradient into gv): offsets to the model's
+    // tables first, their gradient after
+    auto eval = [&](float4 *v, float4 *gv, const int *active) -> cudaError_t {
+        if (ow) {
+            k_offsets_apply<<<g->n_slices, 256, 0, st>>>(dg, ow, os, v, active);
+            count_launches(g, 1);
+        }
+        EI_CUDA_TRY(evaluate(g, v, meas, g->S_dev, gv, true, active, st));
+        if (ow) {
+            EI_CUDA_TRY(launch_shift_grad(g, g->proj, meas, sv->shift, sv->row_sum, active, st));
+            k_offsets_grad<<<g->n_slices, 256, 0, st>>>(dg, ow, os, sv->shift, sv->row_sum, gv, active);
+            count_launches(g, 2);
+        }
+        return cudaGetLastError();
+    };
     // linked mode iterates on h alone: the other lanes of u start and stay at 0
     const float on1 = g->link_gamma > 0.f ? 0.f : 1.f;
     const float4 inv = make_float4(1.f / g->scale[0], on1 / g->scale[1], on1 / g->scale[2], 0.f);
@@ -551,10 +712,14 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     Opts o{opts->tol, opts->c1, opts->curv_eps, opts->max_iter, opts->max_trials};
     const int scalar_threads = 256;
 
-    k_to_scaled<<<NB, T, 0, st>>>(dg, x_dev, sv->u, inv);
+    k_to_scaled<<<NBv, T, 0, st>>>(g->dg, x_dev, sv->u, inv);
     count_launches(g, 1);
+    if (ow) {
+        k_offsets_to_u<<<g->n_slices, 256, 0, st>>>(dg, ow, 1.f / os, sv->u);
+        count_launches(g, 1);
+    }
     EI_CUDA_TRY(cudaGetLastError());
-    EI_CUDA_TRY(evaluate(g, sv->u, meas, g->S_dev, sv->g, true, nullptr, st));
+    EI_CUDA_TRY(eval(sv->u, sv->g, nullptr));
     k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
     count_launches(g, 1);
     EI_CUDA_TRY(cudaGetLastError());
@@ -581,7 +746,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         k_reset_dir<<<NB, T, 0, st>>>(dg, dv);
         k_trial<<<NB, T, 0, st>>>(dg, dv);
         EI_CUDA_TRY(cudaGetLastError());
-        EI_CUDA_TRY(evaluate(g, sv->xt, meas, g->S_dev, sv->gt, true, sv->mask_ls, st));
+        EI_CUDA_TRY(eval(sv->xt, sv->gt, sv->mask_ls));
         k_armijo<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, o);
         k_accept<<<NB, T, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2]);
         k_update<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2], o,
@@ -630,8 +795,12 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (err != cudaSuccess) return err;
-    k_from_scaled<<<NB, T, 0, st>>>(dg, sv->u, x_dev, sc);
+    k_from_scaled<<<NBv, T, 0, st>>>(g->dg, sv->u, x_dev, sc);
     count_launches(g, 1);
+    if (ow) {                                 // the solution's offsets stay in the geometry
+        k_offsets_apply<<<g->n_slices, 256, 0, st>>>(dg, ow, os, sv->u, nullptr);
+        count_launches(g, 1);
+    }
     return cudaGetLastError();
 }
 

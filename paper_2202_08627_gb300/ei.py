@@ -90,7 +90,9 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_get_variant", "ei_last_error", "ei_single_shot_fbp", "ei_unet_create",
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
-            "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad"]
+            "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
+            "ei_set_offset_unknowns", "ei_get_offsets"]
+EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
 
@@ -141,6 +143,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_set_offset_unknowns.argtypes = [c_void_p, c_int, c_double]
+    lib.ei_set_offset_unknowns.restype = c_int
+    lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.ei_get_offsets.restype = c_int
     lib.ei_set_linked.argtypes = [c_void_p, c_double]
     lib.ei_set_linked.restype = c_int
     lib.ei_offset_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
@@ -581,6 +587,24 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+def ei_set_offset_unknowns(geom: Geometry, which: int, scale: float = 0.01) -> None:
+    """Eq. 4's offsets among ei_reconstruct's unknowns: which = EI_OFFSET_MO |
+    EI_OFFSET_MR (0 = fixed), solver scaling m / scale."""
+    _check(load_library().ei_set_offset_unknowns(geom.handle, int(which), float(scale)),
+           "ei_set_offset_unknowns")
+
+
+def ei_get_offsets(geom: Geometry):
+    """The geometry's current (m_o [sum n_theta], m_r [sum n_det]) as numpy arrays."""
+    n_th = sum(sl.n_theta for sl in geom.slices)
+    n_px = sum(sl.n_det for sl in geom.slices)
+    m_o = np.zeros(n_th, np.float32)
+    m_r = np.zeros(n_px, np.float32)
+    _check(load_library().ei_get_offsets(geom.handle, m_o.ctypes.data, m_r.ctypes.data),
+           "ei_get_offsets")
+    return m_o, m_r
 
 
 def ei_set_linked(geom: Geometry, gamma: float) -> None:

@@ -1,8 +1,9 @@
 """The terms of Eq. 4 beyond the three-channel model on the GPU, against the
 FP64 oracle: the gradient with respect to the drift m_o(theta) and the ring
 term m_r(t) (ei_offset_grad), the gauge ambiguity the paper points out for
-them, and the linked single unknown h (mu = h, delta = gamma h, sigma = 0;
-ei_set_linked) through ei_forward, ei_objective_grad and ei_reconstruct."""
+them, the linked single unknown h (mu = h, delta = gamma h, sigma = 0;
+ei_set_linked) through ei_forward, ei_objective_grad and ei_reconstruct, and
+the offsets as unknowns of the solver (ei_set_offset_unknowns)."""
 import numpy as np
 import pytest
 
@@ -153,3 +154,57 @@ def test_set_linked_rejects_bad_gamma():
         with pytest.raises(ei.EIError):
             ei.ei_set_linked(G, bad)
     ei.ei_set_linked(G, 0.0)
+
+
+def test_get_offsets_returns_the_setup_values():
+    from paper_2202_08627_gb300 import ei
+    probs = _with_offsets(SHAPES, 800)
+    specs, geoms, _ = zip(*probs)
+    G = gpu_geometry(list(specs), list(geoms))
+    m_o, m_r = ei.ei_get_offsets(G)
+    np.testing.assert_array_equal(m_o, np.concatenate([g.m_o for g in geoms]).astype(np.float32))
+    np.testing.assert_array_equal(m_r, np.concatenate([g.m_r for g in geoms]).astype(np.float32))
+
+
+def test_joint_offsets_match_oracle_trajectory():
+    """m_o and m_r among the unknowns (the paper's joint minimisation of Eq. 5
+    over the volume and Eq. 4's offsets), with the gauge fixed by keeping the
+    mean of m_r: 20 L-BFGS iterations from zero volume and zero offsets agree
+    with the FP64 oracle running the same algorithm on the same vector
+    [u_volume, m_o / 0.01, m_r / 0.01]."""
+    from paper_2202_08627_gb300 import ei
+    spec = inputs.make_slice(900, 64, 90, 96, 7)
+    truth_geom = oracle_geometry(spec, m_o=inputs.uniform_noise(90, 901, -0.05, 0.05),
+                                 m_r=inputs.uniform_noise(96, 902, -0.03, 0.03))
+    s_exp = measured(spec, truth_geom)
+    geom = oracle_geometry(spec)                          # offsets start at 0
+    G = gpu_geometry([spec], [geom])
+    ei.ei_set_offset_unknowns(G, ei.EI_OFFSET_MO | ei.EI_OFFSET_MR, 0.01)
+    vol = G.empty("vol")
+    rep = ei.ei_reconstruct(G, G.pack_meas([s_exp]), vol, tol=0.0, max_iter=20)
+    m_o, m_r = ei.ei_get_offsets(G)
+
+    n, sc, osc = 64, np.asarray(geom.scale)[:, None, None], 0.01
+    nv = 3 * n * n
+
+    def fun(w):
+        u = w[:nv].reshape(3, n, n)
+        geom.m_o = w[nv:nv + 90] * osc
+        geom.m_r = w[nv + 90:] * osc
+        S, gu = oracle.objective_grad(u, s_exp, geom, scaled=True)
+        g_mo, g_mr = oracle.offset_grads(u * sc, s_exp, geom)
+        g_mr = g_mr - g_mr.mean()                       # the gauge: mean of m_r fixed
+        return S, np.concatenate([gu.ravel(), osc * g_mo, osc * g_mr])
+
+    w_ref, rep_ref = oracle.lbfgs(fun, np.zeros(nv + 90 + 96), oracle.SolveOptions(tol=0.0, max_iter=20))
+    assert rep.iterations[0] == rep_ref.iterations == 20
+    assert abs(rep.f_initial[0] - rep_ref.f_history[0]) <= 1e-5 * rep_ref.f_history[0]
+    assert abs(rep.f_final[0] - rep_ref.f_history[-1]) <= 1e-4 * rep_ref.f_history[-1], \
+        (rep.f_final[0], rep_ref.f_history[-1])
+    assert rel_l2(m_o, w_ref[nv:nv + 90] * osc) <= 2e-2
+    assert rel_l2(m_r, w_ref[nv + 90:] * osc) <= 2e-2
+    assert abs(float(m_r.mean())) <= 1e-6
+    # the joint solve fits the data better than the volume alone from the same start
+    G2 = gpu_geometry([spec], [oracle_geometry(spec)])
+    rep2 = ei.ei_reconstruct(G2, G2.pack_meas([s_exp]), G2.empty("vol"), tol=0.0, max_iter=20)
+    assert rep.f_final[0] < rep2.f_final[0]
