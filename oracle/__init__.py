@@ -27,6 +27,9 @@ What it computes, in the paper's order and notation:
   (mu = h, delta = gamma h, no scatter) and its gradient with respect to h.
 * ``offset_grads`` — the gradient of S with respect to the drift m_o(theta)
   and the ring term m_r(t) of Eq. 4.
+* ``single_shot`` / ``single_shot_eq3`` — non-iterative reconstructions: the
+  three-channel moment retrieval used as the warm-start input, and the
+  paper's single-shot retrieval of Eq. 3 for the linked unknown.
 * ``lbfgs`` / ``reconstruct`` — the L-BFGS minimisation the paper uses
   ("Theoretical basis" section, [Byrd 1995] via SciPy), written out.
 
@@ -525,6 +528,37 @@ def fbp(P: np.ndarray, geom: Geometry) -> np.ndarray:
     scale = np.pi / geom.n_theta / geom.pitch
     return np.stack([scale * backproject(ramp_filter(P[c], geom.pitch), geom)
                      for c in range(P.shape[0])])
+
+
+def eq3_slope(geom: Geometry, m_index: int, gamma: float) -> float:
+    """The length a (cm) of the single-shot retrieval of Eq. 3: linearising
+    Eq. 4 at one mask position m, f(m - shift) ~ f(m) - f'(m) shift with
+    shift = (z/period) gamma dR[h]/dt and dT/dt = -T dR[h]/dt, gives
+    s / f = (1 + a d/dt) T with a = (z/period) gamma f'(m) / f(m), where f is the
+    flat IC averaged over the pixels (the paper's f(m)) and f' its derivative
+    in m."""
+    m = float(geom.m[m_index])
+    A, c, w = geom.flat_A, geom.flat_c, geom.flat_w
+    f = A * np.exp(-(m - c) ** 2 / (2.0 * w * w))
+    df = -f * (m - c) / (w * w)
+    return geom.z_over_p * gamma * float(df.mean()) / float(f.mean())
+
+
+def single_shot_eq3(s_exp: np.ndarray, geom: Geometry, m_index: int, gamma: float):
+    """The paper's single-shot retrieval (Eq. 3) from one mask position and its
+    filtered back-projection, for the homogeneous-sample model mu = h,
+    delta = gamma h (gamma in cm).  Per sinogram row: y = s(t, m) / f(t, m),
+    T = Re F^-1[F[y] / (1 + i q a)] (DFT along t, q = 2 pi x the DFT frequencies
+    / (n_det pitch), the e^{-iqt} convention, a from eq3_slope), R[h] = -ln T
+    (T clamped at 1e-6); then h = FBP of R[h].  The offsets m_o, m_r of Eq. 4
+    are not part of this model.  Returns (R[h] [n_theta][n_det], h [n][n])."""
+    a = eq3_slope(geom, m_index, gamma)
+    f = flat_at_masks(geom)[m_index]
+    y = np.asarray(s_exp, dtype=np.float64)[m_index] / f[None, :]
+    q = 2.0 * np.pi * np.fft.fftfreq(geom.n_det, d=geom.pitch)
+    T = np.real(np.fft.ifft(np.fft.fft(y, axis=1) / (1.0 + 1j * a * q[None, :]), axis=1))
+    P = -np.log(np.maximum(T, 1e-6))
+    return P, fbp(P[None], geom)[0]
 
 
 def single_shot(s_exp: np.ndarray, geom: Geometry) -> np.ndarray:
