@@ -311,6 +311,24 @@ int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int
 int ei_set_linked(ei_geometry *g, double gamma);
 
 /*
+ * The paper's single-shot retrieval (Eq. 3), for the homogeneous-sample model
+ * mu = h, delta = gamma h (gamma in cm, as for ei_set_linked), from the one
+ * mask position m_index of s_exp (an acquisition on the slope of the IC; other
+ * positions are not read), then the filtered back-projection.  Reading of
+ * Eq. 3: linearising Eq. 4 at m gives s / f = (1 + a d/dt) T with
+ * T = exp(-R[h]) and a = (z/period) gamma f'(m) / f(m), f the flat IC averaged
+ * over the slice's pixels; Eq. 3 divides by (1 + i q a) in Fourier space along
+ * t, computed here as the equivalent circular convolution with the real DFT
+ * kernel.  R[h] = -ln T (T clamped at 1e-6), ramp filter, FBP.
+ * vol_out: (h, gamma h, 0, 0) per voxel.  Offsets m_o, m_r are not modelled.
+ * EI_ERR_ARG for m_index outside [0, n_m), a negative or non-finite gamma, or
+ * rows wider than 6257 pixels.  The first call allocates one float per
+ * detector pixel.
+ */
+int ei_single_shot_eq3(ei_geometry *g, const float *s_exp, int m_index, double gamma,
+                       float *vol_out, void *stream);
+
+/*
  * Gradient of S (Eq. 5) with respect to the drift m_o(theta) and the ring
  * term m_r(t) of Eq. 4, at the physical volume vol (layout of ei_forward).
  * Both terms enter only the shift of pixel (theta, t), with coefficient 1:

@@ -794,6 +794,38 @@ int ei_single_shot_fbp(const ei_geometry *gc, const float *s_exp, float *vol_out
     return status_from(e);
 }
 
+int ei_single_shot_eq3(ei_geometry *g, const float *s_exp, int m_index, double gamma,
+                       float *vol_out, void *stream)
+{
+    if (!g || !s_exp || !vol_out || !aligned16(s_exp) || !aligned16(vol_out) || m_index < 0 ||
+        m_index >= g->n_m || !(gamma >= 0.0) || !isfinite(gamma))
+        return EI_ERR_ARG;
+    if (!single_shot_eq3_fits(g)) {
+        record_message("ei_single_shot_eq3: rows of %d pixels exceed its shared-memory rows",
+                       g->dg.max_ndp);
+        return EI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!g->eq3_ker) {
+        int64_t n_px = 0;
+        for (const SliceInfo &si : g->h_slices) n_px += si.n_det;
+        e = dev_alloc(g, &g->eq3_ker, (size_t)n_px);
+        if (e != cudaSuccess) {
+            record_error(e);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+        }
+    }
+    const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    count_launches(g, 2);
+    e = launch_single_shot_eq3(g, s_exp, m_index, (float)gamma, g->eq3_ker, st);
+    if (e == cudaSuccess)
+        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, 0.f,
+                               g->part_adj, nullptr, st);
+    return status_from(e);
+}
+
 int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stream)
 {
     if (!gc || !vol || !s_mod || !aligned16(vol) || !aligned16(s_mod)) return EI_ERR_ARG;

@@ -167,6 +167,7 @@ struct ei_geometry {
     float off_scale = 1.f;             // their solver scaling u = m / off_scale
     float *shift_scratch = nullptr;    // [sino4_count] dS/dshift (ei_offset_grad, allocated on use)
     double *row_sums = nullptr;        // [total_ic]
+    float *eq3_ker = nullptr;          // [sum n_det] Eq. 3 convolution kernels (allocated on use)
     int *dev_status = nullptr;         // [1] device-side error status (bounded waits)
     int num_sms = 0;
     int *work_counter = nullptr;       // [2] work counters of the persistent kernels
@@ -205,6 +206,13 @@ bool ic_pipe_fits(int max_ndp, int n_m);
 // (the adjoint then gives the filtered back-projection).
 cudaError_t launch_single_shot(const ei_geometry *g, const float *meas, cudaStream_t st);
 cudaError_t single_shot_set_smem_limit();
+// The paper's single-shot retrieval (Eq. 3) of the linked unknown from mask
+// position m_index into the packed gradient sinogram (channels R[h], gamma R[h],
+// 0, ramp-filtered with the FBP scale); ker: [sum n_det] scratch for the
+// per-slice convolution kernels.
+cudaError_t launch_single_shot_eq3(const ei_geometry *g, const float *meas, int m_index,
+                                   float gamma, float *ker, cudaStream_t st);
+bool single_shot_eq3_fits(const ei_geometry *g);
 // Packed gradient sinogram from a user sino4 array.
 cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
 // out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial

@@ -91,7 +91,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
-            "ei_set_offset_unknowns", "ei_get_offsets"]
+            "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
@@ -143,6 +143,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_single_shot_eq3.argtypes = [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]
+    lib.ei_single_shot_eq3.restype = c_int
     lib.ei_set_offset_unknowns.argtypes = [c_void_p, c_int, c_double]
     lib.ei_set_offset_unknowns.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -587,6 +589,17 @@ def ei_get_variant(geom: Geometry):
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
     return f.value, a.value, bool(p.value)
+
+
+def ei_single_shot_eq3(geom: Geometry, s_exp, m_index: int, gamma: float, vol_out, stream=None):
+    """The paper's single-shot retrieval (Eq. 3) from one mask position and its
+    FBP into vol_out: (h, gamma h, 0) per voxel."""
+    _check_size(s_exp, geom.meas_count, "s_exp")
+    _check_size(vol_out, geom.vol_count * 4, "vol_out")
+    _check(load_library().ei_single_shot_eq3(geom.handle, _dptr(s_exp, "s_exp"), int(m_index),
+                                             float(gamma), _dptr(vol_out, "vol_out"),
+                                             _stream_ptr(stream)), "ei_single_shot_eq3")
+    return vol_out
 
 
 def ei_set_offset_unknowns(geom: Geometry, which: int, scale: float = 0.01) -> None:
