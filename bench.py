@@ -492,6 +492,49 @@ def run_ours(args, rank, world, local_rank):
     G.close()
 
 
+def run_ttt_linked(args):
+    """The paper's acquisition and model as a baseline run: one mask position
+    on the slope of the IC (m = -0.24 periods), the homogeneous-sample model
+    mu = h, delta = gamma h (gamma = 5e-7 cm), the linked unknown h; every
+    slice of the workload solved to --tol from h = 0 and from the single-shot
+    retrieval of Eq. 3 (CUDA events around start + solve).  Prints one line."""
+    import torch
+    from paper_2202_08627_gb300 import build, ei, synth, warmstart, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    wl = workloads.WORKLOADS[args.workload]()
+    device = torch.device("cuda", 0)
+    gamma, m_pos = 5e-7, -0.24
+    seeds = [wl.seed0 + s for s in range(wl.n_slices)]
+    G, s_exp = synth.build_problem(wl.slices, 1, seeds, device, wl.seed0, m=[m_pos],
+                                   linked_gamma=gamma)
+    G.variant = ei.ei_autotune(G)
+    ei.ei_set_linked(G, gamma)
+    eq = wl.voxel_equiv_1024()
+    out = {}
+    for start in ("zero", "eq3"):
+        vol = G.empty("vol", device)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if start == "eq3":
+            ei.ei_single_shot_eq3(G, s_exp, 0, gamma, vol)
+        rep = ei.ei_reconstruct(G, s_exp, vol, tol=args.tol, max_iter=args.ttt_max_iter,
+                                raise_on_error=False)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        it = rep.iterations
+        out[start] = {"seconds": t, "seconds_per_1024_slice": t / eq,
+                      "iterations_mean": float(it.mean()), "iterations_max": int(it.max()),
+                      "converged": int(rep.converged.sum()),
+                      "f_final_sum": float(np.sum(rep.f_final))}
+    print(json.dumps({"run": "ttt_linked_single_m", "workload": wl.name, "gamma_cm": gamma,
+                      "m": m_pos, "tol": args.tol, "slices": wl.n_slices,
+                      "kernel_variant": list(G.variant), "time_to_tolerance": out}), flush=True)
+    G.close()
+
+
 def run_profile_case(args):
     """The command the ncu summaries are captured with: `--profile-evals N`
     objective+gradient evaluations of the workload (variants as `ei_autotune`
@@ -540,6 +583,8 @@ def main():
     ap.add_argument("--cnn-epochs", type=int, default=20)
     ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")
     ap.add_argument("--cnn-save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--ttt-linked", action="store_true",
+                    help="single-m linked model: time to tolerance from 0 and from Eq. 3, then exit")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
     ap.add_argument("--profile-evals", type=int, default=0,
@@ -549,6 +594,8 @@ def main():
         return run_profile_case(args)
     if args.oracle_timing:
         return run_oracle_timing(args)
+    if args.ttt_linked:
+        return run_ttt_linked(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
