@@ -403,15 +403,17 @@ int ei_set_ic_variant(ei_geometry *g, int variant);
 int ei_get_ic_variant(const ei_geometry *g, int *variant);
 
 /*
- * Learned warm start (not in the paper; the task adds it): a U-Net that maps
+ * Learned warm start (not in the paper): a U-Net that maps
  * the single-shot reconstruction (ei_single_shot_fbp, in the solver's scaled
  * units u = x / scale) to a start near the converged iteration, y = x + net(x).
  * levels L (1..6), base width 32 or 64 (width of level l: base 2^l); per
  * encoder level two 3x3 conv + ReLU (2x2 average pooling between levels), per
  * decoder level a nearest 2x upsample, 3x3 conv + ReLU, 3x3 conv + ReLU over
  * the concatenation with the skip tensor, 3x3 conv + ReLU; a 1x1 head.  BF16
- * activations and tensor-core convolutions with FP32 accumulation, FP32
- * master weights updated by Adam (0.9, 0.999, 1e-8).  height and width must
+ * activations and tensor-core convolutions with FP32 accumulation (tcgen05
+ * with the accumulator in tensor memory, or WMMA mma.sync: see
+ * ei_unet_set_tensor_path), FP32 master weights updated by Adam
+ * (0.9, 0.999, 1e-8).  height and width must
  * be multiples of 2^(L-1); every batch is at most the `batch` of creation.
  * Arrays: x, y, target are device FP32 NHWC [batch][height][width][3].
  * Parameters (export order): each conv's W [tap][c_in][c_out] then b [c_out]
@@ -432,6 +434,13 @@ int64_t ei_unet_num_params(const ei_unet *net);
 int ei_unet_get_params(const ei_unet *net, float *host);
 int ei_unet_set_params(ei_unet *net, const float *host);
 int ei_unet_get_grads(const ei_unet *net, float *host);
+/* Convolution path: 1 (default) tcgen05 implicit-GEMM kernels, used for every
+ * convolution whose channel counts they support (input channels a multiple of
+ * 32; output channels 32, 64, 128 or a multiple of 256); 0 the WMMA (mma.sync)
+ * kernels for all.  Both accumulate in FP32; results agree to FP32 rounding of
+ * the sums.  A tcgen05 kernel whose bounded wait runs out makes the next
+ * synchronising ei_unet_train_step return EI_ERR_TIMEOUT. */
+int ei_unet_set_tensor_path(ei_unet *net, int path);
 
 /*
  * ei_objective_grad_noalloc — S and its gradient for ONE slice with no device

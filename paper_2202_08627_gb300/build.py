@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libei.so")
 SOURCES = ["ei_api.cu", "k_project.cu", "k_ic.cu", "k_backproject.cu", "solver.cu",
-           "ei_noalloc.cu", "k_fbp.cu", "nn_kernels.cu", "nn_unet.cu", "k_peaks.cu"]
+           "ei_noalloc.cu", "k_fbp.cu", "nn_kernels.cu", "nn_unet.cu", "k_peaks.cu", "nn_conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

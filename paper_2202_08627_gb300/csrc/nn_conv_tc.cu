@@ -1,0 +1,263 @@
+// Implicit-GEMM convolution of the learned warm start on the 5th-generation
+// tensor cores (tcgen05, kind::f16: BF16 operands, FP32 accumulation in
+// tensor memory).
+//
+//   Y[p][co] = sum_{tap, ci} X_tap[p][ci] W[tap][ci][co]   (+ bias, ReLU)
+//
+// One CTA computes a tile of 128 pixels (GEMM rows, M = 128) x NT output
+// channels (N = NT <= 256).  The reduction runs over (tap, 32-channel chunk):
+// every chunk, the 4 warps stage the chunk's 128 x 32 activations (the tap's
+// shifted pixels, zero outside the image) and NT x 32 weights in shared memory
+// in the canonical K-major layout without swizzle (core matrices of 8 rows x
+// 16 bytes; 128 bytes between core matrices along K, 512 between groups of 8
+// rows), then one thread issues two tcgen05.mma (K = 16 each) into the
+// accumulator in tensor memory and commits them to the stage's mbarrier.
+// Four stages: the loads of a chunk overlap the tensor-core work on the
+// previous ones; a stage is refilled only after its MMAs have completed.  The
+// epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes =
+// pixels), adds the bias, applies the ReLU, optionally accumulates into the
+// destination, and stores BF16 NHWC; output channels below `split` go to Y1,
+// the others to Y2 (dgrad into a concatenation's two inputs).
+//
+// Weights are read K-major, W_k[taps - 1 - tap][n][k]: for the forward pass
+// that is the flipped, transposed copy the WMMA kernel uses for dgrad, and for
+// dgrad (a forward convolution of dY with the flipped, transposed weights) it
+// is the forward copy itself, so no extra weight layout exists.
+//
+// Every wait on an mbarrier is bounded (1 s); a wait that runs out sets
+// *status, skips the rest of the tile, waits (bounded) for the MMAs already
+// issued, frees the tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "async_copy.h"
+#include "nn_internal.h"
+
+namespace ei {
+namespace nn {
+
+namespace {
+
+constexpr int TC_M = 128;            // pixels per CTA (tcgen05 M)
+constexpr int TC_BK = 32;            // input channels per stage
+constexpr int TC_STAGES = 4;
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+
+// shared-memory descriptor: start, LBO (K direction), SBO (8-row groups),
+// version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+}
+
+// byte offset of element (row, k) of a stage tile (k < 32)
+__device__ __forceinline__ int tile_off(int row, int kg)
+{
+    return (row >> 3) * 512 + kg * 128 + (row & 7) * 16;
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, uint64_t ad, uint64_t bd, unsigned idesc,
+                                       unsigned accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+template <int KS, int NT>
+__global__ void __launch_bounds__(128)
+k_conv_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int C2,
+          const bf16 *__restrict__ Wk, const float *__restrict__ bias, int Cout, int B, int H,
+          int W, int relu, bf16 *__restrict__ Y1, int split, int acc1, bf16 *__restrict__ Y2,
+          int acc2, int *__restrict__ status)
+{
+    constexpr int A_BYTES = TC_M * TC_BK * 2, B_BYTES = NT * TC_BK * 2;
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar_mma[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int P = B * H * W;
+    const int p0 = blockIdx.x * TC_M, co0 = blockIdx.y * NT;
+    const int Cin = C1 + C2;
+    const int chunks = Cin / TC_BK;
+    const int nK = KS * KS * chunks;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_addr(&bar_mma[s]), 1);
+        mbar_init(smem_addr(&bar_done), 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    // D f32, A bf16, B bf16, both K-major, N >> 3, M >> 4
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NT >> 3) << 17) |
+                           ((unsigned)(TC_M >> 4) << 24);
+
+    // this thread's pixel (row of the A tile)
+    const int p = p0 + tid;
+    int pb = 0, py = 0, px = 0;
+    if (p < P) {
+        pb = p / (H * W);
+        const int r = p - pb * H * W;
+        py = r / W;
+        px = r - py * W;
+    }
+    bool aborted = false;
+    for (int kc = 0; kc < nK; ++kc) {
+        const int st = kc % TC_STAGES;
+        unsigned char *As = tc_smem + st * STAGE_BYTES;
+        unsigned char *Bs = As + A_BYTES;
+        bool ok = true;
+        if (kc >= TC_STAGES)               // the stage's previous MMAs must have read it
+            ok = mbar_wait_bounded(smem_addr(&bar_mma[st]), ((kc / TC_STAGES) - 1) & 1, kTcWaitNs);
+        const int tap = kc / chunks, c0 = (kc - tap * chunks) * TC_BK;
+        if (ok) {
+            // A: 128 pixels x 32 channels of the tap's shifted input (zero outside)
+            const int dy = KS == 3 ? tap / 3 - 1 : 0, dx = KS == 3 ? tap % 3 - 1 : 0;
+            const int yy = py + dy, xx = px + dx;
+            const bool inb = p < P && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const int64_t q = ((int64_t)pb * H + yy) * W + xx;
+            const bf16 *src = nullptr;
+            if (inb) src = c0 < C1 ? X1 + q * C1 + c0 : X2 + q * C2 + (c0 - C1);
+#pragma unroll
+            for (int kg = 0; kg < 4; ++kg) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (inb) v = *reinterpret_cast<const uint4 *>(src + kg * 8);
+                *reinterpret_cast<uint4 *>(As + tile_off(tid, kg)) = v;
+            }
+            // B: NT output channels x 32 input channels, K-major, tap flipped
+            const bf16 *wsrc = Wk + ((int64_t)(KS * KS - 1 - tap) * Cout + co0) * Cin + c0;
+#pragma unroll
+            for (int i = 0; i < NT * 4 / 128; ++i) {
+                const int e = tid + i * 128;                // (row, kg) = (e / 4, e % 4)
+                const int n = e >> 2, kg = e & 3;
+                *reinterpret_cast<uint4 *>(Bs + tile_off(n, kg)) =
+                    *reinterpret_cast<const uint4 *>(wsrc + (int64_t)n * Cin + kg * 8);
+            }
+            proxy_fence_async();           // the tensor core reads what the threads wrote
+        }
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned a_addr = smem_addr(As), b_addr = smem_addr(Bs);
+            tc_mma(tmem, smem_desc(a_addr), smem_desc(b_addr), idesc, kc > 0 ? 1u : 0u);
+            tc_mma(tmem, smem_desc(a_addr + 256), smem_desc(b_addr + 256), idesc, 1u);
+            tc_commit(smem_addr(&bar_mma[st]));
+        }
+    }
+    // all issued MMAs complete -> bar_done
+    if (tid == 0) tc_commit(smem_addr(&bar_done));
+    const bool done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (aborted || !done) {
+        if (tid == 0) atomicExch(status, 1);
+    } else {
+        // warp w reads lanes 32w .. 32w + 31 (its pixels); the loads are
+        // warp-collective, the stores only for pixels inside the image
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        for (int c = 0; c < NT; c += 16) {
+            unsigned v[16];
+            tc_ld16(lane_base + c, v);
+            if (p >= P) continue;
+            const int co = co0 + c;
+            const bool first = co < split;
+            bf16 *dst = first ? Y1 + (int64_t)p * split + co
+                              : Y2 + (int64_t)p * (Cout - split) + (co - split);
+            const int acc_mode = first ? acc1 : acc2;
+            __align__(16) __nv_bfloat162 outv[8];
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                float a = __uint_as_float(v[j]), b = __uint_as_float(v[j + 1]);
+                if (bias) a += bias[co + j], b += bias[co + j + 1];
+                if (relu) a = fmaxf(a, 0.f), b = fmaxf(b, 0.f);
+                if (acc_mode) {
+                    const float2 o = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(dst)[j / 2]);
+                    a += o.x, b += o.y;
+                }
+                outv[j / 2] = __floats2bfloat162_rn(a, b);
+            }
+            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(outv)[0];
+            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(outv)[1];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
+}
+
+template <int KS, int NT>
+static cudaError_t launch_tc(const Tensor &x1, const Tensor *x2, int cout, const bf16 *Wk,
+                             const float *bias, bool relu, bf16 *y1, int split, bool acc1,
+                             bf16 *y2, bool acc2, int *status, cudaStream_t st)
+{
+    constexpr int smem = TC_STAGES * (TC_M * TC_BK * 2 + NT * TC_BK * 2);
+    static bool attr = false;
+    if (!attr) {
+        EI_NN_TRY(cudaFuncSetAttribute(k_conv_tc<KS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    const int P = x1.B * x1.H * x1.W;
+    dim3 grid((P + TC_M - 1) / TC_M, cout / NT);
+    k_conv_tc<KS, NT><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0,
+                                               Wk, bias, cout, x1.B, x1.H, x1.W, relu, y1, split,
+                                               acc1, y2, acc2, status);
+    return cudaGetLastError();
+}
+
+bool conv_tc_supported(int cin, int cout, int c1, int split)
+{
+    const int nt = cout >= 256 ? 256 : cout;
+    return cin % TC_BK == 0 && c1 % TC_BK == 0 && split % 16 == 0 &&
+           (nt == 32 || nt == 64 || nt == 128 || nt == 256) && cout % nt == 0;
+}
+
+cudaError_t conv_forward_tc(const Tensor &x1, const Tensor *x2, int cout, int ks, const bf16 *Wk,
+                            const float *bias, bool relu, bf16 *y1, int split, bool acc1, bf16 *y2,
+                            bool acc2, int *status, cudaStream_t st)
+{
+    const int nt = cout >= 256 ? 256 : cout;
+#define EI_TC_CASE(K, N)                                                                     \
+    if (ks == K && nt == N)                                                                  \
+        return launch_tc<K, N>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+    EI_TC_CASE(3, 32) EI_TC_CASE(3, 64) EI_TC_CASE(3, 128) EI_TC_CASE(3, 256)
+    EI_TC_CASE(1, 32) EI_TC_CASE(1, 64) EI_TC_CASE(1, 128) EI_TC_CASE(1, 256)
+#undef EI_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace nn
+}  // namespace ei

@@ -33,6 +33,14 @@ struct ConvParams {
 cudaError_t conv_forward(const Tensor &x1, const Tensor *x2, const ConvParams &cp, int ks,
                          const bf16 *Wb, const float *bias, bool relu, bf16 *y1, int split,
                          bool acc1, bf16 *y2, bool acc2, cudaStream_t st);
+// The same convolution on the tcgen05 tensor cores (nn_conv_tc.cu): Wk is the
+// K-major weight copy read with the tap order flipped (the forward pass passes
+// the dgrad copy, dgrad the forward copy); *status is set if a bounded wait
+// ran out.  conv_tc_supported: channel counts the kernel handles.
+bool conv_tc_supported(int cin, int cout, int c1, int split);
+cudaError_t conv_forward_tc(const Tensor &x1, const Tensor *x2, int cout, int ks, const bf16 *Wk,
+                            const float *bias, bool relu, bf16 *y1, int split, bool acc1, bf16 *y2,
+                            bool acc2, int *status, cudaStream_t st);
 cudaError_t conv_wgrad(const Tensor &x1, const Tensor *x2, const bf16 *g, int cout, int ks,
                        float *partial, int nsplit, float *dw, bool accumulate, cudaStream_t st);
 // db[c] = sum_p g[p][c] through per-block partials (C divides 256)

@@ -50,6 +50,8 @@ struct ei_unet {
     double *mse_part = nullptr, *mse_host = nullptr;
     int64_t partial_count = 0;
     int mse_blocks = 256, head_blocks = 152;
+    int use_tc = 1;                    // convolutions on tcgen05 (1) or WMMA mma.sync (0)
+    int *status = nullptr;             // device: set by a tcgen05 wait that ran out
     std::vector<void *> allocs;
 };
 
@@ -93,6 +95,19 @@ void set_batch(ei_unet *n, int B)
     }
 }
 
+// One convolution: tcgen05 when enabled and the channel counts allow, else
+// WMMA.  Wmn: the [tap][k][n] copy (WMMA); Wk: the flipped K-major copy.
+cudaError_t conv(ei_unet *n, const Tensor &x1, const Tensor *x2, int cout, int ks,
+                 const bf16 *Wmn, const bf16 *Wk, const float *bias, bool relu, bf16 *y1,
+                 int split, bool acc1, bf16 *y2, bool acc2, cudaStream_t st)
+{
+    const int cin = x1.C + (x2 ? x2->C : 0);
+    if (n->use_tc && conv_tc_supported(cin, cout, x1.C, split))
+        return conv_forward_tc(x1, x2, cout, ks, Wk, bias, relu, y1, split, acc1, y2, acc2,
+                               n->status, st);
+    return conv_forward(x1, x2, {cout}, ks, Wmn, bias, relu, y1, split, acc1, y2, acc2, st);
+}
+
 cudaError_t forward(ei_unet *n, const float *x, float *y, cudaStream_t st)
 {
     const int L = n->L;
@@ -101,22 +116,22 @@ cudaError_t forward(ei_unet *n, const float *x, float *y, cudaStream_t st)
     for (int l = 0; l < L; ++l) {
         const Conv &c1 = n->convs[n->enc1[l]], &c2 = n->convs[n->enc2[l]];
         const Tensor &src = l == 0 ? n->in : n->POOL[l];
-        EI_NN_TRY(conv_forward(src, nullptr, {c1.cout}, 3, c1.Wb, c1.b, true, n->E1[l].d, c1.cout,
-                               false, nullptr, false, st));
-        EI_NN_TRY(conv_forward(n->E1[l], nullptr, {c2.cout}, 3, c2.Wb, c2.b, true, n->E2[l].d,
-                               c2.cout, false, nullptr, false, st));
+        EI_NN_TRY(conv(n, src, nullptr, c1.cout, 3, c1.Wb, c1.Wf, c1.b, true, n->E1[l].d, c1.cout,
+                       false, nullptr, false, st));
+        EI_NN_TRY(conv(n, n->E1[l], nullptr, c2.cout, 3, c2.Wb, c2.Wf, c2.b, true, n->E2[l].d,
+                       c2.cout, false, nullptr, false, st));
         if (l < L - 1) EI_NN_TRY(pool2(n->E2[l], n->POOL[l + 1].d, st));
     }
     const Tensor *cur = &n->E2[L - 1];
     for (int d = L - 2; d >= 0; --d) {
         const Conv &cu = n->convs[n->dup[d]], &ca = n->convs[n->da[d]], &cb = n->convs[n->db[d]];
         EI_NN_TRY(up2(*cur, n->U[d].d, st));
-        EI_NN_TRY(conv_forward(n->U[d], nullptr, {cu.cout}, 3, cu.Wb, cu.b, true, n->DUP[d].d,
-                               cu.cout, false, nullptr, false, st));
-        EI_NN_TRY(conv_forward(n->DUP[d], &n->E2[d], {ca.cout}, 3, ca.Wb, ca.b, true, n->DA[d].d,
-                               ca.cout, false, nullptr, false, st));
-        EI_NN_TRY(conv_forward(n->DA[d], nullptr, {cb.cout}, 3, cb.Wb, cb.b, true, n->DB[d].d,
-                               cb.cout, false, nullptr, false, st));
+        EI_NN_TRY(conv(n, n->U[d], nullptr, cu.cout, 3, cu.Wb, cu.Wf, cu.b, true, n->DUP[d].d,
+                       cu.cout, false, nullptr, false, st));
+        EI_NN_TRY(conv(n, n->DUP[d], &n->E2[d], ca.cout, 3, ca.Wb, ca.Wf, ca.b, true, n->DA[d].d,
+                       ca.cout, false, nullptr, false, st));
+        EI_NN_TRY(conv(n, n->DA[d], nullptr, cb.cout, 3, cb.Wb, cb.Wf, cb.b, true, n->DB[d].d,
+                       cb.cout, false, nullptr, false, st));
         cur = &n->DB[d];
     }
     return head_forward(*cur, n->hw, n->hb, x, y, st);
@@ -135,8 +150,8 @@ cudaError_t conv_backward(ei_unet *n, const Conv &c, const Tensor &x1, const Ten
     if (gx1) {
         Tensor gt;
         gt.d = g, gt.B = y.B, gt.H = y.H, gt.W = y.W, gt.C = c.cout;
-        EI_NN_TRY(conv_forward(gt, nullptr, {c.cin()}, c.ks, c.Wf, nullptr, false, gx1, c.cin1,
-                               acc1, gx2, acc2, st));
+        EI_NN_TRY(conv(n, gt, nullptr, c.cin(), c.ks, c.Wf, c.Wb, nullptr, false, gx1, c.cin1,
+                       acc1, gx2, acc2, st));
     }
     return cudaSuccess;
 }
@@ -271,6 +286,8 @@ int ei_unet_create(int levels, int base, int batch, int height, int width,
     if (e == cudaSuccess) e = dalloc(n, &n->head_pb, (int64_t)n->head_blocks * 3);
     if (e == cudaSuccess) e = dalloc(n, &n->mse_part, n->mse_blocks);
     if (e == cudaSuccess) e = cudaMallocHost(&n->mse_host, n->mse_blocks * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(n, &n->status, 1);
+    if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(int));
     for (float **p : {&n->hw, &n->ghw, &n->mhw, &n->vhw})
         if (e == cudaSuccess) e = dalloc(n, p, (int64_t)base * 3);
     for (float **p : {&n->hb, &n->ghb, &n->mhb, &n->vhb})
@@ -346,7 +363,22 @@ int ei_unet_train_step(ei_unet *n, const float *x, const float *target, int batc
             *loss = s / (double)cnt;
         }
     }
+    if (e == cudaSuccess && loss) {                 // synchronised: report a timed-out wait
+        int h = 0;
+        e = cudaMemcpy(&h, n->status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && h) {
+            cudaMemset(n->status, 0, sizeof(int));
+            return EI_ERR_TIMEOUT;
+        }
+    }
     return status(e);
+}
+
+int ei_unet_set_tensor_path(ei_unet *n, int path)
+{
+    if (!n || (path != 0 && path != 1)) return EI_ERR_ARG;
+    n->use_tc = path;
+    return EI_OK;
 }
 
 int64_t ei_unet_num_params(const ei_unet *n)

@@ -91,7 +91,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_destroy", "ei_unet_forward", "ei_unet_train_step", "ei_unet_num_params",
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
-            "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3"]
+            "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
+            "ei_unet_set_tensor_path"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
@@ -143,6 +144,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_variant.restype = c_int
     lib.ei_get_variant.argtypes = [c_void_p, P(c_int), P(c_int), P(c_int)]
     lib.ei_get_variant.restype = c_int
+    lib.ei_unet_set_tensor_path.argtypes = [c_void_p, c_int]
+    lib.ei_unet_set_tensor_path.restype = c_int
     lib.ei_single_shot_eq3.argtypes = [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]
     lib.ei_single_shot_eq3.restype = c_int
     lib.ei_set_offset_unknowns.argtypes = [c_void_p, c_int, c_double]
@@ -725,6 +728,10 @@ class UNet:
         if arr.size != self.num_params:
             raise ValueError("expected %d parameters" % self.num_params)
         _check(load_library().ei_unet_set_params(self.handle, arr.ctypes.data), "ei_unet_set_params")
+
+    def set_tensor_path(self, path: int) -> None:
+        """1: tcgen05 convolutions (default), 0: WMMA mma.sync."""
+        _check(load_library().ei_unet_set_tensor_path(self.handle, int(path)), "ei_unet_set_tensor_path")
 
     def get_grads(self) -> np.ndarray:
         out = np.empty(self.num_params, np.float32)

@@ -1,5 +1,7 @@
 """The learned warm start's network (BF16 tensor-core kernels, FP32
-accumulation) against the FP64 oracle U-Net with the same parameters.
+accumulation; both convolution paths: tcgen05 with the accumulator in tensor
+memory, and WMMA mma.sync) against the FP64 oracle U-Net with the same
+parameters.
 
 The oracle emulates the GPU's BF16 storage of weights and activations in the
 forward pass, so the forward output agrees to ~FP32 accumulation-order noise
@@ -31,9 +33,10 @@ def _cuda():
 LEVELS, BASE, B, H, W = 3, 32, 2, 16, 24
 
 
-def _net_and_params():
+def _net_and_params(path=1):
     from paper_2202_08627_gb300 import ei
     net = ei.UNet(levels=LEVELS, base=BASE, batch=B, height=H, width=W, seed=3)
+    net.set_tensor_path(path)
     flat = net.get_params().astype(np.float64)
     p = ounet.unpack(flat, LEVELS, BASE)
     p["head.W"] = 0.2 * inputs.uniform_noise(p["head.W"].shape, 20)   # make the head matter
@@ -52,16 +55,18 @@ def test_params_round_trip():
     np.testing.assert_array_equal(net.get_params(), a)
 
 
-def test_forward_matches_oracle():
-    net, p = _net_and_params()
+@pytest.mark.parametrize("path", [1, 0])
+def test_forward_matches_oracle(path):
+    net, p = _net_and_params(path)
     x = inputs.uniform_noise((B, H, W, 3), 30, 0.0, 1.0)
     y = net.forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
     ref = ounet.forward(x.astype(np.float32).astype(np.float64), p, LEVELS, bf16=True)
     assert rel_l2(y - x, ref - x) <= 1e-2, rel_l2(y - x, ref - x)
 
 
-def test_gradients_match_oracle():
-    net, p = _net_and_params()
+@pytest.mark.parametrize("path", [1, 0])
+def test_gradients_match_oracle(path):
+    net, p = _net_and_params(path)
     x = inputs.uniform_noise((B, H, W, 3), 31, 0.0, 1.0).astype(np.float32)
     t = inputs.uniform_noise((B, H, W, 3), 32, 0.0, 1.0).astype(np.float32)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
@@ -94,3 +99,15 @@ def test_training_reduces_the_loss():
     for _ in range(200):
         last = net.train_step(x, t, lr=2e-3)
     assert last < 0.1 * first, (first, last)
+
+
+def test_tensor_paths_agree():
+    """tcgen05 and WMMA convolutions differ only in FP32 summation order (and
+    the BF16 rounding that follows), on a batch whose last tile is ragged."""
+    x = torch.from_numpy(inputs.uniform_noise((B, H, W, 3), 40, 0.0, 1.0).astype(np.float32)).cuda()
+    outs = []
+    for path in (1, 0):
+        net, _ = _net_and_params(path)
+        outs.append(net.forward(x).cpu().numpy().astype(np.float64))
+    xn = x.cpu().numpy()
+    assert rel_l2(outs[0] - xn, outs[1] - xn) <= 1e-2
