@@ -88,6 +88,21 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
         : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only); src_bytes < 16
+// fills the rest with zeros (0: nothing is read).  Completion per thread through
+// commit / wait groups.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Orders this thread's earlier generic-proxy shared-memory writes before later
 // async-proxy (bulk copy) accesses to the same locations.
 __device__ __forceinline__ void proxy_fence_async()

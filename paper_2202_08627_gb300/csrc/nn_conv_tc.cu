@@ -12,8 +12,9 @@
 // 16 bytes; 128 bytes between core matrices along K, 512 between groups of 8
 // rows), then one thread issues two tcgen05.mma (K = 16 each) into the
 // accumulator in tensor memory and commits them to the stage's mbarrier.
-// Four stages: the loads of a chunk overlap the tensor-core work on the
-// previous ones; a stage is refilled only after its MMAs have completed.  The
+// Four stages, filled by cp.async two chunks ahead of the MMAs: the global
+// loads of later chunks overlap the tensor-core work on earlier ones; a stage
+// is refilled only after the MMAs that read it have completed.  The
 // epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes =
 // pixels), adds the bias, applies the ReLU, optionally accumulates into the
 // destination, and stores BF16 NHWC; output channels below `split` go to Y1,
@@ -132,52 +133,66 @@ k_conv_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int 
         py = r / W;
         px = r - py * W;
     }
+    // chunk kc into stage kc % TC_STAGES with cp.async (one commit group per chunk)
+    auto issue = [&](int kc) {
+        unsigned char *As = tc_smem + (kc % TC_STAGES) * STAGE_BYTES;
+        unsigned char *Bs = As + A_BYTES;
+        const int tap = kc / chunks, c0 = (kc - tap * chunks) * TC_BK;
+        // A: 128 pixels x 32 channels of the tap's shifted input (zero outside)
+        const int dy = KS == 3 ? tap / 3 - 1 : 0, dx = KS == 3 ? tap % 3 - 1 : 0;
+        const int yy = py + dy, xx = px + dx;
+        const bool inb = p < P && yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const int64_t q = ((int64_t)pb * H + yy) * W + xx;
+        const bf16 *src = X1;
+        if (inb) src = c0 < C1 ? X1 + q * C1 + c0 : X2 + q * C2 + (c0 - C1);
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg)
+            cp_async16(As + tile_off(tid, kg), inb ? src + kg * 8 : X1, inb ? 16u : 0u);
+        // B: NT output channels x 32 input channels, K-major, tap flipped
+        const bf16 *wsrc = Wk + ((int64_t)(KS * KS - 1 - tap) * Cout + co0) * Cin + c0;
+#pragma unroll
+        for (int i = 0; i < NT * 4 / 128; ++i) {
+            const int e = tid + i * 128;                    // (row, kg) = (e / 4, e % 4)
+            const int n = e >> 2, kg = e & 3;
+            cp_async16(Bs + tile_off(n, kg), wsrc + (int64_t)n * Cin + kg * 8, 16u);
+        }
+    };
+    constexpr int DEPTH = 2;                   // chunks in flight ahead of the MMA
+    static_assert(DEPTH < TC_STAGES, "a stage must be free before its refill");
+#pragma unroll
+    for (int i = 0; i < DEPTH; ++i) {
+        if (i < nK) issue(i);
+        cp_async_commit();
+    }
     bool aborted = false;
     for (int kc = 0; kc < nK; ++kc) {
-        const int st = kc % TC_STAGES;
-        unsigned char *As = tc_smem + st * STAGE_BYTES;
-        unsigned char *Bs = As + A_BYTES;
+        // refill: chunk kc + DEPTH into the stage that chunk kc + DEPTH - STAGES used,
+        // once the MMAs that read it have completed
         bool ok = true;
-        if (kc >= TC_STAGES)               // the stage's previous MMAs must have read it
-            ok = mbar_wait_bounded(smem_addr(&bar_mma[st]), ((kc / TC_STAGES) - 1) & 1, kTcWaitNs);
-        const int tap = kc / chunks, c0 = (kc - tap * chunks) * TC_BK;
-        if (ok) {
-            // A: 128 pixels x 32 channels of the tap's shifted input (zero outside)
-            const int dy = KS == 3 ? tap / 3 - 1 : 0, dx = KS == 3 ? tap % 3 - 1 : 0;
-            const int yy = py + dy, xx = px + dx;
-            const bool inb = p < P && yy >= 0 && yy < H && xx >= 0 && xx < W;
-            const int64_t q = ((int64_t)pb * H + yy) * W + xx;
-            const bf16 *src = nullptr;
-            if (inb) src = c0 < C1 ? X1 + q * C1 + c0 : X2 + q * C2 + (c0 - C1);
-#pragma unroll
-            for (int kg = 0; kg < 4; ++kg) {
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (inb) v = *reinterpret_cast<const uint4 *>(src + kg * 8);
-                *reinterpret_cast<uint4 *>(As + tile_off(tid, kg)) = v;
-            }
-            // B: NT output channels x 32 input channels, K-major, tap flipped
-            const bf16 *wsrc = Wk + ((int64_t)(KS * KS - 1 - tap) * Cout + co0) * Cin + c0;
-#pragma unroll
-            for (int i = 0; i < NT * 4 / 128; ++i) {
-                const int e = tid + i * 128;                // (row, kg) = (e / 4, e % 4)
-                const int n = e >> 2, kg = e & 3;
-                *reinterpret_cast<uint4 *>(Bs + tile_off(n, kg)) =
-                    *reinterpret_cast<const uint4 *>(wsrc + (int64_t)n * Cin + kg * 8);
-            }
-            proxy_fence_async();           // the tensor core reads what the threads wrote
+        const int kn = kc + DEPTH;
+        if (kn < nK) {
+            if (kn >= TC_STAGES)
+                ok = mbar_wait_bounded(smem_addr(&bar_mma[kn % TC_STAGES]),
+                                       ((kn / TC_STAGES) - 1) & 1, kTcWaitNs);
+            if (ok) issue(kn);
         }
+        cp_async_commit();
+        cp_async_wait<DEPTH>();                // this thread's copies of chunk kc landed
+        proxy_fence_async();                   // the tensor core reads what the copies wrote
         if (__syncthreads_or(!ok)) {
             aborted = true;
             break;
         }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const unsigned a_addr = smem_addr(As), b_addr = smem_addr(Bs);
+            const unsigned a_addr = smem_addr(tc_smem + (kc % TC_STAGES) * STAGE_BYTES);
+            const unsigned b_addr = a_addr + A_BYTES;
             tc_mma(tmem, smem_desc(a_addr), smem_desc(b_addr), idesc, kc > 0 ? 1u : 0u);
             tc_mma(tmem, smem_desc(a_addr + 256), smem_desc(b_addr + 256), idesc, 1u);
-            tc_commit(smem_addr(&bar_mma[st]));
+            tc_commit(smem_addr(&bar_mma[kc % TC_STAGES]));
         }
     }
+    cp_async_wait<0>();                        // no copy outlives the block
     // all issued MMAs complete -> bar_done
     if (tid == 0) tc_commit(smem_addr(&bar_done));
     const bool done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
