@@ -535,6 +535,32 @@ def run_ttt_linked(args):
     G.close()
 
 
+def run_profile_unet(args):
+    """The command the U-Net launch list is captured with: the warm-start
+    network of the benchmark (4 levels, base 32, batch 16 of 256 x 256), one
+    warm-up forward and training step, then one forward and one training step
+    inside a cudaProfilerStart/Stop range.  Reports no performance number."""
+    import torch
+    from paper_2202_08627_gb300 import build, ei
+    torch.cuda.set_device(0)
+    build.build()
+    net = ei.UNet(levels=4, base=32, batch=16, height=256, width=256, seed=0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.rand(16, 256, 256, 3, device="cuda", generator=g)
+    t = torch.rand(16, 256, 256, 3, device="cuda", generator=g)
+    net.forward(x)
+    net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    net.forward(x)
+    loss = net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_case": "unet_4x32_16x256", "loss": loss}), flush=True)
+    net.close()
+
+
 def run_profile_case(args):
     """The command the ncu summaries are captured with: `--profile-evals N`
     objective+gradient evaluations of the workload (variants as `ei_autotune`
@@ -587,11 +613,15 @@ def main():
                     help="single-m linked model: time to tolerance from 0 and from Eq. 3, then exit")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
+    ap.add_argument("--profile-unet", action="store_true",
+                    help="one U-Net forward + training step for ncu and exit")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="run this many objective+gradient evaluations for ncu and exit")
     args = ap.parse_args()
     if args.profile_evals > 0:
         return run_profile_case(args)
+    if args.profile_unet:
+        return run_profile_unet(args)
     if args.oracle_timing:
         return run_oracle_timing(args)
     if args.ttt_linked:
