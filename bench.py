@@ -492,47 +492,81 @@ def run_ours(args, rank, world, local_rank):
     G.close()
 
 
-def run_ttt_linked(args):
-    """The paper's acquisition and model as a baseline run: one mask position
-    on the slope of the IC (m = -0.24 periods), the homogeneous-sample model
-    mu = h, delta = gamma h (gamma = 5e-7 cm), the linked unknown h; every
-    slice of the workload solved to --tol from h = 0 and from the single-shot
-    retrieval of Eq. 3 (CUDA events around start + solve).  Prints one line."""
+LINKED_GAMMA, SLOPE_M = 5e-7, -0.24      # delta / mu (cm); one mask position on the IC slope
+
+
+def ttt_linked(slices, seed0, tol, max_iter, starts=("zero", "eq3")):
+    """The paper's acquisition and model: one mask position on the slope of the
+    IC, the homogeneous-sample model mu = h, delta = gamma h, the linked unknown
+    h; every slice solved to tol from each start (h = 0, the single-shot
+    retrieval of Eq. 3), CUDA events around start + solve."""
     import torch
-    from paper_2202_08627_gb300 import build, ei, synth, warmstart, workloads
-    torch.cuda.set_device(0)
-    build.build()
-    wl = workloads.WORKLOADS[args.workload]()
+    from paper_2202_08627_gb300 import ei, synth
     device = torch.device("cuda", 0)
-    gamma, m_pos = 5e-7, -0.24
-    seeds = [wl.seed0 + s for s in range(wl.n_slices)]
-    G, s_exp = synth.build_problem(wl.slices, 1, seeds, device, wl.seed0, m=[m_pos],
-                                   linked_gamma=gamma)
+    seeds = [seed0 + s for s in range(len(slices))]
+    G, s_exp = synth.build_problem(slices, 1, seeds, device, seed0, m=[SLOPE_M],
+                                   linked_gamma=LINKED_GAMMA)
     G.variant = ei.ei_autotune(G)
-    ei.ei_set_linked(G, gamma)
-    eq = wl.voxel_equiv_1024()
+    ei.ei_set_linked(G, LINKED_GAMMA)
+    eq = sum(n * n for n, _, _ in slices) / 1024.0 ** 2
     out = {}
-    for start in ("zero", "eq3"):
+    for start in starts:
         vol = G.empty("vol", device)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         if start == "eq3":
-            ei.ei_single_shot_eq3(G, s_exp, 0, gamma, vol)
-        rep = ei.ei_reconstruct(G, s_exp, vol, tol=args.tol, max_iter=args.ttt_max_iter,
-                                raise_on_error=False)
+            ei.ei_single_shot_eq3(G, s_exp, 0, LINKED_GAMMA, vol)
+        rep = ei.ei_reconstruct(G, s_exp, vol, tol=tol, max_iter=max_iter, raise_on_error=False)
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) * 1e-3
         it = rep.iterations
-        out[start] = {"seconds": t, "seconds_per_1024_slice": t / eq,
+        out[start] = {"seconds": t, "seconds_per_slice": t / len(slices),
+                      "seconds_per_1024_slice": t / eq,
                       "iterations_mean": float(it.mean()), "iterations_max": int(it.max()),
                       "converged": int(rep.converged.sum()),
                       "f_final_sum": float(np.sum(rep.f_final))}
-    print(json.dumps({"run": "ttt_linked_single_m", "workload": wl.name, "gamma_cm": gamma,
-                      "m": m_pos, "tol": args.tol, "slices": wl.n_slices,
-                      "kernel_variant": list(G.variant), "time_to_tolerance": out}), flush=True)
+    variant = list(G.variant)
     G.close()
+    return out, variant
+
+
+def run_ttt_linked(args):
+    """Single-mask-position linked model on the workload's slices (see
+    ttt_linked).  Prints one line."""
+    import torch
+    from paper_2202_08627_gb300 import build, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    wl = workloads.WORKLOADS[args.workload]()
+    out, variant = ttt_linked(wl.slices, wl.seed0, args.tol, args.ttt_max_iter)
+    print(json.dumps({"run": "ttt_linked_single_m", "workload": wl.name, "gamma_cm": LINKED_GAMMA,
+                      "m": SLOPE_M, "tol": args.tol, "slices": wl.n_slices,
+                      "kernel_variant": variant, "time_to_tolerance": out}), flush=True)
+
+
+def run_sweep_n(args):
+    """The paper's size sweep (total iteration time for N_t = N_theta = 360,
+    720, 1440 with its single-mask linked model): per size, one slice alone
+    and a batch of 16, solved from h = 0 to --tol.  Prints one line."""
+    import torch
+    from paper_2202_08627_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    rows = []
+    for N in (360, 720, 1440):
+        for batch in (1, 16):
+            out, variant = ttt_linked([(N, N, N)] * batch, 7000 + N, args.tol, args.ttt_max_iter,
+                                      starts=("zero",))
+            z = out["zero"]
+            rows.append({"N": N, "batch": batch, "seconds": z["seconds"],
+                         "seconds_per_slice": z["seconds_per_slice"],
+                         "iterations_mean": z["iterations_mean"], "converged": z["converged"],
+                         "kernel_variant": variant})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"run": "sweep_n_linked_single_m", "tol": args.tol, "gamma_cm": LINKED_GAMMA,
+                      "m": SLOPE_M, "rows": rows}), flush=True)
 
 
 def run_profile_unet(args):
@@ -609,6 +643,8 @@ def main():
     ap.add_argument("--cnn-epochs", type=int, default=20)
     ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")
     ap.add_argument("--cnn-save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--sweep-n", action="store_true",
+                    help="single-m linked model, N_t = N_theta = 360 / 720 / 1440: time to tolerance, then exit")
     ap.add_argument("--ttt-linked", action="store_true",
                     help="single-m linked model: time to tolerance from 0 and from Eq. 3, then exit")
     ap.add_argument("--oracle-timing", action="store_true",
@@ -626,6 +662,8 @@ def main():
         return run_oracle_timing(args)
     if args.ttt_linked:
         return run_ttt_linked(args)
+    if args.sweep_n:
+        return run_sweep_n(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
