@@ -102,6 +102,11 @@ class Geometry:
     lam, scale   per channel (mu, delta, sigma): regulariser weight and the
                  variable scaling u = x / scale the solver works in
     m_o, m_r     optional drift [n_theta] and ring [n_det] offsets (Eq. 4)
+    flat_table   optional sampled flat IC [n_det][K]: f(t, k / K) over one period
+                 (periodic in m with period 1); when given it replaces the
+                 Gaussian (flat_A/c/w) in the model, interpolated in m by
+                 periodic Catmull-Rom splines, and the scatter channel has no
+                 effect
     """
     n: int
     n_theta: int
@@ -119,6 +124,7 @@ class Geometry:
     scale: np.ndarray = field(default_factory=lambda: np.array([1.0, 1e-6, 1.0]))
     m_o: Optional[np.ndarray] = None
     m_r: Optional[np.ndarray] = None
+    flat_table: Optional[np.ndarray] = None
 
     @property
     def n_m(self) -> int:
@@ -185,6 +191,25 @@ def _shift_terms(geom: Geometry, P_delta: np.ndarray) -> np.ndarray:
     return shift
 
 
+def table_interp(table: np.ndarray, x: np.ndarray):
+    """Periodic Catmull-Rom interpolation of per-pixel samples table[t][k] at
+    m = k / K, evaluated at x[..., t] (periods); returns (f, df/dm).  With
+    u = x K = i + s: f = sum_{d=-1..2} table[(i + d) mod K] c_d(s), the cubic
+    Hermite weights with slopes (p_{i+1} - p_{i-1}) / 2."""
+    K = table.shape[1]
+    u = np.asarray(x, dtype=np.float64) * K
+    i = np.floor(u).astype(np.int64)
+    s = u - i
+    cols = np.arange(table.shape[0])
+    p = [table[cols, np.mod(i + d, K)] for d in (-1, 0, 1, 2)]
+    s2, s3 = s * s, s * s * s
+    f = 0.5 * ((-s3 + 2 * s2 - s) * p[0] + (3 * s3 - 5 * s2 + 2) * p[1] +
+               (-3 * s3 + 4 * s2 + s) * p[2] + (s3 - s2) * p[3])
+    df = 0.5 * ((-3 * s2 + 4 * s - 1) * p[0] + (9 * s2 - 10 * s) * p[1] +
+                (-9 * s2 + 8 * s + 1) * p[2] + (3 * s2 - 2 * s) * p[3]) * K
+    return f, df
+
+
 def ic_model(P: np.ndarray, geom: Geometry) -> np.ndarray:
     """s_mod(t, theta, m) from the three projections P = [R mu, R delta, R sigma].
 
@@ -193,10 +218,14 @@ def ic_model(P: np.ndarray, geom: Geometry) -> np.ndarray:
       V = w^2 + kappa R[sigma].
     """
     P_mu, P_delta, P_sigma = P
-    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
     shift = _shift_terms(geom, P_delta)
-    V = w * w + geom.kappa * P_sigma
     out = np.empty((geom.n_m,) + P_mu.shape)
+    if geom.flat_table is not None:                 # sampled flat IC: s = T f_t(m - shift)
+        for k, mk in enumerate(geom.m):
+            out[k] = np.exp(-P_mu) * table_interp(geom.flat_table, mk - shift)[0]
+        return out
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
+    V = w * w + geom.kappa * P_sigma
     for k, mk in enumerate(geom.m):
         q = mk - c - shift
         out[k] = np.exp(-P_mu) * A * (w / np.sqrt(V)) * np.exp(-q * q / (2.0 * V))
@@ -215,8 +244,25 @@ def ic_objective_grad(P: np.ndarray, s_exp: np.ndarray, geom: Geometry,
       dS/dR[sigma] = kappa sum_m 2 e s (q^2 - V) / (2 V^2)
     """
     P_mu, P_delta, P_sigma = P
-    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
     shift = _shift_terms(geom, P_delta)
+    if geom.flat_table is not None:
+        # s = T f_t(m - shift): dS/dR[mu] = sum 2 e (-s), dS/dshift = sum 2 e (-T f')
+        T = np.exp(-P_mu)
+        S, G_mu, G_shift = 0.0, np.zeros_like(P_mu), np.zeros_like(P_mu)
+        for k, mk in enumerate(geom.m):
+            f, df = table_interp(geom.flat_table, mk - shift)
+            s = T * f
+            e = s - s_exp[k]
+            S += float(np.sum(e * e))
+            G_mu += 2.0 * e * (-s)
+            G_shift += 2.0 * e * (-T * df)
+        if not want_grad:
+            return S, None
+        g = np.zeros_like(P)
+        g[0] = G_mu
+        g[1] = geom.z_over_p * deriv_T(G_shift, geom.pitch)
+        return S, g
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
     V = w * w + geom.kappa * P_sigma
     if np.any(V <= 0.01 * w * w):
         return np.inf, (np.zeros_like(P) if want_grad else None)
@@ -247,12 +293,18 @@ def shift_gradient(P: np.ndarray, s_exp: np.ndarray, geom: Geometry) -> np.ndarr
     enters the model only through q = m - c - shift).  Zero where the model
     leaves its domain."""
     P_mu, P_delta, P_sigma = P
-    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
     shift = _shift_terms(geom, P_delta)
+    G = np.zeros_like(P_mu)
+    if geom.flat_table is not None:
+        T = np.exp(-P_mu)
+        for k, mk in enumerate(geom.m):
+            f, df = table_interp(geom.flat_table, mk - shift)
+            G += 2.0 * (T * f - s_exp[k]) * (-T * df)
+        return G
+    A, c, w = geom.flat_A[None, :], geom.flat_c[None, :], geom.flat_w[None, :]
     V = w * w + geom.kappa * P_sigma
     if np.any(V <= 0.01 * w * w):
         return np.zeros_like(P_mu)
-    G = np.zeros_like(P_mu)
     for k, mk in enumerate(geom.m):
         q = mk - c - shift
         s = np.exp(-P_mu) * A * (w / np.sqrt(V)) * np.exp(-q * q / (2.0 * V))
