@@ -339,8 +339,9 @@ int ei_single_shot_eq3(ei_geometry *g, const float *s_exp, int m_index, double g
  * m_o / m_r are shared by every slice, the gradient of the shared array is the
  * sum over slices); either may be NULL.  Values are unspecified where S is
  * +inf.  The first call allocates one float per sinogram pixel of scratch;
- * stream-ordered otherwise.  Not part of the paper's solver here (m_o and m_r
- * stay fixed during ei_reconstruct).
+ * stream-ordered otherwise.  With a sampled flat IC (ei_set_flat_table)
+ * dS/dshift = sum_m 2 (s_mod - s_exp) (-exp(-R[mu]) f'(m - shift)).
+ * ei_set_offset_unknowns makes m_o / m_r unknowns of ei_reconstruct.
  */
 int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *g_mo, float *g_mr,
                    void *stream);
@@ -359,6 +360,27 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
  * evaluation then also computes dS/dshift per pixel (one more pass over the
  * projections and measured ICs).
  */
+/*
+ * Sampled flat IC.  The paper's flat IC is measured by stepping the mask over
+ * one period (acquisition section); instead of its Gaussian fit (flat_A,
+ * flat_c, flat_w of ei_setup_geometry) the model can use the samples
+ * themselves:  s(t, theta, m) = exp(-R[mu]) f_t(m - shift),  shift as in
+ * Eq. 4, with f_t interpolated in m by periodic cubic Catmull-Rom splines
+ * through table[t][k] = f_t(k / K), k = 0 .. K-1 (m in periods, period 1).
+ * table: host or device pointer, [sum n_det][K] floats row-major, pixels in
+ * the order of flat_A (slice by slice); copied into the geometry, which
+ * keeps no reference, after a device synchronisation (no kernel may be
+ * reading the previous table).  R[sigma] has no effect in this model:
+ * its gradient is 0 and V's domain check is off.  Affects ei_ic_model,
+ * ei_forward, ei_objective / ei_objective_grad, ei_offset_grad and
+ * ei_reconstruct (which run the one-block-per-row IC kernel while a table is
+ * set); the single-shot retrievals keep the Gaussian parameters.  table =
+ * NULL or K = 0 restores the Gaussian.  EI_ERR_ARG for K outside
+ * [4, 65536]; EI_ERR_ALLOC / EI_ERR_CUDA when the copy fails, after which
+ * the Gaussian flat is in effect.
+ */
+int ei_set_flat_table(ei_geometry *g, const float *table, int K);
+
 #define EI_OFFSET_MO 1
 #define EI_OFFSET_MR 2
 int ei_set_offset_unknowns(ei_geometry *g, int which, double scale);

@@ -871,6 +871,38 @@ int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r)
     return EI_OK;
 }
 
+int ei_set_flat_table(ei_geometry *g, const float *table, int K)
+{
+    if (!g) return EI_ERR_ARG;
+    if (!table || K == 0) {
+        g->dg.flat_tab = nullptr;
+        g->dg.flat_k = 0;
+        return EI_OK;
+    }
+    if (K < 4 || K > 65536) return EI_ERR_ARG;
+    int64_t n_px = 0;
+    for (const SliceInfo &si : g->h_slices) n_px += si.n_det;
+    const int64_t count = n_px * K;
+    // no kernel of any stream may read the old table while it is overwritten
+    cudaError_t e = cudaDeviceSynchronize();
+    g->dg.flat_tab = nullptr;
+    g->dg.flat_k = 0;
+    if (e == cudaSuccess && count > g->flat_cap) {
+        e = dev_alloc(g, &g->flat_buf, (size_t)count);
+        g->flat_cap = e == cudaSuccess ? count : 0;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->flat_buf, table, (size_t)count * sizeof(float), cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        record_error(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    }
+    g->dg.flat_tab = g->flat_buf;
+    g->dg.flat_k = K;
+    return EI_OK;
+}
+
 int ei_set_linked(ei_geometry *g, double gamma)
 {
     if (!g || !(gamma >= 0.0) || !isfinite(gamma)) return EI_ERR_ARG;

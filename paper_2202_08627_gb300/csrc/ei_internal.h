@@ -111,6 +111,10 @@ struct DevGeom {
     const int *vec_nvb = nullptr;
     const int64_t *off_start = nullptr;
     const int *off_len = nullptr;
+    // sampled flat IC (null: the Gaussian of pix): [sum n_det][flat_k] samples
+    // f(t, k / flat_k) over one mask period, rows in the order of det_off
+    const float *flat_tab = nullptr;
+    int flat_k = 0;
 };
 
 #ifdef __CUDACC__
@@ -168,6 +172,8 @@ struct ei_geometry {
     float *shift_scratch = nullptr;    // [sino4_count] dS/dshift (ei_offset_grad, allocated on use)
     double *row_sums = nullptr;        // [total_ic]
     float *eq3_ker = nullptr;          // [sum n_det] Eq. 3 convolution kernels (allocated on use)
+    float *flat_buf = nullptr;         // storage of dg.flat_tab (allocated on use)
+    int64_t flat_cap = 0;              // its capacity in floats
     int *dev_status = nullptr;         // [1] device-side error status (bounded waits)
     int num_sms = 0;
     int *work_counter = nullptr;       // [2] work counters of the persistent kernels

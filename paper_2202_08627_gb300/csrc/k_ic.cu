@@ -15,6 +15,12 @@
 // D needs R[delta] at t +- 1 and D^T needs G_sh at t +- 1, so the whole row
 // is staged in shared memory (no halo recompute, no atomics).
 //
+// With a sampled flat IC (ei_set_flat_table) variant 0 runs with the Gaussian
+// replaced by f(t, m - shift), f interpolated in m by periodic Catmull-Rom
+// splines of the pixel's K samples over one period:
+//   s_m = exp(-R[mu]) f(m - shift),  ds_m/dshift = -exp(-R[mu]) f'(m - shift)
+// and R[sigma] has no effect (its gradient is 0).
+//
 // Memory traffic per pixel (M = n_m): 12 B of projections + 4M B of s_exp
 // read, 24 B of packed g written; the per-pixel flat IC table is shared by all angles
 // and stays in L2.  The kernel is HBM-bound.
@@ -60,7 +66,31 @@ __device__ __forceinline__ float deriv_at(const float *ps, int j, int n, float i
     return (ps[j + 1] - ps[j - 1]) * (0.5f * inv_h);
 }
 
-template <int MODE>
+// Periodic Catmull-Rom interpolation of one pixel's K samples p_k = f(k / K)
+// at x (in periods): with u = x K = i + r (0 <= r < 1) the cubic Hermite
+// segment between p_i and p_{i+1} whose end slopes are the central
+// differences (p_{i+1} - p_{i-1}) / 2 and (p_{i+2} - p_i) / 2; indices mod K.
+// f and df = df/dx.  Every index stays in [0, K) for any x, NaN included.
+__device__ __forceinline__ void flat_table_eval(const float *__restrict__ tab, int K, float x,
+                                                float &f, float &df)
+{
+    const float u = x * (float)K;
+    const float fl = floorf(u);
+    const float r = u - fl;
+    int i = (int)fl % K;                     // cvt saturates (NaN -> 0): i in (-K, K)
+    if (i < 0) i += K;
+    const int im = i == 0 ? K - 1 : i - 1;
+    const int i1 = i + 1 == K ? 0 : i + 1;
+    const int i2 = i1 + 1 == K ? 0 : i1 + 1;
+    const float p0 = __ldg(tab + im), p1 = __ldg(tab + i), p2 = __ldg(tab + i1), p3 = __ldg(tab + i2);
+    const float m1 = 0.5f * (p2 - p0), m2 = 0.5f * (p3 - p1), d = p2 - p1;
+    // Hermite form: f = p1 + r (m1 + r (3d - 2 m1 - m2 + r (m1 + m2 - 2d)))
+    const float c2 = 3.f * d - 2.f * m1 - m2, c3 = m1 + m2 - 2.f * d;
+    f = fmaf(r, fmaf(r, fmaf(r, c3, c2), m1), p1);
+    df = (float)K * fmaf(r, fmaf(r, 3.f * c3, 2.f * c2), m1);
+}
+
+template <int MODE, bool TABLE>
 __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
                      float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
                      double *__restrict__ part, const int *__restrict__ active)
@@ -103,6 +133,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
         const float pmv[4] = {pm4.x, pm4.y, pm4.z, pm4.w};
         const float psv[4] = {ps4.x, ps4.y, ps4.z, ps4.w};
         float c[4], shift[4], iV[4], amp[4];
+        const float *tab[4];
         bool ok[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -111,11 +142,18 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
             const float4 fl = ok[q] ? __ldg(pix + j) : make_float4(0.f, 0.f, 1.f, 0.f);  // A, c, w, m_r
             c[q] = fl.y;
             shift[q] = ok[q] ? zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w : 0.f;
-            const float V = fmaf(kappa, psv[q], fl.z * fl.z);
-            if (ok[q] && !(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
-            const float Vs = fmaxf(V, 1e-30f);
-            iV[q] = 1.0f / Vs;
-            amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
+            if (TABLE) {
+                // amp = transmission; the padding pixels read the slice's first row
+                tab[q] = dg.flat_tab + (int64_t)(si.det_off + (ok[q] ? j : 0)) * dg.flat_k;
+                iV[q] = 1.f;
+                amp[q] = ok[q] ? expf(-pmv[q]) : 0.f;
+            } else {
+                const float V = fmaf(kappa, psv[q], fl.z * fl.z);
+                if (ok[q] && !(V > 0.01f * fl.z * fl.z)) out_of_domain = true;
+                const float Vs = fmaxf(V, 1e-30f);
+                iV[q] = 1.0f / Vs;
+                amp[q] = ok[q] ? fl.x * fl.z * rsqrtf(Vs) : 0.f;
+            }
         }
         float st[4] = {0.f, 0.f, 0.f, 0.f}, stq[4] = {0.f, 0.f, 0.f, 0.f},
               stq2[4] = {0.f, 0.f, 0.f, 0.f};
@@ -126,8 +164,16 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
             float sv[4], qd[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                qd[q] = mk - c[q] - shift[q];
-                sv[q] = amp[q] * expf(-pmv[q] - 0.5f * qd[q] * qd[q] * iV[q]);
+                if (TABLE) {
+                    // qd = ds/dshift = -T f' (the Gaussian's s q / V with V = 1)
+                    float f, df;
+                    flat_table_eval(tab[q], dg.flat_k, mk - shift[q], f, df);
+                    sv[q] = amp[q] * f;
+                    qd[q] = -amp[q] * df;
+                } else {
+                    qd[q] = mk - c[q] - shift[q];
+                    sv[q] = amp[q] * expf(-pmv[q] - 0.5f * qd[q] * qd[q] * iV[q]);
+                }
             }
             if (MODE == IC_MODEL) {
                 reinterpret_cast<float4 *>(s_mod + si.meas_off + rbase)[k * plane4 + gi] =
@@ -143,8 +189,12 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
                     if (MODE == IC_OBJECTIVE_GRAD) {
                         const float t = 2.f * e * sv[q];
                         st[q] += t;
-                        stq[q] = fmaf(t, qd[q], stq[q]);
-                        stq2[q] = fmaf(t * qd[q], qd[q], stq2[q]);
+                        if (TABLE) {
+                            stq[q] = fmaf(2.f * e, qd[q], stq[q]);
+                        } else {
+                            stq[q] = fmaf(t, qd[q], stq[q]);
+                            stq2[q] = fmaf(t * qd[q], qd[q], stq2[q]);
+                        }
                     }
                 }
             }
@@ -155,7 +205,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 gsh[q] = stq[q] * iV[q];
-                gvv[q] = kappa * 0.5f * iV[q] * (stq2[q] * iV[q] - st[q]);
+                gvv[q] = TABLE ? 0.f : kappa * 0.5f * iV[q] * (stq2[q] * iV[q] - st[q]);
             }
             s_gsh4[gi] = make_float4(gsh[0], gsh[1], gsh[2], gsh[3]);
             s_gmu4[gi] = make_float4(-st[0], -st[1], -st[2], -st[3]);
@@ -568,6 +618,7 @@ static cudaError_t ic_pipe_set_smem_limit()
 // k_offset_sums: one block per slice, FP64 sums over the slice's angles in
 // angle order.  Deterministic; not on the solver's path.
 // ---------------------------------------------------------------------------
+template <bool TABLE>
 __global__ void k_shift_grad(DevGeom dg, const float *__restrict__ proj,
                              const float *__restrict__ meas, float *__restrict__ shift,
                              double *__restrict__ row_sum, const int *__restrict__ active)
@@ -594,18 +645,31 @@ __global__ void k_shift_grad(DevGeom dg, const float *__restrict__ proj,
         float g = 0.f;
         if (j < nd) {
             const float4 fl = __ldg(pix + j);           // A, c, w, m_r
-            const float cs = fl.y + zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w;
-            const float Vs = fmaxf(fmaf(kappa, Ps[j], fl.z * fl.z), 1e-30f);
-            const float iV = 1.0f / Vs;
-            const float amp = fl.x * fl.z * rsqrtf(Vs);
+            const float shift = zp * deriv_at(s_pd, j, nd, si.inv_pitch) + mo + fl.w;
             const float pm = Pm[j];
-            float stq = 0.f;
-            for (int k = 0; k < dg.mc.n_m; ++k) {
-                const float q = dg.mc.m[k] - cs;
-                const float sv = amp * expf(-pm - 0.5f * q * q * iV);
-                stq = fmaf((sv - Sx[k * plane + j]) * sv, q, stq);
+            if (TABLE) {                                // ds/dshift = -T f'(m - shift)
+                const float *tab = dg.flat_tab + (int64_t)(si.det_off + j) * dg.flat_k;
+                const float T = expf(-pm);
+                float acc2 = 0.f;
+                for (int k = 0; k < dg.mc.n_m; ++k) {
+                    float f, df;
+                    flat_table_eval(tab, dg.flat_k, dg.mc.m[k] - shift, f, df);
+                    acc2 = fmaf(T * f - Sx[k * plane + j], -T * df, acc2);
+                }
+                g = 2.f * acc2;
+            } else {
+                const float cs = fl.y + shift;
+                const float Vs = fmaxf(fmaf(kappa, Ps[j], fl.z * fl.z), 1e-30f);
+                const float iV = 1.0f / Vs;
+                const float amp = fl.x * fl.z * rsqrtf(Vs);
+                float stq = 0.f;
+                for (int k = 0; k < dg.mc.n_m; ++k) {
+                    const float q = dg.mc.m[k] - cs;
+                    const float sv = amp * expf(-pm - 0.5f * q * q * iV);
+                    stq = fmaf((sv - Sx[k * plane + j]) * sv, q, stq);
+                }
+                g = 2.f * stq * iV;
             }
-            g = 2.f * stq * iV;
         }
         shift[si.sino_off + rbase + j] = g;
         acc += (double)g;
@@ -645,15 +709,44 @@ cudaError_t launch_shift_grad(const ei_geometry *g, const float *proj, const flo
                               float *shift, double *row_sum, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
-    k_shift_grad<<<g->dg.total_ic, 256, (size_t)g->dg.max_ndp * sizeof(float), st>>>(
-        g->dg, proj, meas, shift, row_sum, active);
+    const size_t smem = (size_t)g->dg.max_ndp * sizeof(float);
+    if (g->dg.flat_tab)
+        k_shift_grad<true><<<g->dg.total_ic, 256, smem, st>>>(g->dg, proj, meas, shift, row_sum, active);
+    else
+        k_shift_grad<false><<<g->dg.total_ic, 256, smem, st>>>(g->dg, proj, meas, shift, row_sum, active);
     return cudaGetLastError();
+}
+
+template <bool TABLE>
+static void launch_ic_rows(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
+                           double *part, IcMode mode, const int *active, cudaStream_t st)
+{
+    const int threads = ic_threads(g, 4, 512);
+    const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
+    switch (mode) {
+    case IC_MODEL:
+        k_ic<IC_MODEL, TABLE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA,
+                                                                      g->gB, part, active);
+        break;
+    case IC_OBJECTIVE:
+        k_ic<IC_OBJECTIVE, TABLE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
+                                                                          g->gA, g->gB, part, active);
+        break;
+    default:
+        k_ic<IC_OBJECTIVE_GRAD, TABLE><<<g->dg.total_ic, threads, smem, st>>>(
+            g->dg, proj, meas, s_mod, g->gA, g->gB, part, active);
+        break;
+    }
 }
 
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
                       double *part, IcMode mode, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
+    if (g->dg.flat_tab) {                        // the sampled flat runs one block per row
+        launch_ic_rows<true>(g, proj, meas, s_mod, part, mode, active, st);
+        return cudaGetLastError();
+    }
     if (g->ic_variant == 1) {
         switch (mode) {
         case IC_MODEL: return launch_ic_pipe<IC_MODEL>(g, proj, meas, s_mod, part, active, st);
@@ -661,31 +754,25 @@ cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas
         default: return launch_ic_pipe<IC_OBJECTIVE_GRAD>(g, proj, meas, s_mod, part, active, st);
         }
     }
-    const int threads = ic_threads(g, 4, 512);
-    const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
-    switch (mode) {
-    case IC_MODEL:
-        k_ic<IC_MODEL><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA,
-                                                               g->gB, part, active);
-        break;
-    case IC_OBJECTIVE:
-        k_ic<IC_OBJECTIVE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
-                                                                   g->gA, g->gB, part, active);
-        break;
-    default:
-        k_ic<IC_OBJECTIVE_GRAD><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
-                                                                        g->gA, g->gB, part, active);
-        break;
-    }
+    launch_ic_rows<false>(g, proj, meas, s_mod, part, mode, active, st);
     return cudaGetLastError();
+}
+
+template <bool TABLE>
+static cudaError_t ic_rows_set_smem_limit(int bytes)
+{
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_MODEL, TABLE>, a, bytes));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE, TABLE>, a, bytes));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE_GRAD, TABLE>, a, bytes));
+    return cudaSuccess;
 }
 
 cudaError_t ic_set_smem_limit()
 {
     const int bytes = 4 * EI_MAX_NDET * (int)sizeof(float);
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    EI_CUDA_TRY(cudaFuncSetAttribute(k_ic<IC_OBJECTIVE_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    EI_CUDA_TRY(ic_rows_set_smem_limit<false>(bytes));
+    EI_CUDA_TRY(ic_rows_set_smem_limit<true>(bytes));
     EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_MODEL>());
     EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_OBJECTIVE>());
     EI_CUDA_TRY(ic_pipe_set_smem_limit<IC_OBJECTIVE_GRAD>());

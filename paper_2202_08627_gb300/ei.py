@@ -92,7 +92,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
             "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
-            "ei_unet_set_tensor_path"]
+            "ei_unet_set_tensor_path", "ei_set_flat_table"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
@@ -152,6 +152,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_offset_unknowns.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ei_get_offsets.restype = c_int
+    lib.ei_set_flat_table.argtypes = [c_void_p, c_void_p, c_int]
+    lib.ei_set_flat_table.restype = c_int
     lib.ei_set_linked.argtypes = [c_void_p, c_double]
     lib.ei_set_linked.restype = c_int
     lib.ei_offset_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
@@ -621,6 +623,25 @@ def ei_get_offsets(geom: Geometry):
     _check(load_library().ei_get_offsets(geom.handle, m_o.ctypes.data, m_r.ctypes.data),
            "ei_get_offsets")
     return m_o, m_r
+
+
+def ei_set_flat_table(geom: Geometry, table) -> None:
+    """Sampled flat IC [sum n_det][K] (f(t, k / K) over one mask period, float32
+    numpy array or CUDA tensor); None restores the Gaussian flat."""
+    lib = load_library()
+    if table is None:
+        _check(lib.ei_set_flat_table(geom.handle, None, 0), "ei_set_flat_table")
+        return
+    n_px = sum(sl.n_det for sl in geom.slices)
+    if len(table.shape) != 2 or table.shape[0] != n_px:
+        raise ValueError("flat table must be [%d][K], got %s" % (n_px, tuple(table.shape)))
+    K = int(table.shape[1])
+    if isinstance(table, np.ndarray):
+        host = np.ascontiguousarray(table, dtype=np.float32)
+        _check(lib.ei_set_flat_table(geom.handle, host.ctypes.data, K), "ei_set_flat_table")
+    else:
+        dev = table.contiguous().float()
+        _check(lib.ei_set_flat_table(geom.handle, _dptr(dev, "table"), K), "ei_set_flat_table")
 
 
 def ei_set_linked(geom: Geometry, gamma: float) -> None:
