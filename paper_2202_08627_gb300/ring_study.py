@@ -13,14 +13,19 @@ for noise-free data).  Errors of the estimated flat are fixed per detector
 pixel and become ring artifacts; the ring term m_r(t) of Eq. 4, solved for
 together with h, absorbs the shift part of them.
 
+With --asym a > 0 the true flat is not a Gaussian: the periodised Gaussian
+times (1 + a sin 2 pi (m - c)), so the Gaussian fit has a model error.
+
 Reconstructions: the iterative method (linked unknown h, relative change
-1e-6) with m_r fixed at 0 or among the unknowns, and the single-shot
-retrieval of Eq. 3 + FBP.  Measures: the CNR of Eq. 7 between every pair of
-granules over discs of 0.6 granule radius; the FRC of Eq. 6 between the
+1e-6) with m_r fixed at 0 or among the unknowns, the iterative method with
+the averaged flat scans themselves as a sampled flat (no fit, "iter_tab"),
+the iterative method with the true flat ("iter_true_flat", the bound), and
+the single-shot retrieval of Eq. 3 + FBP.  Measures: the CNR of Eq. 7
+between every pair of granules over discs of 0.6 granule radius; the FRC of Eq. 6 between the
 reconstructions of the odd and of the even angles (independent noise), over
 the central 140/220 of the slice, with the 0.5 cutoff.
 
-    python -m paper_2202_08627_gb300.ring_study --n 256 --n-theta 400
+    python -m paper_2202_08627_gb300.ring_study --n 256 --n-theta 400 [--asym 0.15]
 """
 from __future__ import annotations
 
@@ -47,15 +52,52 @@ def phantom():
             for (x, y, r, mu) in GRANULES]
 
 
-def estimate_flat(A, c, w, repeats: int, seed: int):
-    """Per-pixel Gaussian (A, c, w) fitted to `repeats` averaged flat scans."""
+def flat_positions():
+    """Mask positions of a flat scan: FLAT_STEPS steps from -0.5 to 0.5 periods
+    (the two ends are the same phase)."""
+    return -0.5 + np.arange(FLAT_STEPS) / (FLAT_STEPS - 1)
+
+
+def true_flat(A, c, w, asym: float, m):
+    """The true flat IC f_t(m), [len(m)][n_det]: the Gaussian (A, c, w) for
+    asym = 0, else the Gaussian summed over its periodic images times
+    (1 + asym sin 2 pi (m - c)), an asymmetric, periodic curve that no
+    Gaussian fits exactly."""
+    m = np.asarray(m, dtype=np.float64)[:, None]
+    if asym == 0.0:
+        return A[None, :] * np.exp(-(m - c[None, :]) ** 2 / (2 * w[None, :] ** 2))
+    d = m - c[None, :]
+    g = sum(np.exp(-(d + j) ** 2 / (2 * w[None, :] ** 2)) for j in range(-3, 4))
+    return A[None, :] * g * (1.0 + asym * np.sin(2 * np.pi * d))
+
+
+def flat_scans(A, c, w, repeats: int, seed: int, asym: float = 0.0):
+    """`repeats` flat scans with Poisson counts, averaged: [steps][n_det] counts."""
     rng = np.random.Generator(np.random.PCG64([seed, 91]))
-    m = -0.5 + np.arange(FLAT_STEPS) / (FLAT_STEPS - 1)
-    lam = FLAT_COUNTS * A[None, :] * np.exp(-(m[:, None] - c[None, :]) ** 2 / (2 * w[None, :] ** 2))
-    f = rng.poisson(lam[None].repeat(repeats, 0)).mean(axis=0)          # [steps][n_det]
+    lam = FLAT_COUNTS * true_flat(A, c, w, asym, flat_positions())
+    return rng.poisson(lam[None].repeat(repeats, 0)).mean(axis=0)
+
+
+def flat_table(f):
+    """The averaged scans as a sampled flat over one period, [n_det][K] with
+    K = FLAT_STEPS - 1 samples at phase k / K (the duplicated end phase
+    averaged), normalised like the model's intensities."""
+    K = FLAT_STEPS - 1
+    steps = f / FLAT_COUNTS
+    per = steps[:K].copy()
+    per[0] = 0.5 * (steps[0] + steps[K])
+    phase = np.rint((flat_positions()[:K] % 1.0) * K).astype(int) % K
+    table = np.empty((f.shape[1], K))
+    table[:, phase] = per.T
+    return table
+
+
+def estimate_flat(f):
+    """Per-pixel Gaussian (A, c, w) fitted to averaged flat scans f [steps][n_det]."""
+    m = flat_positions()
     # weighted least squares of log f = a0 + a1 m + a2 m^2, weights f (Poisson variance of log f ~ 1/f)
     X = np.stack([np.ones_like(m), m, m * m], axis=1)
-    A_e, c_e, w_e = np.empty_like(A), np.empty_like(c), np.empty_like(w)
+    A_e, c_e, w_e = (np.empty(f.shape[1]) for _ in range(3))
     for j in range(f.shape[1]):
         wt = f[:, j]
         ok = wt > 0
@@ -76,10 +118,13 @@ def geometry(n, theta, A, c, w):
         scale=inputs.SCALE)
 
 
-def measure(n, theta, A, c, w, seed, device="cuda"):
+def measure(n, theta, A, c, w, seed, device="cuda", asym: float = 0.0):
     """Sample scan with the true flat: exact line integrals of the granules,
-    the library's IC model, Poisson noise."""
+    the library's IC model (for asym > 0 with the true flat tabulated at 512
+    steps), Poisson noise."""
     G = geometry(n, theta, A, c, w)
+    if asym != 0.0:
+        ei.ei_set_flat_table(G, true_flat(A, c, w, asym, np.arange(512) / 512).T.astype(np.float32))
     P = inputs.ellipse_line_integrals_torch(phantom(), theta, n, inputs.pitch_for(n), device)
     proj = G.empty("proj", device)
     proj.view(3, len(theta), G.slices[0].n_dp)[:, :, :n] = P
@@ -89,10 +134,14 @@ def measure(n, theta, A, c, w, seed, device="cuda"):
     return inputs.poisson_noise_torch(clean, seed=seed)
 
 
-def reconstruct(n, theta, flat, s_exp, mode: str, tol: float = 1e-6, max_iter: int = 300):
+def reconstruct(n, theta, flat, s_exp, mode: str, tol: float = 1e-6, max_iter: int = 300,
+                table=None):
     """h [n][n] from one of: "iter" (m_r = 0), "iter_mr" (m_r among the
-    unknowns), "eq3" (single shot)."""
+    unknowns), "eq3" (single shot), with the flat IC `flat` = (A, c, w) or, for
+    the iterative modes when `table` ([n_det][K]) is given, that sampled flat."""
     G = geometry(n, theta, *flat)
+    if table is not None and mode != "eq3":
+        ei.ei_set_flat_table(G, np.ascontiguousarray(table, dtype=np.float32))
     vol = G.empty("vol", s_exp.device)
     info = {}
     if mode == "eq3":
@@ -114,11 +163,11 @@ def subset(s_exp, n_theta, n_dp, idx, device):
 
 
 def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed: int = 3,
-        device="cuda"):
+        device="cuda", asym: float = 0.0):
     import torch
     theta = inputs.angles(n_theta)
     A, c, w = inputs.flat_ic(seed, n)
-    s_exp = measure(n, theta, A, c, w, seed, device)
+    s_exp = measure(n, theta, A, c, w, seed, device, asym)
     n_dp = inputs.round_up4(n)
     half = 0.5 * n
     centres = [(half - y * half, half + x * half, r * half) for (x, y, r, _) in GRANULES]
@@ -126,28 +175,38 @@ def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed
     pairs = [(0, 1), (0, 2), (1, 2)]
     crop = slice(int(n * (0.5 - 70 / 220)), int(n * (0.5 + 70 / 220)))
     rows = []
+    odd, even = np.arange(1, n_theta, 2), np.arange(0, n_theta, 2)
+    truth = (A, c, w), (None if asym == 0.0 else true_flat(A, c, w, asym, np.arange(512) / 512).T)
+
+    def study(R, method, mode, flat, table, err):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h, info = reconstruct(n, theta, flat, s_exp, mode, table=table)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h_odd, _ = reconstruct(n, theta[odd], flat, subset(s_exp, n_theta, n_dp, odd, device), mode,
+                               table=table)
+        h_even, _ = reconstruct(n, theta[even], flat, subset(s_exp, n_theta, n_dp, even, device),
+                                mode, table=table)
+        curve = metrics.frc(h_odd[crop, crop], h_even[crop, crop])
+        row = {"flat_scans": R, "method": method, "seconds": dt, **info,
+               "cnr": {"%d-%d" % p: metrics.cnr(h, masks[p[0]], masks[p[1]]) for p in pairs},
+               "frc_resolution_px": metrics.frc_resolution(curve, crop.stop - crop.start),
+               "flat_error": err}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+
+    study(0, "iter_true_flat", "iter", truth[0], truth[1], {})
     for R in repeats:
-        flat = estimate_flat(A, c, w, R, seed + R)
+        scans = flat_scans(A, c, w, R, seed + R, asym)
+        flat = estimate_flat(scans)
         err = {"c_rms": float(np.sqrt(np.mean((flat[1] - c) ** 2))),
                "w_rel_rms": float(np.sqrt(np.mean((flat[2] / w - 1) ** 2))),
                "A_rel_rms": float(np.sqrt(np.mean((flat[0] / A - 1) ** 2)))}
         for mode in ("eq3", "iter", "iter_mr"):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            h, info = reconstruct(n, theta, flat, s_exp, mode)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            odd, even = np.arange(1, n_theta, 2), np.arange(0, n_theta, 2)
-            h_odd, _ = reconstruct(n, theta[odd], flat, subset(s_exp, n_theta, n_dp, odd, device), mode)
-            h_even, _ = reconstruct(n, theta[even], flat, subset(s_exp, n_theta, n_dp, even, device), mode)
-            curve = metrics.frc(h_odd[crop, crop], h_even[crop, crop])
-            row = {"flat_scans": R, "method": mode, "seconds": dt, **info,
-                   "cnr": {"%d-%d" % p: metrics.cnr(h, masks[p[0]], masks[p[1]]) for p in pairs},
-                   "frc_resolution_px": metrics.frc_resolution(curve, crop.stop - crop.start),
-                   "flat_error": err}
-            rows.append(row)
-            print(json.dumps(row), flush=True)
-    return {"n": n, "n_theta": n_theta, "gamma_cm": GAMMA, "m": SLOPE_M, "rows": rows}
+            study(R, mode, mode, flat, None, err)
+        study(R, "iter_tab", "iter", flat, flat_table(scans), err)
+    return {"n": n, "n_theta": n_theta, "gamma_cm": GAMMA, "m": SLOPE_M, "asym": asym, "rows": rows}
 
 
 def main(argv=None):
@@ -156,9 +215,11 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--n-theta", type=int, default=400)
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--asym", type=float, default=0.0,
+                    help="asymmetry of the true flat IC (0: Gaussian)")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
-    print(json.dumps(run(args.n, args.n_theta, seed=args.seed)))
+    print(json.dumps(run(args.n, args.n_theta, seed=args.seed, asym=args.asym)))
 
 
 if __name__ == "__main__":
