@@ -506,8 +506,8 @@ def ttt_linked(slices, seed0, tol, max_iter, starts=("zero", "eq3")):
     seeds = [seed0 + s for s in range(len(slices))]
     G, s_exp = synth.build_problem(slices, 1, seeds, device, seed0, m=[SLOPE_M],
                                    linked_gamma=LINKED_GAMMA)
-    G.variant = ei.ei_autotune(G)
     ei.ei_set_linked(G, LINKED_GAMMA)
+    G.variant = ei.ei_autotune(G)                 # the single-channel kernels
     eq = sum(n * n for n, _, _ in slices) / 1024.0 ** 2
     out = {}
     for start in starts:

@@ -114,20 +114,22 @@ void trace_end(ei_geometry *g, TracedKernel k, cudaEvent_t begin, cudaStream_t s
 }
 
 // Launch helpers that count and (when tracing) time the three path kernels.
-static cudaError_t traced_project(ei_geometry *g, float *proj, const int *active, cudaStream_t st)
+static cudaError_t traced_project(ei_geometry *g, float *proj, float link, const int *active,
+                                  cudaStream_t st)
 {
     cudaEvent_t b = trace_begin(g, st);
-    cudaError_t e = launch_project(g, proj, active, st);
+    cudaError_t e = launch_project(g, proj, link, active, st);
     trace_end(g, TK_PROJECT, b, st);
     count_launches(g, 1);
     return e;
 }
 
 static cudaError_t traced_ic(ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                             double *part, IcMode mode, const int *active, cudaStream_t st)
+                             double *part, IcMode mode, float link, const int *active,
+                             cudaStream_t st)
 {
     cudaEvent_t b = trace_begin(g, st);
-    cudaError_t e = launch_ic(g, proj, meas, s_mod, part, mode, active, st);
+    cudaError_t e = launch_ic(g, proj, meas, s_mod, part, mode, link, active, st);
     trace_end(g, TK_IC, b, st);
     count_launches(g, 1);
     return e;
@@ -185,10 +187,13 @@ cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double 
         reg1 = make_float4(g->lambda[0] * k[0], on1 * g->lambda[1] * k[1],
                            on1 * g->lambda[2] * k[2], 0.f);
     }
+    // linked: single-channel staging, projection and adjoint (the IC kernel
+    // combines the gradient sinogram into g_mu + gamma g_delta)
+    const float link = linked ? gam : 0.f;
     EI_CUDA_TRY(counted_prep(g, v, mult, linked, active, st));
-    EI_CUDA_TRY(traced_project(g, g->proj, active, st));
+    EI_CUDA_TRY(traced_project(g, g->proj, link, active, st));
     EI_CUDA_TRY(traced_ic(g, g->proj, meas, nullptr, g->part_ic,
-                          grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, active, st));
+                          grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, link, active, st));
     EI_CUDA_TRY(traced_backproject(g, grad != nullptr, v, grad, out_mult, reg2, reg1,
                                    linked ? gam : 0.f, g->part_adj, active, st));
     count_launches(g, 1);
@@ -601,7 +606,9 @@ static std::string tune_key(const ei_geometry *g)
     for (char &c : name)
         if (c == ' ') c = '_';
     char buf[64];
-    snprintf(buf, sizeof buf, "|%016llx|v1", (unsigned long long)g->shape_hash);
+    // linked geometries run the single-channel kernels: tuned separately
+    snprintf(buf, sizeof buf, "|%016llx|v1%s", (unsigned long long)g->shape_hash,
+             g->link_gamma > 0.f ? "L" : "");
     return name + buf;
 }
 
@@ -617,10 +624,11 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
     const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const int reps_ = reps;
     (void)reps_;
+    const float link = g->link_gamma;              // the kernels this geometry's evaluations run
     auto launch = [&]() {
-        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero, 0.f,
+        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero, link,
                                             g->part_adj, nullptr, st)
-                       : launch_project(g, g->proj, nullptr, st);
+                       : launch_project(g, g->proj, link, nullptr, st);
     };
     cudaError_t e = launch();                       // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -754,7 +762,7 @@ int ei_project(const ei_geometry *gc, const float *vol, float *proj, void *strea
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = counted_prep(g, (const float4 *)vol, make_float4(1.f, 1.f, 1.f, 0.f), false,
                                  nullptr, st);
-    if (e == cudaSuccess) e = traced_project(g, proj, nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, proj, 0.f, nullptr, st);
     return status_from(e);
 }
 
@@ -776,7 +784,7 @@ int ei_ic_model(const ei_geometry *gc, const float *proj, float *s_mod, void *st
 {
     if (!gc || !proj || !s_mod || !aligned16(proj) || !aligned16(s_mod)) return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
-    return status_from(traced_ic(g, proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr,
+    return status_from(traced_ic(g, proj, nullptr, s_mod, g->part_ic, IC_MODEL, 0.f, nullptr,
                                  (cudaStream_t)stream));
 }
 
@@ -833,9 +841,9 @@ int ei_forward(const ei_geometry *gc, const float *vol, float *s_mod, void *stre
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = counted_prep(g, (const float4 *)vol, physical_mult(g), g->link_gamma > 0.f,
                                  nullptr, st);
-    if (e == cudaSuccess) e = traced_project(g, g->proj, nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, g->proj, g->link_gamma, nullptr, st);
     if (e == cudaSuccess)
-        e = traced_ic(g, g->proj, nullptr, s_mod, g->part_ic, IC_MODEL, nullptr, st);
+        e = traced_ic(g, g->proj, nullptr, s_mod, g->part_ic, IC_MODEL, 0.f, nullptr, st);
     return status_from(e);
 }
 
@@ -927,7 +935,7 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
         }
     }
     e = counted_prep(g, (const float4 *)vol, physical_mult(g), g->link_gamma > 0.f, nullptr, st);
-    if (e == cudaSuccess) e = traced_project(g, g->proj, nullptr, st);
+    if (e == cudaSuccess) e = traced_project(g, g->proj, g->link_gamma, nullptr, st);
     if (e == cudaSuccess) {
         count_launches(g, 2);
         e = launch_offset_grads(g, g->proj, s_exp, g->shift_scratch, g->row_sums, g_mo, g_mr, st);

@@ -198,14 +198,18 @@ cudaEvent_t trace_begin(ei_geometry *g, cudaStream_t st);
 void trace_end(ei_geometry *g, TracedKernel k, cudaEvent_t begin, cudaStream_t st);
 
 // Kernel launchers (each returns cudaGetLastError()).
-// Packed volume copies of mult * vol (row-major and transposed) in the workspace.
+// Packed volume copies of mult * vol (row-major and transposed) in the workspace;
+// linked: single-channel copies of mult.x * vol.x (the B arrays only).
 cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bool linked,
                         const int *active, cudaStream_t st);
-// proj = R[x] from the packed copies.
-cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st);
-// IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram.
+// proj = R[x] from the packed copies; link > 0 (after a linked prep): the three
+// planes are (R[h], link R[h], 0).
+cudaError_t launch_project(const ei_geometry *g, float *proj, float link, const int *active,
+                           cudaStream_t st);
+// IC model; in IC_OBJECTIVE_GRAD mode it writes the packed gradient sinogram, or
+// with link > 0 only the single pair-packed sinogram g_mu + link g_delta (in gB).
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                      double *part, IcMode mode, const int *active, cudaStream_t st);
+                      double *part, IcMode mode, float link, const int *active, cudaStream_t st);
 // Whether the bulk-copy IC variant's two row buffers fit in shared memory.
 bool ic_pipe_fits(int max_ndp, int n_m);
 // Single-shot retrieval + ramp filter into the packed gradient sinogram
@@ -223,8 +227,9 @@ bool single_shot_eq3_fits(const ei_geometry *g);
 cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
 // out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial
 // sums of sum_c reg1_c v_c^2.  with_sino == false: only the regulariser (out not written).
-// link > 0 (the linked unknown h of Eq. 4): out = (out_mult.x (R^T g_mu + link R^T g_delta)
-// + reg2.x v.x, 0, 0, 0) and the partial sums take the mu lane only.
+// link > 0 (the linked unknown h of Eq. 4; gB then holds the single sinogram
+// g_mu + link g_delta that launch_ic wrote): out = (out_mult.x R^T g + reg2.x v.x,
+// 0, 0, 0) and the partial sums take the mu lane only.
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
                                float4 *out, float4 out_mult, float4 reg2, float4 reg1, float link,
                                double *part, const int *active, cudaStream_t st);

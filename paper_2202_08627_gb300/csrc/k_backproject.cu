@@ -21,6 +21,11 @@
 // fixed point and splits it into an integer J and a fraction phi; each voxel
 // adds only its small local offset dc cos - dr sin in FP32.
 //
+// Linked unknown of Eq. 4 (mu = h, delta = gamma h): by linearity
+// R^T g_mu + gamma R^T g_delta = R^T (g_mu + gamma g_delta), so the IC kernel
+// writes that single sinogram, pair-packed, and the linked instantiation loads
+// one 8-B entry per voxel and angle (a third of the bytes) and does 2 FMAs.
+//
 // Also fused: out = out_mult * R^T g + reg2 * v (the regulariser's gradient)
 // and per-tile FP64 partial sums of sum_c reg1_c v_c^2 (its value); v may be
 // null (no regulariser).
@@ -59,7 +64,7 @@ struct AdjShared {
 // group's 16-byte loads in one pass when they share a 128-byte line).  A
 // voxel's computation does not depend on the lane order, and angles are
 // summed in order whatever PASSES.
-template <int PASSES, bool QUAD>
+template <int PASSES, bool QUAD, bool LINKED>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -119,13 +124,18 @@ __device__ __forceinline__ void backproject_item(
                     const float fl = floorf(vl);
                     const int jj = (int)fl;
                     const float d0 = vl - fl;
-                    const float4 ta = __ldg(rA + jj);
-                    const float2 tb = __ldg(rB + jj);
                     const float w0 = fmaxf(0.f, fmaf(-d0, cs.z, cs.w));
                     const float w1 = fmaxf(0.f, fmaf(d0, cs.z, jp.z));
-                    acc[p][0] = fmaf(w0, ta.x, fmaf(w1, ta.w, acc[p][0]));
-                    acc[p][1] = fmaf(w0, ta.y, fmaf(w1, tb.x, acc[p][1]));
-                    acc[p][2] = fmaf(w0, ta.z, fmaf(w1, tb.y, acc[p][2]));
+                    if (LINKED) {                   // one 8-byte entry: g(j), g(j + 1)
+                        const float2 tb = __ldg(rB + jj);
+                        acc[p][0] = fmaf(w0, tb.x, fmaf(w1, tb.y, acc[p][0]));
+                    } else {
+                        const float4 ta = __ldg(rA + jj);
+                        const float2 tb = __ldg(rB + jj);
+                        acc[p][0] = fmaf(w0, ta.x, fmaf(w1, ta.w, acc[p][0]));
+                        acc[p][1] = fmaf(w0, ta.y, fmaf(w1, tb.x, acc[p][1]));
+                        acc[p][2] = fmaf(w0, ta.z, fmaf(w1, tb.y, acc[p][2]));
+                    }
                 }
                 rowA += si.gw;
                 rowB += si.gw;
@@ -141,12 +151,12 @@ __device__ __forceinline__ void backproject_item(
         if (r < n && c < n) {
             const int64_t idx = si.vol_off + (int64_t)r * n + c;
             const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (link > 0.f) {
-                // linked unknown h in the mu lane: dS/dh = R^T g_mu + link R^T g_delta
+            if (LINKED) {
+                // linked unknown h in the mu lane: dS/dh = R^T (g_mu + link g_delta),
+                // the sinogram the IC kernel combined
                 regv += (double)(reg1.x * x.x * x.x);
                 if (with_sino && out != nullptr)
-                    out[idx] = make_float4(fmaf(out_mult.x, fmaf(link, acc[p][1], acc[p][0]),
-                                                reg2.x * x.x), 0.f, 0.f, 0.f);
+                    out[idx] = make_float4(fmaf(out_mult.x, acc[p][0], reg2.x * x.x), 0.f, 0.f, 0.f);
             } else {
                 regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
                         (double)(reg1.z * x.z * x.z);
@@ -161,7 +171,7 @@ __device__ __forceinline__ void backproject_item(
     if (threadIdx.x == 0) part[item] = tot;
 }
 
-template <int PASSES, int MINB, bool QUAD>
+template <int PASSES, int MINB, bool QUAD, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
               const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -169,13 +179,13 @@ k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restri
               double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
-    backproject_item<PASSES, QUAD>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
+    backproject_item<PASSES, QUAD, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
                                    out_mult, reg2, reg1, link, part, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
 // launch) until the list is exhausted; no block waits on another.
-template <int PASSES, int MINB, bool QUAD>
+template <int PASSES, int MINB, bool QUAD, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
@@ -191,9 +201,34 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        backproject_item<PASSES, QUAD>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
+        backproject_item<PASSES, QUAD, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
                                        reg2, reg1, link, part, active);
     }
+}
+
+template <int P, int M, bool Q, bool L>
+static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const float4 *v,
+                                  float4 *out, float4 out_mult, float4 reg2, float4 reg1,
+                                  float link, double *part, const int *active, cudaStream_t st)
+{
+    const AdjVariant &av = g->adj_variant;
+    if (av.total == 0) return cudaSuccess;
+    if (!g->persistent) {
+        k_backproject<P, M, Q, L><<<av.total, ADJ_THREADS, 0, st>>>(
+            g->dg, av.prefix, g->gA, g->gB, with_sino, v, out, out_mult, reg2, reg1, link, part,
+            active);
+    } else {
+        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
+        if (per_sm == 0)
+            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_backproject_persistent<P, M, Q, L>, ADJ_THREADS, 0));
+        const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
+        EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
+        k_backproject_persistent<P, M, Q, L><<<grid, ADJ_THREADS, 0, st>>>(
+            g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
+            out_mult, reg2, reg1, link, part, active);
+    }
+    return cudaGetLastError();
 }
 
 template <int P, int M, bool Q>
@@ -201,24 +236,11 @@ static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const
                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                      float link, double *part, const int *active, cudaStream_t st)
 {
-    const AdjVariant &av = g->adj_variant;
-    if (av.total == 0) return cudaSuccess;
-    if (!g->persistent) {
-        k_backproject<P, M, Q><<<av.total, ADJ_THREADS, 0, st>>>(g->dg, av.prefix, g->gA, g->gB,
-                                                              with_sino, v, out, out_mult, reg2,
-                                                              reg1, link, part, active);
-    } else {
-        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
-        if (per_sm == 0)
-            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_backproject_persistent<P, M, Q>, ADJ_THREADS, 0));
-        const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
-        EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
-        k_backproject_persistent<P, M, Q><<<grid, ADJ_THREADS, 0, st>>>(
-            g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
-            out_mult, reg2, reg1, link, part, active);
-    }
-    return cudaGetLastError();
+    return link > 0.f
+               ? launch_bp_mode<P, M, Q, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part,
+                                               active, st)
+               : launch_bp_mode<P, M, Q, false>(g, with_sino, v, out, out_mult, reg2, reg1, 0.f,
+                                                part, active, st);
 }
 
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,

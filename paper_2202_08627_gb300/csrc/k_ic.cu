@@ -93,7 +93,7 @@ __device__ __forceinline__ void flat_table_eval(const float *__restrict__ tab, i
 template <int MODE, bool TABLE>
 __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
                      float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
-                     double *__restrict__ part, const int *__restrict__ active)
+                     double *__restrict__ part, const int *__restrict__ active, float link)
 {
     extern __shared__ float4 sm4[];
     __shared__ double red[32];
@@ -231,18 +231,33 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
         const float *gdl = reinterpret_cast<const float *>(s_pd4);
         const float *gsg = reinterpret_cast<const float *>(s_gv4);
         const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
-        for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+        if (link > 0.f) {
+            // linked unknown (Eq. 4): the single sinogram g_mu + gamma g_delta,
+            // pair-packed in gB, is all the adjoint needs
+            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * gi + q;
-                const bool nx = j + 1 < ndp;
-                gA[dst + j] = make_float4(gmu[j], gdl[j], gsg[j], nx ? gmu[j + 1] : 0.f);
-                gB[dst + j] = make_float2(nx ? gdl[j + 1] : 0.f, nx ? gsg[j + 1] : 0.f);
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * gi + q;
+                    const bool nx = j + 1 < ndp;
+                    gB[dst + j] = make_float2(fmaf(link, gdl[j], gmu[j]),
+                                              nx ? fmaf(link, gdl[j + 1], gmu[j + 1]) : 0.f);
+                }
             }
-        }
-        if (threadIdx.x == 0) {                     // entry of pixel -1: (0, g(0))
-            gA[dst - 1] = make_float4(0.f, 0.f, 0.f, gmu[0]);
-            gB[dst - 1] = make_float2(gdl[0], gsg[0]);
+            if (threadIdx.x == 0) gB[dst - 1] = make_float2(0.f, fmaf(link, gdl[0], gmu[0]));
+        } else {
+            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * gi + q;
+                    const bool nx = j + 1 < ndp;
+                    gA[dst + j] = make_float4(gmu[j], gdl[j], gsg[j], nx ? gmu[j + 1] : 0.f);
+                    gB[dst + j] = make_float2(nx ? gdl[j + 1] : 0.f, nx ? gsg[j + 1] : 0.f);
+                }
+            }
+            if (threadIdx.x == 0) {                 // entry of pixel -1: (0, g(0))
+                gA[dst - 1] = make_float4(0.f, 0.f, 0.f, gmu[0]);
+                gB[dst - 1] = make_float2(gdl[0], gsg[0]);
+            }
         }
     }
     const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(1024)
 k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ meas,
           float *__restrict__ s_mod, float4 *__restrict__ gA, float2 *__restrict__ gB,
           double *__restrict__ part, const int *__restrict__ active, int *__restrict__ status,
-          int nst)
+          int nst, float link)
 {
     extern __shared__ float4 sm4[];
     __shared__ uint64_t bars[kIcPipeMaxStages];
@@ -514,9 +529,14 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                 const float d0 = j >= 0 && j < nd ? kdt * fmaf(e0, g0, gm1 - g1) : 0.f;
                 const float d1 = j + 1 < nd ? kdt * fmaf(e1, g1, g0 - g2) : 0.f;
                 const bool cur = j >= 0, nx = j + 1 < ndp;
-                gA[m.gp_off + j] = make_float4(cur ? g_mu[j] : 0.f, d0, cur ? g_v[j] : 0.f,
-                                               nx ? g_mu[j + 1] : 0.f);
-                gB[m.gp_off + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
+                if (link > 0.f) {        // linked unknown: g_mu + gamma g_delta only
+                    gB[m.gp_off + j] = make_float2(fmaf(link, d0, cur ? g_mu[j] : 0.f),
+                                                   fmaf(link, d1, nx ? g_mu[j + 1] : 0.f));
+                } else {
+                    gA[m.gp_off + j] = make_float4(cur ? g_mu[j] : 0.f, d0, cur ? g_v[j] : 0.f,
+                                                   nx ? g_mu[j + 1] : 0.f);
+                    gB[m.gp_off + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
+                }
             }
         }
         if (MODE != IC_MODEL) {
@@ -572,7 +592,8 @@ bool ic_pipe_fits(int max_ndp, int n_m) { return ic_pipe_stages(max_ndp, n_m) > 
 
 template <int MODE, int NM>
 static cudaError_t launch_ic_pipe_nm(const ei_geometry *g, const float *proj, const float *meas,
-                                     float *s_mod, double *part, const int *active, cudaStream_t st)
+                                     float *s_mod, double *part, const int *active, float link,
+                                     cudaStream_t st)
 {
     const int threads = ic_threads(g, 2, 1024 - 32) + 32;      // consumers + one producer warp
     const int nst = ic_pipe_stages(g->dg.max_ndp, g->dg.mc.n_m);
@@ -581,19 +602,20 @@ static cudaError_t launch_ic_pipe_nm(const ei_geometry *g, const float *proj, co
     EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ic_pipe<MODE, NM>, threads, smem));
     const int grid = std::max(1, std::min(g->dg.total_ic, std::max(1, per_sm) * g->num_sms));
     k_ic_pipe<MODE, NM><<<grid, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA, g->gB, part,
-                                                     active, g->dev_status, nst);
+                                                     active, g->dev_status, nst, link);
     return cudaGetLastError();
 }
 
 // M = 7 (the paper's scans) and M = 5 get fully unrolled loops over m.
 template <int MODE>
 static cudaError_t launch_ic_pipe(const ei_geometry *g, const float *proj, const float *meas,
-                                  float *s_mod, double *part, const int *active, cudaStream_t st)
+                                  float *s_mod, double *part, const int *active, float link,
+                                  cudaStream_t st)
 {
     switch (g->dg.mc.n_m) {
-    case 7: return launch_ic_pipe_nm<MODE, 7>(g, proj, meas, s_mod, part, active, st);
-    case 5: return launch_ic_pipe_nm<MODE, 5>(g, proj, meas, s_mod, part, active, st);
-    default: return launch_ic_pipe_nm<MODE, 0>(g, proj, meas, s_mod, part, active, st);
+    case 7: return launch_ic_pipe_nm<MODE, 7>(g, proj, meas, s_mod, part, active, link, st);
+    case 5: return launch_ic_pipe_nm<MODE, 5>(g, proj, meas, s_mod, part, active, link, st);
+    default: return launch_ic_pipe_nm<MODE, 0>(g, proj, meas, s_mod, part, active, link, st);
     }
 }
 
@@ -719,42 +741,44 @@ cudaError_t launch_shift_grad(const ei_geometry *g, const float *proj, const flo
 
 template <bool TABLE>
 static void launch_ic_rows(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                           double *part, IcMode mode, const int *active, cudaStream_t st)
+                           double *part, IcMode mode, const int *active, float link,
+                           cudaStream_t st)
 {
     const int threads = ic_threads(g, 4, 512);
     const size_t smem = (size_t)4 * g->dg.max_ndp * sizeof(float);
     switch (mode) {
     case IC_MODEL:
         k_ic<IC_MODEL, TABLE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod, g->gA,
-                                                                      g->gB, part, active);
+                                                                      g->gB, part, active, link);
         break;
     case IC_OBJECTIVE:
-        k_ic<IC_OBJECTIVE, TABLE><<<g->dg.total_ic, threads, smem, st>>>(g->dg, proj, meas, s_mod,
-                                                                          g->gA, g->gB, part, active);
+        k_ic<IC_OBJECTIVE, TABLE><<<g->dg.total_ic, threads, smem, st>>>(
+            g->dg, proj, meas, s_mod, g->gA, g->gB, part, active, link);
         break;
     default:
         k_ic<IC_OBJECTIVE_GRAD, TABLE><<<g->dg.total_ic, threads, smem, st>>>(
-            g->dg, proj, meas, s_mod, g->gA, g->gB, part, active);
+            g->dg, proj, meas, s_mod, g->gA, g->gB, part, active, link);
         break;
     }
 }
 
 cudaError_t launch_ic(const ei_geometry *g, const float *proj, const float *meas, float *s_mod,
-                      double *part, IcMode mode, const int *active, cudaStream_t st)
+                      double *part, IcMode mode, float link, const int *active, cudaStream_t st)
 {
     if (g->dg.total_ic == 0) return cudaSuccess;
     if (g->dg.flat_tab) {                        // the sampled flat runs one block per row
-        launch_ic_rows<true>(g, proj, meas, s_mod, part, mode, active, st);
+        launch_ic_rows<true>(g, proj, meas, s_mod, part, mode, active, link, st);
         return cudaGetLastError();
     }
     if (g->ic_variant == 1) {
         switch (mode) {
-        case IC_MODEL: return launch_ic_pipe<IC_MODEL>(g, proj, meas, s_mod, part, active, st);
-        case IC_OBJECTIVE: return launch_ic_pipe<IC_OBJECTIVE>(g, proj, meas, s_mod, part, active, st);
-        default: return launch_ic_pipe<IC_OBJECTIVE_GRAD>(g, proj, meas, s_mod, part, active, st);
+        case IC_MODEL: return launch_ic_pipe<IC_MODEL>(g, proj, meas, s_mod, part, active, link, st);
+        case IC_OBJECTIVE:
+            return launch_ic_pipe<IC_OBJECTIVE>(g, proj, meas, s_mod, part, active, link, st);
+        default: return launch_ic_pipe<IC_OBJECTIVE_GRAD>(g, proj, meas, s_mod, part, active, link, st);
         }
     }
-    launch_ic_rows<false>(g, proj, meas, s_mod, part, mode, active, st);
+    launch_ic_rows<false>(g, proj, meas, s_mod, part, mode, active, link, st);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,9 @@
 //    and a block covers FWD_ANGLES angles so its warps re-use each other's
 //    lines in L1;
 //  - several samples per loop iteration keep independent loads in flight;
+//  - for the linked unknown of Eq. 4 (mu = h, delta = gamma h, sigma = 0) the
+//    copies hold h alone, 8 B per entry, and R[delta] = gamma R[h] is written
+//    from the same sum: a third of the bytes per sample;
 //  - the crossing position is carried in 32.32 fixed point (int64): one
 //    integer add per sample; the integer part is the voxel index and the low
 //    word the interpolation weight, exact to ~1e-7 voxel at any slice size.
@@ -31,8 +34,9 @@ namespace ei {
 
 // --------------------------------------------------------------------------
 // Staging: packed row-major and transposed copies of mult * vol, or with
-// `linked` (the single unknown h of Eq. 4 in the mu lane) of
-// (mult.x h, mult.y h, 0).  One block per 32 x 32 tile of entries; the tile
+// `linked` (the single unknown h of Eq. 4 in the mu lane) single-channel
+// copies of mult.x h, 8 bytes per entry in the B arrays (the linked projector
+// derives R[delta] = gamma R[mu]).  One block per 32 x 32 tile of entries; the tile
 // loads the voxels it needs (with a one-voxel halo above and to the left)
 // into shared memory.
 // --------------------------------------------------------------------------
@@ -67,14 +71,19 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, bool linked, flo
     }
     __syncthreads();
     const int64_t w = n + 1;
-    // row-major entries (r, e): voxels (r, e - 1) and (r, e)
+    // row-major entries (r, e): voxels (r, e - 1) and (r, e); linked: the
+    // single channel's (value, difference) in the B copy only
     for (int dy = threadIdx.y; dy < PREP_TILE; dy += blockDim.y) {
         const int r = R0 + dy, e = C0 + threadIdx.x;
         if (r < n && e <= n) {
             const float4 a = T[dy + 1][threadIdx.x], b = T[dy + 1][threadIdx.x + 1];
             const int64_t k = si.pp_off + (int64_t)r * w + e;
-            xpA[k] = make_float4(a.x, a.y, a.z, b.x - a.x);
-            xpB[k] = make_float2(b.y - a.y, b.z - a.z);
+            if (linked) {
+                xpB[k] = make_float2(a.x, b.x - a.x);
+            } else {
+                xpA[k] = make_float4(a.x, a.y, a.z, b.x - a.x);
+                xpB[k] = make_float2(b.y - a.y, b.z - a.z);
+            }
         }
     }
     // transposed entries (c, e): voxels (e - 1, c) and (e, c)
@@ -83,8 +92,12 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, bool linked, flo
         if (c < n && e <= n) {
             const float4 a = T[threadIdx.x][dx + 1], b = T[threadIdx.x + 1][dx + 1];
             const int64_t k = si.pp_off + (int64_t)c * w + e;
-            xtA[k] = make_float4(a.x, a.y, a.z, b.x - a.x);
-            xtB[k] = make_float2(b.y - a.y, b.z - a.z);
+            if (linked) {
+                xtB[k] = make_float2(a.x, b.x - a.x);
+            } else {
+                xtA[k] = make_float4(a.x, a.y, a.z, b.x - a.x);
+                xtB[k] = make_float2(b.y - a.y, b.z - a.z);
+            }
         }
     }
 }
@@ -100,13 +113,14 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, bool linked, flo
 // tile shape, the warp shape and the unroll so the autotuner can choose among
 // instantiations.
 // --------------------------------------------------------------------------
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
 __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
                                              const float4 *__restrict__ xpA,
                                              const float2 *__restrict__ xpB,
                                              const float4 *__restrict__ xtA,
                                              const float2 *__restrict__ xtB,
-                                             float *__restrict__ proj, const int *__restrict__ active)
+                                             float *__restrict__ proj, float link,
+                                             const int *__restrict__ active)
 {
     const int s = find_slice(prefix, dg.n_slices, item);
     if (active && !active[s]) return;
@@ -170,6 +184,35 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
     // samples are summed in row order whatever the unroll, so every variant
     // gives bit-identical projections
     int o = o_lo;
+    if (LINKED) {
+        // one channel, one 8-byte (value, difference) entry per sample; then
+        // R[mu] = pch sum and R[delta] = gamma R[mu] (Eq. 4: delta = gamma mu)
+        for (; o + UNROLL - 1 <= o_hi; o += UNROLL) {
+            float2 vb[UNROLL];
+            float f[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const long long q = pos + u * p1;
+                f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
+                vb[u] = __ldg(rowB + u * w + (int)(q >> 32));
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) ax += fmaf(f[u], vb[u].y, vb[u].x);
+            pos += UNROLL * p1;
+            rowB += UNROLL * w;
+        }
+        for (; o <= o_hi; ++o) {
+            const float2 vb = __ldg(rowB + (int)(pos >> 32));
+            ax += fmaf((float)(unsigned)(pos & 0xffffffffLL) * inv32, vb.y, vb.x);
+            pos += p1;
+            rowB += w;
+        }
+        const float pm = ax * an.pch;
+        out[0] = pm;
+        out[plane] = link * pm;
+        out[2 * plane] = 0.f;
+        return;
+    }
     for (; o + UNROLL - 1 <= o_hi; o += UNROLL) {
         float4 va[UNROLL];
         float2 vb[UNROLL];
@@ -210,25 +253,26 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
 }
 
 // One block per work item.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
           const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
-          const float2 *__restrict__ xtB, float *__restrict__ proj, const int *__restrict__ active)
+          const float2 *__restrict__ xtB, float *__restrict__ proj, float link,
+          const int *__restrict__ active)
 {
-    project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST>(dg, prefix, blockIdx.x, xpA, xpB, xtA, xtB,
-                                                     proj, active);
+    project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED>(dg, prefix, blockIdx.x, xpA, xpB, xtA,
+                                                             xtB, proj, link, active);
 }
 
 // Persistent: a GPU-sized grid whose blocks take work items from a counter
 // (set to 0 before the launch) until the list is exhausted; no block waits on
 // another.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                      const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
                      const float4 *__restrict__ xtA, const float2 *__restrict__ xtB,
-                     float *__restrict__ proj, const int *__restrict__ active)
+                     float *__restrict__ proj, float link, const int *__restrict__ active)
 {
     __shared__ int s_item;
     for (;;) {
@@ -237,32 +281,40 @@ k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int 
         const int item = s_item;
         __syncthreads();
         if (item >= total) return;
-        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST>(dg, prefix, item, xpA, xpB, xtA, xtB, proj,
-                                                         active);
+        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED>(dg, prefix, item, xpA, xpB, xtA, xtB,
+                                                                 proj, link, active);
     }
 }
 
-template <int R, int A, int U, int W, bool F>
-static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, const int *active,
-                                          cudaStream_t st)
+template <int R, int A, int U, int W, bool F, bool L>
+static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float link,
+                                       const int *active, cudaStream_t st)
 {
     const FwdVariant &v = g->fwd_variant;
     if (v.total == 0) return cudaSuccess;
     if (!g->persistent) {
-        k_project<R, A, U, W, F><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB, g->xtA,
-                                                       g->xtB, proj, active);
+        k_project<R, A, U, W, F, L><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB,
+                                                              g->xtA, g->xtB, proj, link, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
             EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_project_persistent<R, A, U, W, F>, R * A, 0));
+                &per_sm, k_project_persistent<R, A, U, W, F, L>, R * A, 0));
         const int grid = std::max(1, std::min(v.total, per_sm * g->num_sms));
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter, 0, sizeof(int), st));
-        k_project_persistent<R, A, U, W, F><<<grid, R * A, 0, st>>>(g->dg, v.prefix, v.total,
-                                                             g->work_counter, g->xpA, g->xpB,
-                                                             g->xtA, g->xtB, proj, active);
+        k_project_persistent<R, A, U, W, F, L><<<grid, R * A, 0, st>>>(
+            g->dg, v.prefix, v.total, g->work_counter, g->xpA, g->xpB, g->xtA, g->xtB, proj, link,
+            active);
     }
     return cudaGetLastError();
+}
+
+template <int R, int A, int U, int W, bool F>
+static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, float link,
+                                          const int *active, cudaStream_t st)
+{
+    return link > 0.f ? launch_project_mode<R, A, U, W, F, true>(g, proj, link, active, st)
+                      : launch_project_mode<R, A, U, W, F, false>(g, proj, 0.f, active, st);
 }
 
 cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bool linked,
@@ -274,20 +326,21 @@ cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bo
     return cudaGetLastError();
 }
 
-cudaError_t launch_project(const ei_geometry *g, float *proj, const int *active, cudaStream_t st)
+cudaError_t launch_project(const ei_geometry *g, float *proj, float link, const int *active,
+                           cudaStream_t st)
 {
     switch (g->fwd_variant.id) {
-    case 0: return launch_project_variant<16, 16, 4, 8, false>(g, proj, active, st);
-    case 1: return launch_project_variant<32, 8, 4, 8, false>(g, proj, active, st);
-    case 2: return launch_project_variant<32, 16, 4, 8, false>(g, proj, active, st);
-    case 3: return launch_project_variant<16, 16, 2, 8, false>(g, proj, active, st);
-    case 4: return launch_project_variant<32, 8, 4, 32, false>(g, proj, active, st);
-    case 5: return launch_project_variant<16, 16, 4, 16, false>(g, proj, active, st);
-    case 6: return launch_project_variant<32, 16, 4, 32, false>(g, proj, active, st);
-    case 7: return launch_project_variant<16, 16, 4, 4, true>(g, proj, active, st);
-    case 8: return launch_project_variant<8, 32, 4, 4, true>(g, proj, active, st);
-    case 9: return launch_project_variant<32, 8, 4, 4, true>(g, proj, active, st);
-    default: return launch_project_variant<16, 16, 4, 2, true>(g, proj, active, st);
+    case 0: return launch_project_variant<16, 16, 4, 8, false>(g, proj, link, active, st);
+    case 1: return launch_project_variant<32, 8, 4, 8, false>(g, proj, link, active, st);
+    case 2: return launch_project_variant<32, 16, 4, 8, false>(g, proj, link, active, st);
+    case 3: return launch_project_variant<16, 16, 2, 8, false>(g, proj, link, active, st);
+    case 4: return launch_project_variant<32, 8, 4, 32, false>(g, proj, link, active, st);
+    case 5: return launch_project_variant<16, 16, 4, 16, false>(g, proj, link, active, st);
+    case 6: return launch_project_variant<32, 16, 4, 32, false>(g, proj, link, active, st);
+    case 7: return launch_project_variant<16, 16, 4, 4, true>(g, proj, link, active, st);
+    case 8: return launch_project_variant<8, 32, 4, 4, true>(g, proj, link, active, st);
+    case 9: return launch_project_variant<32, 8, 4, 4, true>(g, proj, link, active, st);
+    default: return launch_project_variant<16, 16, 4, 2, true>(g, proj, link, active, st);
     }
 }
 
