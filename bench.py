@@ -133,9 +133,8 @@ def build_problem(wl, rank: int, device):
 # from ncu captures of the kernel variants named, on 8 slices of 1024^2 with 1800
 # angles and 1536 pixels (the working set per slice fits L2, so the ratio
 # carries over to other batches of such slices).  Kernel changes void them.
-PROFILED_TRAFFIC = {("project", 0): 706.8e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
-                    ("project", 8): 683.9e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
-                    ("backproject", 0): 877.0e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
+PROFILED_TRAFFIC = {("project", 8): 684.0e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
+                    ("backproject", 0): 879.9e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
 
 
 def projector_samples(slices):

@@ -643,6 +643,11 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
     return e == cudaSuccess ? EI_OK : EI_ERR_CUDA;
 }
 
+// A candidate replaces the incumbent (the lower id, or one-block-per-item
+// launches) only when it is at least 1% faster: variants within timing noise
+// of each other then get the same, reproducible choice.
+static const double kTuneMargin = 0.99;
+
 int ei_autotune(ei_geometry *g, int flags, void *stream)
 {
     if (!g) return EI_ERR_ARG;
@@ -674,14 +679,14 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
             double ms = 0;
             const int rc = time_kernel(g, false, st, 3, &ms);
             if (rc != EI_OK) return rc;
-            if (ms < fbest) fbest = ms, fid[pers] = v;
+            if (ms < fbest * kTuneMargin) fbest = ms, fid[pers] = v;
         }
         for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
             select_variants(g, fid[pers], v, pers != 0);
             double ms = 0;
             const int rc = time_kernel(g, true, st, 3, &ms);
             if (rc != EI_OK) return rc;
-            if (ms < abest) abest = ms, aid[pers] = v;
+            if (ms < abest * kTuneMargin) abest = ms, aid[pers] = v;
         }
     }
     // stage 2: the two launch modes' winners re-timed alternately, 3 rounds,
@@ -698,7 +703,7 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
             tf[pers] = std::min(tf[pers], mf);
             ta[pers] = std::min(ta[pers], ma);
         }
-    const int bp = tf[1] + ta[1] < tf[0] + ta[0] ? 1 : 0;
+    const int bp = tf[1] + ta[1] < (tf[0] + ta[0]) * kTuneMargin ? 1 : 0;
     const int bf = fid[bp], ba = aid[bp];
     const double best_f = tf[bp], best_a = ta[bp];
     select_variants(g, bf, ba, bp != 0);
