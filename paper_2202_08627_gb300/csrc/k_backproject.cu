@@ -65,7 +65,7 @@ struct AdjShared {
 // voxel's computation does not depend on the lane order, and angles are
 // summed in order whatever PASSES.
 template <int PASSES, bool QUAD, bool LINKED>
-__device__ __forceinline__ void backproject_item(
+__device__ __forceinline__ void backproject_single_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
     float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
@@ -171,7 +171,169 @@ __device__ __forceinline__ void backproject_item(
     if (threadIdx.x == 0) part[item] = tot;
 }
 
-template <int PASSES, int MINB, bool QUAD, bool LINKED>
+// Voxel pairs.  Two horizontally adjacent voxels project |cos| <= 1 pixel
+// apart, so at every angle their four taps lie among three consecutive pixels
+// j, j + 1, j + 2 (j: the lower tap of the pair's lower-u voxel), and the
+// packed sinogram already holds g(j + 2) in the second half of entry j + 1.
+// A thread owns a pair: per angle it loads entry j, and of entry j + 1 only the
+// second half (3 of its 6 floats), 36 B for two voxels instead of 48, and
+// shares the index arithmetic.  The lower-u voxel adds its two taps as the
+// single-voxel kernel does; the other one, whose lower tap is j + o with
+// o = [d + |cos| >= 1], adds the three slots with weights (w0, w1, 0) or
+// (0, w0, w1): the same FMAs in the same order, plus one with a zero weight.
+// Warp: 8 pairs x 4 rows; a tile is 32 columns x 16 PASSES rows.
+template <int PASSES, bool LINKED, bool SWAP>
+__device__ __forceinline__ void pair_angle(float (&acc)[PASSES][2][3], const float4 *rA,
+                                           const float2 *rB, float v0, float step, float a,
+                                           float4 cs, float4 jp)
+{
+    constexpr int LO = SWAP ? 1 : 0, HI = SWAP ? 0 : 1;    // lower-u voxel: left unless cos < 0
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const float vl = fmaf((float)p, step, v0);
+        const float fl = floorf(vl);
+        const int jj = (int)fl;
+        const float d0 = vl - fl;
+        float dh = d0 + a;
+        const bool o = dh >= 1.f;
+        dh = o ? dh - 1.f : dh;
+        const float w0l = fmaxf(0.f, fmaf(-d0, cs.z, cs.w)), w1l = fmaxf(0.f, fmaf(d0, cs.z, jp.z));
+        const float w0h = fmaxf(0.f, fmaf(-dh, cs.z, cs.w)), w1h = fmaxf(0.f, fmaf(dh, cs.z, jp.z));
+        const float s0 = o ? 0.f : w0h, s1 = o ? w0h : w1h, s2 = o ? w1h : 0.f;
+        if (LINKED) {
+            const float2 t = __ldg(rB + jj);                                  // g(j), g(j + 1)
+            const float g2 = __ldg(reinterpret_cast<const float *>(rB + jj + 1) + 1);   // g(j + 2)
+            acc[p][LO][0] = fmaf(w0l, t.x, fmaf(w1l, t.y, acc[p][LO][0]));
+            acc[p][HI][0] = fmaf(s0, t.x, fmaf(s1, t.y, fmaf(s2, g2, acc[p][HI][0])));
+        } else {
+            const float4 ta = __ldg(rA + jj);       // mu(j), delta(j), sigma(j), mu(j + 1)
+            const float2 tb = __ldg(rB + jj);       // delta(j + 1), sigma(j + 1)
+            const float m2 = __ldg(reinterpret_cast<const float *>(rA + jj + 1) + 3);  // mu(j + 2)
+            const float2 tc = __ldg(rB + jj + 1);   // delta(j + 2), sigma(j + 2)
+            acc[p][LO][0] = fmaf(w0l, ta.x, fmaf(w1l, ta.w, acc[p][LO][0]));
+            acc[p][LO][1] = fmaf(w0l, ta.y, fmaf(w1l, tb.x, acc[p][LO][1]));
+            acc[p][LO][2] = fmaf(w0l, ta.z, fmaf(w1l, tb.y, acc[p][LO][2]));
+            acc[p][HI][0] = fmaf(s0, ta.x, fmaf(s1, ta.w, fmaf(s2, m2, acc[p][HI][0])));
+            acc[p][HI][1] = fmaf(s0, ta.y, fmaf(s1, tb.x, fmaf(s2, tc.x, acc[p][HI][1])));
+            acc[p][HI][2] = fmaf(s0, ta.z, fmaf(s1, tb.y, fmaf(s2, tc.y, acc[p][HI][2])));
+        }
+    }
+}
+
+template <int PASSES, bool LINKED, bool COMPACT>
+__device__ __forceinline__ void backproject_pair_item(
+    const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
+    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
+    double *__restrict__ part, const int *__restrict__ active)
+{
+    constexpr int TR = 16 * PASSES;
+    const int s = find_slice(prefix, dg.n_slices, item);
+    if (active && !active[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int n = si.n;
+    const int ntc = (n + ADJ_TC - 1) / ADJ_TC;
+    const int local = item - prefix[s];
+    const int r_t = (local / ntc) * TR, c_t = (local % ntc) * ADJ_TC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // left voxel of the pair and its row at pass 0 (passes add 16): 8 lanes cover
+    // 8 pairs of one row, or (COMPACT) 2 pairs x 4 rows
+    const int dc = (warp & 1) * 16 + (COMPACT ? 4 * (lane >> 3) + 2 * (lane & 1) : 2 * (lane & 7));
+    const int dr0 = (warp >> 1) * 4 + (COMPACT ? (lane >> 1) & 3 : lane >> 3);
+
+    float acc[PASSES][2][3];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) acc[p][h][0] = acc[p][h][1] = acc[p][h][2] = 0.f;
+
+    if (with_sino) {
+        const float4 *rowA0 = gA + si.gp_off + si.marg;
+        const float2 *rowB0 = gB + si.gp_off + si.marg;
+        const long long two_ct = 2LL * c_t - (n - 1);              // 2 (c_t - hn)
+        const long long two_rt = (long long)(n - 1) - 2LL * r_t;   // 2 (hn - r_t)
+        const long long hd2 = (long long)(si.n_det - 1) << 32;     // 2 hd in 32.32
+        const float fx = (float)dc, fy = (float)dr0;
+        for (int a0 = 0; a0 < si.n_theta; a0 += ADJ_CHUNK) {
+            const int na = min(ADJ_CHUNK, si.n_theta - a0);
+            __syncthreads();
+            if ((int)threadIdx.x < na) {
+                const AngleInfo an = dg.ang[si.ang_off + a0 + threadIdx.x];
+                const long long U = (two_ct * an.cos_fx + two_rt * an.sin_fx + hd2) >> 1;
+                const float pi = an.pch * an.inv_ch;
+                sh.cs[threadIdx.x] = make_float4(an.cosf, an.sinf, pi, an.pch);
+                sh.jp[threadIdx.x] = make_float4(
+                    __int_as_float((int)(U >> 32)),
+                    (float)(unsigned)(U & 0xffffffffLL) * 2.3283064365386963e-10f, an.pch - pi, 0.f);
+            }
+            __syncthreads();
+            const float4 *rowA = rowA0 + (int64_t)a0 * si.gw;
+            const float2 *rowB = rowB0 + (int64_t)a0 * si.gw;
+            for (int k = 0; k < na; ++k) {
+                const float4 cs = sh.cs[k];
+                const float4 jp = sh.jp[k];
+                const int J = __float_as_int(jp.x);
+                // detector position of the pair's lower-u voxel at pass 0
+                const float v0 = fmaf(fx, cs.x, fmaf(-fy, cs.y, jp.y)) + fminf(cs.x, 0.f);
+                const float step = -16.f * cs.y;
+                if (cs.x >= 0.f)
+                    pair_angle<PASSES, LINKED, false>(acc, rowA + J, rowB + J, v0, step, cs.x, cs, jp);
+                else
+                    pair_angle<PASSES, LINKED, true>(acc, rowA + J, rowB + J, v0, step, -cs.x, cs, jp);
+                rowA += si.gw;
+                rowB += si.gw;
+            }
+        }
+    }
+
+    double regv = 0.0;
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const int r = r_t + dr0 + 16 * p;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c_t + dc + h;
+            if (r < n && c < n) {
+                const int64_t idx = si.vol_off + (int64_t)r * n + c;
+                const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (LINKED) {
+                    regv += (double)(reg1.x * x.x * x.x);
+                    if (with_sino && out != nullptr)
+                        out[idx] = make_float4(fmaf(out_mult.x, acc[p][h][0], reg2.x * x.x), 0.f, 0.f, 0.f);
+                } else {
+                    regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
+                            (double)(reg1.z * x.z * x.z);
+                    if (with_sino && out != nullptr)
+                        out[idx] = make_float4(fmaf(out_mult.x, acc[p][h][0], reg2.x * x.x),
+                                               fmaf(out_mult.y, acc[p][h][1], reg2.y * x.y),
+                                               fmaf(out_mult.z, acc[p][h][2], reg2.z * x.z), 0.f);
+                }
+            }
+        }
+    }
+    const double tot = block_sum_double_adj(regv, sh.red);
+    if (threadIdx.x == 0) part[item] = tot;
+}
+
+// LAY: 0 lanes along rows of 8 voxels, 1 lanes on 2 x 4 sub-patches, 2 voxel
+// pairs along rows, 3 voxel pairs on 4 x 4 sub-patches.
+template <int PASSES, int LAY, bool LINKED>
+__device__ __forceinline__ void backproject_item(
+    const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
+    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
+    double *__restrict__ part, const int *__restrict__ active)
+{
+    if constexpr (LAY >= 2)
+        backproject_pair_item<PASSES, LINKED, LAY == 3>(dg, prefix, item, sh, gA, gB, with_sino, v,
+                                                        out, out_mult, reg2, reg1, part, active);
+    else
+        backproject_single_item<PASSES, LAY == 1, LINKED>(dg, prefix, item, sh, gA, gB, with_sino,
+                                                          v, out, out_mult, reg2, reg1, link, part,
+                                                          active);
+}
+
+template <int PASSES, int MINB, int LAY, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
               const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -179,13 +341,13 @@ k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restri
               double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
-    backproject_item<PASSES, QUAD, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
+    backproject_item<PASSES, LAY, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
                                    out_mult, reg2, reg1, link, part, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
 // launch) until the list is exhausted; no block waits on another.
-template <int PASSES, int MINB, bool QUAD, bool LINKED>
+template <int PASSES, int MINB, int LAY, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
@@ -201,12 +363,12 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        backproject_item<PASSES, QUAD, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
+        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
                                        reg2, reg1, link, part, active);
     }
 }
 
-template <int P, int M, bool Q, bool L>
+template <int P, int M, int Q, bool L>
 static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const float4 *v,
                                   float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                   float link, double *part, const int *active, cudaStream_t st)
@@ -231,7 +393,7 @@ static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const fl
     return cudaGetLastError();
 }
 
-template <int P, int M, bool Q>
+template <int P, int M, int Q>
 static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const float4 *v,
                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                      float link, double *part, const int *active, cudaStream_t st)
@@ -248,19 +410,22 @@ cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float
                                double *part, const int *active, cudaStream_t st)
 {
     switch (g->adj_variant.id) {
-    case 0: return launch_bp_variant<8, 4, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 1: return launch_bp_variant<4, 1, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 2: return launch_bp_variant<16, 2, false>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 3: return launch_bp_variant<8, 4, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    default: return launch_bp_variant<16, 2, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 0: return launch_bp_variant<8, 4, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 1: return launch_bp_variant<4, 1, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 2: return launch_bp_variant<16, 2, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 3: return launch_bp_variant<8, 4, 1>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 4: return launch_bp_variant<16, 2, 1>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    // voxel pairs, 4 passes of 16 rows
+    case 5: return launch_bp_variant<4, 4, 2>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    default: return launch_bp_variant<4, 4, 3>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
     }
 }
 
 // Voxel rows per tile of adjoint variant `id` (see launch_backproject).
 int backproject_variant_rows(int id)
 {
-    static const int P[N_ADJ_VARIANTS] = {8, 4, 16, 8, 16};
-    return 8 * P[id];
+    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64};
+    return R[id];
 }
 
 // ----------------------------------------------------------------------------

@@ -95,7 +95,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_set_tensor_path", "ei_set_flat_table"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 5
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 7
 
 _lib = None
 

@@ -122,6 +122,46 @@ def test_linked_objective_gradient_and_forward_match_oracle():
     assert not np.any(gv[:, 3])
 
 
+@pytest.mark.parametrize("adj_variant", [0, 3, 5, 6])
+def test_linked_kernels_agree_with_the_three_channel_path(adj_variant):
+    """The single-channel linked kernels against the three-channel ones on the
+    same model (lambda = 0, so only the data term): S(h) = S(h, gamma h, 0),
+    dS/dh = dS/dmu + gamma dS/ddelta, and the forward ICs agree; both paths in
+    FP32 with different summation orders.  Adjoint variants: rows of 8 voxels,
+    2 x 4 sub-patches, voxel pairs along rows and on 4 x 4 sub-patches."""
+    from paper_2202_08627_gb300 import ei
+    probs = _linked_problems(SHAPES, 550)
+    specs = [p[0] for p in probs]
+    geoms = [oracle_geometry(sp, lam=(0.0, 0.0, 0.0), m_o=p[1].m_o) for sp, p in zip(specs, probs)]
+    meas = [p[2] for p in probs]
+    G = gpu_geometry(specs, geoms)
+    ei.ei_set_variant(G, 8, adj_variant, False)
+    hs = [sp.truth[0] * 0.8 for sp in specs]
+    m = G.pack_meas(meas)
+    out = {}
+    for mode in ("three", "linked"):
+        if mode == "linked":
+            ei.ei_set_linked(G, GAMMA)
+            vol = G.pack_volume([np.stack([h, np.zeros_like(h), np.zeros_like(h)]) for h in hs])
+        else:
+            ei.ei_set_linked(G, 0.0)
+            vol = G.pack_volume([np.stack([h, GAMMA * h, np.zeros_like(h)]) for h in hs])
+        S = torch.zeros(G.n_slices, dtype=torch.float64, device="cuda")
+        grad = G.empty("vol")
+        ei.ei_objective_grad(G, vol, m, S, grad)
+        s_mod = G.empty("meas")
+        ei.ei_forward(G, vol, s_mod)
+        torch.cuda.synchronize()
+        out[mode] = (S.cpu().numpy(), G.unpack_volume(grad), G.unpack_meas(s_mod))
+    S3, g3, f3 = out["three"]
+    S1, g1, f1 = out["linked"]
+    np.testing.assert_allclose(S1, S3, rtol=2e-6)
+    for i in range(len(specs)):
+        ref = g3[i][0] + GAMMA * g3[i][1]
+        assert rel_l2(g1[i][0], ref) <= 2e-5, (i, rel_l2(g1[i][0], ref))
+        assert rel_l2(f1[i], f3[i]) <= 1e-6, i
+
+
 def test_linked_reconstruct_matches_oracle_trajectory():
     """20 L-BFGS iterations on the linked unknown from h = 0: the final
     objective agrees with the FP64 oracle's within 1e-4 relative, and the
