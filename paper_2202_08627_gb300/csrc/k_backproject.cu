@@ -68,7 +68,7 @@ template <int PASSES, bool QUAD, bool LINKED>
 __device__ __forceinline__ void backproject_single_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
     double *__restrict__ part, const int *__restrict__ active)
 {
     constexpr int TR = 8 * PASSES;
@@ -321,7 +321,7 @@ template <int PASSES, int LAY, bool LINKED>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
+    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
     double *__restrict__ part, const int *__restrict__ active)
 {
     if constexpr (LAY >= 2)
@@ -329,7 +329,7 @@ __device__ __forceinline__ void backproject_item(
                                                         out, out_mult, reg2, reg1, part, active);
     else
         backproject_single_item<PASSES, LAY == 1, LINKED>(dg, prefix, item, sh, gA, gB, with_sino,
-                                                          v, out, out_mult, reg2, reg1, link, part,
+                                                          v, out, out_mult, reg2, reg1, part,
                                                           active);
 }
 
@@ -337,12 +337,12 @@ template <int PASSES, int MINB, int LAY, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
               const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1, float link,
+              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
               double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
     backproject_item<PASSES, LAY, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
-                                   out_mult, reg2, reg1, link, part, active);
+                                          out_mult, reg2, reg1, part, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
                          bool with_sino, const float4 *__restrict__ v, float4 *__restrict__ out,
-                         float4 out_mult, float4 reg2, float4 reg1, float link,
+                         float4 out_mult, float4 reg2, float4 reg1,
                          double *__restrict__ part, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
@@ -363,22 +363,21 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out, out_mult,
-                                       reg2, reg1, link, part, active);
+        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out,
+                                              out_mult, reg2, reg1, part, active);
     }
 }
 
 template <int P, int M, int Q, bool L>
 static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const float4 *v,
                                   float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                  float link, double *part, const int *active, cudaStream_t st)
+                                  double *part, const int *active, cudaStream_t st)
 {
     const AdjVariant &av = g->adj_variant;
     if (av.total == 0) return cudaSuccess;
     if (!g->persistent) {
         k_backproject<P, M, Q, L><<<av.total, ADJ_THREADS, 0, st>>>(
-            g->dg, av.prefix, g->gA, g->gB, with_sino, v, out, out_mult, reg2, reg1, link, part,
-            active);
+            g->dg, av.prefix, g->gA, g->gB, with_sino, v, out, out_mult, reg2, reg1, part, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
@@ -388,7 +387,7 @@ static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const fl
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
         k_backproject_persistent<P, M, Q, L><<<grid, ADJ_THREADS, 0, st>>>(
             g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
-            out_mult, reg2, reg1, link, part, active);
+            out_mult, reg2, reg1, part, active);
     }
     return cudaGetLastError();
 }
@@ -398,11 +397,12 @@ static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const
                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
                                      float link, double *part, const int *active, cudaStream_t st)
 {
+    // link > 0: the linked single-channel gather over the combined sinogram
     return link > 0.f
-               ? launch_bp_mode<P, M, Q, true>(g, with_sino, v, out, out_mult, reg2, reg1, link, part,
+               ? launch_bp_mode<P, M, Q, true>(g, with_sino, v, out, out_mult, reg2, reg1, part,
                                                active, st)
-               : launch_bp_mode<P, M, Q, false>(g, with_sino, v, out, out_mult, reg2, reg1, 0.f,
-                                                part, active, st);
+               : launch_bp_mode<P, M, Q, false>(g, with_sino, v, out, out_mult, reg2, reg1, part,
+                                                active, st);
 }
 
 cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
