@@ -407,6 +407,19 @@ typedef struct {
 int ei_measure_peaks(ei_peaks *out, void *stream);
 
 /*
+ * Failure-detection self-test of the bounded waits.  The bulk-copy kernels
+ * (the IC pipeline, the tensor-core convolutions) wait on mbarriers for at
+ * most a fixed time and then report EI_ERR_TIMEOUT through a device status
+ * word instead of hanging.  This runs that wait on an mbarrier that nothing
+ * ever completes, limited to limit_us microseconds (1 .. 2e6), on the current
+ * device (synchronous), and stores the status the kernel recorded in
+ * *status_out: EI_ERR_TIMEOUT when the wait gave up as it must.  Returns
+ * EI_ERR_ARG for a bad limit or NULL status_out, EI_ERR_CUDA if the launch or
+ * copy failed; the CUDA context stays usable.
+ */
+int ei_selftest_wait_timeout(unsigned limit_us, int *status_out);
+
+/*
  * IC kernel variant (the fused Eq. 2 model, Eq. 5 residual and gradient).
  *   0: one block per sinogram row; any row width and M.
  *   1: persistent blocks (as many as fit on the GPU) that stream rows through

@@ -67,15 +67,18 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Wait for the phase with the given parity to complete, for at most
-// `limit_ns` nanoseconds of wall time; false if it did not.
+// `limit_ns` nanoseconds of wall time; false if it did not.  The tries are also
+// capped at 2^22 (each suspends for up to ~20 us), so the wait ends even if the
+// global timer did not advance.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    for (unsigned i = 1;; ++i) {
+    for (unsigned i = 1; i < (1u << 22); ++i) {
         if (mbar_try_wait(bar, parity, 20000u)) return true;      // sleep up to ~20 us a try
         if ((i & 15u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
+    return false;
 }
 
 // Copy `bytes` from global `src` to shared `dst`; completion is counted on `bar`.

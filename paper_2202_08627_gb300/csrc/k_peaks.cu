@@ -13,6 +13,7 @@
 // counts, so every launch ends.
 #include <algorithm>
 
+#include "async_copy.h"
 #include "ei_internal.h"
 
 namespace ei {
@@ -139,5 +140,48 @@ extern "C" int ei_measure_peaks(ei_peaks *out, void *stream)
     out->l1_load_tbs = bytes / (t_l1 * 1e-3) / 1e12;
     out->smem_load_tbs = bytes / (t_sm * 1e-3) / 1e12;
     out->num_sms = sms;
+    return EI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Failure-detection self-test: one thread initialises an mbarrier that
+// nothing ever arrives on (no copy, no other thread) and waits on it with the
+// same bounded wait the bulk-copy kernels use, limited to `limit_ns`; it
+// records whether the wait gave up.  Nothing is in flight when it returns,
+// so the context stays usable.
+// ---------------------------------------------------------------------------
+namespace ei {
+
+__global__ void k_wait_selftest(uint64_t limit_ns, int *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_addr(&bar), 1);
+    mbar_init_fence();
+    const bool landed = mbar_wait_bounded(smem_addr(&bar), 0u, limit_ns);
+    *status = landed ? (int)EI_OK : (int)EI_ERR_TIMEOUT;
+}
+
+}  // namespace ei
+
+extern "C" int ei_selftest_wait_timeout(unsigned limit_us, int *status_out)
+{
+    using namespace ei;
+    if (!status_out || limit_us == 0 || limit_us > 2000000u) return EI_ERR_ARG;
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>((uint64_t)limit_us * 1000u, d);
+        e = cudaGetLastError();
+    }
+    int st = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    *status_out = st;
     return EI_OK;
 }

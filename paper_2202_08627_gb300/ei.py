@@ -92,7 +92,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
             "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
-            "ei_unet_set_tensor_path", "ei_set_flat_table"]
+            "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 7
@@ -152,6 +152,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_offset_unknowns.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ei_get_offsets.restype = c_int
+    lib.ei_selftest_wait_timeout.argtypes = [ctypes.c_uint, P(c_int)]
+    lib.ei_selftest_wait_timeout.restype = c_int
     lib.ei_set_flat_table.argtypes = [c_void_p, c_void_p, c_int]
     lib.ei_set_flat_table.restype = c_int
     lib.ei_set_linked.argtypes = [c_void_p, c_double]
@@ -623,6 +625,15 @@ def ei_get_offsets(geom: Geometry):
     _check(load_library().ei_get_offsets(geom.handle, m_o.ctypes.data, m_r.ctypes.data),
            "ei_get_offsets")
     return m_o, m_r
+
+
+def ei_selftest_wait_timeout(limit_us: int) -> int:
+    """Runs the bounded mbarrier wait on a barrier nothing completes, limited to
+    limit_us; returns the status the kernel recorded (EI_ERR_TIMEOUT expected)."""
+    st = c_int(-1)
+    _check(load_library().ei_selftest_wait_timeout(int(limit_us), ctypes.byref(st)),
+           "ei_selftest_wait_timeout")
+    return st.value
 
 
 def ei_set_flat_table(geom: Geometry, table) -> None:

@@ -68,6 +68,15 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
         assert err.value.status == ei.EI_ERR_ARG, bad
 
 
+def test_wait_selftest_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_2202_08627_gb300 import ei
+    st = ctypes.c_int(-1)
+    assert lib.ei_selftest_wait_timeout(0, ctypes.byref(st)) == ei.EI_ERR_ARG
+    assert lib.ei_selftest_wait_timeout(2000001, ctypes.byref(st)) == ei.EI_ERR_ARG
+    assert lib.ei_selftest_wait_timeout(1000, None) == ei.EI_ERR_ARG
+    assert st.value == -1
+
+
 def test_null_handle_calls_are_argument_errors(lib):
     from paper_2202_08627_gb300 import ei
     assert lib.ei_project(None, None, None, None) == ei.EI_ERR_ARG
