@@ -113,6 +113,145 @@ k_prep(DevGeom dg, const float4 *__restrict__ vol, float4 mult, bool linked, flo
 // tile shape, the warp shape and the unroll so the autotuner can choose among
 // instantiations.
 // --------------------------------------------------------------------------
+// Ray (pixel j, angle an) through an n x n slice: its inner position at outer
+// index o is (base + o p1) / 2^32 voxels (32.32 fixed point), and it samples
+// the rows o_lo .. o_hi, those whose position lies in [-1, n) (empty when
+// o_lo > o_hi).
+struct RaySetup {
+    long long base, p1;
+    int o_lo, o_hi;
+};
+
+__device__ __forceinline__ RaySetup ray_setup(const AngleInfo &an, int j, int n, int n_det)
+{
+    const double hd = 0.5 * (n_det - 1);
+    // inner position at o = 0, in 32.32 fixed point
+    const double P0 = (j - hd) * an.inv_dom + an.k0;
+    const double TWO32 = 4294967296.0;
+    RaySetup r;
+    r.base = __double2ll_rn(P0 * TWO32);
+    r.p1 = an.p1_fx;
+    const long long base = r.base, p1 = r.p1;
+    const long long lo_lim = -(1LL << 32);               // position >= -1
+    const long long hi_lim = (long long)n << 32;         // position <  n
+    // valid outer range [o_lo, o_hi]: an FP64 estimate, then exact int64 checks
+    int o_lo, o_hi;
+    if (p1 == 0) {
+        const bool in = base >= lo_lim && base < hi_lim;
+        o_lo = in ? 0 : 1;
+        o_hi = in ? n - 1 : 0;
+    } else {
+        const double e1 = (-1.0 - P0) * an.inv_p1, e2 = (n - P0) * an.inv_p1;
+        o_lo = (int)fmax(0.0, fmin((double)n, ceil(fmin(e1, e2))));
+        o_hi = (int)fmin((double)(n - 1), fmax(-1.0, floor(fmax(e1, e2))));
+        auto inr = [&](int o) {
+            const long long q = base + (long long)o * p1;
+            return q >= lo_lim && q < hi_lim;
+        };
+        while (o_lo <= o_hi && !inr(o_lo)) ++o_lo;
+        while (o_hi >= o_lo && !inr(o_hi)) --o_hi;
+        while (o_lo > 0 && inr(o_lo - 1)) --o_lo;
+        while (o_hi < n - 1 && inr(o_hi + 1)) ++o_hi;
+    }
+    r.o_lo = o_lo;
+    r.o_hi = o_hi;
+    return r;
+}
+
+// Adds the samples of rows o0 .. o1 of one ray to acc (row order, so any split
+// of a ray's rows into consecutive segments gives the same sums).  A, B: the
+// packed copy's entries of position 0 of row 0 (entry i0 + 1 holds the voxel
+// at i0 and its difference to the next).
+template <int UNROLL, bool LINKED>
+__device__ __forceinline__ void ray_rows(const RaySetup &rs, int o0, int o1, const float4 *A,
+                                         const float2 *B, int64_t w, float (&acc)[3])
+{
+    if (o0 > o1) return;
+    const float inv32 = 2.3283064365386963e-10f;   // 2^-32
+    long long pos = rs.base + (long long)o0 * rs.p1;
+    const float4 *rowA = A + o0 * w;
+    const float2 *rowB = B + o0 * w;
+    const long long p1 = rs.p1;
+    int o = o0;
+    for (; o + UNROLL - 1 <= o1; o += UNROLL) {
+        float4 va[UNROLL];
+        float2 vb[UNROLL];
+        float f[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const long long q = pos + u * p1;
+            const int i0 = (int)(q >> 32);                     // floor of the position
+            f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
+            if (!LINKED) va[u] = __ldg(rowA + u * w + i0);
+            vb[u] = __ldg(rowB + u * w + i0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (LINKED) {
+                acc[0] += fmaf(f[u], vb[u].y, vb[u].x);
+            } else {
+                acc[0] += fmaf(f[u], va[u].w, va[u].x);
+                acc[1] += fmaf(f[u], vb[u].x, va[u].y);
+                acc[2] += fmaf(f[u], vb[u].y, va[u].z);
+            }
+        }
+        pos += UNROLL * p1;
+        rowA += UNROLL * w;
+        rowB += UNROLL * w;
+    }
+    for (; o <= o1; ++o) {
+        const int i0 = (int)(pos >> 32);
+        const float f = (float)(unsigned)(pos & 0xffffffffLL) * inv32;
+        const float2 vb = __ldg(rowB + i0);
+        if (LINKED) {
+            acc[0] += fmaf(f, vb.y, vb.x);
+        } else {
+            const float4 va = __ldg(rowA + i0);
+            acc[0] += fmaf(f, va.w, va.x);
+            acc[1] += fmaf(f, vb.x, va.y);
+            acc[2] += fmaf(f, vb.y, va.z);
+        }
+        pos += p1;
+        rowA += w;
+        rowB += w;
+    }
+}
+
+// The three output planes of one ray: (R[mu], R[delta], R[sigma]), or linked
+// (R[h], gamma R[h], 0).
+template <bool LINKED>
+__device__ __forceinline__ void ray_store(float *out, int64_t plane, const float (&acc)[3],
+                                          float pch, float link)
+{
+    if (LINKED) {
+        const float pm = acc[0] * pch;
+        out[0] = pm;
+        out[plane] = link * pm;
+        out[2 * plane] = 0.f;
+    } else {
+        out[0] = acc[0] * pch;
+        out[plane] = acc[1] * pch;
+        out[2 * plane] = acc[2] * pch;
+    }
+}
+
+// The full ray of pixel j at angle an.
+template <int UNROLL, bool LINKED>
+__device__ __forceinline__ void project_ray(const SliceInfo &si, const AngleInfo &an, int j,
+                                            const float4 *__restrict__ xpA,
+                                            const float2 *__restrict__ xpB,
+                                            const float4 *__restrict__ xtA,
+                                            const float2 *__restrict__ xtB, float *out,
+                                            int64_t plane, float link)
+{
+    const RaySetup rs = ray_setup(an, j, si.n, si.n_det);
+    const int64_t off = si.pp_off + 1;
+    float acc[3] = {0.f, 0.f, 0.f};
+    ray_rows<UNROLL, LINKED>(rs, rs.o_lo, rs.o_hi, (an.col_dom ? xtA : xpA) + off,
+                             (an.col_dom ? xtB : xpB) + off, si.n + 1, acc);
+    ray_store<LINKED>(out, plane, acc, an.pch, link);
+}
+
 template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
 __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
                                              const float4 *__restrict__ xpA,
@@ -144,112 +283,7 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
         out[2 * plane] = 0.f;
         return;
     }
-    const AngleInfo an = dg.ang[si.ang_off + a];
-    const int n = si.n;
-    const double hd = 0.5 * (si.n_det - 1);
-    // inner position at o = 0, in 32.32 fixed point
-    const double P0 = (j - hd) * an.inv_dom + an.k0;
-    const double TWO32 = 4294967296.0;
-    const long long base = __double2ll_rn(P0 * TWO32);
-    const long long p1 = an.p1_fx;
-    const long long lo_lim = -(1LL << 32);               // position >= -1
-    const long long hi_lim = (long long)n << 32;         // position <  n
-    // valid outer range [o_lo, o_hi]: an FP64 estimate, then exact int64 checks
-    int o_lo, o_hi;
-    if (p1 == 0) {
-        const bool in = base >= lo_lim && base < hi_lim;
-        o_lo = in ? 0 : 1;
-        o_hi = in ? n - 1 : 0;
-    } else {
-        const double e1 = (-1.0 - P0) * an.inv_p1, e2 = (n - P0) * an.inv_p1;
-        o_lo = (int)fmax(0.0, fmin((double)n, ceil(fmin(e1, e2))));
-        o_hi = (int)fmin((double)(n - 1), fmax(-1.0, floor(fmax(e1, e2))));
-        auto inr = [&](int o) {
-            const long long q = base + (long long)o * p1;
-            return q >= lo_lim && q < hi_lim;
-        };
-        while (o_lo <= o_hi && !inr(o_lo)) ++o_lo;
-        while (o_hi >= o_lo && !inr(o_hi)) --o_hi;
-        while (o_lo > 0 && inr(o_lo - 1)) --o_lo;
-        while (o_hi < n - 1 && inr(o_hi + 1)) ++o_hi;
-    }
-    const int64_t w = n + 1;
-    const int64_t row0 = si.pp_off + (int64_t)o_lo * w + 1;   // entry of position i0 is i0 + 1
-    const float4 *rowA = (an.col_dom ? xtA : xpA) + row0;
-    const float2 *rowB = (an.col_dom ? xtB : xpB) + row0;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    long long pos = base + (long long)o_lo * p1;
-    const float inv32 = 2.3283064365386963e-10f;   // 2^-32
-    // UNROLL samples per iteration, their loads independent of each other; the
-    // samples are summed in row order whatever the unroll, so every variant
-    // gives bit-identical projections
-    int o = o_lo;
-    if (LINKED) {
-        // one channel, one 8-byte (value, difference) entry per sample; then
-        // R[mu] = pch sum and R[delta] = gamma R[mu] (Eq. 4: delta = gamma mu)
-        for (; o + UNROLL - 1 <= o_hi; o += UNROLL) {
-            float2 vb[UNROLL];
-            float f[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                const long long q = pos + u * p1;
-                f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
-                vb[u] = __ldg(rowB + u * w + (int)(q >> 32));
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) ax += fmaf(f[u], vb[u].y, vb[u].x);
-            pos += UNROLL * p1;
-            rowB += UNROLL * w;
-        }
-        for (; o <= o_hi; ++o) {
-            const float2 vb = __ldg(rowB + (int)(pos >> 32));
-            ax += fmaf((float)(unsigned)(pos & 0xffffffffLL) * inv32, vb.y, vb.x);
-            pos += p1;
-            rowB += w;
-        }
-        const float pm = ax * an.pch;
-        out[0] = pm;
-        out[plane] = link * pm;
-        out[2 * plane] = 0.f;
-        return;
-    }
-    for (; o + UNROLL - 1 <= o_hi; o += UNROLL) {
-        float4 va[UNROLL];
-        float2 vb[UNROLL];
-        float f[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            const long long q = pos + u * p1;
-            const int i0 = (int)(q >> 32);                     // floor of the position
-            f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
-            va[u] = __ldg(rowA + u * w + i0);
-            vb[u] = __ldg(rowB + u * w + i0);
-        }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            ax += fmaf(f[u], va[u].w, va[u].x);
-            ay += fmaf(f[u], vb[u].x, va[u].y);
-            az += fmaf(f[u], vb[u].y, va[u].z);
-        }
-        pos += UNROLL * p1;
-        rowA += UNROLL * w;
-        rowB += UNROLL * w;
-    }
-    for (; o <= o_hi; ++o) {
-        const int i0 = (int)(pos >> 32);
-        const float f = (float)(unsigned)(pos & 0xffffffffLL) * inv32;
-        const float4 va = __ldg(rowA + i0);
-        const float2 vb = __ldg(rowB + i0);
-        ax += fmaf(f, va.w, va.x);
-        ay += fmaf(f, vb.x, va.y);
-        az += fmaf(f, vb.y, va.z);
-        pos += p1;
-        rowA += w;
-        rowB += w;
-    }
-    out[0] = ax * an.pch;
-    out[plane] = ay * an.pch;
-    out[2 * plane] = az * an.pch;
+    project_ray<UNROLL, LINKED>(si, dg.ang[si.ang_off + a], j, xpA, xpB, xtA, xtB, out, plane, link);
 }
 
 // One block per work item.
