@@ -213,6 +213,8 @@ typedef struct {
     int max_trials;    /* step halvings per line search (20) */
     double curv_eps;   /* keep a pair only if s.y > curv_eps |s| |y| (1e-10) */
     int use_graph;     /* 1: capture one solver round into a CUDA graph and replay it (1) */
+    int resume;        /* 1: continue from the solver state instead of starting at vol_inout (0);
+                          see ei_solver_save / ei_solver_load */
 } ei_solve_opts;
 
 /* Per-slice results; every pointer is a caller-owned HOST array of n_slices
@@ -246,8 +248,32 @@ typedef struct {
 int ei_reconstruct(const ei_geometry *g, const float *s_exp, float *vol_inout,
                    const ei_solve_opts *opts, ei_solve_report *report, void *stream);
 
-/* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10, graphs on. */
+/* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10, graphs on,
+ * no resume. */
 void ei_default_solve_opts(ei_solve_opts *opts);
+
+/*
+ * Checkpoint / resume of the solver.  After ei_reconstruct returns, the
+ * geometry keeps the L-BFGS state of every slice: the iterate u = x / scale
+ * and its gradient, the search direction, the m most recent (s, y) pairs and
+ * their 1 / s.y, the accepted-step count k, the current and initial S, and
+ * whether the slice converged, failed, or is between steps.
+ *   ei_solver_state_size: bytes of that state for this geometry and lbfgs_m.
+ *   ei_solver_save: copies it to buf (host or device, >= the size); EI_ERR_ARG
+ *     when no solve has completed on this geometry.
+ *   ei_solver_load: installs a saved state in a geometry of the same slices,
+ *     unknowns (linked mode, offsets) and lbfgs_m; EI_ERR_ARG when the header
+ *     does not match.
+ * ei_reconstruct with opts.resume = 1 then continues from the state (vol_inout
+ * is output only, s_exp must be the same data): slices that stopped at
+ * max_iter resume with the new max_iter (k counts from the original start),
+ * converged or failed slices stay so, and the iterates are bit-identical to
+ * one uninterrupted solve with the larger max_iter.  The state holds
+ * (2 m + 5) vectors of the volume's size plus small per-slice records.
+ */
+int ei_solver_state_size(const ei_geometry *g, int lbfgs_m, size_t *bytes);
+int ei_solver_save(const ei_geometry *g, void *buf, size_t bytes);
+int ei_solver_load(ei_geometry *g, int lbfgs_m, const void *buf, size_t bytes);
 
 /*
  * Tracing: per-kernel CUDA-event timings and a count of every kernel this

@@ -58,7 +58,7 @@ void record_error(cudaError_t e)
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-static void record_message(const char *fmt, ...)
+void record_message(const char *fmt, ...)
 {
     va_list ap;
     va_start(ap, fmt);
@@ -236,6 +236,7 @@ void ei_default_solve_opts(ei_solve_opts *o)
     o->max_trials = 20;
     o->curv_eps = 1e-10;
     o->use_graph = 1;
+    o->resume = 0;
 }
 
 static void release_events(ei_geometry *g)
@@ -972,6 +973,25 @@ int ei_objective_grad(const ei_geometry *gc, const float *vol, const float *s_ex
     return EI_OK;
 }
 
+int ei_solver_state_size(const ei_geometry *g, int lbfgs_m, size_t *bytes)
+{
+    if (!g || !bytes || lbfgs_m < 1 || lbfgs_m > 32) return EI_ERR_ARG;
+    *bytes = ei::solver_state_size(g, lbfgs_m);
+    return EI_OK;
+}
+
+int ei_solver_save(const ei_geometry *g, void *buf, size_t bytes)
+{
+    if (!g || !buf) return EI_ERR_ARG;
+    return ei::solver_save(g, buf, bytes);
+}
+
+int ei_solver_load(ei_geometry *g, int lbfgs_m, const void *buf, size_t bytes)
+{
+    if (!g || !buf || lbfgs_m < 1 || lbfgs_m > 32) return EI_ERR_ARG;
+    return ei::solver_load(g, lbfgs_m, buf, bytes);
+}
+
 int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
                    const ei_solve_opts *opts, ei_solve_report *report, void *stream)
 {
@@ -980,7 +1000,7 @@ int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
     ei_default_solve_opts(&o);
     if (opts) o = *opts;
     if (!(o.tol >= 0) || o.max_iter < 0 || o.lbfgs_m < 1 || o.lbfgs_m > 32 || !(o.c1 > 0) ||
-        o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0))
+        o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0) || (o.resume != 0 && o.resume != 1))
         return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     const int r = ei::reconstruct(g, s_exp, vol_inout, &o, report, (cudaStream_t)stream);

@@ -258,9 +258,15 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
                 ei_solve_report *report, cudaStream_t st);
 // Remember the last CUDA error of this thread (reported by ei_last_error).
 void record_error(cudaError_t e);
+// Remember a formatted message as the last error of this thread.
+void record_message(const char *fmt, ...);
 // Select kernel variants (ids in range) and the launch mode.
 void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent);
 void destroy_solver(ei_geometry *g);
+// Checkpoint of the solver state (ei_solver_state_size / _save / _load).
+size_t solver_state_size(const ei_geometry *g, int m);
+int solver_save(const ei_geometry *g, void *buf, size_t bytes);
+int solver_load(ei_geometry *g, int m, const void *buf, size_t bytes);
 
 }  // namespace ei
 

@@ -59,6 +59,7 @@ struct Solver {
     int *summary = nullptr;                 // [2]: slices still running, slices in line search
     int *summary_h = nullptr;               // pinned host copy
     cudaStream_t stream = nullptr;          // the solver's own stream (capturable)
+    bool has_state = false;                 // a completed solve (or a loaded checkpoint)
     std::vector<void *> allocs;
 };
 
@@ -484,6 +485,28 @@ __global__ void k_init_state(DevGeom dg, SolverDev sv, const double *__restrict_
     if (threadIdx.x == 0) summary[0] = acc, summary[1] = 0;
 }
 
+// resume from a kept or loaded state: slices that stopped at max_iter (between
+// steps, not converged, no error) need a direction again under the new limit
+__global__ void k_resume_state(DevGeom dg, SolverDev sv, int max_iter, int *summary)
+{
+    int running = 0, in_ls = 0;
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        const SliceState &q = sv.st[s];
+        sv.mask_acc[s] = 0;
+        if (q.status == EI_OK && !q.converged && !sv.mask_ls[s] && q.k < max_iter)
+            sv.mask_dir[s] = 1;
+        running += sv.mask_dir[s] | sv.mask_ls[s];
+        in_ls += sv.mask_ls[s];
+    }
+    __shared__ int a0, a1;
+    if (threadIdx.x == 0) a0 = 0, a1 = 0;
+    __syncthreads();
+    atomicAdd(&a0, running);
+    atomicAdd(&a1, in_ls);
+    __syncthreads();
+    if (threadIdx.x == 0) summary[0] = a0, summary[1] = a1;
+}
+
 // direction finished: choose the first trial step
 __global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ p_gd,
                            const double *__restrict__ p_gg)
@@ -712,18 +735,27 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     Opts o{opts->tol, opts->c1, opts->curv_eps, opts->max_iter, opts->max_trials};
     const int scalar_threads = 256;
 
-    k_to_scaled<<<NBv, T, 0, st>>>(g->dg, x_dev, sv->u, inv);
-    count_launches(g, 1);
-    if (ow) {
-        k_offsets_to_u<<<g->n_slices, 256, 0, st>>>(dg, ow, 1.f / os, sv->u);
+    sv->has_state = false;                    // until this solve completes
+    if (opts->resume) {
+        // continue from the kept state: u, its gradient, the memory, the slices' records
+        k_resume_state<<<1, scalar_threads, 0, st>>>(dg, dv, opts->max_iter, sv->summary);
         count_launches(g, 1);
+        EI_CUDA_TRY(cudaGetLastError());
+        *evals = 0;
+    } else {
+        k_to_scaled<<<NBv, T, 0, st>>>(g->dg, x_dev, sv->u, inv);
+        count_launches(g, 1);
+        if (ow) {
+            k_offsets_to_u<<<g->n_slices, 256, 0, st>>>(dg, ow, 1.f / os, sv->u);
+            count_launches(g, 1);
+        }
+        EI_CUDA_TRY(cudaGetLastError());
+        EI_CUDA_TRY(eval(sv->u, sv->g, nullptr));
+        k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
+        count_launches(g, 1);
+        EI_CUDA_TRY(cudaGetLastError());
+        *evals = 1;
     }
-    EI_CUDA_TRY(cudaGetLastError());
-    EI_CUDA_TRY(eval(sv->u, sv->g, nullptr));
-    k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
-    count_launches(g, 1);
-    EI_CUDA_TRY(cudaGetLastError());
-    *evals = 1;
     EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     EI_CUDA_TRY(cudaStreamSynchronize(st));
 
@@ -795,6 +827,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (err != cudaSuccess) return err;
+    sv->has_state = true;
     k_from_scaled<<<NBv, T, 0, st>>>(g->dg, sv->u, x_dev, sc);
     count_launches(g, 1);
     if (ow) {                                 // the solution's offsets stay in the geometry
@@ -808,6 +841,12 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
                 ei_solve_report *report, cudaStream_t st)
 {
     const auto t0 = std::chrono::steady_clock::now();
+    if (opts->resume && !(g->solver && g->solver->has_state && g->solver->m == opts->lbfgs_m &&
+                          g->solver->off_which == g->off_which)) {
+        record_message("ei_reconstruct: resume needs the state of a completed solve or a "
+                       "loaded checkpoint with the same lbfgs_m and unknowns");
+        return EI_ERR_ARG;
+    }
     cudaError_t e = ensure_solver(g, opts->lbfgs_m);
     if (e != cudaSuccess) {
         record_error(e);
@@ -837,7 +876,7 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
     }
     if (e == cudaSuccess && !vol_dev) {
         if (!sv->vol_stage) e = salloc(sv, &sv->vol_stage, (size_t)g->vol_count);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !opts->resume)     // resume: vol_inout is output only
             e = cudaMemcpyAsync(sv->vol_stage, vol_inout, (size_t)g->vol_count * sizeof(float4),
                                 cudaMemcpyHostToDevice, st);
         x = sv->vol_stage;
@@ -876,6 +915,140 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return first_err;
+}
+
+// --------------------------------------------------------------------------
+// checkpoint: the state a solve leaves (or a resumed solve continues from),
+// behind a header that names the geometry it belongs to
+// --------------------------------------------------------------------------
+struct StateHeader {
+    uint64_t magic;          // "EISOLVER" + layout version
+    int n_slices, m, ring, off_which;
+    int linked, slice_state_bytes;
+    int64_t vol_count;       // float4 per solver vector (volumes + offsets segments)
+    uint64_t shape_hash;
+};
+
+static const uint64_t kStateMagic = 0x4549534f4c564531ull;   // "EISOLVE1"
+
+static int64_t solver_vol_count(const ei_geometry *g)
+{
+    int64_t ext = g->vol_count;
+    if (g->off_which)
+        for (const SliceInfo &si : g->h_slices) {
+            const int K = ((g->off_which & EI_OFFSET_MO) ? si.n_theta : 0) +
+                          ((g->off_which & EI_OFFSET_MR) ? si.n_det : 0);
+            ext += (K + 2) / 3;
+        }
+    return ext;
+}
+
+static StateHeader state_header(const ei_geometry *g, int m)
+{
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.n_slices = g->n_slices;
+    h.m = m;
+    h.ring = m + 1;
+    h.off_which = g->off_which;
+    h.linked = g->link_gamma > 0.f ? 1 : 0;
+    h.slice_state_bytes = (int)sizeof(SliceState);
+    h.vol_count = solver_vol_count(g);
+    h.shape_hash = g->shape_hash;
+    return h;
+}
+
+// The state's pieces in checkpoint order: device pointer and bytes.
+static std::vector<std::pair<void *, size_t>> state_pieces(const Solver *s, int n_slices)
+{
+    const size_t V = (size_t)s->vol_count * sizeof(float4), S = (size_t)n_slices;
+    return {{s->u, V},
+            {s->g, V},
+            {s->d, V},
+            {s->Sr, V * s->ring},
+            {s->Yr, V * s->ring},
+            {s->rho, sizeof(double) * s->ring * S},
+            {s->st, sizeof(SliceState) * S},
+            {s->mask_dir, sizeof(int) * S},
+            {s->mask_ls, sizeof(int) * S},
+            {s->mask_acc, sizeof(int) * S}};
+}
+
+size_t solver_state_size(const ei_geometry *g, int m)
+{
+    const size_t V = (size_t)solver_vol_count(g) * sizeof(float4), S = (size_t)g->n_slices;
+    const size_t ring = (size_t)m + 1;
+    return sizeof(StateHeader) + V * (3 + 2 * ring) + sizeof(double) * ring * S +
+           sizeof(SliceState) * S + 3 * sizeof(int) * S;
+}
+
+int solver_save(const ei_geometry *g, void *buf, size_t bytes)
+{
+    const Solver *s = g->solver;
+    if (!s || !s->has_state) {
+        record_message("ei_solver_save: no completed solve on this geometry");
+        return EI_ERR_ARG;
+    }
+    if (bytes < solver_state_size(g, s->m)) return EI_ERR_ARG;
+    const StateHeader h = state_header(g, s->m);
+    char *p = static_cast<char *>(buf);
+    cudaError_t e = cudaMemcpy(p, &h, sizeof h, cudaMemcpyDefault);
+    p += sizeof h;
+    for (const auto &pc : state_pieces(s, g->n_slices)) {
+        if (e != cudaSuccess) break;
+        e = cudaMemcpy(p, pc.first, pc.second, cudaMemcpyDefault);
+        p += pc.second;
+    }
+    if (e != cudaSuccess) {
+        record_error(e);
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    return EI_OK;
+}
+
+int solver_load(ei_geometry *g, int m, const void *buf, size_t bytes)
+{
+    if (bytes < solver_state_size(g, m)) return EI_ERR_ARG;
+    StateHeader h{};
+    const char *p = static_cast<const char *>(buf);
+    cudaError_t e = cudaMemcpy(&h, p, sizeof h, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        record_error(e);
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    const StateHeader want = state_header(g, m);
+    if (h.magic != want.magic || h.n_slices != want.n_slices || h.m != want.m ||
+        h.ring != want.ring || h.off_which != want.off_which || h.linked != want.linked ||
+        h.slice_state_bytes != want.slice_state_bytes || h.vol_count != want.vol_count ||
+        h.shape_hash != want.shape_hash) {
+        record_message("ei_solver_load: the checkpoint belongs to another geometry, mode or lbfgs_m");
+        return EI_ERR_ARG;
+    }
+    e = ensure_solver(g, m);
+    if (e != cudaSuccess) {
+        record_error(e);
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        destroy_solver(g);
+        return oom ? EI_ERR_ALLOC : EI_ERR_CUDA;
+    }
+    Solver *s = g->solver;
+    s->has_state = false;
+    p += sizeof h;
+    for (const auto &pc : state_pieces(s, g->n_slices)) {
+        if (e != cudaSuccess) break;
+        e = cudaMemcpy(pc.first, p, pc.second, cudaMemcpyDefault);
+        p += pc.second;
+    }
+    if (e != cudaSuccess) {
+        record_error(e);
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    s->has_state = true;
+    return EI_OK;
 }
 
 }  // namespace ei

@@ -61,7 +61,8 @@ class ei_layout(ctypes.Structure):
 
 class ei_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("lbfgs_m", c_int), ("c1", c_double),
-                ("max_trials", c_int), ("curv_eps", c_double), ("use_graph", c_int)]
+                ("max_trials", c_int), ("curv_eps", c_double), ("use_graph", c_int),
+                ("resume", c_int)]
 
 
 class ei_solve_report(ctypes.Structure):
@@ -92,7 +93,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_get_params", "ei_unet_set_params", "ei_unet_get_grads", "ei_set_ic_variant",
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
             "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
-            "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout"]
+            "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout",
+            "ei_solver_state_size", "ei_solver_save", "ei_solver_load"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 7
@@ -152,6 +154,12 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_offset_unknowns.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ei_get_offsets.restype = c_int
+    lib.ei_solver_state_size.argtypes = [c_void_p, c_int, P(ctypes.c_size_t)]
+    lib.ei_solver_state_size.restype = c_int
+    lib.ei_solver_save.argtypes = [c_void_p, c_void_p, ctypes.c_size_t]
+    lib.ei_solver_save.restype = c_int
+    lib.ei_solver_load.argtypes = [c_void_p, c_int, c_void_p, ctypes.c_size_t]
+    lib.ei_solver_load.restype = c_int
     lib.ei_selftest_wait_timeout.argtypes = [ctypes.c_uint, P(c_int)]
     lib.ei_selftest_wait_timeout.restype = c_int
     lib.ei_set_flat_table.argtypes = [c_void_p, c_void_p, c_int]
@@ -491,14 +499,16 @@ class SolveReport:
 
 def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbfgs_m=10,
                    c1=1e-4, max_trials=20, curv_eps=1e-10, use_graph=True, stream=None,
-                   raise_on_error: bool = True) -> SolveReport:
+                   raise_on_error: bool = True, resume: bool = False) -> SolveReport:
     """Batched L-BFGS minimisation of S.  s_exp / vol_inout: CUDA tensors, or
-    pinned/pageable CPU tensors (the library stages host arrays)."""
+    pinned/pageable CPU tensors (the library stages host arrays).  resume:
+    continue from the geometry's solver state (the last solve or
+    ei_solver_load) instead of starting at vol_inout."""
     import torch
     if s_exp.numel() < geom.meas_count or vol_inout.numel() < 4 * geom.vol_count:
         raise ValueError("s_exp / vol_inout smaller than the layout")
     o = ei_solve_opts(float(tol), int(max_iter), int(lbfgs_m), float(c1), int(max_trials),
-                      float(curv_eps), int(bool(use_graph)))
+                      float(curv_eps), int(bool(use_graph)), int(bool(resume)))
     S = geom.n_slices
     it = np.zeros(S, np.int32)
     st = np.zeros(S, np.int32)
@@ -518,6 +528,27 @@ def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbf
     if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE):
         raise EIError(rc, "ei_reconstruct")
     return out
+
+
+def ei_solver_state_size(geom: Geometry, lbfgs_m: int = 10) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().ei_solver_state_size(geom.handle, int(lbfgs_m), ctypes.byref(n)),
+           "ei_solver_state_size")
+    return n.value
+
+
+def ei_solver_save(geom: Geometry, lbfgs_m: int = 10) -> np.ndarray:
+    """The solver state of the last solve as a host byte array."""
+    buf = np.empty(ei_solver_state_size(geom, lbfgs_m), np.uint8)
+    _check(load_library().ei_solver_save(geom.handle, buf.ctypes.data, buf.nbytes),
+           "ei_solver_save")
+    return buf
+
+
+def ei_solver_load(geom: Geometry, buf: np.ndarray, lbfgs_m: int = 10) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().ei_solver_load(geom.handle, int(lbfgs_m), buf.ctypes.data, buf.nbytes),
+           "ei_solver_load")
 
 
 def ei_profile_enable(geom: Geometry, on: bool = True) -> None:

@@ -51,6 +51,16 @@ def test_default_options(lib):
     from paper_2202_08627_gb300 import ei
     o = ei.ei_default_solve_opts()
     assert (o.tol, o.max_iter, o.lbfgs_m, o.c1, o.max_trials) == (1e-6, 100, 10, 1e-4, 20)
+    assert (o.use_graph, o.resume) == (1, 0)
+
+
+def test_checkpoint_calls_reject_bad_arguments_before_touching_the_gpu(lib):
+    from paper_2202_08627_gb300 import ei
+    n = ctypes.c_size_t(0)
+    buf = (ctypes.c_char * 16)()
+    assert lib.ei_solver_state_size(None, 10, ctypes.byref(n)) == ei.EI_ERR_ARG
+    assert lib.ei_solver_save(None, buf, 16) == ei.EI_ERR_ARG
+    assert lib.ei_solver_load(None, 10, buf, 16) == ei.EI_ERR_ARG
 
 
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
