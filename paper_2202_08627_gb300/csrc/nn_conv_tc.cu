@@ -253,6 +253,211 @@ static cudaError_t launch_tc(const Tensor &x1, const Tensor *x2, int cout, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores:
+//   dW[tap][ci][co] = sum_p X_tap[p][ci] G[p][co]
+// as a GEMM whose rows are r = tap Cin + ci (M = 128 rows per CTA; rows past
+// KS^2 Cin are zero), whose columns are the output channels (N = NT), and
+// whose reduction runs over the pixels in chunks of 32, split over the grid's
+// z dimension (FP32 partials, summed by k_sum_splits in a fixed order).  Both
+// operands are read straight from the NHWC activations: with the pixels as the
+// reduction dimension the channels are the contiguous one, so the tiles are
+// MN-major (tcgen05 instruction descriptor bits 15 and 16): core matrices of
+// 8 pixels x 8 channels whose 16-byte rows are 8 consecutive channels of one
+// pixel, 128 bytes between core matrices along the pixels and 512 between
+// groups of 8 rows, the same descriptor strides as the K-major tiles.  The
+// pipeline, the bounded waits and the tensor-memory handling are those of
+// k_conv_tc.
+// ---------------------------------------------------------------------------
+template <int KS, int NT>
+__global__ void __launch_bounds__(128)
+k_conv_wgrad_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int C2,
+                const bf16 *__restrict__ G, int Cout, int B, int H, int W, int per_split,
+                float *__restrict__ partial, int *__restrict__ status)
+{
+    constexpr int A_BYTES = TC_M * TC_BK * 2, B_BYTES = NT * TC_BK * 2;
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar_mma[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int P = B * H * W;
+    const int Cin = C1 + C2;
+    const int R = KS * KS * Cin;
+    const int r0 = blockIdx.x * TC_M, co0 = blockIdx.y * NT, split = blockIdx.z;
+    const int pa = split * per_split, pe = min(P, pa + per_split);
+    const int nK = pe > pa ? (pe - pa + TC_BK - 1) / TC_BK : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_addr(&bar_mma[s]), 1);
+        mbar_init(smem_addr(&bar_done), 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    // D f32, A bf16, B bf16, both MN-major, N >> 3, M >> 4
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((unsigned)(NT >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
+
+    // this thread stages, in every chunk, pixel kp of the chunk for the A row
+    // groups gq, gq + 4, gq + 8, gq + 12 and the B column groups gq + 4 j
+    const int kp = tid & 31, gq = tid >> 5;
+    int g_dy[4], g_dx[4], g_ci[4];
+    bool g_ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + 8 * (gq + 4 * i);
+        g_ok[i] = r < R;
+        const int tap = g_ok[i] ? r / Cin : 0;
+        g_ci[i] = g_ok[i] ? r - tap * Cin : 0;
+        g_dy[i] = KS == 3 ? tap / 3 - 1 : 0;
+        g_dx[i] = KS == 3 ? tap % 3 - 1 : 0;
+    }
+    const int cell = (kp >> 3) * 128 + (kp & 7) * 16;       // this pixel's 16 bytes in a row group
+    auto issue = [&](int kc) {
+        unsigned char *As = tc_smem + (kc % TC_STAGES) * STAGE_BYTES;
+        unsigned char *Bs = As + A_BYTES;
+        const int p = pa + kc * TC_BK + kp;
+        const bool pin = p < pe;
+        int pb = 0, py = 0, px = 0;
+        if (pin) {
+            pb = p / (H * W);
+            const int rr = p - pb * H * W;
+            py = rr / W;
+            px = rr - py * W;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int yy = py + g_dy[i], xx = px + g_dx[i];
+            const bool inb = pin && g_ok[i] && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const int64_t q = ((int64_t)pb * H + yy) * W + xx;
+            const int ci = g_ci[i];
+            const bf16 *src = X1;
+            if (inb) src = ci < C1 ? X1 + q * C1 + ci : X2 + q * C2 + (ci - C1);
+            cp_async16(As + (gq + 4 * i) * 512 + cell, src, inb ? 16u : 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < NT / 32; ++j) {
+            const int g = gq + 4 * j;
+            cp_async16(Bs + g * 512 + cell, pin ? G + (int64_t)p * Cout + co0 + 8 * g : G,
+                       pin ? 16u : 0u);
+        }
+    };
+    constexpr int DEPTH = 2;                   // chunks in flight ahead of the MMA
+#pragma unroll
+    for (int i = 0; i < DEPTH; ++i) {
+        if (i < nK) issue(i);
+        cp_async_commit();
+    }
+    bool aborted = false;
+    for (int kc = 0; kc < nK; ++kc) {
+        bool ok = true;
+        const int kn = kc + DEPTH;
+        if (kn < nK) {
+            if (kn >= TC_STAGES)
+                ok = mbar_wait_bounded(smem_addr(&bar_mma[kn % TC_STAGES]),
+                                       ((kn / TC_STAGES) - 1) & 1, kTcWaitNs);
+            if (ok) issue(kn);
+        }
+        cp_async_commit();
+        cp_async_wait<DEPTH>();
+        proxy_fence_async();
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned a_addr = smem_addr(tc_smem + (kc % TC_STAGES) * STAGE_BYTES);
+            const unsigned b_addr = a_addr + A_BYTES;
+            tc_mma(tmem, smem_desc(a_addr), smem_desc(b_addr), idesc, kc > 0 ? 1u : 0u);
+            tc_mma(tmem, smem_desc(a_addr + 256), smem_desc(b_addr + 256), idesc, 1u);
+            tc_commit(smem_addr(&bar_mma[kc % TC_STAGES]));
+        }
+    }
+    cp_async_wait<0>();
+    bool done = true;
+    if (nK > 0) {
+        if (tid == 0) tc_commit(smem_addr(&bar_done));
+        done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int r = r0 + warp * 32 + (tid & 31);                // this thread's row (its lane)
+    float *dst = partial + ((int64_t)split * R + r) * Cout + co0;
+    if (aborted || !done) {
+        if (tid == 0) atomicExch(status, 1);
+    } else if (nK == 0) {                      // an empty pixel range: zero partials
+        if (r < R)
+            for (int c = 0; c < NT; c += 4) reinterpret_cast<float4 *>(dst + c)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        for (int c = 0; c < NT; c += 16) {
+            unsigned v[16];
+            tc_ld16(lane_base + c, v);
+            if (r >= R) continue;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                reinterpret_cast<float4 *>(dst + c + j)[0] =
+                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
+}
+
+template <int KS, int NT>
+static cudaError_t launch_wgrad_tc(const Tensor &x1, const Tensor *x2, const bf16 *g, int cout,
+                                   float *partial, int nsplit, int *status, cudaStream_t st)
+{
+    constexpr int smem = TC_STAGES * (TC_M * TC_BK * 2 + NT * TC_BK * 2);
+    static bool attr = false;
+    if (!attr) {
+        EI_NN_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<KS, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    const int P = x1.B * x1.H * x1.W;
+    const int cin = x1.C + (x2 ? x2->C : 0);
+    const int R = KS * KS * cin;
+    const int per = ((P + nsplit - 1) / nsplit + TC_BK - 1) / TC_BK * TC_BK;
+    dim3 grid((R + TC_M - 1) / TC_M, cout / NT, nsplit);
+    k_conv_wgrad_tc<KS, NT><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr,
+                                                     x2 ? x2->C : 0, g, cout, x1.B, x1.H, x1.W,
+                                                     per, partial, status);
+    return cudaGetLastError();
+}
+
+bool wgrad_tc_supported(int cin, int cout, int c1)
+{
+    const int nt = cout >= 256 ? 256 : cout;
+    return cin % TC_BK == 0 && c1 % 8 == 0 && (nt == 32 || nt == 64 || nt == 128 || nt == 256) &&
+           cout % nt == 0;
+}
+
+cudaError_t conv_wgrad_tc(const Tensor &x1, const Tensor *x2, const bf16 *g, int cout, int ks,
+                          float *partial, int nsplit, int *status, cudaStream_t st)
+{
+    const int nt = cout >= 256 ? 256 : cout;
+#define EI_WG_CASE(K, N)                                                                     \
+    if (ks == K && nt == N) return launch_wgrad_tc<K, N>(x1, x2, g, cout, partial, nsplit, status, st);
+    EI_WG_CASE(3, 32) EI_WG_CASE(3, 64) EI_WG_CASE(3, 128) EI_WG_CASE(3, 256)
+    EI_WG_CASE(1, 32) EI_WG_CASE(1, 64) EI_WG_CASE(1, 128) EI_WG_CASE(1, 256)
+#undef EI_WG_CASE
+    return cudaErrorInvalidValue;
+}
+
 bool conv_tc_supported(int cin, int cout, int c1, int split)
 {
     const int nt = cout >= 256 ? 256 : cout;

@@ -43,6 +43,15 @@ cudaError_t conv_forward_tc(const Tensor &x1, const Tensor *x2, int cout, int ks
                             bool acc2, int *status, cudaStream_t st);
 cudaError_t conv_wgrad(const Tensor &x1, const Tensor *x2, const bf16 *g, int cout, int ks,
                        float *partial, int nsplit, float *dw, bool accumulate, cudaStream_t st);
+// The weight gradient's per-split partials on the tcgen05 tensor cores
+// (nn_conv_tc.cu): partial[split][tap Cin + ci][co], the layout conv_wgrad's
+// partials have; sum them with sum_splits.  *status is set if a bounded wait ran out.
+bool wgrad_tc_supported(int cin, int cout, int c1);
+cudaError_t conv_wgrad_tc(const Tensor &x1, const Tensor *x2, const bf16 *g, int cout, int ks,
+                          float *partial, int nsplit, int *status, cudaStream_t st);
+// out[i] (+)= sum_s partial[s][i] over nsplit splits of n values, in split order.
+cudaError_t sum_splits(const float *partial, int nsplit, int64_t n, float *out, bool accumulate,
+                       cudaStream_t st);
 // db[c] = sum_p g[p][c] through per-block partials (C divides 256)
 cudaError_t bias_grad(const bf16 *g, int C, int64_t P, float *db, float *partial, cudaStream_t st);
 cudaError_t prepare_weights(const float *Wm, int taps, int cin, int cout, bf16 *Wb, bf16 *Wf,

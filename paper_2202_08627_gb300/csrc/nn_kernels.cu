@@ -459,6 +459,13 @@ cudaError_t conv_wgrad(const Tensor &x1, const Tensor *x2, const bf16 *g, int co
     return cudaGetLastError();
 }
 
+cudaError_t sum_splits(const float *partial, int nsplit, int64_t n, float *out, bool accumulate,
+                       cudaStream_t st)
+{
+    k_sum_splits<<<grid_for(n), 256, 0, st>>>(partial, nsplit, n, out, accumulate);
+    return cudaGetLastError();
+}
+
 cudaError_t bias_grad(const bf16 *g, int C, int64_t P, float *db, float *partial, cudaStream_t st)
 {
     const int blocks = (int)std::min<int64_t>(256, std::max<int64_t>(1, P / 1024));

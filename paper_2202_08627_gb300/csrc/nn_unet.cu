@@ -145,7 +145,14 @@ cudaError_t conv_backward(ei_unet *n, const Conv &c, const Tensor &x1, const Ten
 {
     const int64_t P = (int64_t)y.B * y.H * y.W;
     if (c.relu) EI_NN_TRY(relu_mask(g, y.d, P * c.cout, st));
-    EI_NN_TRY(conv_wgrad(x1, x2, g, c.cout, c.ks, n->partial, nsplit_for(P), c.gW, false, st));
+    const int nsplit = nsplit_for(P);
+    if (n->use_tc && wgrad_tc_supported(c.cin(), c.cout, x1.C)) {
+        EI_NN_TRY(conv_wgrad_tc(x1, x2, g, c.cout, c.ks, n->partial, nsplit, n->status, st));
+        EI_NN_TRY(sum_splits(n->partial, nsplit, (int64_t)c.ks * c.ks * c.cin() * c.cout, c.gW,
+                             false, st));
+    } else {
+        EI_NN_TRY(conv_wgrad(x1, x2, g, c.cout, c.ks, n->partial, nsplit, c.gW, false, st));
+    }
     EI_NN_TRY(bias_grad(g, c.cout, P, c.gb, n->bias_part, st));
     if (gx1) {
         Tensor gt;
