@@ -496,10 +496,10 @@ int64_t ei_unet_num_params(const ei_unet *net);
 int ei_unet_get_params(const ei_unet *net, float *host);
 int ei_unet_set_params(ei_unet *net, const float *host);
 int ei_unet_get_grads(const ei_unet *net, float *host);
-/* Convolution path: 1 (default) tcgen05 implicit-GEMM kernels, used for every
- * convolution whose channel counts they support (input channels a multiple of
- * 32; output channels 32, 64, 128 or a multiple of 256); 0 the WMMA (mma.sync)
- * kernels for all.  Both accumulate in FP32; results agree to FP32 rounding of
+/* Convolution path: 1 (default) tcgen05 implicit-GEMM kernels for the forward
+ * pass, the input gradients and the weight gradients of every convolution whose
+ * channel counts they support (input channels a multiple of 32; output channels
+ * 32, 64, 128 or a multiple of 256); 0 the WMMA (mma.sync) kernels for all.  Both accumulate in FP32; results agree to FP32 rounding of
  * the sums.  A tcgen05 kernel whose bounded wait runs out makes the next
  * synchronising ei_unet_train_step return EI_ERR_TIMEOUT. */
 int ei_unet_set_tensor_path(ei_unet *net, int path);
