@@ -496,6 +496,12 @@ int64_t ei_unet_num_params(const ei_unet *net);
 int ei_unet_get_params(const ei_unet *net, float *host);
 int ei_unet_set_params(ei_unet *net, const float *host);
 int ei_unet_get_grads(const ei_unet *net, float *host);
+/* Adam's state for a training checkpoint: the first and second moments
+ * (host arrays of ei_unet_num_params floats, the parameters' order) and the
+ * step count; with the parameters (ei_unet_get_params / _set_params) a restored
+ * network continues training bit-identically.  Synchronous. */
+int ei_unet_get_optimizer(const ei_unet *net, float *m_host, float *v_host, int *step);
+int ei_unet_set_optimizer(ei_unet *net, const float *m_host, const float *v_host, int step);
 /* Convolution path: 1 (default) tcgen05 implicit-GEMM kernels for the forward
  * pass, the input gradients and the weight gradients of every convolution whose
  * channel counts they support (input channels a multiple of 32; output channels

@@ -401,14 +401,14 @@ static int copy_params(ei_unet *n, float *host, int which, bool to_host)
     if (!n || !host) return EI_ERR_ARG;
     cudaError_t e = cudaDeviceSynchronize();
     int64_t off = 0;
-    for_each_param(n, [&](float *p, float *g, float *, float *, int64_t k) {
-        float *d = which == 0 ? p : g;
+    for_each_param(n, [&](float *p, float *g, float *m, float *v, int64_t k) {
+        float *d = which == 0 ? p : which == 1 ? g : which == 2 ? m : v;
         if (e == cudaSuccess)
             e = to_host ? cudaMemcpy(host + off, d, k * 4, cudaMemcpyDeviceToHost)
                         : cudaMemcpy(d, host + off, k * 4, cudaMemcpyHostToDevice);
         off += k;
     });
-    if (e == cudaSuccess && !to_host) e = refresh_bf16(n, 0);
+    if (e == cudaSuccess && !to_host && which == 0) e = refresh_bf16(n, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return status(e);
 }
@@ -416,5 +416,24 @@ static int copy_params(ei_unet *n, float *host, int which, bool to_host)
 int ei_unet_get_params(const ei_unet *n, float *host) { return copy_params(const_cast<ei_unet *>(n), host, 0, true); }
 int ei_unet_set_params(ei_unet *n, const float *host) { return copy_params(n, const_cast<float *>(host), 0, false); }
 int ei_unet_get_grads(const ei_unet *n, float *host) { return copy_params(const_cast<ei_unet *>(n), host, 1, true); }
+
+int ei_unet_get_optimizer(const ei_unet *n, float *m_host, float *v_host, int *step)
+{
+    if (!n || !m_host || !v_host || !step) return EI_ERR_ARG;
+    ei_unet *u = const_cast<ei_unet *>(n);
+    int r = copy_params(u, m_host, 2, true);
+    if (r == EI_OK) r = copy_params(u, v_host, 3, true);
+    if (r == EI_OK) *step = n->step;
+    return r;
+}
+
+int ei_unet_set_optimizer(ei_unet *n, const float *m_host, const float *v_host, int step)
+{
+    if (!n || !m_host || !v_host || step < 0) return EI_ERR_ARG;
+    int r = copy_params(n, const_cast<float *>(m_host), 2, false);
+    if (r == EI_OK) r = copy_params(n, const_cast<float *>(v_host), 3, false);
+    if (r == EI_OK) n->step = step;
+    return r;
+}
 
 }  // extern "C"

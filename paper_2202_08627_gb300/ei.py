@@ -94,7 +94,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_get_ic_variant", "ei_measure_peaks", "ei_set_linked", "ei_offset_grad",
             "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
             "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout",
-            "ei_solver_state_size", "ei_solver_save", "ei_solver_load"]
+            "ei_solver_state_size", "ei_solver_save", "ei_solver_load",
+            "ei_unet_get_optimizer", "ei_unet_set_optimizer"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 11, 7
@@ -154,6 +155,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_set_offset_unknowns.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ei_get_offsets.restype = c_int
+    lib.ei_unet_get_optimizer.argtypes = [c_void_p, c_void_p, c_void_p, P(c_int)]
+    lib.ei_unet_get_optimizer.restype = c_int
+    lib.ei_unet_set_optimizer.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
+    lib.ei_unet_set_optimizer.restype = c_int
     lib.ei_solver_state_size.argtypes = [c_void_p, c_int, P(ctypes.c_size_t)]
     lib.ei_solver_state_size.restype = c_int
     lib.ei_solver_save.argtypes = [c_void_p, c_void_p, ctypes.c_size_t]
@@ -795,6 +800,23 @@ class UNet:
     def set_tensor_path(self, path: int) -> None:
         """1: tcgen05 convolutions (default), 0: WMMA mma.sync."""
         _check(load_library().ei_unet_set_tensor_path(self.handle, int(path)), "ei_unet_set_tensor_path")
+
+    def get_optimizer(self):
+        """Adam's (m, v, step) for a training checkpoint."""
+        m = np.empty(self.num_params, np.float32)
+        v = np.empty(self.num_params, np.float32)
+        step = c_int(0)
+        _check(load_library().ei_unet_get_optimizer(self.handle, m.ctypes.data, v.ctypes.data,
+                                                    ctypes.byref(step)), "ei_unet_get_optimizer")
+        return m, v, step.value
+
+    def set_optimizer(self, m, v, step: int) -> None:
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if m.size != self.num_params or v.size != self.num_params:
+            raise ValueError("optimizer state must have num_params entries")
+        _check(load_library().ei_unet_set_optimizer(self.handle, m.ctypes.data, v.ctypes.data,
+                                                    int(step)), "ei_unet_set_optimizer")
 
     def get_grads(self) -> np.ndarray:
         out = np.empty(self.num_params, np.float32)

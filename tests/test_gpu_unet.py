@@ -55,6 +55,34 @@ def test_params_round_trip():
     np.testing.assert_array_equal(net.get_params(), a)
 
 
+def test_training_checkpoint_resumes_bit_identically():
+    """Parameters + Adam moments + step restored into a fresh network: the
+    next training steps give bit-identical parameters."""
+    from paper_2202_08627_gb300 import ei
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    xs = [torch.rand(B, H, W, 3, device="cuda", generator=g) for _ in range(5)]
+    ts = [torch.rand(B, H, W, 3, device="cuda", generator=g) for _ in range(5)]
+    a, _ = _net_and_params()
+    for k in range(3):
+        a.train_step(xs[k], ts[k], 1e-3)
+    params = a.get_params()
+    m, v, step = a.get_optimizer()
+    assert step == 3 and np.any(m != 0) and np.any(v != 0)
+    b = ei.UNet(levels=LEVELS, base=BASE, batch=B, height=H, width=W, seed=99)
+    b.set_params(params)
+    b.set_optimizer(m, v, step)
+    for k in range(3, 5):
+        a.train_step(xs[k], ts[k], 1e-3)
+        b.train_step(xs[k], ts[k], 1e-3)
+    np.testing.assert_array_equal(a.get_params(), b.get_params())
+    ma, va, sa = a.get_optimizer()
+    mb, vb, sb = b.get_optimizer()
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(va, vb)
+    assert sa == sb == 5
+
+
 @pytest.mark.parametrize("path", [1, 0])
 def test_forward_matches_oracle(path):
     net, p = _net_and_params(path)
