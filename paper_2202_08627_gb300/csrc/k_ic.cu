@@ -7,7 +7,8 @@
 //   shift = (z/period) D R[delta] + m_o(theta) + m_r(t)      (D: finite difference)
 //   V     = w^2 + kappa R[sigma]
 //   s_m   = A (w / sqrt(V)) exp(-R[mu] - (m - c - shift)^2 / (2 V))   for every m
-//   e_m   = s_m - s_exp_m ;  objective partial sum_m e_m^2 (FP64 per block)
+//   e_m   = s_m - s_exp_m ;  objective partial sum_m e_m^2 (FP32 within a warp,
+//           FP64 across the warps of a row)
 //   G_mu  = -sum 2 e s,  G_sh = sum 2 e s q / V,  G_V = sum 2 e s (q^2 - V) / (2 V^2)
 // and the gradient sinogram row
 //   g = (G_mu, (z/period) D^T G_sh, kappa G_V),
@@ -28,6 +29,26 @@
 #include "ei_internal.h"
 
 namespace ei {
+
+// Row objective: each warp sums its lanes' FP32 partials (a fixed shuffle
+// tree over at most a few hundred squared residuals), and the warp sums are
+// added in FP64 by warp 0.  FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this GPU, so it is kept to one add per warp and level rather
+// than one per lane.
+__device__ __forceinline__ double block_sum_rows(float v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        t = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;   // valid in thread 0
+}
 
 __device__ __forceinline__ double block_sum_double(double v, double *red)
 {
@@ -126,7 +147,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
     for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) s_pd4[gi] = __ldg(Pde + gi);
     __syncthreads();
 
-    double e2 = 0.0;
+    float e2 = 0.f;
     bool out_of_domain = false;
     for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
         const float4 pm4 = __ldg(Pmu + gi), ps4 = __ldg(Psg + gi);
@@ -199,7 +220,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
                 }
             }
         }
-        if (MODE != IC_MODEL) e2 += (double)e2f;
+        if (MODE != IC_MODEL) e2 += e2f;
         if (MODE == IC_OBJECTIVE_GRAD) {
             float gsh[4], gvv[4];
 #pragma unroll
@@ -261,7 +282,7 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
         }
     }
     const int bad = __syncthreads_or(out_of_domain ? 1 : 0);
-    const double tot = block_sum_double(e2, red);
+    const double tot = block_sum_rows(e2, red);
     if (threadIdx.x == 0) part[row] = bad ? __longlong_as_double(0x7ff0000000000000LL) : tot;
 }
 
@@ -437,7 +458,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         const float2 *Ps2 = reinterpret_cast<const float2 *>(stg + 2 * mx);
         const float4 *pix = dg.pix + m.pix_off;
         const float h_in = zp * m.inv_pitch;                 // (z/period) / pitch
-        double e2 = landed ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
+        float e2 = landed ? 0.f : __int_as_float(0x7fc00000);     // NaN if the row never landed
         for (int h = threadIdx.x; h < nh && (int)threadIdx.x < n_cons; h += n_cons) {
             const float2 pm = Pm2[h], ps = Ps2[h];
             const float pmv[2] = {pm.x, pm.y}, psv[2] = {ps.x, ps.y};
@@ -497,7 +518,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                     }
                 }
             }
-            if (MODE != IC_MODEL) e2 += (double)e2f;
+            if (MODE != IC_MODEL) e2 += e2f;
             if (MODE == IC_OBJECTIVE_GRAD) {
                 float gsw[2];
 #pragma unroll
@@ -540,7 +561,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             }
         }
         if (MODE != IC_MODEL) {
-            const double tot = block_sum_double(e2, red[it & 1u]);  // its barrier releases the row
+            const double tot = block_sum_rows(e2, red[it & 1u]);    // its barrier releases the row
             if (threadIdx.x == 0) part[m.row] = tot;
         } else {
             __syncthreads();
