@@ -252,7 +252,7 @@ __device__ __forceinline__ void project_ray(const SliceInfo &si, const AngleInfo
     ray_store<LINKED>(out, plane, acc, an.pch, link);
 }
 
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS = false>
 __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
                                              const float4 *__restrict__ xpA,
                                              const float2 *__restrict__ xpB,
@@ -269,11 +269,22 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
     const int ab = local / nrb, rb = local - ab * nrb;
     static_assert(RAYS % WRAYS == 0 && 32 % WRAYS == 0 && ANGLES % (32 / WRAYS) == 0,
                   "block tile must be a whole number of warp tiles");
+    static_assert(!QUADS || WRAYS == 4, "2 x 4 lane groups need warps of 4 rays x 8 angles");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int WR = RAYS / WRAYS;                   // warps along the rays
     constexpr int WA = 32 / WRAYS;                     // angles per warp
-    const int a = ab * ANGLES + (warp / WR) * WA + (AFAST ? lane % WA : lane / WRAYS);
-    const int j = rb * RAYS + (warp % WR) * WRAYS + (AFAST ? lane / WA : lane % WRAYS);
+    // lane order within the warp's WRAYS x WA tile: rays first, angles first
+    // (AFAST), or (QUADS, for 4 x 8 warps) groups of 8 lanes on 2 rays x 4 angles
+    int la, lr;
+    if (QUADS) {
+        la = (lane & 3) | (((lane >> 3) & 1) << 2);
+        lr = ((lane >> 2) & 1) | (((lane >> 4) & 1) << 1);
+    } else {
+        la = AFAST ? lane % WA : lane / WRAYS;
+        lr = AFAST ? lane / WA : lane % WRAYS;
+    }
+    const int a = ab * ANGLES + (warp / WR) * WA + la;
+    const int j = rb * RAYS + (warp % WR) * WRAYS + lr;
     if (a >= si.n_theta || j >= si.n_dp) return;
     const int64_t plane = (int64_t)si.n_theta * si.n_dp;
     float *out = proj + si.proj_off + (int64_t)a * si.n_dp + j;
@@ -287,21 +298,21 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
 }
 
 // One block per work item.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
           const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
           const float2 *__restrict__ xtB, float *__restrict__ proj, float link,
           const int *__restrict__ active)
 {
-    project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED>(dg, prefix, blockIdx.x, xpA, xpB, xtA,
+    project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED, QUADS>(dg, prefix, blockIdx.x, xpA, xpB, xtA,
                                                              xtB, proj, link, active);
 }
 
 // Persistent: a GPU-sized grid whose blocks take work items from a counter
 // (set to 0 before the launch) until the list is exhausted; no block waits on
 // another.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                      const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
@@ -315,40 +326,40 @@ k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int 
         const int item = s_item;
         __syncthreads();
         if (item >= total) return;
-        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED>(dg, prefix, item, xpA, xpB, xtA, xtB,
+        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED, QUADS>(dg, prefix, item, xpA, xpB, xtA, xtB,
                                                                  proj, link, active);
     }
 }
 
-template <int R, int A, int U, int W, bool F, bool L>
+template <int R, int A, int U, int W, bool F, bool L, bool Q>
 static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float link,
                                        const int *active, cudaStream_t st)
 {
     const FwdVariant &v = g->fwd_variant;
     if (v.total == 0) return cudaSuccess;
     if (!g->persistent) {
-        k_project<R, A, U, W, F, L><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB,
+        k_project<R, A, U, W, F, L, Q><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB,
                                                               g->xtA, g->xtB, proj, link, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
             EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_project_persistent<R, A, U, W, F, L>, R * A, 0));
+                &per_sm, k_project_persistent<R, A, U, W, F, L, Q>, R * A, 0));
         const int grid = std::max(1, std::min(v.total, per_sm * g->num_sms));
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter, 0, sizeof(int), st));
-        k_project_persistent<R, A, U, W, F, L><<<grid, R * A, 0, st>>>(
+        k_project_persistent<R, A, U, W, F, L, Q><<<grid, R * A, 0, st>>>(
             g->dg, v.prefix, v.total, g->work_counter, g->xpA, g->xpB, g->xtA, g->xtB, proj, link,
             active);
     }
     return cudaGetLastError();
 }
 
-template <int R, int A, int U, int W, bool F>
+template <int R, int A, int U, int W, bool F, bool Q = false>
 static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, float link,
                                           const int *active, cudaStream_t st)
 {
-    return link > 0.f ? launch_project_mode<R, A, U, W, F, true>(g, proj, link, active, st)
-                      : launch_project_mode<R, A, U, W, F, false>(g, proj, 0.f, active, st);
+    return link > 0.f ? launch_project_mode<R, A, U, W, F, true, Q>(g, proj, link, active, st)
+                      : launch_project_mode<R, A, U, W, F, false, Q>(g, proj, 0.f, active, st);
 }
 
 cudaError_t launch_prep(const ei_geometry *g, const float4 *vol, float4 mult, bool linked,
@@ -374,15 +385,18 @@ cudaError_t launch_project(const ei_geometry *g, float *proj, float link, const 
     case 7: return launch_project_variant<16, 16, 4, 4, true>(g, proj, link, active, st);
     case 8: return launch_project_variant<8, 32, 4, 4, true>(g, proj, link, active, st);
     case 9: return launch_project_variant<32, 8, 4, 4, true>(g, proj, link, active, st);
-    default: return launch_project_variant<16, 16, 4, 2, true>(g, proj, link, active, st);
+    case 10: return launch_project_variant<16, 16, 4, 2, true>(g, proj, link, active, st);
+    // groups of 8 lanes on 2 rays x 4 angles
+    case 11: return launch_project_variant<8, 32, 4, 4, true, true>(g, proj, link, active, st);
+    default: return launch_project_variant<16, 16, 4, 4, true, true>(g, proj, link, active, st);
     }
 }
 
 // Tile shape (rays, angles) of projector variant `id` (see launch_project).
 void project_variant_shape(int id, int *rays, int *angles)
 {
-    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16},
-                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16};
+    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16, 8, 16},
+                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16, 32, 16};
     *rays = R[id];
     *angles = A[id];
 }
