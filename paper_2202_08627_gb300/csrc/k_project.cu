@@ -252,7 +252,7 @@ __device__ __forceinline__ void project_ray(const SliceInfo &si, const AngleInfo
     ray_store<LINKED>(out, plane, acc, an.pch, link);
 }
 
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS = false>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, int QUADS = 0>
 __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefix, int item,
                                              const float4 *__restrict__ xpA,
                                              const float2 *__restrict__ xpB,
@@ -269,16 +269,21 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
     const int ab = local / nrb, rb = local - ab * nrb;
     static_assert(RAYS % WRAYS == 0 && 32 % WRAYS == 0 && ANGLES % (32 / WRAYS) == 0,
                   "block tile must be a whole number of warp tiles");
-    static_assert(!QUADS || WRAYS == 4, "2 x 4 lane groups need warps of 4 rays x 8 angles");
+    static_assert(QUADS == 0 || WRAYS == 4, "2 x 4 lane groups need warps of 4 rays x 8 angles");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int WR = RAYS / WRAYS;                   // warps along the rays
     constexpr int WA = 32 / WRAYS;                     // angles per warp
     // lane order within the warp's WRAYS x WA tile: rays first, angles first
-    // (AFAST), or (QUADS, for 4 x 8 warps) groups of 8 lanes on 2 rays x 4 angles
+    // (AFAST), or (QUADS, for 4 x 8 warps) groups of 8 lanes on 2 rays x 4
+    // angles, their pairs on 2 rays x 8 angles (QUADS == 1) or 4 rays x 4
+    // angles (QUADS == 2)
     int la, lr;
-    if (QUADS) {
+    if (QUADS == 1) {
         la = (lane & 3) | (((lane >> 3) & 1) << 2);
         lr = ((lane >> 2) & 1) | (((lane >> 4) & 1) << 1);
+    } else if (QUADS == 2) {
+        la = (lane & 3) | (((lane >> 4) & 1) << 2);
+        lr = (lane >> 2) & 3;
     } else {
         la = AFAST ? lane % WA : lane / WRAYS;
         lr = AFAST ? lane / WA : lane % WRAYS;
@@ -298,7 +303,7 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
 }
 
 // One block per work item.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, int QUADS>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
           const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
@@ -312,7 +317,7 @@ k_project(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__
 // Persistent: a GPU-sized grid whose blocks take work items from a counter
 // (set to 0 before the launch) until the list is exhausted; no block waits on
 // another.
-template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, bool QUADS>
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, int QUADS>
 __global__ void __launch_bounds__(RAYS * ANGLES)
 k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                      const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
@@ -331,7 +336,7 @@ k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int 
     }
 }
 
-template <int R, int A, int U, int W, bool F, bool L, bool Q>
+template <int R, int A, int U, int W, bool F, bool L, int Q>
 static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float link,
                                        const int *active, cudaStream_t st)
 {
@@ -354,7 +359,7 @@ static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float 
     return cudaGetLastError();
 }
 
-template <int R, int A, int U, int W, bool F, bool Q = false>
+template <int R, int A, int U, int W, bool F, int Q = 0>
 static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, float link,
                                           const int *active, cudaStream_t st)
 {
@@ -386,17 +391,17 @@ cudaError_t launch_project(const ei_geometry *g, float *proj, float link, const 
     case 8: return launch_project_variant<8, 32, 4, 4, true>(g, proj, link, active, st);
     case 9: return launch_project_variant<32, 8, 4, 4, true>(g, proj, link, active, st);
     case 10: return launch_project_variant<16, 16, 4, 2, true>(g, proj, link, active, st);
-    // groups of 8 lanes on 2 rays x 4 angles
-    case 11: return launch_project_variant<8, 32, 4, 4, true, true>(g, proj, link, active, st);
-    default: return launch_project_variant<16, 16, 4, 4, true, true>(g, proj, link, active, st);
+    // groups of 8 lanes on 2 rays x 4 angles (pairs of groups on 2 x 8 or 4 x 4)
+    case 11: return launch_project_variant<8, 32, 4, 4, true, 1>(g, proj, link, active, st);
+    default: return launch_project_variant<8, 32, 4, 4, true, 2>(g, proj, link, active, st);
     }
 }
 
 // Tile shape (rays, angles) of projector variant `id` (see launch_project).
 void project_variant_shape(int id, int *rays, int *angles)
 {
-    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16, 8, 16},
-                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16, 32, 16};
+    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16, 8, 8},
+                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16, 32, 32};
     *rays = R[id];
     *angles = A[id];
 }
