@@ -135,6 +135,7 @@ def build_problem(wl, rank: int, device):
 # carries over to other batches of such slices).  Kernel changes void them.
 PROFILED_TRAFFIC = {("project", 8): 684.0e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("project", 11): 684.5e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
+                    ("project", 12): 684.7e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("backproject", 0): 879.9e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
                     ("backproject", 6): 871.7e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
 
