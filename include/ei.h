@@ -315,7 +315,7 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * keyed by the GPU name, the slice sizes and whether the geometry is linked
  * (ei_set_linked: the single-channel kernels are timed), and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..12, adjoint 0..6).
+ * report a variant explicitly (ids: projector 0..12, adjoint 0..7).
  */
 #define EI_TUNE_FORCE 1
 #define EI_TUNE_NO_CACHE_WRITE 2

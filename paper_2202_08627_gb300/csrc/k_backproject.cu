@@ -220,7 +220,7 @@ __device__ __forceinline__ void pair_angle(float (&acc)[PASSES][2][3], const flo
     }
 }
 
-template <int PASSES, bool LINKED, bool COMPACT>
+template <int PASSES, bool LINKED, int COMPACT>
 __device__ __forceinline__ void backproject_pair_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
@@ -237,9 +237,16 @@ __device__ __forceinline__ void backproject_pair_item(
     const int r_t = (local / ntc) * TR, c_t = (local % ntc) * ADJ_TC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // left voxel of the pair and its row at pass 0 (passes add 16): 8 lanes cover
-    // 8 pairs of one row, or (COMPACT) 2 pairs x 4 rows
-    const int dc = (warp & 1) * 16 + (COMPACT ? 4 * (lane >> 3) + 2 * (lane & 1) : 2 * (lane & 7));
-    const int dr0 = (warp >> 1) * 4 + (COMPACT ? (lane >> 1) & 3 : lane >> 3);
+    // 8 pairs of one row (COMPACT 0) or 2 pairs x 4 rows; a warp covers 16
+    // columns x 4 rows (COMPACT 0, 1) or 8 columns x 8 rows (COMPACT 2)
+    int dc, dr0;
+    if (COMPACT == 2) {
+        dc = (warp & 3) * 8 + 2 * (lane & 1) + 4 * ((lane >> 3) & 1);
+        dr0 = (warp >> 2) * 8 + ((lane >> 1) & 3) + 4 * (lane >> 4);
+    } else {
+        dc = (warp & 1) * 16 + (COMPACT ? 4 * (lane >> 3) + 2 * (lane & 1) : 2 * (lane & 7));
+        dr0 = (warp >> 1) * 4 + (COMPACT ? (lane >> 1) & 3 : lane >> 3);
+    }
 
     float acc[PASSES][2][3];
 #pragma unroll
@@ -316,7 +323,8 @@ __device__ __forceinline__ void backproject_pair_item(
 }
 
 // LAY: 0 lanes along rows of 8 voxels, 1 lanes on 2 x 4 sub-patches, 2 voxel
-// pairs along rows, 3 voxel pairs on 4 x 4 sub-patches.
+// pairs along rows, 3 voxel pairs on 4 x 4 sub-patches (warps of 16 x 4), 4 the
+// same sub-patches in warps of 8 x 8.
 template <int PASSES, int LAY, bool LINKED>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
@@ -325,8 +333,8 @@ __device__ __forceinline__ void backproject_item(
     double *__restrict__ part, const int *__restrict__ active)
 {
     if constexpr (LAY >= 2)
-        backproject_pair_item<PASSES, LINKED, LAY == 3>(dg, prefix, item, sh, gA, gB, with_sino, v,
-                                                        out, out_mult, reg2, reg1, part, active);
+        backproject_pair_item<PASSES, LINKED, LAY - 2>(dg, prefix, item, sh, gA, gB, with_sino, v,
+                                                       out, out_mult, reg2, reg1, part, active);
     else
         backproject_single_item<PASSES, LAY == 1, LINKED>(dg, prefix, item, sh, gA, gB, with_sino,
                                                           v, out, out_mult, reg2, reg1, part,
@@ -417,14 +425,15 @@ cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float
     case 4: return launch_bp_variant<16, 2, 1>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
     // voxel pairs, 4 passes of 16 rows
     case 5: return launch_bp_variant<4, 4, 2>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    default: return launch_bp_variant<4, 4, 3>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 6: return launch_bp_variant<4, 4, 3>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    default: return launch_bp_variant<4, 4, 4>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
     }
 }
 
 // Voxel rows per tile of adjoint variant `id` (see launch_backproject).
 int backproject_variant_rows(int id)
 {
-    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64};
+    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64, 64};
     return R[id];
 }
 

@@ -98,7 +98,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_get_optimizer", "ei_unet_set_optimizer"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 7
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 8
 
 _lib = None
 
