@@ -122,7 +122,7 @@ def test_linked_objective_gradient_and_forward_match_oracle():
     assert not np.any(gv[:, 3])
 
 
-@pytest.mark.parametrize("adj_variant", [0, 3, 5, 6])
+@pytest.mark.parametrize("adj_variant", [0, 3, 5, 6, 7])
 def test_linked_kernels_agree_with_the_three_channel_path(adj_variant):
     """The single-channel linked kernels against the three-channel ones on the
     same model (lambda = 0, so only the data term): S(h) = S(h, gamma h, 0),
