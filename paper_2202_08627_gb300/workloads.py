@@ -43,7 +43,8 @@ class Workload:
     def per_slice(self):
         return [(n, nth, nd, inputs.pitch_for(n)) for (n, nth, nd) in self.slices]
 
-    # algorithmic bytes of one objective+gradient evaluation:
+    # algorithmic bytes of one objective+gradient evaluation: what each kernel
+    # must read and write once, whatever its traffic through the caches:
     #   projector 16 n^2 + 12 n_theta n_det, adjoint 32 n^2 + 16 n_theta n_det,
     #   IC kernel (12 + 4 M + 16) n_theta n_det
     def fwd_bytes(self) -> int:
