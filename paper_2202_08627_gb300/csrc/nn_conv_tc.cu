@@ -25,6 +25,9 @@
 // dgrad (a forward convolution of dY with the flipped, transposed weights) it
 // is the forward copy itself, so no extra weight layout exists.
 //
+// The weight gradients (k_conv_wgrad_tc, below) run on the same pipeline with
+// the pixels as the reduction dimension and MN-major operand tiles.
+//
 // Every wait on an mbarrier is bounded (1 s); a wait that runs out sets
 // *status, skips the rest of the tile, waits (bounded) for the MMAs already
 // issued, frees the tensor memory and returns.
