@@ -410,10 +410,11 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
     const int n_m = NM > 0 ? NM : dg.mc.n_m;     // NM > 0: M known at compile time
     const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
     float *const bufs = reinterpret_cast<float *>(sm4);           // nst buffers of n_in * mx
-    // G_shift weighted by its row of D (one zero entry in front), G_mu, G_V
-    float *const g_sw = bufs + nst * n_in * mx + 4;
-    float *const g_mu = g_sw + mx + 4;
-    float *const g_v = g_mu + mx;
+    // per row parity b: G_shift weighted by its row of D (one zero entry in
+    // front, two behind), G_mu, G_V; two sets, so that a row's packing loop and
+    // the next row's computation do not share them
+    float *const gbase = bufs + nst * n_in * mx;
+    const int gspan = 3 * mx + 8;
     const int step = gridDim.x;
     const float zp = dg.mc.z_over_p, kappa = dg.mc.kappa;
     // the last warp produces (its lane 0 issues the copies and runs ahead over
@@ -426,7 +427,8 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         for (int i = 0; i < nst; ++i) mbar_init(smem_addr(&bars[i]), 1);
         mbar_init_fence();
         s_abort = 0;
-        g_sw[-1] = 0.f;
+        gbase[3] = 0.f;                            // g_sw[-1] of both sets
+        gbase[gspan + 3] = 0.f;
         walk.start(dg, active, blockIdx.x, step);
         while (issued < (unsigned)nst - 1) {
             ic_issue_row(dg, walk, proj, meas, bufs + issued * n_in * mx, mx, n_in,
@@ -436,11 +438,16 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         }
     }
     __syncthreads();
+    int prev_row = -1;                   // gradient mode: the row whose objective is pending
+    unsigned prev_it = 0;                // and its iteration (the parity of its warp sums)
     for (unsigned it = 0;; ++it) {
         const unsigned slot = it % nst;
         const IcRow m = metas[slot];
         if (m.row < 0) break;
         float *const stg = bufs + slot * n_in * mx;
+        float *const g_sw = gbase + (it & 1u) * gspan + 4;
+        float *const g_mu = g_sw + mx + 4;
+        float *const g_v = g_mu + mx;
         // the buffer of iteration it - 1 was released by that row's last barrier
         if (producer) {
             const unsigned sl = issued % nst;
@@ -537,7 +544,29 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         }
         if (MODE == IC_OBJECTIVE_GRAD) {
             if (threadIdx.x == 0) g_sw[ndp] = g_sw[ndp + 1] = 0.f;   // D^T reads past the row
-            __syncthreads();                       // every G_shift of the row is in place
+            // every G_shift of the row is in place; every read of the row's staged
+            // inputs is done (its buffer may be refilled); the previous row's warp
+            // sums are written
+            __syncthreads();
+            if (prev_row >= 0 && threadIdx.x < 32) {
+                double t = (int)threadIdx.x < ((int)blockDim.x >> 5) ? red[prev_it & 1u][threadIdx.x] : 0.0;
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+                if (threadIdx.x == 0) part[prev_row] = t;
+            }
+            if (s_abort) {
+                // the row never arrived: report it, poison this block's remaining
+                // rows, and give the copies still in flight a bounded chance to land
+                // before the block's shared memory is released
+                if (producer) {
+                    atomicExch(status, (int)EI_ERR_TIMEOUT);
+                    for (int q = m.row; q < dg.total_ic; q = ic_next_row(dg, active, q + step, step))
+                        part[q] = __longlong_as_double(0x7ff8000000000000LL);
+                    for (unsigned i = it; i < issued; ++i)
+                        if (metas[i % nst].row >= 0)
+                            mbar_wait_bounded(smem_addr(&bars[i % nst]), (i / nst) & 1u, kIcWaitNs);
+                }
+                return;
+            }
             // packed row: the entry of pixel j holds g(j) and g(j + 1), with
             // g_delta(j) = (z/period) (D^T G_shift)(j)
             //            = (z/period)/(2 pitch) (gsw(j-1) - gsw(j+1) + e(j) gsw(j)),
@@ -559,6 +588,15 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                     gB[m.gp_off + j] = make_float2(d1, nx ? g_v[j + 1] : 0.f);
                 }
             }
+        }
+        if (MODE == IC_OBJECTIVE_GRAD) {
+            // this row's warp sums; warp 0 adds them after the next row's barrier
+            float v = e2;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[it & 1u][threadIdx.x >> 5] = (double)v;
+            prev_row = m.row;
+            prev_it = it;
+            continue;
         }
         if (MODE != IC_MODEL) {
             const double tot = block_sum_rows(e2, red[it & 1u]);    // its barrier releases the row
@@ -582,6 +620,14 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             return;
         }
     }
+    if (MODE == IC_OBJECTIVE_GRAD) {
+        __syncthreads();                           // the last row's warp sums are written
+        if (prev_row >= 0 && threadIdx.x < 32) {
+            double t = (int)threadIdx.x < ((int)blockDim.x >> 5) ? red[prev_it & 1u][threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (threadIdx.x == 0) part[prev_row] = t;
+        }
+    }
 }
 
 static const int kIcPipeSmemLimit = 220 * 1024;
@@ -597,7 +643,7 @@ static int ic_threads(const ei_geometry *g, int px, int cap)
 static size_t ic_pipe_smem_stages(int max_ndp, int n_m, IcMode mode, int nst)
 {
     const int n_in = mode == IC_MODEL ? 3 : 3 + n_m;
-    return ((size_t)(nst * n_in + 3) * max_ndp + 16) * sizeof(float);
+    return ((size_t)(nst * n_in + 6) * max_ndp + 16) * sizeof(float);   // + two gradient sets
 }
 
 // Row buffers of the bulk-copy variant: 3 when they fit, else 2, else 0.
