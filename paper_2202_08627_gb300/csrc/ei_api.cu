@@ -366,7 +366,6 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     };
     int64_t vol_off = 0, pp_off = 0, gp_off = 0, sino_off = 0, proj_off = 0, meas_off = 0;
     int ang_off = 0, pix_off = 0, pix_in_off = 0, max_ndp = 4, max_nth = 1;
-    const double TWO32 = 4294967296.0;
     for (int s = 0; s < n_slices; ++s) {
         const ei_slice_dims &q = dims[s];
         SliceInfo si{};
@@ -397,31 +396,9 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         si.proj_off = proj_off;
         si.meas_off = meas_off;
         g->h_slices.push_back(si);
-        const double hn = 0.5 * (q.n - 1);
         for (int a = 0; a < q.n_theta; ++a) {
             double th = d->theta ? d->theta[(uniform ? 0 : ang_off) + a] : a * M_PI / q.n_theta;
-            double ct = cos(th), st = sin(th);
-            AngleInfo an{};
-            const double ch = std::max(fabs(ct), fabs(st));
-            an.col_dom = fabs(st) > fabs(ct) ? 1 : 0;
-            if (!an.col_dom) {
-                an.inv_dom = 1.0 / ct;
-                an.p1 = st / ct;
-            } else {
-                an.inv_dom = -1.0 / st;
-                an.p1 = ct / st;
-            }
-            an.k0 = hn - hn * an.p1;
-            an.inv_p1 = an.p1 != 0.0 ? 1.0 / an.p1 : 0.0;
-            an.p1_fx = llrint(an.p1 * TWO32);
-            if (an.p1_fx == 0) an.p1 = 0.0, an.inv_p1 = 0.0;
-            an.cos_fx = llrint(ct * TWO32);
-            an.sin_fx = llrint(st * TWO32);
-            an.cosf = (float)ct;
-            an.sinf = (float)st;
-            an.inv_ch = (float)(1.0 / ch);
-            an.pch = (float)(q.pitch_cm / ch);
-            ang.push_back(an);
+            ang.push_back(make_angle_info(th, q.n, q.pitch_cm));
             m_o.push_back(d->m_o ? fmo[(uniform ? 0 : ang_off) + a] : 0.f);
         }
         const int src_off = uniform ? 0 : pix_in_off;

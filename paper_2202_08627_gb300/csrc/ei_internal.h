@@ -59,6 +59,36 @@ struct AngleInfo {
     int pad_;
 };
 
+// The constants of angle th for a slice of n x n voxels of the given pitch
+// (the setup on the host and the allocation-free path's table kernel share it).
+__host__ __device__ inline AngleInfo make_angle_info(double th, int n, double pitch)
+{
+    const double TWO32 = 4294967296.0;
+    const double hn = 0.5 * (n - 1);
+    const double ct = cos(th), st = sin(th);
+    const double ch = fmax(fabs(ct), fabs(st));
+    AngleInfo an{};
+    an.col_dom = fabs(st) > fabs(ct) ? 1 : 0;
+    if (!an.col_dom) {
+        an.inv_dom = 1.0 / ct;
+        an.p1 = st / ct;
+    } else {
+        an.inv_dom = -1.0 / st;
+        an.p1 = ct / st;
+    }
+    an.k0 = hn - hn * an.p1;
+    an.inv_p1 = an.p1 != 0.0 ? 1.0 / an.p1 : 0.0;
+    an.p1_fx = llrint(an.p1 * TWO32);
+    if (an.p1_fx == 0) an.p1 = 0.0, an.inv_p1 = 0.0;
+    an.cos_fx = llrint(ct * TWO32);
+    an.sin_fx = llrint(st * TWO32);
+    an.cosf = (float)ct;
+    an.sinf = (float)st;
+    an.inv_ch = (float)(1.0 / ch);
+    an.pch = (float)(pitch / ch);
+    return an;
+}
+
 struct ModelConsts {
     float z_over_p;       // shift in periods per unit dR[delta]/dt
     float kappa;          // IC variance per unit R[sigma]

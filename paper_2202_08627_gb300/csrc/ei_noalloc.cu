@@ -74,32 +74,9 @@ __global__ void k_noalloc_tables(SliceInfo si, double pitch, const double *theta
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    const double hn = 0.5 * (si.n - 1);
-    const double TWO32 = 4294967296.0;
     for (int a = tid; a < si.n_theta; a += stride) {
         const double th = uniform_theta ? a * 3.141592653589793 / si.n_theta : theta[a];
-        const double ct = cos(th), st = sin(th);
-        AngleInfo an{};
-        const double ch = fmax(fabs(ct), fabs(st));
-        an.col_dom = fabs(st) > fabs(ct) ? 1 : 0;
-        if (!an.col_dom) {
-            an.inv_dom = 1.0 / ct;
-            an.p1 = st / ct;
-        } else {
-            an.inv_dom = -1.0 / st;
-            an.p1 = ct / st;
-        }
-        an.k0 = hn - hn * an.p1;
-        an.inv_p1 = an.p1 != 0.0 ? 1.0 / an.p1 : 0.0;
-        an.p1_fx = llrint(an.p1 * TWO32);
-        if (an.p1_fx == 0) an.p1 = 0.0, an.inv_p1 = 0.0;
-        an.cos_fx = llrint(ct * TWO32);
-        an.sin_fx = llrint(st * TWO32);
-        an.cosf = (float)ct;
-        an.sinf = (float)st;
-        an.inv_ch = (float)(1.0 / ch);
-        an.pch = (float)(pitch / ch);
-        ang[a] = an;
+        ang[a] = make_angle_info(th, si.n, pitch);
         m_o[a] = mo ? mo[a] : 0.f;
     }
     for (int j = tid; j < si.n_dp; j += stride)
