@@ -215,6 +215,12 @@ typedef struct {
     int use_graph;     /* 1: capture one solver round into a CUDA graph and replay it (1) */
     int resume;        /* 1: continue from the solver state instead of starting at vol_inout (0);
                           see ei_solver_save / ei_solver_load */
+    double max_seconds; /* wall-clock budget of the call, 0 = none (0).  Checked on the host
+                          before each solver round, when no work of the call is in flight:
+                          once it has run out the call stops, the slices still iterating
+                          report EI_ERR_TIMEOUT and return their last accepted iterate, and
+                          the kept solver state is left as it was, so a call with resume = 1
+                          continues them exactly where they stopped */
 } ei_solve_opts;
 
 /* Per-slice results; every pointer is a caller-owned HOST array of n_slices
@@ -222,7 +228,8 @@ typedef struct {
 typedef struct {
     int *iterations;   /* accepted steps */
     int *status;       /* ei_status per slice: EI_OK (converged or max_iter reached),
-                          EI_ERR_LINESEARCH, EI_ERR_NONFINITE */
+                          EI_ERR_LINESEARCH, EI_ERR_NONFINITE, EI_ERR_TIMEOUT (still
+                          iterating when max_seconds ran out) */
     int *converged;    /* 1 if the tol test stopped the slice, 0 if max_iter or an error did */
     double *f_final;   /* final S */
     double *f_initial; /* S at x0 */
@@ -242,14 +249,15 @@ typedef struct {
  * memory inside the call).  report may be NULL.  Synchronous: `stream` is
  * synchronised first, the iterations run on a stream the solver owns (one
  * solver round is captured into a CUDA graph and replayed), and the call
- * returns when every slice has stopped.  Returns EI_OK when every slice converged or
- * reached max_iter, else the first per-slice error.
+ * returns when every slice has stopped or max_seconds has run out.  Returns EI_OK
+ * when every slice converged or reached max_iter, else the first per-slice error;
+ * EI_ERR_ARG for invalid options (max_seconds negative or NaN among them).
  */
 int ei_reconstruct(const ei_geometry *g, const float *s_exp, float *vol_inout,
                    const ei_solve_opts *opts, ei_solve_report *report, void *stream);
 
 /* Default options: tol 1e-6, max_iter 100, m 10, c1 1e-4, 20 trials, 1e-10, graphs on,
- * no resume. */
+ * no resume, no time budget. */
 void ei_default_solve_opts(ei_solve_opts *opts);
 
 /*
@@ -300,8 +308,13 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * iteration, lanes ray-major: 0 16x16/8x4/4, 1 32x8/8x4/4, 2 32x16/8x4/4,
  * 3 16x16/8x4/2, 4 32x8/32x1/4, 5 16x16/16x2/4, 6 32x16/32x1/4; lanes
  * angle-major: 7 16x16/4x8/4, 8 8x32/4x8/4, 9 32x8/4x8/4, 10 16x16/2x16/4;
- * adjoint: 0 8, 1 4, 2 16 voxels per thread with lanes along rows of 8 voxels,
- * 3 8 and 4 16 voxels per thread with 8-lane groups on 2 x 4 sub-patches), and
+ * lanes in groups of 8 on 2 rays x 4 angles: 11 8x32/4x8/4, and 12 the same
+ * with groups of 16 on 4 rays x 4 angles; adjoint: 0 8, 1 4, 2 16 voxels per
+ * thread with lanes along rows of 8 voxels, 3 8 and 4 16 voxels per thread
+ * with 8-lane groups on 2 x 4 sub-patches, 5-7 four pairs of horizontally
+ * adjacent voxels per thread (the pair shares its three detector pixels per
+ * angle) with lanes along rows of 16 voxels, on 4 x 4 sub-patches in warps of
+ * 16 x 4, or in warps of 8 x 8), and
  * either as one block per work item or as a persistent GPU-sized grid whose
  * blocks take work items from a counter.  Projector variants compute every
  * ray identically (bit-identical projections); adjoint variants sum every
@@ -444,6 +457,25 @@ int ei_measure_peaks(ei_peaks *out, void *stream);
  * copy failed; the CUDA context stays usable.
  */
 int ei_selftest_wait_timeout(unsigned limit_us, int *status_out);
+
+/*
+ * Failure injection on the host, for testing the clean-up paths.  Every
+ * device allocation the library makes for a geometry, its solver and a U-Net
+ * goes through one allocator that counts the live allocations.
+ *   ei_fail_alloc_after(n), n >= 0: the next n allocations succeed and the
+ *     one after them fails as if the device were out of memory (the call that
+ *     made it then returns EI_ERR_ALLOC after freeing what it had allocated);
+ *     the trigger is then disarmed.  n = -1 disarms it.  Process-wide.
+ *     EI_ERR_ARG for n < -1.
+ *   ei_fail_alloc_pending(*n): the allocations still to pass before the
+ *     armed failure, or -1 when none is armed (it fired or was disarmed).
+ *   ei_live_allocations(*n): device allocations currently held by the
+ *     library (all geometries and networks).  EI_ERR_ARG for NULL.
+ * No kernel, device fault or GPU state is involved.
+ */
+int ei_fail_alloc_after(int n);
+int ei_fail_alloc_pending(int *n);
+int ei_live_allocations(int64_t *n);
 
 /*
  * IC kernel variant (the fused Eq. 2 model, Eq. 5 residual and gradient).

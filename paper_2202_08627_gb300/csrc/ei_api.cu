@@ -14,8 +14,33 @@
 #include <vector>
 
 #include "ei_internal.h"
+#include "lib_alloc.h"
+
+#include <atomic>
 
 namespace ei {
+
+static std::atomic<int> g_fail_alloc{-1};      // allocations to pass before one fails
+static std::atomic<int64_t> g_live_allocs{0};
+
+cudaError_t lib_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    int n = g_fail_alloc.load();
+    while (n >= 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) return cudaErrorMemoryAllocation;      // the armed failure (now disarmed)
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ++g_live_allocs;
+    return e;
+}
+
+void lib_free(void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    --g_live_allocs;
+}
 
 cudaError_t ic_set_smem_limit();
 
@@ -26,7 +51,7 @@ static cudaError_t dev_alloc(ei_geometry *g, T **p, size_t count)
 {
     void *ptr = nullptr;
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&ptr, bytes);
+    cudaError_t e = lib_malloc(&ptr, bytes);
     if (e != cudaSuccess) return e;
     g->allocs.push_back(ptr);
     g->workspace_bytes += (int64_t)bytes;
@@ -237,6 +262,28 @@ void ei_default_solve_opts(ei_solve_opts *o)
     o->curv_eps = 1e-10;
     o->use_graph = 1;
     o->resume = 0;
+    o->max_seconds = 0.0;
+}
+
+int ei_fail_alloc_after(int n)
+{
+    if (n < -1) return EI_ERR_ARG;
+    ei::g_fail_alloc.store(n);
+    return EI_OK;
+}
+
+int ei_fail_alloc_pending(int *n)
+{
+    if (!n) return EI_ERR_ARG;
+    *n = std::max(-1, ei::g_fail_alloc.load());
+    return EI_OK;
+}
+
+int ei_live_allocations(int64_t *n)
+{
+    if (!n) return EI_ERR_ARG;
+    *n = ei::g_live_allocs.load();
+    return EI_OK;
 }
 
 static void release_events(ei_geometry *g)
@@ -291,7 +338,7 @@ void ei_destroy_geometry(ei_geometry *g)
     release_events(g);
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     ei::destroy_solver(g);
-    for (void *p : g->allocs) cudaFree(p);
+    for (void *p : g->allocs) ei::lib_free(p);
     cudaSetDevice(prev);
     delete g;
 }
@@ -977,7 +1024,8 @@ int ei_reconstruct(const ei_geometry *gc, const float *s_exp, float *vol_inout,
     ei_default_solve_opts(&o);
     if (opts) o = *opts;
     if (!(o.tol >= 0) || o.max_iter < 0 || o.lbfgs_m < 1 || o.lbfgs_m > 32 || !(o.c1 > 0) ||
-        o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0) || (o.resume != 0 && o.resume != 1))
+        o.c1 >= 1 || o.max_trials < 1 || !(o.curv_eps >= 0) || (o.resume != 0 && o.resume != 1) ||
+        !(o.max_seconds >= 0))
         return EI_ERR_ARG;
     ei_geometry *g = const_cast<ei_geometry *>(gc);
     const int r = ei::reconstruct(g, s_exp, vol_inout, &o, report, (cudaStream_t)stream);

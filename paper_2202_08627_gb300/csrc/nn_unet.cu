@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ei.h"
+#include "lib_alloc.h"
 #include "nn_internal.h"
 
 using namespace ei::nn;
@@ -61,7 +62,7 @@ template <class T>
 cudaError_t dalloc(ei_unet *n, T **p, int64_t count)
 {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<int64_t>(count, 1) * sizeof(T));
+    cudaError_t e = ei::lib_malloc(&q, std::max<int64_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return e;
     n->allocs.push_back(q);
     *p = static_cast<T *>(q);
@@ -333,7 +334,7 @@ void ei_unet_destroy(ei_unet *n)
 {
     if (!n) return;
     cudaDeviceSynchronize();
-    for (void *p : n->allocs) cudaFree(p);
+    for (void *p : n->allocs) ei::lib_free(p);
     if (n->mse_host) cudaFreeHost(n->mse_host);
     delete n;
 }

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "ei_internal.h"
+#include "lib_alloc.h"
 
 namespace ei {
 
@@ -599,7 +600,7 @@ template <class T>
 static cudaError_t salloc(Solver *s, T **p, size_t count)
 {
     void *ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
+    cudaError_t e = lib_malloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
     if (e != cudaSuccess) return e;
     s->allocs.push_back(ptr);
     *p = static_cast<T *>(ptr);
@@ -609,7 +610,7 @@ static cudaError_t salloc(Solver *s, T **p, size_t count)
 void destroy_solver(ei_geometry *g)
 {
     if (!g->solver) return;
-    for (void *p : g->solver->allocs) cudaFree(p);
+    for (void *p : g->solver->allocs) lib_free(p);
     if (g->solver->summary_h) cudaFreeHost(g->solver->summary_h);
     if (g->solver->stream) cudaStreamDestroy(g->solver->stream);
     delete g->solver;
@@ -702,8 +703,11 @@ static bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// deadline: the time budget's end (opts->max_seconds > 0), checked before each
+// round; *timed_out tells whether it stopped the rounds
 static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
-                              const ei_solve_opts *opts, int *evals, cudaStream_t st)
+                              const ei_solve_opts *opts, int *evals, cudaStream_t st,
+                              std::chrono::steady_clock::time_point deadline, bool *timed_out)
 {
     Solver *sv = g->solver;
     const SolverDev dv = dev_view(sv);
@@ -814,7 +818,12 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     }
     cudaError_t err = cudaSuccess;
     const long long max_rounds = (long long)opts->max_iter * (opts->max_trials + 1) + 2;
+    *timed_out = false;
     for (long long r = 0; sv->summary_h[0] > 0 && r < max_rounds; ++r) {
+        if (opts->max_seconds > 0 && std::chrono::steady_clock::now() >= deadline) {
+            *timed_out = true;                // between rounds: nothing in flight
+            break;
+        }
         if (exec) {
             err = cudaGraphLaunch(exec, st);
             g->launches += launches_per_round;
@@ -882,13 +891,23 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
         x = sv->vol_stage;
     }
     int evals = 0;
-    if (e == cudaSuccess) e = run_solver(g, meas, x, opts, &evals, st);
+    bool timed_out = false;
+    const auto deadline = t0 + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                   std::chrono::duration<double>(std::min(opts->max_seconds, 1e9)));
+    if (e == cudaSuccess) e = run_solver(g, meas, x, opts, &evals, st, deadline, &timed_out);
     if (e == cudaSuccess && !vol_dev)
         e = cudaMemcpyAsync(vol_inout, sv->vol_stage, (size_t)g->vol_count * sizeof(float4),
                             cudaMemcpyDeviceToHost, st);
     std::vector<SliceState> hs(g->n_slices);
+    std::vector<int> still_dir(timed_out ? g->n_slices : 0), still_ls(still_dir.size());
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hs.data(), sv->st, sizeof(SliceState) * g->n_slices,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && timed_out)        // which slices the budget stopped
+        e = cudaMemcpyAsync(still_dir.data(), sv->mask_dir, sizeof(int) * g->n_slices,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && timed_out)
+        e = cudaMemcpyAsync(still_ls.data(), sv->mask_ls, sizeof(int) * g->n_slices,
                             cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -899,6 +918,7 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
     for (int s = 0; s < g->n_slices; ++s) {
         int status = hs[s].status;
         if (status == EI_OK && isnan(hs[s].f)) status = EI_ERR_NONFINITE;
+        if (status == EI_OK && timed_out && (still_dir[s] | still_ls[s])) status = EI_ERR_TIMEOUT;
         if (status != EI_OK && first_err == EI_OK) first_err = status;
         if (report) {
             if (report->iterations) report->iterations[s] = hs[s].k;

@@ -62,7 +62,7 @@ class ei_layout(ctypes.Structure):
 class ei_solve_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("lbfgs_m", c_int), ("c1", c_double),
                 ("max_trials", c_int), ("curv_eps", c_double), ("use_graph", c_int),
-                ("resume", c_int)]
+                ("resume", c_int), ("max_seconds", c_double)]
 
 
 class ei_solve_report(ctypes.Structure):
@@ -95,7 +95,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_set_offset_unknowns", "ei_get_offsets", "ei_single_shot_eq3",
             "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout",
             "ei_solver_state_size", "ei_solver_save", "ei_solver_load",
-            "ei_unet_get_optimizer", "ei_unet_set_optimizer"]
+            "ei_unet_get_optimizer", "ei_unet_set_optimizer", "ei_fail_alloc_after",
+            "ei_fail_alloc_pending", "ei_live_allocations"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 8
@@ -167,6 +168,12 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_solver_load.restype = c_int
     lib.ei_selftest_wait_timeout.argtypes = [ctypes.c_uint, P(c_int)]
     lib.ei_selftest_wait_timeout.restype = c_int
+    lib.ei_fail_alloc_after.argtypes = [c_int]
+    lib.ei_fail_alloc_after.restype = c_int
+    lib.ei_fail_alloc_pending.argtypes = [P(c_int)]
+    lib.ei_fail_alloc_pending.restype = c_int
+    lib.ei_live_allocations.argtypes = [P(c_int64)]
+    lib.ei_live_allocations.restype = c_int
     lib.ei_set_flat_table.argtypes = [c_void_p, c_void_p, c_int]
     lib.ei_set_flat_table.restype = c_int
     lib.ei_set_linked.argtypes = [c_void_p, c_double]
@@ -504,16 +511,20 @@ class SolveReport:
 
 def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbfgs_m=10,
                    c1=1e-4, max_trials=20, curv_eps=1e-10, use_graph=True, stream=None,
-                   raise_on_error: bool = True, resume: bool = False) -> SolveReport:
+                   raise_on_error: bool = True, resume: bool = False,
+                   max_seconds: float = 0.0) -> SolveReport:
     """Batched L-BFGS minimisation of S.  s_exp / vol_inout: CUDA tensors, or
     pinned/pageable CPU tensors (the library stages host arrays).  resume:
     continue from the geometry's solver state (the last solve or
-    ei_solver_load) instead of starting at vol_inout."""
+    ei_solver_load) instead of starting at vol_inout.  max_seconds > 0: time
+    budget of the call; slices it stops report EI_ERR_TIMEOUT (not raised) and
+    continue exactly under resume=True."""
     import torch
     if s_exp.numel() < geom.meas_count or vol_inout.numel() < 4 * geom.vol_count:
         raise ValueError("s_exp / vol_inout smaller than the layout")
     o = ei_solve_opts(float(tol), int(max_iter), int(lbfgs_m), float(c1), int(max_trials),
-                      float(curv_eps), int(bool(use_graph)), int(bool(resume)))
+                      float(curv_eps), int(bool(use_graph)), int(bool(resume)),
+                      float(max_seconds))
     S = geom.n_slices
     it = np.zeros(S, np.int32)
     st = np.zeros(S, np.int32)
@@ -530,7 +541,8 @@ def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbf
                                        _dptr(vol_inout, "vol_inout", torch.float32),
                                        ctypes.byref(o), ctypes.byref(rep), _stream_ptr(stream))
     out = SolveReport(it, st, cv, ff, f0, ev, rep.evaluations, rep.seconds, rc)
-    if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE):
+    budget_stop = rc == EI_ERR_TIMEOUT and max_seconds > 0 and bool((st == EI_ERR_TIMEOUT).any())
+    if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE) and not budget_stop:
         raise EIError(rc, "ei_reconstruct")
     return out
 
@@ -670,6 +682,27 @@ def ei_selftest_wait_timeout(limit_us: int) -> int:
     _check(load_library().ei_selftest_wait_timeout(int(limit_us), ctypes.byref(st)),
            "ei_selftest_wait_timeout")
     return st.value
+
+
+def ei_fail_alloc_after(n: int) -> None:
+    """Host-side failure injection: the next n device allocations of the
+    library succeed and the one after them fails as out of memory (n = -1
+    disarms)."""
+    _check(load_library().ei_fail_alloc_after(int(n)), "ei_fail_alloc_after")
+
+
+def ei_fail_alloc_pending() -> int:
+    """Allocations still to pass before the armed failure, -1 when none is armed."""
+    n = c_int(0)
+    _check(load_library().ei_fail_alloc_pending(ctypes.byref(n)), "ei_fail_alloc_pending")
+    return n.value
+
+
+def ei_live_allocations() -> int:
+    """Device allocations the library currently holds."""
+    n = c_int64(0)
+    _check(load_library().ei_live_allocations(ctypes.byref(n)), "ei_live_allocations")
+    return n.value
 
 
 def ei_set_flat_table(geom: Geometry, table) -> None:

@@ -51,7 +51,9 @@ def test_default_options(lib):
     from paper_2202_08627_gb300 import ei
     o = ei.ei_default_solve_opts()
     assert (o.tol, o.max_iter, o.lbfgs_m, o.c1, o.max_trials) == (1e-6, 100, 10, 1e-4, 20)
-    assert (o.use_graph, o.resume) == (1, 0)
+    assert (o.use_graph, o.resume, o.max_seconds) == (1, 0, 0.0)
+    assert ctypes.sizeof(ei.ei_solve_opts) == 56      # the C layout (gcc: 56 B, max_seconds at 48)
+    assert ei.ei_solve_opts.max_seconds.offset == 48
 
 
 def test_checkpoint_calls_reject_bad_arguments_before_touching_the_gpu(lib):
@@ -93,3 +95,17 @@ def test_null_handle_calls_are_argument_errors(lib):
     assert lib.ei_objective_grad(None, None, None, None, None, None) == ei.EI_ERR_ARG
     assert lib.ei_reconstruct(None, None, None, None, None, None) == ei.EI_ERR_ARG
     lib.ei_destroy_geometry(None)
+
+
+def test_allocation_failure_trigger_without_a_gpu(lib):
+    """The trigger is host state: arming, reading and disarming it need no
+    device; nothing is allocated while no geometry exists."""
+    from paper_2202_08627_gb300 import ei
+    assert lib.ei_fail_alloc_after(-2) == ei.EI_ERR_ARG
+    assert lib.ei_fail_alloc_pending(None) == ei.EI_ERR_ARG
+    assert lib.ei_live_allocations(None) == ei.EI_ERR_ARG
+    ei.ei_fail_alloc_after(3)
+    assert ei.ei_fail_alloc_pending() == 3
+    ei.ei_fail_alloc_after(-1)
+    assert ei.ei_fail_alloc_pending() == -1
+    assert ei.ei_live_allocations() == 0
