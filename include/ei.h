@@ -72,8 +72,10 @@ typedef enum {
     EI_ERR_CUDA = 2,         /* a CUDA call failed (launch, copy, allocation) */
     EI_ERR_NONFINITE = 3,    /* the objective is NaN (non-finite data or iterate) */
     EI_ERR_LINESEARCH = 4,   /* Armijo backtracking found no acceptable step */
-    EI_ERR_TIMEOUT = 5,      /* a bounded wait ran out (device or host watchdog) */
-    EI_ERR_DEVICE_CHECK = 6, /* a kernel's own bounds check fired */
+    EI_ERR_TIMEOUT = 5,      /* a kernel's bounded wait ran out, or a solve's time budget
+                                (ei_solve_opts.max_seconds) did */
+    EI_ERR_DEVICE_CHECK = 6, /* reserved for kernels' own bounds checks (no build of the
+                                library returns it) */
     EI_ERR_ALLOC = 7         /* workspace allocation failed */
 } ei_status;
 
@@ -268,7 +270,8 @@ void ei_default_solve_opts(ei_solve_opts *opts);
  * whether the slice converged, failed, or is between steps.
  *   ei_solver_state_size: bytes of that state for this geometry and lbfgs_m.
  *   ei_solver_save: copies it to buf (host or device, >= the size); EI_ERR_ARG
- *     when no solve has completed on this geometry.
+ *     when no ei_reconstruct call has returned its state on this geometry (a
+ *     call stopped by its time budget does).
  *   ei_solver_load: installs a saved state in a geometry of the same slices,
  *     unknowns (linked mode, offsets) and lbfgs_m; EI_ERR_ARG when the header
  *     does not match.
@@ -400,6 +403,13 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
  * evaluation then also computes dS/dshift per pixel (one more pass over the
  * projections and measured ICs).
  */
+#define EI_OFFSET_MO 1
+#define EI_OFFSET_MR 2
+int ei_set_offset_unknowns(ei_geometry *g, int which, double scale);
+/* The geometry's current m_o [sum n_theta] and m_r [sum n_det], per slice in
+ * slice order, into host or device arrays (either may be NULL).  Synchronous. */
+int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r);
+
 /*
  * Sampled flat IC.  The paper's flat IC is measured by stepping the mask over
  * one period (acquisition section); instead of its Gaussian fit (flat_A,
@@ -420,13 +430,6 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
  * the Gaussian flat is in effect.
  */
 int ei_set_flat_table(ei_geometry *g, const float *table, int K);
-
-#define EI_OFFSET_MO 1
-#define EI_OFFSET_MR 2
-int ei_set_offset_unknowns(ei_geometry *g, int which, double scale);
-/* The geometry's current m_o [sum n_theta] and m_r [sum n_det], per slice in
- * slice order, into host or device arrays (either may be NULL).  Synchronous. */
-int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r);
 
 /*
  * On-chip throughput of the current GPU, measured by microbenchmarks (each the
