@@ -405,7 +405,10 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
     __shared__ uint64_t bars[kIcPipeMaxStages];
     __shared__ IcRow metas[kIcPipeMaxStages];
     __shared__ double red[2][32];        // alternate rows: no barrier between one
-    __shared__ int s_abort;              // row's final read and the next row's writes
+                                         // row's final read and the next row's writes
+    // a row that never landed, per iteration parity: set before the row's
+    // barrier, read after it, so every thread takes the same decision
+    __shared__ int s_abort[2];
     const int mx = dg.max_ndp;
     const int n_m = NM > 0 ? NM : dg.mc.n_m;     // NM > 0: M known at compile time
     const int n_in = MODE == IC_MODEL ? 3 : 3 + n_m;
@@ -426,7 +429,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
     if (producer) {
         for (int i = 0; i < nst; ++i) mbar_init(smem_addr(&bars[i]), 1);
         mbar_init_fence();
-        s_abort = 0;
+        s_abort[0] = s_abort[1] = 0;
         gbase[3] = 0.f;                            // g_sw[-1] of both sets
         gbase[gspan + 3] = 0.f;
         walk.start(dg, active, blockIdx.x, step);
@@ -457,7 +460,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             ++issued;
         }
         const bool landed = mbar_wait_bounded(smem_addr(&bars[slot]), (it / nst) & 1u, kIcWaitNs);
-        if (!landed) s_abort = 1;        // finish the row on whatever is there; reported below
+        if (!landed) s_abort[it & 1u] = 1;   // finish the row on whatever is there; reported below
 
         const int nd = m.nd, ndp = m.ndp, nh = ndp >> 1;
         const float *Pd = stg + mx;
@@ -553,7 +556,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
                 if (threadIdx.x == 0) part[prev_row] = t;
             }
-            if (s_abort) {
+            if (s_abort[it & 1u]) {
                 // the row never arrived: report it, poison this block's remaining
                 // rows, and give the copies still in flight a bounded chance to land
                 // before the block's shared memory is released
@@ -604,7 +607,7 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
         } else {
             __syncthreads();
         }
-        if (s_abort) {
+        if (s_abort[it & 1u]) {
             // a row never arrived: report it, poison this block's remaining rows,
             // and give the copies still in flight a bounded chance to land before
             // the block's shared memory is released
