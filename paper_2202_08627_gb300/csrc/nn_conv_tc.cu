@@ -199,8 +199,11 @@ k_conv_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int 
     // all issued MMAs complete -> bar_done
     if (tid == 0) tc_commit(smem_addr(&bar_done));
     const bool done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
+    // one decision for the whole block: the accumulator loads below are
+    // warp-collective, so no lane may skip them while another takes them
+    const bool failed = __syncthreads_or(aborted || !done);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (aborted || !done) {
+    if (failed) {
         if (tid == 0) atomicExch(status, 1);
     } else {
         // warp w reads lanes 32w .. 32w + 31 (its pixels); the loads are
@@ -393,10 +396,11 @@ k_conv_wgrad_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2
         if (tid == 0) tc_commit(smem_addr(&bar_done));
         done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
     }
+    const bool failed = __syncthreads_or(aborted || !done);   // block-uniform, as above
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int r = r0 + warp * 32 + (tid & 31);                // this thread's row (its lane)
     float *dst = partial + ((int64_t)split * R + r) * Cout + co0;
-    if (aborted || !done) {
+    if (failed) {
         if (tid == 0) atomicExch(status, 1);
     } else if (nK == 0) {                      // an empty pixel range: zero partials
         if (r < R)
