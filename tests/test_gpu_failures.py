@@ -3,6 +3,9 @@ the geometry's set-up, of the solver's state and of a U-Net's creation leaves
 nothing allocated and the library usable; a solve's time budget stops it
 between rounds, and a resumed call continues it bit for bit.  Nothing here
 faults, traps or stalls the GPU: the failures are host decisions."""
+import contextlib
+import gc
+
 import numpy as np
 import pytest
 
@@ -26,6 +29,19 @@ def _cuda():
     ei.ei_fail_alloc_after(-1)
 
 
+@contextlib.contextmanager
+def _counting():
+    """Objects of earlier tests that the cyclic collector frees would change
+    the live count in the middle of a comparison: collect them first and keep
+    the collector off while counting."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
+
+
 def _problem(seed0):
     specs = [inputs.make_slice(seed0 + i, *sh) for i, sh in enumerate(SHAPES)]
     geoms = [oracle_geometry(sp) for sp in specs]
@@ -34,8 +50,13 @@ def _problem(seed0):
 
 
 def test_setup_frees_everything_when_any_allocation_fails():
-    from paper_2202_08627_gb300 import ei
     specs, geoms, _ = _problem(1700)
+    with _counting():
+        _setup_failures(specs, geoms)
+
+
+def _setup_failures(specs, geoms):
+    from paper_2202_08627_gb300 import ei
     base = ei.ei_live_allocations()
     G = gpu_geometry(specs, geoms)
     count = ei.ei_live_allocations() - base
@@ -67,14 +88,15 @@ def test_solver_allocation_failure_leaves_the_geometry_usable():
     R.close()
     G = gpu_geometry(specs, geoms)
     m = G.pack_meas(meas)
-    base = ei.ei_live_allocations()
     vol = G.empty("vol")
-    for k in (0, 1, 6, 12):                                 # inside the solver's state
-        ei.ei_fail_alloc_after(k)
-        rep = ei.ei_reconstruct(G, m, vol, tol=0.0, max_iter=5, raise_on_error=False)
-        assert rep.return_status == ei.EI_ERR_ALLOC, k
-        assert ei.ei_live_allocations() == base, k
-    ei.ei_fail_alloc_after(-1)
+    with _counting():
+        base = ei.ei_live_allocations()
+        for k in (0, 1, 6, 12):                             # inside the solver's state
+            ei.ei_fail_alloc_after(k)
+            rep = ei.ei_reconstruct(G, m, vol, tol=0.0, max_iter=5, raise_on_error=False)
+            assert rep.return_status == ei.EI_ERR_ALLOC, k
+            assert ei.ei_live_allocations() == base, k
+        ei.ei_fail_alloc_after(-1)
     vol.zero_()
     rep = ei.ei_reconstruct(G, m, vol, tol=0.0, max_iter=5)
     torch.cuda.synchronize()
@@ -84,6 +106,11 @@ def test_solver_allocation_failure_leaves_the_geometry_usable():
 
 
 def test_unet_creation_frees_everything_when_an_allocation_fails():
+    with _counting():
+        _unet_failures()
+
+
+def _unet_failures():
     from paper_2202_08627_gb300 import ei
     base = ei.ei_live_allocations()
     net = ei.UNet(levels=2, base=32, batch=2, height=32, width=32, seed=3)
