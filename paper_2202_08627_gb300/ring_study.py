@@ -42,6 +42,7 @@ GAMMA = 5e-7                 # delta / mu (cm)
 SLOPE_M = -0.24              # mask position on the slope of the IC (periods)
 FLAT_STEPS = 33              # mask positions of a flat scan over one period
 FLAT_COUNTS = 1000.0         # expected counts at the IC peak per flat exposure
+FRC_CROP = 140 / 220         # central part of the slice the FRC compares (140 of 220 voxels)
 # granules: (x0, y0, radius) as fractions of the half field of view, attenuation (1/cm)
 GRANULES = [(-0.40, 0.30, 0.28, 0.50), (0.40, 0.30, 0.28, 0.55), (0.0, -0.40, 0.28, 0.70)]
 
@@ -173,7 +174,7 @@ def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed
     centres = [(half - y * half, half + x * half, r * half) for (x, y, r, _) in GRANULES]
     masks = [metrics.disc_mask(n, cy, cx, 0.6 * r) for (cy, cx, r) in centres]
     pairs = [(0, 1), (0, 2), (1, 2)]
-    crop = slice(int(n * (0.5 - 70 / 220)), int(n * (0.5 + 70 / 220)))
+    crop = slice(int(n * (0.5 - FRC_CROP / 2)), int(n * (0.5 + FRC_CROP / 2)))
     rows = []
     odd, even = np.arange(1, n_theta, 2), np.arange(0, n_theta, 2)
     truth = (A, c, w), (None if asym == 0.0 else true_flat(A, c, w, asym, np.arange(512) / 512).T)
