@@ -21,6 +21,11 @@ What it computes, in the paper's order and notation:
   m_r(t) of Eq. 4 and by a scatter broadening: the Gaussian flat IC
   f(t, m) = A_t exp(-(m - c_t)^2 / (2 w_t^2)) is convolved with a Gaussian of
   variance kappa R[sigma], which keeps its area.
+* ``table_interp`` and the table branches of ``ic_model``,
+  ``ic_objective_grad`` and ``shift_gradient`` — the flat IC taken as the
+  samples of a mask scan over one period (the "Experimental improvements"
+  section measures it in 33 steps) instead of its Gaussian fit, interpolated
+  in m by periodic cubic Catmull-Rom splines: s = exp(-R[mu]) f_t(m - shift).
 * ``objective_grad`` — the cost S of Eq. 5 (sum of squared residuals plus an
   L2 regulariser) and its analytic gradient.
 * ``objective_grad_linked`` — the same cost for the single unknown h of Eq. 4
