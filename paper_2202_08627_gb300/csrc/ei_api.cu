@@ -630,10 +630,11 @@ static std::string tune_key(const ei_geometry *g)
     if (cudaGetDeviceProperties(&prop, g->device) == cudaSuccess) name = prop.name;
     for (char &c : name)
         if (c == ' ') c = '_';
-    char buf[64];
-    // linked geometries run the single-channel kernels: tuned separately
-    snprintf(buf, sizeof buf, "|%016llx|v1%s", (unsigned long long)g->shape_hash,
-             g->link_gamma > 0.f ? "L" : "");
+    char buf[80];
+    // linked geometries run the single-channel kernels: tuned separately; the
+    // variant counts make entries tuned before a variant was added stale
+    snprintf(buf, sizeof buf, "|%016llx|v1f%da%d%s", (unsigned long long)g->shape_hash,
+             N_FWD_VARIANTS, N_ADJ_VARIANTS, g->link_gamma > 0.f ? "L" : "");
     return name + buf;
 }
 
@@ -647,8 +648,6 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
         return EI_ERR_CUDA;
     }
     const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int reps_ = reps;
-    (void)reps_;
     const float link = g->link_gamma;              // the kernels this geometry's evaluations run
     auto launch = [&]() {
         return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero, link,
