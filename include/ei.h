@@ -328,8 +328,9 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * ei_autotune times every candidate with CUDA events on this geometry's
  * workspace (synchronises `stream`) and selects the fastest; the choice is
  * cached in a text file (EI_TUNE_CACHE, default ~/.cache/ei_gb300_autotune.txt)
- * keyed by the GPU name, the slice sizes and whether the geometry is linked
- * (ei_set_linked: the single-channel kernels are timed), and read back on later calls
+ * keyed by the GPU name, the slice sizes, whether the geometry is linked
+ * (ei_set_linked: the single-channel kernels are timed) and the number of
+ * variants this build has, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
  * report a variant explicitly (ids: projector 0..12, adjoint 0..7).
  */
