@@ -279,6 +279,38 @@ def run_oracle_timing(args):
                       "runs": runs}), flush=True)
 
 
+def oracle_time_to_tolerance():
+    """The FP64 oracle, as it stands, solving to relative change 1e-6 on this
+    machine's host cores: one 64x64 slice (90 angles, 96 pixels, M=7, at most
+    20 iterations) with all cores, 3 threads (the paper's OpenMP count) and 1,
+    and one 256x256 slice (720 angles, 384 pixels, M=7) with all cores and 3
+    threads.  Returns a list of runs."""
+    import oracle
+    from paper_2202_08627_gb300 import inputs
+    nproc = os.cpu_count() or 1
+    runs = []
+    for name, (n, nth, nd), max_iter, threads in (
+            ("64x64, 90 angles, 96 pixels, M=7, at most 20 iterations", (64, 90, 96), 20,
+             (nproc, 3, 1)),
+            ("256x256, 720 angles, 384 pixels, M=7", (256, 720, 384), 400, (nproc, 3))):
+        spec = inputs.make_slice(7, n, nth, nd, 7)
+        geom = oracle.Geometry(n=n, n_theta=nth, n_det=nd, pitch=spec.pitch, theta=spec.theta,
+                               m=spec.m, z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM,
+                               kappa=inputs.KAPPA, flat_A=spec.flat_A, flat_c=spec.flat_c,
+                               flat_w=spec.flat_w)
+        s_exp = inputs.poisson_noise(oracle.ic_model(spec.P_exact, geom), spec.seed)
+        for t in threads:
+            oracle.set_num_threads(t)
+            t0 = time.perf_counter()
+            _, rep = oracle.reconstruct(s_exp, geom,
+                                        opts=oracle.SolveOptions(tol=1e-6, max_iter=max_iter))
+            dt = time.perf_counter() - t0
+            runs.append({"case": name, "threads": t, "seconds": dt, "iterations": rep.iterations,
+                         "seconds_per_1024_slice": dt * 1024.0 ** 2 / (n * n)})
+    oracle.set_num_threads(nproc)
+    return runs
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -358,20 +390,26 @@ def run_ours(args, rank, world, local_rank):
     rep_k = ei.ei_reconstruct(G, s_exp, vol, tol=0.0, max_iter=steps)
     prof = ei.ei_profile_read(G)
     ei.ei_profile_enable(G, False)
-    # algorithmic bytes actually processed (per-slice evaluation counts)
-    per_slice_fa = np.array([48 * n * n + 28 * nth * nd for (n, nth, nd) in wl.slices], dtype=np.float64)
-    fa_bytes = float(np.sum(per_slice_fa * rep.slice_evaluations))
+    # algorithmic bytes actually processed: per slice, its projections (the
+    # initial point and every iteration's first trial) and its adjoints (the
+    # initial point and every accepted step); backtracking trials cost the IC
+    # kernel only
+    fwd_b = np.array([16 * n * n + 12 * nth * nd for (n, nth, nd) in wl.slices], dtype=np.float64)
+    adj_b = np.array([32 * n * n + 16 * nth * nd for (n, nth, nd) in wl.slices], dtype=np.float64)
+
+    def fa_bytes_of(r):
+        return float(np.sum(fwd_b * r.slice_projections) + np.sum(adj_b * r.slice_adjoints))
+
+    fa_bytes = fa_bytes_of(rep)
     value = world * fa_bytes / (t_ms * 1e-3) / 1e9
 
     # per-kernel CUDA-event timings inside the timed region
-    taps_eval = float(np.sum(np.array([2.0 * n * n * nth for (n, nth, nd) in wl.slices]) *
-                             rep_k.slice_evaluations)) / max(1, prof["project_launches"])
     kern = {}
     for k in ("project", "ic", "backproject"):
         L = prof[k + "_launches"]
         kern[k] = {"launches": L, "total_ms": prof[k + "_ms"],
                    "avg_ms": prof[k + "_ms"] / L if L else None}
-    fa_bytes_k = float(np.sum(per_slice_fa * rep_k.slice_evaluations))
+    fa_bytes_k = fa_bytes_of(rep_k)
     fa_kernel_gbs = fa_bytes_k / ((prof["project_ms"] + prof["backproject_ms"]) * 1e-3) / 1e9 \
         if prof["project_ms"] + prof["backproject_ms"] > 0 else None
     dom = "backproject" if prof["backproject_ms"] >= prof["project_ms"] else "project"
@@ -379,18 +417,26 @@ def run_ours(args, rank, world, local_rank):
     # bandwidth; bytes its loads bring from L1 into registers against the
     # measured L1 load rate; FP32 flops against the measured FMA rate
     onchip = ei.ei_measure_peaks()
-    evals = np.asarray(rep_k.slice_evaluations, dtype=np.float64)
-    n_launch = max(1, prof["project_launches"])
-    per_launch = lambda per_slice: float(np.sum(np.asarray(per_slice, dtype=np.float64) * evals)) / n_launch
+    # work per launch of each kernel: the slices it evaluated over its launches
+    counts = {"project": (rep_k.slice_projections, prof["project_launches"]),
+              "backproject": (rep_k.slice_adjoints, prof["backproject_launches"]),
+              "ic": (rep_k.slice_evaluations, prof["ic_launches"])}
+
+    def per_launch(kernel, per_slice):
+        c, L = counts[kernel]
+        return float(np.sum(np.asarray(per_slice, dtype=np.float64) *
+                            np.asarray(c, dtype=np.float64))) / max(1, L)
+
     samples = projector_samples(wl.slices)
+    vox_ang = [float(n * n * nth) for (n, nth, nd) in wl.slices]
     alg = {
-        "project": {"hbm": per_launch([16 * n * n + 12 * nth * nd for (n, nth, nd) in wl.slices]),
-                    "l1": per_launch(24.0 * samples),
-                    "flops": per_launch(6.0 * samples)},
-        "backproject": {"hbm": per_launch([32 * n * n + 16 * nth * nd for (n, nth, nd) in wl.slices]),
-                        "l1": per_launch([24.0 * n * n * nth for (n, nth, nd) in wl.slices]),
-                        "flops": per_launch([6.0 * n * n * nth for (n, nth, nd) in wl.slices])},
-        "ic": {"hbm": per_launch([(28 + 4 * wl.n_m) * nth * nd for (n, nth, nd) in wl.slices])},
+        "project": {"hbm": per_launch("project", fwd_b),
+                    "l1": per_launch("project", 24.0 * samples),
+                    "flops": per_launch("project", 6.0 * samples)},
+        "backproject": {"hbm": per_launch("backproject", adj_b),
+                        "l1": per_launch("backproject", [24.0 * x for x in vox_ang]),
+                        "flops": per_launch("backproject", [6.0 * x for x in vox_ang])},
+        "ic": {"hbm": per_launch("ic", [(28 + 4 * wl.n_m) * nth * nd for (n, nth, nd) in wl.slices])},
     }
     hbm_peak = float(peaks.get("hbm_gbs", 6686.8))
     views = {}
@@ -421,20 +467,25 @@ def run_ours(args, rank, world, local_rank):
     ic_gbs = views["ic"]["hbm"]["achieved_gbs"] if "ic" in views else None
     clocks = clk.summary(float(peaks.get("sm_max_mhz", 2070.0)))
 
-    # time to tolerance from zero and from the single-shot start (optional)
+    # the headline: time to tolerance per 1024^2 slice from x0 = 0 (the plain
+    # GPU solve), from the single-shot FBP and from the learned warm start
     ttt = None
-    if args.ttt:
+    if not args.no_ttt:
         from paper_2202_08627_gb300 import warmstart
         starts, net, training = ["zero", "single_shot"], None, None
-        if args.cnn:
+        if not args.no_cnn:
             net, training = train_warm_start(args, wl, device)
             starts.append("cnn")
         ttt = warmstart.time_to_tolerance(G, s_exp, starts, args.tol, args.ttt_max_iter, net)
         ttt["tol"] = args.tol
+        ttt["timing"] = ("CUDA events around the start's own computation (none / FBP / FBP + "
+                         "U-Net inference) and the solve of every slice to the tolerance; the "
+                         "network's training (on pairs of other seeds) is not included")
         if training:
             ttt["cnn_training"] = training
         if net is not None:
             net.close()
+        print(json.dumps({"time_to_tolerance": ttt}), file=sys.stderr, flush=True)
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -452,7 +503,7 @@ def run_ours(args, rank, world, local_rank):
             tt = torch.tensor([te], device=device)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             te = float(tt.item())
-        fa2 = float(np.sum(per_slice_fa * rep2.slice_evaluations))
+        fa2 = fa_bytes_of(rep2)
         h2d = s_host.numel() * 4 + v_host.numel() * 4
         d2h = v_host.numel() * 4 + G.n_slices * 8 * 2
         e2e = {"value": world * fa2 / te / 1e9, "unit": "GB/s",
@@ -492,7 +543,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         dt, nbytes, cores, desc = cpu_oracle_sample(wl, 1, evals=8)
         line["cpu_baseline"] = {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": cores,
-                                "kind": "oracle", "sample": desc, "seconds": dt}
+                                "kind": "oracle", "sample": desc, "seconds": dt,
+                                "time_to_tolerance": oracle_time_to_tolerance()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     G.close()
@@ -639,12 +691,13 @@ def main():
     ap.add_argument("--workload", default="uneven1024")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ttt", action="store_true",
-                    help="also solve every slice to --tol from x0 = 0 and from the single-shot start")
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="skip the time to tolerance (every slice solved to --tol from x0 = 0, "
+                         "the single-shot start and the learned start)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--ttt-max-iter", type=int, default=400)
-    ap.add_argument("--cnn", action="store_true",
-                    help="with --ttt: also solve from the learned warm start (trained first)")
+    ap.add_argument("--no-cnn", action="store_true",
+                    help="time to tolerance without the learned warm start (no training)")
     ap.add_argument("--cnn-pairs", type=int, default=256)
     ap.add_argument("--cnn-epochs", type=int, default=20)
     ap.add_argument("--cnn-weights", default=None, help="trained parameters (.npy) to load")

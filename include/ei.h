@@ -235,9 +235,15 @@ typedef struct {
     int *converged;    /* 1 if the tol test stopped the slice, 0 if max_iter or an error did */
     double *f_final;   /* final S */
     double *f_initial; /* S at x0 */
-    int *slice_evaluations; /* objective+gradient evaluations of each slice */
+    int *slice_evaluations; /* objective evaluations of each slice (every line-search
+                          trial and the initial point) */
     int evaluations;   /* batched evaluation rounds, the initial one included (out) */
     double seconds;    /* wall time of the call (out) */
+    int *slice_projections; /* forward projections of each slice: the initial point and
+                          the first trial of every iteration (a backtracking trial's
+                          projections are interpolated, R being linear) */
+    int *slice_adjoints; /* adjoint back-projections of each slice: the initial point and
+                          every accepted step */
 } ei_solve_report;
 
 /*
@@ -245,7 +251,13 @@ typedef struct {
  * two-loop recursion with H0 = (s.y / y.y) I, Armijo backtracking (first
  * trial 1/|g| while no pair is kept, then 1, halving), pair kept when the
  * curvature condition holds, stop on the relative decrease of S or max_iter.
- * The iterate is u = x / scale.
+ * The iterate is u = x / scale.  R is linear, so along a search direction
+ * the projections of u + alpha d are P(u) + alpha P(d): each iteration
+ * projects its first trial point only, a backtracking trial interpolates
+ * between the projections of u and of the previous trial (a rejected trial
+ * costs the IC model alone), and the adjoint runs at accepted points only
+ * (the "Algorithmic improvements" section's removal of superfluous Radon
+ * calls).
  * s_exp: measurement layout, vol_inout: vol layout (x0 in, solution out);
  * both may be device or host memory (host arrays are staged through device
  * memory inside the call).  report may be NULL.  Synchronous: `stream` is
@@ -266,8 +278,9 @@ void ei_default_solve_opts(ei_solve_opts *opts);
  * Checkpoint / resume of the solver.  After ei_reconstruct returns, the
  * geometry keeps the L-BFGS state of every slice: the iterate u = x / scale
  * and its gradient, the search direction, the m most recent (s, y) pairs and
- * their 1 / s.y, the accepted-step count k, the current and initial S, and
- * whether the slice converged, failed, or is between steps.
+ * their 1 / s.y, the projections of u and of the latest trial point, the
+ * accepted-step count k, the current and initial S, and whether the slice
+ * converged, failed, or is between steps.
  *   ei_solver_state_size: bytes of that state for this geometry and lbfgs_m.
  *   ei_solver_save: copies it to buf (host or device, >= the size); EI_ERR_ARG
  *     when no ei_reconstruct call has returned its state on this geometry (a
@@ -280,7 +293,8 @@ void ei_default_solve_opts(ei_solve_opts *opts);
  * max_iter resume with the new max_iter (k counts from the original start),
  * converged or failed slices stay so, and the iterates are bit-identical to
  * one uninterrupted solve with the larger max_iter.  The state holds
- * (2 m + 5) vectors of the volume's size plus small per-slice records.
+ * (2 m + 5) vectors of the volume's size, two sets of the three projection
+ * planes, and small per-slice records.
  */
 int ei_solver_state_size(const ei_geometry *g, int lbfgs_m, size_t *bytes);
 int ei_solver_save(const ei_geometry *g, void *buf, size_t bytes);
@@ -407,6 +421,25 @@ int ei_offset_grad(ei_geometry *g, const float *vol, const float *s_exp, float *
 #define EI_OFFSET_MO 1
 #define EI_OFFSET_MR 2
 int ei_set_offset_unknowns(ei_geometry *g, int which, double scale);
+
+/*
+ * Restrict the ring term m_r(t) of Eq. 4, when it is among the solver's
+ * unknowns, to pixel-to-pixel (ring) frequencies: each slice's m_r gradient
+ * is projected onto the orthogonal complement of the K lowest orthonormal
+ * DCT-II modes across its detector,
+ *   b_k(j) = sqrt((2 - [k = 0]) / n_det) cos(pi k (j + 1/2) / n_det),  k < K,
+ * so m_r keeps its starting component in those modes.  A ring artefact is a
+ * per-pixel error of the flat IC, present at every frequency, while the shift
+ * that the object's angle-averaged projection causes varies slowly across
+ * the detector: a free m_r absorbs that part of the object's signal too (the
+ * paper's "Experimental improvements" section introduces m_r against rings;
+ * the restriction is this library's reading).  K = 0 (the default): no
+ * restriction beyond the zero-mean gauge of ei_set_offset_unknowns; K >= 1
+ * includes that gauge.  0 <= K <= EI_MAX_RING_MODES and K <= every slice's
+ * n_det, else EI_ERR_ARG.  Takes effect from the next ei_reconstruct call.
+ */
+#define EI_MAX_RING_MODES 1024
+int ei_set_ring_modes(ei_geometry *g, int K);
 /* The geometry's current m_o [sum n_theta] and m_r [sum n_det], per slice in
  * slice order, into host or device arrays (either may be NULL).  Synchronous. */
 int ei_get_offsets(const ei_geometry *g, float *m_o, float *m_r);
@@ -549,16 +582,20 @@ int ei_unet_set_tensor_path(ei_unet *net, int path);
 /*
  * ei_objective_grad_noalloc — S and its gradient for ONE slice with no device
  * allocation at all.  The paper has no counterpart; this exists for callers
- * that cannot allocate GPU memory: code running while a stream is captured
- * into a CUDA graph (cudaMalloc cannot be captured), frameworks that have
- * reserved the device memory in their own pool and forbid allocations outside
- * it, and latency-sensitive loops that cannot afford cudaMalloc's implicit
- * device synchronisation.  Such callers cannot use ei_setup_geometry (it
- * allocates a workspace), so the geometry description is passed directly.
+ * that may not allocate GPU memory themselves: frameworks that have reserved
+ * the device memory for their own pool and forbid allocations outside it, and
+ * latency-sensitive loops that cannot afford cudaMalloc's implicit device
+ * synchronisation.  Such callers cannot use ei_setup_geometry (it allocates a
+ * workspace), so the geometry description is passed directly.
  *
  * desc: as for ei_setup_geometry with a uniform batch of one slice (desc->n,
- *   n_theta, n_det, pitch_cm; flat_*, m_o, m_r host or device).
+ *   n_theta, n_det, pitch_cm; flat_*, m_o, m_r host or device), checked as
+ *   ei_setup_geometry checks it (flat_w > 0, finite flat_A and flat_c, finite
+ *   constants), device arrays included: they are read back through `stream`.
  * vol, s_exp, grad (nullable), S_out: as for ei_objective_grad, one slice.
+ * Kernels: variant 0 of the projector, the IC kernel and the adjoint, so the
+ *   results equal those of ei_objective_grad on a geometry of the same slice
+ *   set to those variants (ei_set_variant(g, 0, 0, 0), ei_set_ic_variant(g, 0)).
  * Scratch: every intermediate lives in one static device array of
  *   EI_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until the
  *   process exits.  A slice needs about 48 n(n+1) + 12 n_theta n_dp
@@ -566,15 +603,16 @@ int ei_unet_set_tensor_path(ei_unet *net, int path);
  *   max(2, 0.71 n - n_det/2 + 3) pixels); larger slices return EI_ERR_ARG
  *   before any GPU work.  (A 256x256 slice with 720 angles and 384 pixels
  *   needs ~14 MB.)
- * First call on a device: resolves the array's device address
- *   (cudaGetSymbolAddress) and sets a kernel attribute; make that first call
- *   before any stream capture.  Later calls only copy the description's
- *   arrays, clear the parts of the array that must start at zero, and launch
- *   the same kernels as ei_objective_grad.
+ * Every call looks up the array's address in the current context
+ *   (cudaGetSymbolAddress) and sets the IC kernel's shared-memory limit; no
+ *   state is kept between calls but the array's contents.
  * Concurrency: every call uses the same array, and its contents are whatever
- *   the last call left; calls that overlap on the GPU (other streams, other
- *   threads) race and must be serialised by the caller.
- * Host arrays in desc and a host S_out make the call synchronise the stream.
+ *   the last call left (the call clears what must start at zero); calls that
+ *   overlap on the GPU (other streams, other threads) race and must be
+ *   serialised by the caller.
+ * The call synchronises `stream` (it reads the per-pixel arrays on the host)
+ *   and returns EI_ERR_ARG for invalid arguments before it launches a kernel or
+ *   writes device memory.
  */
 #define EI_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ei_objective_grad_noalloc(const ei_geometry_desc *desc, const float *vol, const float *s_exp,

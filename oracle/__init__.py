@@ -31,7 +31,8 @@ What it computes, in the paper's order and notation:
 * ``objective_grad_linked`` — the same cost for the single unknown h of Eq. 4
   (mu = h, delta = gamma h, no scatter) and its gradient with respect to h.
 * ``offset_grads`` — the gradient of S with respect to the drift m_o(theta)
-  and the ring term m_r(t) of Eq. 4.
+  and the ring term m_r(t) of Eq. 4; ``ring_project`` restricts m_r's steps
+  to ring (pixel-to-pixel) frequencies.
 * ``single_shot`` / ``single_shot_eq3`` — non-iterative reconstructions: the
   three-channel moment retrieval used as the warm-start input, and the
   paper's single-shot retrieval of Eq. 3 for the linked unknown.
@@ -326,6 +327,26 @@ def offset_grads(x: np.ndarray, s_exp: np.ndarray, geom: Geometry):
     P = np.stack([project(np.asarray(x[ch], dtype=np.float64), geom) for ch in range(3)])
     G = shift_gradient(P, s_exp, geom)
     return G.sum(axis=1), G.sum(axis=0)
+
+
+def ring_project(g: np.ndarray, K: int) -> np.ndarray:
+    """The ring term m_r(t) of Eq. 4 restricted to pixel-to-pixel (ring)
+    frequencies: the orthogonal projection of a per-pixel vector g [n_det]
+    onto the complement of the K lowest orthonormal DCT-II modes across the
+    detector (K = 0: g unchanged; K = 1: g minus its mean).  A ring artefact is
+    a per-pixel error of the flat IC, present at every frequency, while the
+    shift that the object's angle-averaged projection causes varies slowly
+    across the detector; restricting m_r's steps to this subspace keeps it
+    from absorbing the latter.  The restriction is a reading: the paper leaves
+    m_r unconstrained.  The orthonormal DCT-II (scipy) serves as the change of
+    basis."""
+    from scipy.fft import dct, idct
+    g = np.asarray(g, dtype=np.float64)
+    if K <= 0:
+        return g.copy()
+    c = dct(g, type=2, norm="ortho")
+    c[:K] = 0.0
+    return idct(c, type=2, norm="ortho")
 
 
 def objective_grad_linked(h: np.ndarray, s_exp: np.ndarray, geom: Geometry, gamma: float,

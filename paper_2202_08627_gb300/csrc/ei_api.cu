@@ -160,14 +160,13 @@ static cudaError_t traced_ic(ei_geometry *g, const float *proj, const float *mea
     return e;
 }
 
-static cudaError_t traced_backproject(ei_geometry *g, bool with_sino, const float4 *v,
-                                      float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                      float link, double *part, const int *active, cudaStream_t st)
+static cudaError_t traced_backproject(ei_geometry *g, const float4 *v, float4 *out,
+                                      float4 out_mult, float4 reg2, float link, const int *active,
+                                      cudaStream_t st)
 {
-    cudaEvent_t b = with_sino ? trace_begin(g, st) : nullptr;
-    cudaError_t e = launch_backproject(g, with_sino, v, out, out_mult, reg2, reg1, link, part,
-                                       active, st);
-    if (with_sino) trace_end(g, TK_BACKPROJECT, b, st);
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_backproject(g, v, out, out_mult, reg2, link, active, st);
+    trace_end(g, TK_BACKPROJECT, b, st);
     count_launches(g, 1);
     return e;
 }
@@ -187,42 +186,50 @@ static float4 physical_mult(const ei_geometry *g)
                                : make_float4(1.f, 1.f, 1.f, 0.f);
 }
 
-cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
-                     float4 *grad, bool scaled, const int *active, cudaStream_t st)
+EvalConsts eval_consts(const ei_geometry *g, bool scaled)
 {
     // linked mode: the unknown is h in the mu lane, mu = h, delta = gamma h,
     // sigma = 0, regularised by lambda_mu only (Eq. 4, Eq. 5)
     const bool linked = g->link_gamma > 0.f;
     const float gam = g->link_gamma;
     const float on1 = linked ? 0.f : 1.f;
-    float4 mult, out_mult, reg2, reg1;
+    EvalConsts c;
     if (scaled) {
-        mult = linked ? make_float4(g->scale[0], gam * g->scale[0], 0.f, 0.f)
-                      : make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
-        out_mult = make_float4(g->scale[0], on1 * g->scale[1], on1 * g->scale[2], 0.f);
-        reg2 = make_float4(2.f * g->lambda[0], on1 * 2.f * g->lambda[1], on1 * 2.f * g->lambda[2], 0.f);
-        reg1 = make_float4(g->lambda[0], on1 * g->lambda[1], on1 * g->lambda[2], 0.f);
+        c.mult = linked ? make_float4(g->scale[0], gam * g->scale[0], 0.f, 0.f)
+                        : make_float4(g->scale[0], g->scale[1], g->scale[2], 0.f);
+        c.out_mult = make_float4(g->scale[0], on1 * g->scale[1], on1 * g->scale[2], 0.f);
+        c.reg2 = make_float4(2.f * g->lambda[0], on1 * 2.f * g->lambda[1], on1 * 2.f * g->lambda[2], 0.f);
+        c.reg1 = make_float4(g->lambda[0], on1 * g->lambda[1], on1 * g->lambda[2], 0.f);
     } else {
-        mult = physical_mult(g);
-        out_mult = make_float4(1.f, on1, on1, 0.f);
+        c.mult = physical_mult(g);
+        c.out_mult = make_float4(1.f, on1, on1, 0.f);
         float k[3];
-        for (int c = 0; c < 3; ++c) k[c] = (float)(1.0 / ((double)g->scale[c] * g->scale[c]));
-        reg2 = make_float4(2.f * g->lambda[0] * k[0], on1 * 2.f * g->lambda[1] * k[1],
-                           on1 * 2.f * g->lambda[2] * k[2], 0.f);
-        reg1 = make_float4(g->lambda[0] * k[0], on1 * g->lambda[1] * k[1],
-                           on1 * g->lambda[2] * k[2], 0.f);
+        for (int i = 0; i < 3; ++i) k[i] = (float)(1.0 / ((double)g->scale[i] * g->scale[i]));
+        c.reg2 = make_float4(2.f * g->lambda[0] * k[0], on1 * 2.f * g->lambda[1] * k[1],
+                             on1 * 2.f * g->lambda[2] * k[2], 0.f);
+        c.reg1 = make_float4(g->lambda[0] * k[0], on1 * g->lambda[1] * k[1],
+                             on1 * g->lambda[2] * k[2], 0.f);
     }
     // linked: single-channel staging, projection and adjoint (the IC kernel
     // combines the gradient sinogram into g_mu + gamma g_delta)
-    const float link = linked ? gam : 0.f;
-    EI_CUDA_TRY(counted_prep(g, v, mult, linked, active, st));
-    EI_CUDA_TRY(traced_project(g, g->proj, link, active, st));
+    c.link = linked ? gam : 0.f;
+    return c;
+}
+
+cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
+                     float4 *grad, bool scaled, const int *active, cudaStream_t st)
+{
+    const EvalConsts c = eval_consts(g, scaled);
+    const bool linked = c.link > 0.f;
+    EI_CUDA_TRY(counted_prep(g, v, c.mult, linked, active, st));
+    EI_CUDA_TRY(traced_project(g, g->proj, c.link, active, st));
     EI_CUDA_TRY(traced_ic(g, g->proj, meas, nullptr, g->part_ic,
-                          grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, link, active, st));
-    EI_CUDA_TRY(traced_backproject(g, grad != nullptr, v, grad, out_mult, reg2, reg1,
-                                   linked ? gam : 0.f, g->part_adj, active, st));
-    count_launches(g, 1);
-    EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, g->part_adj, S_dev, active, st));
+                          grad ? IC_OBJECTIVE_GRAD : IC_OBJECTIVE, c.link, active, st));
+    count_launches(g, 2);
+    EI_CUDA_TRY(launch_reg_partials(g->dg, v, c.reg1, g->part_reg, active, st));
+    EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, g->dg.vec_prefix, g->part_reg, S_dev,
+                                          active, st));
+    if (grad) EI_CUDA_TRY(traced_backproject(g, v, grad, c.out_mult, c.reg2, c.link, active, st));
     return cudaSuccess;
 }
 
@@ -463,10 +470,8 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
             const int nab = (q.n_theta + angles - 1) / angles;
             fwd_p[v].push_back(fwd_p[v].back() + nab * nrb);
         }
-        for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
-            const int tr = backproject_variant_rows(v);
-            adj_p[v].push_back(adj_p[v].back() + ((q.n + ADJ_TC - 1) / ADJ_TC) * ((q.n + tr - 1) / tr));
-        }
+        for (int v = 0; v < N_ADJ_VARIANTS; ++v)
+            adj_p[v].push_back(adj_p[v].back() + backproject_variant_items(v, q.n));
         mix((uint64_t)q.n), mix((uint64_t)q.n_theta), mix((uint64_t)q.n_det);
         ic_p.push_back(ic_p.back() + q.n_theta);
         const int pt = (q.n + 1 + PREP_TILE - 1) / PREP_TILE;
@@ -518,7 +523,6 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     float *d_mo = nullptr;
     float4 *d_pix = nullptr;
     int *d_ic = nullptr, *d_prep = nullptr, *d_vec = nullptr;
-    int max_adj_total = 0;
     for (int v = 0; v < N_FWD_VARIANTS; ++v) {
         int *dp = nullptr;
         if (e == cudaSuccess) e = upload(g, &dp, fwd_p[v]);
@@ -530,7 +534,6 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
         if (e == cudaSuccess) e = upload(g, &dp, adj_p[v]);
         g->adj_prefixes[v] = dp;
         g->adj_totals[v] = adj_p[v].back();
-        max_adj_total = std::max(max_adj_total, adj_p[v].back());
     }
     g->shape_hash = hash ^ (uint64_t)n_slices;
     if (e == cudaSuccess) e = upload(g, &d_sl, g->h_slices);
@@ -548,7 +551,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = dev_alloc(g, &g->gA, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->gB, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_ic, (size_t)dg.total_ic);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->part_adj, (size_t)max_adj_total);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->part_reg, (size_t)std::max(1, dg.total_vec));
     if (e == cudaSuccess) e = dev_alloc(g, &g->work_counter, 2);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
@@ -639,7 +642,8 @@ static std::string tune_key(const ei_geometry *g)
 }
 
 // Mean duration (ms) of `reps` launches of the selected projector or adjoint variant.
-static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, double *ms)
+static int time_kernel(ei_geometry *g, bool adjoint, float4 *adj_out, cudaStream_t st, int reps,
+                       double *ms)
 {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return EI_ERR_CUDA;
@@ -650,8 +654,7 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
     const float4 one = make_float4(1.f, 1.f, 1.f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float link = g->link_gamma;              // the kernels this geometry's evaluations run
     auto launch = [&]() {
-        return adjoint ? launch_backproject(g, true, nullptr, nullptr, one, zero, zero, link,
-                                            g->part_adj, nullptr, st)
+        return adjoint ? launch_backproject(g, nullptr, adj_out, one, zero, link, nullptr, st)
                        : launch_project(g, g->proj, link, nullptr, st);
     };
     cudaError_t e = launch();                       // warm-up
@@ -671,6 +674,8 @@ static int time_kernel(ei_geometry *g, bool adjoint, cudaStream_t st, int reps, 
 // launches) only when it is at least 1% faster: variants within timing noise
 // of each other then get the same, reproducible choice.
 static const double kTuneMargin = 0.99;
+static thread_local double g_tune_last[2];     // the chosen variants' times (ms)
+static int autotune_timed(ei_geometry *g, float4 *adj_out, cudaStream_t st);
 
 int ei_autotune(ei_geometry *g, int flags, void *stream)
 {
@@ -693,6 +698,39 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // the adjoint's output while it is timed (a volume, freed below)
+    float4 *adj_out = nullptr;
+    {
+        void *p = nullptr;
+        const cudaError_t e = lib_malloc(&p, (size_t)std::max<int64_t>(1, g->vol_count) * sizeof(float4));
+        if (e != cudaSuccess) {
+            record_error(e);
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? EI_ERR_ALLOC : EI_ERR_CUDA;
+        }
+        adj_out = static_cast<float4 *>(p);
+    }
+    const int rc = autotune_timed(g, adj_out, st);
+    lib_free(adj_out);
+    if (rc != EI_OK) return rc;
+    const int bf = g->fwd_variant.id, ba = g->adj_variant.id, bp = g->persistent ? 1 : 0;
+    if (!(flags & EI_TUNE_NO_CACHE_WRITE)) {
+        const size_t slash = path.find_last_of('/');
+        if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+        FILE *f = fopen(path.c_str(), "a");       // best effort: no cache if not writable
+        if (f) {
+            fprintf(f, "%s %d %d %d %.6f %.6f\n", key.c_str(), bf, ba, bp, g_tune_last[0],
+                    g_tune_last[1]);
+            fclose(f);
+        }
+    }
+    return EI_OK;
+}
+
+// The timed part of ei_autotune: selects the fastest variants and launch mode
+// (their times in g_tune_last).
+static int autotune_timed(ei_geometry *g, float4 *adj_out, cudaStream_t st)
+{
     // stage 1: every projector and adjoint variant, one-block-per-item and
     // persistent launches, 3 launches each
     int fid[2] = {0, 0}, aid[2] = {0, 0};
@@ -701,14 +739,14 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
         for (int v = 0; v < N_FWD_VARIANTS; ++v) {
             select_variants(g, v, 0, pers != 0);
             double ms = 0;
-            const int rc = time_kernel(g, false, st, 3, &ms);
+            const int rc = time_kernel(g, false, adj_out, st, 3, &ms);
             if (rc != EI_OK) return rc;
             if (ms < fbest * kTuneMargin) fbest = ms, fid[pers] = v;
         }
         for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
             select_variants(g, fid[pers], v, pers != 0);
             double ms = 0;
-            const int rc = time_kernel(g, true, st, 3, &ms);
+            const int rc = time_kernel(g, true, adj_out, st, 3, &ms);
             if (rc != EI_OK) return rc;
             if (ms < abest * kTuneMargin) abest = ms, aid[pers] = v;
         }
@@ -721,25 +759,16 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
         for (int pers = 0; pers < 2; ++pers) {
             select_variants(g, fid[pers], aid[pers], pers != 0);
             double mf = 0, ma = 0;
-            int rc = time_kernel(g, false, st, 2, &mf);
-            if (rc == EI_OK) rc = time_kernel(g, true, st, 2, &ma);
+            int rc = time_kernel(g, false, adj_out, st, 2, &mf);
+            if (rc == EI_OK) rc = time_kernel(g, true, adj_out, st, 2, &ma);
             if (rc != EI_OK) return rc;
             tf[pers] = std::min(tf[pers], mf);
             ta[pers] = std::min(ta[pers], ma);
         }
     const int bp = tf[1] + ta[1] < (tf[0] + ta[0]) * kTuneMargin ? 1 : 0;
-    const int bf = fid[bp], ba = aid[bp];
-    const double best_f = tf[bp], best_a = ta[bp];
-    select_variants(g, bf, ba, bp != 0);
-    if (!(flags & EI_TUNE_NO_CACHE_WRITE)) {
-        const size_t slash = path.find_last_of('/');
-        if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
-        FILE *f = fopen(path.c_str(), "a");       // best effort: no cache if not writable
-        if (f) {
-            fprintf(f, "%s %d %d %d %.6f %.6f\n", key.c_str(), bf, ba, bp, best_f, best_a);
-            fclose(f);
-        }
-    }
+    select_variants(g, fid[bp], aid[bp], bp != 0);
+    g_tune_last[0] = tf[bp];
+    g_tune_last[1] = ta[bp];
     return EI_OK;
 }
 
@@ -804,8 +833,7 @@ int ei_backproject(const ei_geometry *gc, const float *sino4, float *vol, void *
     count_launches(g, 1);
     cudaError_t e = launch_pack_sino(g, (const float4 *)sino4, st);
     if (e == cudaSuccess)
-        e = traced_backproject(g, true, nullptr, (float4 *)vol, one, zero, zero, 0.f, g->part_adj,
-                               nullptr, st);
+        e = traced_backproject(g, nullptr, (float4 *)vol, one, zero, 0.f, nullptr, st);
     return status_from(e);
 }
 
@@ -826,8 +854,7 @@ int ei_single_shot_fbp(const ei_geometry *gc, const float *s_exp, float *vol_out
     count_launches(g, 1);
     cudaError_t e = launch_single_shot(g, s_exp, st);
     if (e == cudaSuccess)
-        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, 0.f,
-                               g->part_adj, nullptr, st);
+        e = traced_backproject(g, nullptr, (float4 *)vol_out, one, zero, 0.f, nullptr, st);
     return status_from(e);
 }
 
@@ -858,8 +885,7 @@ int ei_single_shot_eq3(ei_geometry *g, const float *s_exp, int m_index, double g
     count_launches(g, 2);
     e = launch_single_shot_eq3(g, s_exp, m_index, (float)gamma, g->eq3_ker, st);
     if (e == cudaSuccess)
-        e = traced_backproject(g, true, nullptr, (float4 *)vol_out, one, zero, zero, 0.f,
-                               g->part_adj, nullptr, st);
+        e = traced_backproject(g, nullptr, (float4 *)vol_out, one, zero, 0.f, nullptr, st);
     return status_from(e);
 }
 
@@ -882,6 +908,15 @@ int ei_set_offset_unknowns(ei_geometry *g, int which, double scale)
         return EI_ERR_ARG;
     g->off_which = which;
     g->off_scale = (float)scale;
+    return EI_OK;
+}
+
+int ei_set_ring_modes(ei_geometry *g, int K)
+{
+    if (!g || K < 0 || K > EI_MAX_RING_MODES) return EI_ERR_ARG;
+    for (const SliceInfo &si : g->h_slices)
+        if (K > si.n_det) return EI_ERR_ARG;
+    g->ring_modes = K;
     return EI_OK;
 }
 

@@ -107,9 +107,10 @@ constexpr int VEC_THREADS = 256;
 // Kernel variants the autotuner chooses among (instantiated in k_project.cu /
 // k_backproject.cu).  Each has its own work decomposition.
 constexpr int N_FWD_VARIANTS = 13;          // projector tile (rays x angles, warp shape, unroll)
-constexpr int N_ADJ_VARIANTS = 8;          // adjoint voxels per thread and occupancy
+constexpr int N_ADJ_VARIANTS = 11;         // adjoint voxels per thread and occupancy
 void project_variant_shape(int id, int *rays, int *angles);
 int backproject_variant_rows(int id);
+int backproject_variant_items(int id, int n);
 
 struct FwdVariant {
     int id = 0;
@@ -181,7 +182,7 @@ struct ei_geometry {
     float4 *gA = nullptr;          // packed gradient sinogram
     float2 *gB = nullptr;
     double *part_ic = nullptr;     // [total_ic]
-    double *part_adj = nullptr;    // [total_adj]
+    double *part_reg = nullptr;    // [total_vec] regulariser partial sums
     double *S_dev = nullptr;       // [n_slices]
     int64_t vol_count = 0, pp_count = 0, gp_count = 0, proj_count = 0, sino4_count = 0,
             meas_count = 0;
@@ -199,6 +200,7 @@ struct ei_geometry {
     float link_gamma = 0.f;            // > 0: linked unknown h (mu = h, delta = gamma h, sigma = 0)
     int off_which = 0;                 // Eq. 4 offsets among the solver's unknowns (EI_OFFSET_*)
     float off_scale = 1.f;             // their solver scaling u = m / off_scale
+    int ring_modes = 0;                // m_r steps orthogonal to the K lowest DCT-II modes
     float *shift_scratch = nullptr;    // [sino4_count] dS/dshift (ei_offset_grad, allocated on use)
     double *row_sums = nullptr;        // [total_ic]
     float *eq3_ker = nullptr;          // [sum n_det] Eq. 3 convolution kernels (allocated on use)
@@ -255,14 +257,18 @@ cudaError_t launch_single_shot_eq3(const ei_geometry *g, const float *meas, int 
 bool single_shot_eq3_fits(const ei_geometry *g);
 // Packed gradient sinogram from a user sino4 array.
 cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStream_t st);
-// out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram); per-tile partial
-// sums of sum_c reg1_c v_c^2.  with_sino == false: only the regulariser (out not written).
+// out = out_mult * R^T g + reg2 * v (g: the packed gradient sinogram; v may be null).
 // link > 0 (the linked unknown h of Eq. 4; gB then holds the single sinogram
 // g_mu + link g_delta that launch_ic wrote): out = (out_mult.x R^T g + reg2.x v.x,
-// 0, 0, 0) and the partial sums take the mu lane only.
-cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
-                               float4 *out, float4 out_mult, float4 reg2, float4 reg1, float link,
-                               double *part, const int *active, cudaStream_t st);
+// 0, 0, 0).
+cudaError_t launch_backproject(const ei_geometry *g, const float4 *v, float4 *out,
+                               float4 out_mult, float4 reg2, float link, const int *active,
+                               cudaStream_t st);
+// The regulariser's value: per vector block of dg (volume blocks; an offsets
+// block of a solver view writes 0) the FP64 sum of sum_c reg1_c v_c^2 over its
+// voxels, into part[block].
+cudaError_t launch_reg_partials(const DevGeom &dg, const float4 *v, float4 reg1, double *part,
+                                const int *active, cudaStream_t st);
 // dS/dshift per sinogram pixel into shift (sino layout, one float per pixel) and its
 // FP64 sum over each row into row_sum; then per slice dS/dm_o (the row sums) into
 // g_mo [sum n_theta] and dS/dm_r (FP64 sums over angles) into g_mr [sum n_det].
@@ -273,10 +279,23 @@ cudaError_t launch_offset_grads(const ei_geometry *g, const float *proj, const f
 // dS/dshift into shift, its row sums into row_sum.
 cudaError_t launch_shift_grad(const ei_geometry *g, const float *proj, const float *meas,
                               float *shift, double *row_sum, const int *active, cudaStream_t st);
-// S[s] = sum of part_ic over the slice's rows + sum of part_adj over its tiles.
+// S[s] = sum of part_ic over the slice's rows + sum of part_reg over its vector
+// blocks reg_prefix[s] .. reg_prefix[s + 1] - 1 (device prefix table).
 cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_ic,
-                                      const double *part_adj, double *S, const int *active,
-                                      cudaStream_t st);
+                                      const int *reg_prefix, const double *part_reg, double *S,
+                                      const int *active, cudaStream_t st);
+
+// The constants an evaluation stages and finishes with.  scaled == false: the
+// unknown is the physical x (regulariser lambda ||x / scale||^2); scaled ==
+// true: u = x / scale (the solver's).  Linked mode: h in the mu lane.
+struct EvalConsts {
+    float4 mult;       // staging multipliers (projections of mult * v)
+    float4 out_mult;   // adjoint: out = out_mult R^T g + reg2 v
+    float4 reg2;
+    float4 reg1;       // regulariser's value: sum_c reg1_c v_c^2
+    float link;        // gamma of the linked unknown, 0 otherwise
+};
+EvalConsts eval_consts(const ei_geometry *g, bool scaled);
 
 // S (and grad when non-null) for every active slice, on the geometry's workspace.
 // scaled == false: v is the physical x (P = R x, grad wrt x, regulariser on x/scale).

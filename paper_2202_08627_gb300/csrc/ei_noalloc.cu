@@ -2,19 +2,18 @@
 // device allocation.  Every intermediate (geometry tables, staged volume,
 // projections, gradient sinogram, partial sums) lives in one file-scope
 // __device__ array of EI_NOALLOC_SCRATCH_BYTES; the kernels are the same ones
-// ei_objective_grad runs.
+// ei_objective_grad runs (variant 0 of each).
 //
-// Who needs this: code that runs while a CUDA stream is being captured into a
-// graph (cudaMalloc cannot be captured), frameworks that have reserved the
-// device memory in their own pool and forbid allocations outside it, and
-// latency-sensitive loops that cannot afford cudaMalloc's implicit device
-// synchronisation.  Such callers cannot call ei_setup_geometry either (it
-// allocates the workspace), so this entry point takes the geometry
-// description directly.
+// Who needs this: callers that may not allocate GPU memory themselves, such
+// as frameworks that have reserved the device memory for their own pool and
+// forbid allocations outside it, and latency-sensitive loops that cannot
+// afford cudaMalloc's implicit device synchronisation.  Such callers cannot
+// call ei_setup_geometry either (it allocates the workspace), so this entry
+// point takes the geometry description directly.
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
+#include <vector>
 
 #include "ei_internal.h"
 
@@ -25,30 +24,9 @@ cudaError_t ic_set_smem_limit();
 namespace {
 
 // The scratch array.  In host code `g_scratch` only names the symbol; its
-// device address comes from cudaGetSymbolAddress (see scratch_for_device).
+// device address in the current context comes from cudaGetSymbolAddress,
+// which every call asks for (a cached address would outlive a context reset).
 __device__ __align__(256) unsigned char g_scratch[EI_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char *g_dev_ptr[kMaxDevices] = {};
-
-// Once per device, with that device current: resolve the scratch address and
-// raise the IC kernel's shared-memory limit.
-cudaError_t scratch_for_device(int dev, unsigned char **out)
-{
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_dev_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        e = ic_set_smem_limit();
-        if (e != cudaSuccess) return e;
-        g_dev_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_dev_ptr[dev];
-    return cudaSuccess;
-}
 
 // Bump allocator over the scratch array (256-byte aligned pieces).
 struct Carver {
@@ -61,34 +39,18 @@ struct Carver {
     }
 };
 
-struct Counts {
-    int c[5];   // work items of the projector, IC rows, adjoint tiles, staging tiles, vector blocks
-};
-
-// Geometry tables of one slice, written on the device from the description
-// (same formulas as ei_setup_geometry's host code).
-__global__ void k_noalloc_tables(SliceInfo si, double pitch, const double *theta, int uniform_theta,
-                                 const float *fA, const float *fc, const float *fw,
-                                 const float *mo, const float *mr, AngleInfo *ang, float *m_o,
-                                 float4 *pix, SliceInfo *slices, int *prefixes, Counts counts)
+// n floats from host or device memory into dst, ordered after the work queued
+// on st (false: not a valid pointer, or the copy failed).
+bool fetch(const float *src, int n, std::vector<float> &dst, cudaStream_t st)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    for (int a = tid; a < si.n_theta; a += stride) {
-        const double th = uniform_theta ? a * 3.141592653589793 / si.n_theta : theta[a];
-        ang[a] = make_angle_info(th, si.n, pitch);
-        m_o[a] = mo ? mo[a] : 0.f;
+    dst.resize(n);
+    cudaError_t e = cudaMemcpyAsync(dst.data(), src, (size_t)n * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-    for (int j = tid; j < si.n_dp; j += stride)
-        pix[j] = j < si.n_det ? make_float4(fA[j], fc[j], fw[j], mr ? mr[j] : 0.f)
-                              : make_float4(0.f, 0.f, 1.f, 0.f);
-    if (tid == 0) {
-        slices[0] = si;
-        for (int k = 0; k < 5; ++k) {
-            prefixes[2 * k] = 0;
-            prefixes[2 * k + 1] = counts.c[k];
-        }
-    }
+    return true;
 }
 
 int status_of(cudaError_t e)
@@ -105,19 +67,26 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
                                          const float *s_exp, double *S_out, float *grad,
                                          void *stream)
 {
-    // ---- arguments (nothing touches the GPU before these pass)
+    // ---- arguments (nothing is queued on the GPU before these pass; the same
+    // checks as ei_setup_geometry)
     if (!d || !vol || !s_exp || !S_out) return EI_ERR_ARG;
     if ((((uintptr_t)vol) & 15u) || (((uintptr_t)s_exp) & 15u) || (grad && (((uintptr_t)grad) & 15u)))
         return EI_ERR_ARG;
     if (d->n < 1 || d->n > 16384 || d->n_theta < 1 || d->n_det < 1 || d->n_det > EI_MAX_NDET ||
         !(d->pitch_cm > 0) || !isfinite(d->pitch_cm) || d->n_m < 1 || d->n_m > EI_MAX_NM || !d->m ||
-        !(d->z_cm >= 0) || !(d->period_cm > 0) || !(d->kappa_sigma >= 0) || !d->flat_A ||
-        !d->flat_c || !d->flat_w)
+        !(d->z_cm >= 0) || !isfinite(d->z_cm) || !(d->period_cm > 0) || !isfinite(d->period_cm) ||
+        !(d->kappa_sigma >= 0) || !isfinite(d->kappa_sigma) || !d->flat_A || !d->flat_c ||
+        !d->flat_w)
         return EI_ERR_ARG;
     for (int c = 0; c < 3; ++c)
-        if (!(d->scale[c] > 0) || !(d->lambda[c] >= 0) || !isfinite(d->lambda[c])) return EI_ERR_ARG;
+        if (!(d->scale[c] > 0) || !isfinite(d->scale[c]) || !(d->lambda[c] >= 0) ||
+            !isfinite(d->lambda[c]))
+            return EI_ERR_ARG;
     for (int k = 0; k < d->n_m; ++k)
         if (!isfinite(d->m[k])) return EI_ERR_ARG;
+    if (d->theta)
+        for (int a = 0; a < d->n_theta; ++a)
+            if (!isfinite(d->theta[a])) return EI_ERR_ARG;
 
     const int n = d->n, nth = d->n_theta, nd = d->n_det, ndp = (nd + 3) / 4 * 4;
     SliceInfo si{};
@@ -138,9 +107,8 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     // default kernel variants (0): their work decompositions
     int rays = 0, angles = 0;
     project_variant_shape(0, &rays, &angles);
-    const int adj_rows = backproject_variant_rows(0);
     const int n_fwd = ((nth + angles - 1) / angles) * ((ndp + rays - 1) / rays);
-    const int n_adj = ((n + ADJ_TC - 1) / ADJ_TC) * ((n + adj_rows - 1) / adj_rows);
+    const int n_adj = backproject_variant_items(0, n);
     const int pt = (n + 1 + PREP_TILE - 1) / PREP_TILE;
     const int n_prep = pt * pt;
     const int n_vec = (int)(((int64_t)n * n + VEC_BLK - 1) / VEC_BLK);
@@ -153,10 +121,6 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     const size_t o_ang = cv.take((size_t)nth * sizeof(AngleInfo));
     const size_t o_mo = cv.take((size_t)nth * sizeof(float));
     const size_t o_pix = cv.take((size_t)ndp * sizeof(float4));
-    const size_t o_theta = cv.take(d->theta ? (size_t)nth * sizeof(double) : 0);
-    const size_t o_flat = cv.take((size_t)3 * nd * sizeof(float));
-    const size_t o_mos = cv.take(d->m_o ? (size_t)nth * sizeof(float) : 0);
-    const size_t o_mrs = cv.take(d->m_r ? (size_t)nd * sizeof(float) : 0);
     const size_t o_xpA = cv.take((size_t)pp * sizeof(float4));
     const size_t o_xtA = cv.take((size_t)pp * sizeof(float4));
     const size_t o_xpB = cv.take((size_t)pp * sizeof(float2));
@@ -165,54 +129,75 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     const size_t o_gA = cv.take((size_t)gp * sizeof(float4));
     const size_t o_gB = cv.take((size_t)gp * sizeof(float2));
     const size_t o_pic = cv.take((size_t)nth * sizeof(double));
-    const size_t o_pad = cv.take((size_t)n_adj * sizeof(double));
+    const size_t o_preg = cv.take((size_t)n_vec * sizeof(double));
     const size_t o_S = cv.take(sizeof(double));
     if (cv.used > (size_t)EI_NOALLOC_SCRATCH_BYTES) return EI_ERR_ARG;
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return EI_ERR_CUDA;
-    unsigned char *base = nullptr;
-    e = scratch_for_device(dev, &base);
-    if (e != cudaSuccess) return EI_ERR_CUDA;
+    // ---- the per-pixel and per-angle inputs (host or device arrays), checked
+    // and tabulated on the host exactly as ei_setup_geometry does
     cudaStream_t st = (cudaStream_t)stream;
-
-    // ---- inputs of the tables (host or device arrays) into the scratch
-    float *flat = (float *)(base + o_flat);
-    e = cudaMemcpyAsync(flat, d->flat_A, nd * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(flat + nd, d->flat_c, nd * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(flat + 2 * nd, d->flat_w, nd * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess && d->theta)
-        e = cudaMemcpyAsync(base + o_theta, d->theta, nth * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && d->m_o)
-        e = cudaMemcpyAsync(base + o_mos, d->m_o, nth * sizeof(float), cudaMemcpyDefault, st);
-    if (e == cudaSuccess && d->m_r)
-        e = cudaMemcpyAsync(base + o_mrs, d->m_r, nd * sizeof(float), cudaMemcpyDefault, st);
-    // the gradient sinogram's margins and padding must read as zero; the scratch keeps
-    // whatever the previous call left, so clear it
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gA, 0, (size_t)gp * sizeof(float4), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gB, 0, (size_t)gp * sizeof(float2), st);
-    if (e != cudaSuccess) return status_of(e);
-
+    std::vector<float> fA, fc, fw, fmo, fmr;
+    if (!fetch(d->flat_A, nd, fA, st) || !fetch(d->flat_c, nd, fc, st) || !fetch(d->flat_w, nd, fw, st) ||
+        (d->m_o && !fetch(d->m_o, nth, fmo, st)) || (d->m_r && !fetch(d->m_r, nd, fmr, st)))
+        return EI_ERR_ARG;
+    for (int j = 0; j < nd; ++j)
+        if (!(fw[j] > 0) || !isfinite(fA[j]) || !isfinite(fc[j])) return EI_ERR_ARG;
+    std::vector<AngleInfo> ang(nth);
+    std::vector<float> m_o(nth);
+    for (int a = 0; a < nth; ++a) {
+        const double th = d->theta ? d->theta[a] : a * M_PI / nth;
+        ang[a] = make_angle_info(th, n, d->pitch_cm);
+        m_o[a] = d->m_o ? fmo[a] : 0.f;
+    }
+    std::vector<float4> pix(ndp);
+    for (int j = 0; j < ndp; ++j)
+        pix[j] = j < nd ? make_float4(fA[j], fc[j], fw[j], d->m_r ? fmr[j] : 0.f)
+                        : make_float4(0.f, 0.f, 1.f, 0.f);
     si.ang_off = 0;
     si.pix_off = 0;
+    si.det_off = 0;
     si.vol_off = 0;
     si.pp_off = 0;
     si.gp_off = 0;
     si.sino_off = 0;
     si.proj_off = 0;
     si.meas_off = 0;
-    int *pref = (int *)(base + o_pref);
-    const Counts counts{{n_fwd, nth, n_adj, n_prep, n_vec}};
-    k_noalloc_tables<<<std::max(1, (std::max(nth, ndp) + 255) / 256), 256, 0, st>>>(
-        si, d->pitch_cm, d->theta ? (const double *)(base + o_theta) : nullptr, d->theta ? 0 : 1,
-        flat, flat + nd, flat + 2 * nd, d->m_o ? (const float *)(base + o_mos) : nullptr,
-        d->m_r ? (const float *)(base + o_mrs) : nullptr, (AngleInfo *)(base + o_ang),
-        (float *)(base + o_mo), (float4 *)(base + o_pix), (SliceInfo *)(base + o_slice), pref,
-        counts);
-    e = cudaGetLastError();
+    // work-item prefix tables [0, count] of the projector, IC rows, adjoint,
+    // staging tiles and vector blocks
+    const int pref_h[10] = {0, n_fwd, 0, nth, 0, n_adj, 0, n_prep, 0, n_vec};
+
+    // ---- the scratch array's address in the current context
+    unsigned char *base = nullptr;
+    {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return EI_ERR_CUDA;
+        }
+        base = static_cast<unsigned char *>(p);
+    }
+    if (ic_set_smem_limit() != cudaSuccess) {
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EI_ERR_CUDA;
+
+    // ---- tables into the scratch (the host buffers may be released once a
+    // pageable copy returns); the gradient sinogram's margins and padding must
+    // read as zero, and the scratch keeps whatever the previous call left, so
+    // clear it
+    cudaError_t e = cudaMemcpyAsync(base + o_slice, &si, sizeof si, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_pref, pref_h, sizeof pref_h, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_ang, ang.data(), nth * sizeof(AngleInfo), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_mo, m_o.data(), nth * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_pix, pix.data(), ndp * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gA, 0, (size_t)gp * sizeof(float4), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gB, 0, (size_t)gp * sizeof(float2), st);
     if (e != cudaSuccess) return status_of(e);
 
     // ---- a geometry view over the scratch (no host or device allocation)
@@ -224,6 +209,7 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
         g.lambda[c] = (float)d->lambda[c];
         g.scale[c] = (float)d->scale[c];
     }
+    int *pref = (int *)(base + o_pref);
     DevGeom &dg = g.dg;
     dg.slices = (const SliceInfo *)(base + o_slice);
     dg.ang = (const AngleInfo *)(base + o_ang);
@@ -256,7 +242,7 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     g.gA = (float4 *)(base + o_gA);
     g.gB = (float2 *)(base + o_gB);
     g.part_ic = (double *)(base + o_pic);
-    g.part_adj = (double *)(base + o_pad);
+    g.part_reg = (double *)(base + o_preg);
     g.S_dev = (double *)(base + o_S);
     g.vol_count = (int64_t)n * n;
 

@@ -26,9 +26,11 @@
 // writes that single sinogram, pair-packed, and the linked instantiation loads
 // one 8-B entry per voxel and angle (a third of the bytes) and does 2 FMAs.
 //
-// Also fused: out = out_mult * R^T g + reg2 * v (the regulariser's gradient)
-// and per-tile FP64 partial sums of sum_c reg1_c v_c^2 (its value); v may be
-// null (no regulariser).
+// Also fused: out = out_mult * R^T g + reg2 * v (the regulariser's gradient;
+// v may be null).  The regulariser's value sum_c lambda_c ||u_c||^2 is summed
+// elsewhere (k_reg_partials, or the solver's trial-point kernel), so that the
+// objective at a point never needs this kernel: the solver runs it only where
+// a line-search trial was accepted.
 #include <algorithm>
 
 #include "ei_internal.h"
@@ -37,7 +39,7 @@ namespace ei {
 
 constexpr int ADJ_CHUNK = 128;           // angles staged per shared-memory chunk
 
-__device__ __forceinline__ double block_sum_double_adj(double v, double *red)
+__device__ __forceinline__ double block_sum_double_fin(double v, double *red)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -53,9 +55,26 @@ __device__ __forceinline__ double block_sum_double_adj(double v, double *red)
 
 struct AdjShared {
     float4 cs[ADJ_CHUNK];   // cos, sin, pitch/(ch*ch), pitch/ch
-    float4 jp[ADJ_CHUNK];   // J (int bits), phi, pitch/ch - pitch/(ch*ch), -
-    double red[32];
+    float4 jp[ADJ_CHUNK];   // J (int bits), phi, pitch/ch - pitch/(ch*ch), mirror variant: phi_B
+    int jb[ADJ_CHUNK];      // mirror variant: J_B
 };
+
+// One voxel's output: out = out_mult R^T g + reg2 v; linked: the unknown h
+// in the mu lane, dS/dh = R^T (g_mu + link g_delta), the sinogram the IC
+// kernel combined.
+template <bool LINKED>
+__device__ __forceinline__ void adj_store(float4 *__restrict__ out, int64_t idx,
+                                          const float4 *__restrict__ v, const float (&acc)[3],
+                                          float4 out_mult, float4 reg2)
+{
+    const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (LINKED)
+        out[idx] = make_float4(fmaf(out_mult.x, acc[0], reg2.x * x.x), 0.f, 0.f, 0.f);
+    else
+        out[idx] = make_float4(fmaf(out_mult.x, acc[0], reg2.x * x.x),
+                               fmaf(out_mult.y, acc[1], reg2.y * x.y),
+                               fmaf(out_mult.z, acc[2], reg2.z * x.z), 0.f);
+}
 
 // One work item: a 32-column x (8 PASSES)-row voxel tile, 8 x 4 voxel patch per
 // warp and pass, one voxel per thread and pass.  Lanes run along the patch's
@@ -67,9 +86,8 @@ struct AdjShared {
 template <int PASSES, bool QUAD, bool LINKED>
 __device__ __forceinline__ void backproject_single_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
-    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
-    double *__restrict__ part, const int *__restrict__ active)
+    const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
+    float4 out_mult, float4 reg2, const int *__restrict__ active)
 {
     constexpr int TR = 8 * PASSES;
     const int s = find_slice(prefix, dg.n_slices, item);
@@ -88,7 +106,7 @@ __device__ __forceinline__ void backproject_single_item(
 #pragma unroll
     for (int p = 0; p < PASSES; ++p) acc[p][0] = acc[p][1] = acc[p][2] = 0.f;
 
-    if (with_sino) {
+    {
         const float4 *rowA0 = gA + si.gp_off + si.marg;
         const float2 *rowB0 = gB + si.gp_off + si.marg;
         const long long two_ct = 2LL * c_t - (n - 1);              // 2 (c_t - hn)
@@ -143,32 +161,15 @@ __device__ __forceinline__ void backproject_single_item(
         }
     }
 
-    double regv = 0.0;
     const int c = c_t + dc;
 #pragma unroll
     for (int p = 0; p < PASSES; ++p) {
         const int r = r_t + dr0 + 8 * p;
         if (r < n && c < n) {
             const int64_t idx = si.vol_off + (int64_t)r * n + c;
-            const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (LINKED) {
-                // linked unknown h in the mu lane: dS/dh = R^T (g_mu + link g_delta),
-                // the sinogram the IC kernel combined
-                regv += (double)(reg1.x * x.x * x.x);
-                if (with_sino && out != nullptr)
-                    out[idx] = make_float4(fmaf(out_mult.x, acc[p][0], reg2.x * x.x), 0.f, 0.f, 0.f);
-            } else {
-                regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
-                        (double)(reg1.z * x.z * x.z);
-                if (with_sino && out != nullptr)
-                    out[idx] = make_float4(fmaf(out_mult.x, acc[p][0], reg2.x * x.x),
-                                           fmaf(out_mult.y, acc[p][1], reg2.y * x.y),
-                                           fmaf(out_mult.z, acc[p][2], reg2.z * x.z), 0.f);
-            }
+            adj_store<LINKED>(out, idx, v, acc[p], out_mult, reg2);
         }
     }
-    const double tot = block_sum_double_adj(regv, sh.red);
-    if (threadIdx.x == 0) part[item] = tot;
 }
 
 // Voxel pairs.  Two horizontally adjacent voxels project |cos| <= 1 pixel
@@ -223,9 +224,8 @@ __device__ __forceinline__ void pair_angle(float (&acc)[PASSES][2][3], const flo
 template <int PASSES, bool LINKED, int COMPACT>
 __device__ __forceinline__ void backproject_pair_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
-    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
-    double *__restrict__ part, const int *__restrict__ active)
+    const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
+    float4 out_mult, float4 reg2, const int *__restrict__ active)
 {
     constexpr int TR = 16 * PASSES;
     const int s = find_slice(prefix, dg.n_slices, item);
@@ -254,7 +254,7 @@ __device__ __forceinline__ void backproject_pair_item(
 #pragma unroll
         for (int h = 0; h < 2; ++h) acc[p][h][0] = acc[p][h][1] = acc[p][h][2] = 0.f;
 
-    if (with_sino) {
+    {
         const float4 *rowA0 = gA + si.gp_off + si.marg;
         const float2 *rowB0 = gB + si.gp_off + si.marg;
         const long long two_ct = 2LL * c_t - (n - 1);              // 2 (c_t - hn)
@@ -293,7 +293,6 @@ __device__ __forceinline__ void backproject_pair_item(
         }
     }
 
-    double regv = 0.0;
 #pragma unroll
     for (int p = 0; p < PASSES; ++p) {
         const int r = r_t + dr0 + 16 * p;
@@ -302,55 +301,228 @@ __device__ __forceinline__ void backproject_pair_item(
             const int c = c_t + dc + h;
             if (r < n && c < n) {
                 const int64_t idx = si.vol_off + (int64_t)r * n + c;
-                const float4 x = v ? v[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (LINKED) {
-                    regv += (double)(reg1.x * x.x * x.x);
-                    if (with_sino && out != nullptr)
-                        out[idx] = make_float4(fmaf(out_mult.x, acc[p][h][0], reg2.x * x.x), 0.f, 0.f, 0.f);
-                } else {
-                    regv += (double)(reg1.x * x.x * x.x) + (double)(reg1.y * x.y * x.y) +
-                            (double)(reg1.z * x.z * x.z);
-                    if (with_sino && out != nullptr)
-                        out[idx] = make_float4(fmaf(out_mult.x, acc[p][h][0], reg2.x * x.x),
-                                               fmaf(out_mult.y, acc[p][h][1], reg2.y * x.y),
-                                               fmaf(out_mult.z, acc[p][h][2], reg2.z * x.z), 0.f);
-                }
+                adj_store<LINKED>(out, idx, v, acc[p][h], out_mult, reg2);
             }
         }
     }
-    const double tot = block_sum_double_adj(regv, sh.red);
-    if (threadIdx.x == 0) part[item] = tot;
+}
+
+// Mirror images.  Voxel (x, y) of a slice, in pitch units about its centre,
+// projects to u(x, y) = hd + x cos + y sin; its point mirror (-x, -y) to
+// 2 hd - u = (n_det - 1) - u.  With u = j + d the mirror's taps are pixels
+// n_det - 1 - j and n_det - 2 - j with the SAME hat weights (the entry
+// weights depend on |u - j| only), so one detector-coordinate split and one
+// weight computation serve a voxel and its point mirror.  A thread owns a
+// voxel pair of the slice's top-left quadrant (rows r < ceil(n / 2), columns
+// c < ceil(n / 2)) and the pair's three images: family A = the pair and its
+// point mirror, family B = its row mirror (x, -y) and that one's point mirror
+// (-x, y); each family needs one split per angle (two per 8 voxels instead
+// of four).  The point mirror of a pair is again a horizontally adjacent
+// pair, so its loads keep the pair shape (one entry and the second half of
+// the next), taken from the mirrored end of the row: the slot of pixel j + k
+// of the pair is pixel n_det - 1 - j - k of its image.  Every voxel is written
+// by exactly one (thread, image): the pair itself where it lies in the
+// quadrant, an image where it lies in the other half (an odd slice's centre
+// row and column belong to the quadrant).  The mirrored detector coordinate
+// is exact only up to FP32 rounding of d, so results agree with the other
+// variants to FP32 rounding, not bit for bit.
+template <bool LINKED, bool SWAP, int q0, int q1>
+__device__ __forceinline__ void mirror_pair_angle(float (&acc)[4][2][3], const float4 *rA,
+                                                  const float2 *rB, const float4 *mA,
+                                                  const float2 *mB, float vl, float a, float4 cs,
+                                                  float4 jp)
+{
+    // vl: detector position of the pair's lower-u voxel; a = |cos|; q0, q1:
+    // the acc indices of the pair (direct) and of its point mirror
+    const float fl = floorf(vl);
+    const int jj = (int)fl;
+    const float d0 = vl - fl;
+    float dh = d0 + a;
+    const bool o = dh >= 1.f;
+    dh = o ? dh - 1.f : dh;
+    const float w0l = fmaxf(0.f, fmaf(-d0, cs.z, cs.w)), w1l = fmaxf(0.f, fmaf(d0, cs.z, jp.z));
+    const float w0h = fmaxf(0.f, fmaf(-dh, cs.z, cs.w)), w1h = fmaxf(0.f, fmaf(dh, cs.z, jp.z));
+    const float s0 = o ? 0.f : w0h, s1 = o ? w0h : w1h, s2 = o ? w1h : 0.f;
+    // lower-u voxel: left unless cos < 0; acc[q1][h] holds the image of voxel h,
+    // which takes voxel h's weights at the mirrored pixels
+    constexpr int LO = SWAP ? 1 : 0, HI = SWAP ? 0 : 1;
+    if (LINKED) {
+        const float2 t = __ldg(rB + jj);                                         // slots 0, 1
+        const float g2 = __ldg(reinterpret_cast<const float *>(rB + jj + 1) + 1);      // slot 2
+        acc[q0][LO][0] = fmaf(w0l, t.x, fmaf(w1l, t.y, acc[q0][LO][0]));
+        acc[q0][HI][0] = fmaf(s0, t.x, fmaf(s1, t.y, fmaf(s2, g2, acc[q0][HI][0])));
+        const float2 u = __ldg(mB - jj);                                         // slots 2, 1
+        const float g0 = __ldg(reinterpret_cast<const float *>(mB - jj + 1) + 1);      // slot 0
+        acc[q1][LO][0] = fmaf(w0l, g0, fmaf(w1l, u.y, acc[q1][LO][0]));
+        acc[q1][HI][0] = fmaf(s0, g0, fmaf(s1, u.y, fmaf(s2, u.x, acc[q1][HI][0])));
+    } else {
+        const float4 ta = __ldg(rA + jj);       // slot 0 (mu, delta, sigma), slot 1 mu
+        const float2 tb = __ldg(rB + jj);       // slot 1 (delta, sigma)
+        const float m2 = __ldg(reinterpret_cast<const float *>(rA + jj + 1) + 3);  // slot 2 mu
+        const float2 tc = __ldg(rB + jj + 1);   // slot 2 (delta, sigma)
+        acc[q0][LO][0] = fmaf(w0l, ta.x, fmaf(w1l, ta.w, acc[q0][LO][0]));
+        acc[q0][LO][1] = fmaf(w0l, ta.y, fmaf(w1l, tb.x, acc[q0][LO][1]));
+        acc[q0][LO][2] = fmaf(w0l, ta.z, fmaf(w1l, tb.y, acc[q0][LO][2]));
+        acc[q0][HI][0] = fmaf(s0, ta.x, fmaf(s1, ta.w, fmaf(s2, m2, acc[q0][HI][0])));
+        acc[q0][HI][1] = fmaf(s0, ta.y, fmaf(s1, tb.x, fmaf(s2, tc.x, acc[q0][HI][1])));
+        acc[q0][HI][2] = fmaf(s0, ta.z, fmaf(s1, tb.y, fmaf(s2, tc.y, acc[q0][HI][2])));
+        const float4 ma = __ldg(mA - jj);       // slot 2 (mu, delta, sigma), slot 1 mu
+        const float2 mb = __ldg(mB - jj);       // slot 1 (delta, sigma)
+        const float n0 = __ldg(reinterpret_cast<const float *>(mA - jj + 1) + 3);  // slot 0 mu
+        const float2 mc = __ldg(mB - jj + 1);   // slot 0 (delta, sigma)
+        acc[q1][LO][0] = fmaf(w0l, n0, fmaf(w1l, ma.w, acc[q1][LO][0]));
+        acc[q1][LO][1] = fmaf(w0l, mc.x, fmaf(w1l, mb.x, acc[q1][LO][1]));
+        acc[q1][LO][2] = fmaf(w0l, mc.y, fmaf(w1l, mb.y, acc[q1][LO][2]));
+        acc[q1][HI][0] = fmaf(s0, n0, fmaf(s1, ma.w, fmaf(s2, ma.x, acc[q1][HI][0])));
+        acc[q1][HI][1] = fmaf(s0, mc.x, fmaf(s1, mb.x, fmaf(s2, ma.y, acc[q1][HI][1])));
+        acc[q1][HI][2] = fmaf(s0, mc.y, fmaf(s1, mb.y, fmaf(s2, ma.z, acc[q1][HI][2])));
+    }
+}
+
+// Voxel rows of a mirror-variant tile: 16 per pass.
+template <int PASSES, bool LINKED>
+__device__ __forceinline__ void backproject_mirror_item(
+    const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
+    const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
+    float4 out_mult, float4 reg2, const int *__restrict__ active)
+{
+    constexpr int TR = 16 * PASSES;
+    const int s = find_slice(prefix, dg.n_slices, item);
+    if (active && !active[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int n = si.n;
+    const int hq = (n + 1) >> 1;                        // quadrant: rows and columns [0, hq)
+    const int ntc = (hq + ADJ_TC - 1) / ADJ_TC;
+    const int local = item - prefix[s];
+    const int r_t = (local / ntc) * TR, c_t = (local % ntc) * ADJ_TC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // left voxel of the pair and its row at pass 0 (passes add 16): warps of
+    // 4 pairs x 8 rows, lanes in groups of 8 on 2 pairs x 4 rows
+    const int dc = (warp & 3) * 8 + 2 * (lane & 1) + 4 * ((lane >> 3) & 1);
+    const int dr0 = (warp >> 2) * 8 + ((lane >> 1) & 3) + 4 * (lane >> 4);
+
+    // acc[p][image][voxel of the pair (0 = left column)][channel]; images:
+    // 0 the pair (r, c..c+1), 1 its point mirror (n-1-r, n-1-c-h),
+    // 2 its row mirror (n-1-r, c..c+1), 3 that one's point mirror (r, n-1-c-h)
+    float acc[PASSES][4][2][3];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) acc[p][q][h][0] = acc[p][q][h][1] = acc[p][q][h][2] = 0.f;
+
+    {
+        const float4 *rowA0 = gA + si.gp_off + si.marg;
+        const float2 *rowB0 = gB + si.gp_off + si.marg;
+        const long long two_ct = 2LL * c_t - (n - 1);              // 2 (c_t - hn)
+        const long long two_rt = (long long)(n - 1) - 2LL * r_t;   // 2 (hn - r_t): family A
+        const long long hd2 = (long long)(si.n_det - 1) << 32;     // 2 hd in 32.32
+        const float fx = (float)dc, fy = (float)dr0;
+        const int nm3 = si.n_det - 3;                              // image of entry j: nm3 - j
+        for (int a0 = 0; a0 < si.n_theta; a0 += ADJ_CHUNK) {
+            const int na = min(ADJ_CHUNK, si.n_theta - a0);
+            __syncthreads();
+            if ((int)threadIdx.x < na) {
+                const AngleInfo an = dg.ang[si.ang_off + a0 + threadIdx.x];
+                // the detector coordinate at the two families' tile origins: family
+                // A's at row r_t, family B's at the mirrored row n - 1 - r_t
+                const long long UA = (two_ct * an.cos_fx + two_rt * an.sin_fx + hd2) >> 1;
+                const long long UB = (two_ct * an.cos_fx - two_rt * an.sin_fx + hd2) >> 1;
+                const float pi = an.pch * an.inv_ch;
+                sh.cs[threadIdx.x] = make_float4(an.cosf, an.sinf, pi, an.pch);
+                sh.jp[threadIdx.x] = make_float4(
+                    __int_as_float((int)(UA >> 32)),
+                    (float)(unsigned)(UA & 0xffffffffLL) * 2.3283064365386963e-10f, an.pch - pi,
+                    (float)(unsigned)(UB & 0xffffffffLL) * 2.3283064365386963e-10f);
+                sh.jb[threadIdx.x] = (int)(UB >> 32);
+            }
+            __syncthreads();
+            const float4 *rowA = rowA0 + (int64_t)a0 * si.gw;
+            const float2 *rowB = rowB0 + (int64_t)a0 * si.gw;
+            for (int k = 0; k < na; ++k) {
+                const float4 cs = sh.cs[k];
+                const float4 jp = sh.jp[k];
+                const int JA = __float_as_int(jp.x), JB = sh.jb[k];
+                // lower-u voxel of the pair at pass 0, family A (rows go down: y falls)
+                // and family B (the mirrored rows go up: y rises)
+                const float lo = fminf(cs.x, 0.f);
+                const float vA = fmaf(fx, cs.x, fmaf(-fy, cs.y, jp.y)) + lo;
+                const float vB = fmaf(fx, cs.x, fmaf(fy, cs.y, jp.w)) + lo;
+                const float step = 16.f * cs.y;
+                const float a = fabsf(cs.x);
+                const float4 *aA = rowA + JA, *aM = rowA + (nm3 - JA);
+                const float2 *bA = rowB + JA, *bM = rowB + (nm3 - JA);
+                const float4 *cA = rowA + JB, *cM = rowA + (nm3 - JB);
+                const float2 *dA = rowB + JB, *dM = rowB + (nm3 - JB);
+                if (cs.x >= 0.f) {
+#pragma unroll
+                    for (int p = 0; p < PASSES; ++p) {
+                        mirror_pair_angle<LINKED, false, 0, 1>(acc[p], aA, bA, aM, bM,
+                                                               fmaf((float)p, -step, vA), a, cs, jp);
+                        mirror_pair_angle<LINKED, false, 2, 3>(acc[p], cA, dA, cM, dM,
+                                                               fmaf((float)p, step, vB), a, cs, jp);
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < PASSES; ++p) {
+                        mirror_pair_angle<LINKED, true, 0, 1>(acc[p], aA, bA, aM, bM,
+                                                              fmaf((float)p, -step, vA), a, cs, jp);
+                        mirror_pair_angle<LINKED, true, 2, 3>(acc[p], cA, dA, cM, dM,
+                                                              fmaf((float)p, step, vB), a, cs, jp);
+                    }
+                }
+                rowA += si.gw;
+                rowB += si.gw;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const int r = r_t + dr0 + 16 * p, rm = n - 1 - r;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c_t + dc + h, cm = n - 1 - c;
+            const int64_t base = si.vol_off;
+            if (r < hq && c < hq) adj_store<LINKED>(out, base + (int64_t)r * n + c, v, acc[p][0][h], out_mult, reg2);
+            if (rm >= hq && cm >= hq) adj_store<LINKED>(out, base + (int64_t)rm * n + cm, v, acc[p][1][h], out_mult, reg2);
+            if (rm >= hq && c < hq) adj_store<LINKED>(out, base + (int64_t)rm * n + c, v, acc[p][2][h], out_mult, reg2);
+            if (r < hq && cm >= hq) adj_store<LINKED>(out, base + (int64_t)r * n + cm, v, acc[p][3][h], out_mult, reg2);
+        }
+    }
 }
 
 // LAY: 0 lanes along rows of 8 voxels, 1 lanes on 2 x 4 sub-patches, 2 voxel
 // pairs along rows, 3 voxel pairs on 4 x 4 sub-patches (warps of 16 x 4), 4 the
-// same sub-patches in warps of 8 x 8.
+// same sub-patches in warps of 8 x 8, 5 pairs with their mirror images.
 template <int PASSES, int LAY, bool LINKED>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
-    const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-    float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
-    double *__restrict__ part, const int *__restrict__ active)
+    const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
+    float4 out_mult, float4 reg2, const int *__restrict__ active)
 {
-    if constexpr (LAY >= 2)
-        backproject_pair_item<PASSES, LINKED, LAY - 2>(dg, prefix, item, sh, gA, gB, with_sino, v,
-                                                       out, out_mult, reg2, reg1, part, active);
+    if constexpr (LAY == 5)
+        backproject_mirror_item<PASSES, LINKED>(dg, prefix, item, sh, gA, gB, v, out, out_mult,
+                                                reg2, active);
+    else if constexpr (LAY >= 2)
+        backproject_pair_item<PASSES, LINKED, LAY - 2>(dg, prefix, item, sh, gA, gB, v, out,
+                                                       out_mult, reg2, active);
     else
-        backproject_single_item<PASSES, LAY == 1, LINKED>(dg, prefix, item, sh, gA, gB, with_sino,
-                                                          v, out, out_mult, reg2, reg1, part,
-                                                          active);
+        backproject_single_item<PASSES, LAY == 1, LINKED>(dg, prefix, item, sh, gA, gB, v, out,
+                                                          out_mult, reg2, active);
 }
 
 template <int PASSES, int MINB, int LAY, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ gA,
-              const float2 *__restrict__ gB, bool with_sino, const float4 *__restrict__ v,
-              float4 *__restrict__ out, float4 out_mult, float4 reg2, float4 reg1,
-              double *__restrict__ part, const int *__restrict__ active)
+              const float2 *__restrict__ gB, const float4 *__restrict__ v,
+              float4 *__restrict__ out, float4 out_mult, float4 reg2,
+              const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
-    backproject_item<PASSES, LAY, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, with_sino, v, out,
-                                          out_mult, reg2, reg1, part, active);
+    backproject_item<PASSES, LAY, LINKED>(dg, prefix, blockIdx.x, sh, gA, gB, v, out, out_mult,
+                                          reg2, active);
 }
 
 // Persistent: GPU-sized grid, blocks take tiles from a counter (0 before the
@@ -359,9 +531,8 @@ template <int PASSES, int MINB, int LAY, bool LINKED>
 __global__ void __launch_bounds__(ADJ_THREADS, MINB)
 k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int *counter,
                          const float4 *__restrict__ gA, const float2 *__restrict__ gB,
-                         bool with_sino, const float4 *__restrict__ v, float4 *__restrict__ out,
-                         float4 out_mult, float4 reg2, float4 reg1,
-                         double *__restrict__ part, const int *__restrict__ active)
+                         const float4 *__restrict__ v, float4 *__restrict__ out,
+                         float4 out_mult, float4 reg2, const int *__restrict__ active)
 {
     __shared__ AdjShared sh;
     __shared__ int s_item;
@@ -371,21 +542,20 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
         __syncthreads();
         const int item = s_item;
         if (item >= total) return;
-        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, with_sino, v, out,
-                                              out_mult, reg2, reg1, part, active);
+        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, v, out, out_mult,
+                                              reg2, active);
     }
 }
 
 template <int P, int M, int Q, bool L>
-static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const float4 *v,
-                                  float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                  double *part, const int *active, cudaStream_t st)
+static cudaError_t launch_bp_mode(const ei_geometry *g, const float4 *v, float4 *out,
+                                  float4 out_mult, float4 reg2, const int *active, cudaStream_t st)
 {
     const AdjVariant &av = g->adj_variant;
     if (av.total == 0) return cudaSuccess;
     if (!g->persistent) {
         k_backproject<P, M, Q, L><<<av.total, ADJ_THREADS, 0, st>>>(
-            g->dg, av.prefix, g->gA, g->gB, with_sino, v, out, out_mult, reg2, reg1, part, active);
+            g->dg, av.prefix, g->gA, g->gB, v, out, out_mult, reg2, active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)
@@ -394,47 +564,57 @@ static cudaError_t launch_bp_mode(const ei_geometry *g, bool with_sino, const fl
         const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
         EI_CUDA_TRY(cudaMemsetAsync(g->work_counter + 1, 0, sizeof(int), st));
         k_backproject_persistent<P, M, Q, L><<<grid, ADJ_THREADS, 0, st>>>(
-            g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, with_sino, v, out,
-            out_mult, reg2, reg1, part, active);
+            g->dg, av.prefix, av.total, g->work_counter + 1, g->gA, g->gB, v, out, out_mult, reg2,
+            active);
     }
     return cudaGetLastError();
 }
 
 template <int P, int M, int Q>
-static cudaError_t launch_bp_variant(const ei_geometry *g, bool with_sino, const float4 *v,
-                                     float4 *out, float4 out_mult, float4 reg2, float4 reg1,
-                                     float link, double *part, const int *active, cudaStream_t st)
+static cudaError_t launch_bp_variant(const ei_geometry *g, const float4 *v, float4 *out,
+                                     float4 out_mult, float4 reg2, float link, const int *active,
+                                     cudaStream_t st)
 {
     // link > 0: the linked single-channel gather over the combined sinogram
-    return link > 0.f
-               ? launch_bp_mode<P, M, Q, true>(g, with_sino, v, out, out_mult, reg2, reg1, part,
-                                               active, st)
-               : launch_bp_mode<P, M, Q, false>(g, with_sino, v, out, out_mult, reg2, reg1, part,
-                                                active, st);
+    return link > 0.f ? launch_bp_mode<P, M, Q, true>(g, v, out, out_mult, reg2, active, st)
+                      : launch_bp_mode<P, M, Q, false>(g, v, out, out_mult, reg2, active, st);
 }
 
-cudaError_t launch_backproject(const ei_geometry *g, bool with_sino, const float4 *v,
-                               float4 *out, float4 out_mult, float4 reg2, float4 reg1, float link,
-                               double *part, const int *active, cudaStream_t st)
+cudaError_t launch_backproject(const ei_geometry *g, const float4 *v, float4 *out,
+                               float4 out_mult, float4 reg2, float link, const int *active,
+                               cudaStream_t st)
 {
     switch (g->adj_variant.id) {
-    case 0: return launch_bp_variant<8, 4, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 1: return launch_bp_variant<4, 1, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 2: return launch_bp_variant<16, 2, 0>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 3: return launch_bp_variant<8, 4, 1>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 4: return launch_bp_variant<16, 2, 1>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 0: return launch_bp_variant<8, 4, 0>(g, v, out, out_mult, reg2, link, active, st);
+    case 1: return launch_bp_variant<4, 1, 0>(g, v, out, out_mult, reg2, link, active, st);
+    case 2: return launch_bp_variant<16, 2, 0>(g, v, out, out_mult, reg2, link, active, st);
+    case 3: return launch_bp_variant<8, 4, 1>(g, v, out, out_mult, reg2, link, active, st);
+    case 4: return launch_bp_variant<16, 2, 1>(g, v, out, out_mult, reg2, link, active, st);
     // voxel pairs, 4 passes of 16 rows
-    case 5: return launch_bp_variant<4, 4, 2>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    case 6: return launch_bp_variant<4, 4, 3>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
-    default: return launch_bp_variant<4, 4, 4>(g, with_sino, v, out, out_mult, reg2, reg1, link, part, active, st);
+    case 5: return launch_bp_variant<4, 4, 2>(g, v, out, out_mult, reg2, link, active, st);
+    case 6: return launch_bp_variant<4, 4, 3>(g, v, out, out_mult, reg2, link, active, st);
+    case 7: return launch_bp_variant<4, 4, 4>(g, v, out, out_mult, reg2, link, active, st);
+    // voxel pairs with their three mirror images, quadrant tiles of 16 or 32 rows
+    case 8: return launch_bp_variant<1, 4, 5>(g, v, out, out_mult, reg2, link, active, st);
+    case 9: return launch_bp_variant<1, 3, 5>(g, v, out, out_mult, reg2, link, active, st);
+    default: return launch_bp_variant<2, 2, 5>(g, v, out, out_mult, reg2, link, active, st);
     }
 }
 
 // Voxel rows per tile of adjoint variant `id` (see launch_backproject).
 int backproject_variant_rows(int id)
 {
-    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64, 64};
+    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64, 64, 16, 16, 32};
     return R[id];
+}
+
+// Work items (tiles) of adjoint variant `id` for an n x n slice: tiles of 32
+// columns over the slice, or (the mirror variants) over its top-left quadrant.
+int backproject_variant_items(int id, int n)
+{
+    const int tr = backproject_variant_rows(id);
+    const int ext = id >= 8 ? (n + 1) / 2 : n;
+    return ((ext + ADJ_TC - 1) / ADJ_TC) * ((ext + tr - 1) / tr);
 }
 
 // ----------------------------------------------------------------------------
@@ -467,11 +647,13 @@ cudaError_t launch_pack_sino(const ei_geometry *g, const float4 *sino4, cudaStre
 }
 
 // ----------------------------------------------------------------------------
-// S[s] = sum_rows part_ic + sum_tiles part_adj, one block per slice, fixed order.
+// S[s] = sum over the slice's rows of part_ic (the data term) + sum over its
+// blocks reg_prefix[s] .. reg_prefix[s + 1] - 1 of part_reg (the regulariser),
+// one block per slice, fixed order.
 // ----------------------------------------------------------------------------
-__global__ void k_finalize_objective(DevGeom dg, const int *__restrict__ adj_prefix,
+__global__ void k_finalize_objective(DevGeom dg, const int *__restrict__ reg_prefix,
                                      const double *__restrict__ part_ic,
-                                     const double *__restrict__ part_adj, double *__restrict__ S,
+                                     const double *__restrict__ part_reg, double *__restrict__ S,
                                      const int *__restrict__ active)
 {
     __shared__ double red[32];
@@ -480,18 +662,18 @@ __global__ void k_finalize_objective(DevGeom dg, const int *__restrict__ adj_pre
     double acc = 0.0;
     for (int i = dg.ic_prefix[s] + threadIdx.x; i < dg.ic_prefix[s + 1]; i += blockDim.x)
         acc += part_ic[i];
-    for (int i = adj_prefix[s] + threadIdx.x; i < adj_prefix[s + 1]; i += blockDim.x)
-        acc += part_adj[i];
-    const double tot = block_sum_double_adj(acc, red);
+    for (int i = reg_prefix[s] + threadIdx.x; i < reg_prefix[s + 1]; i += blockDim.x)
+        acc += part_reg[i];
+    const double tot = block_sum_double_fin(acc, red);
     if (threadIdx.x == 0) S[s] = tot;
 }
 
 cudaError_t launch_finalize_objective(const ei_geometry *g, const double *part_ic,
-                                      const double *part_adj, double *S, const int *active,
-                                      cudaStream_t st)
+                                      const int *reg_prefix, const double *part_reg, double *S,
+                                      const int *active, cudaStream_t st)
 {
-    k_finalize_objective<<<g->n_slices, 256, 0, st>>>(g->dg, g->adj_variant.prefix, part_ic,
-                                                       part_adj, S, active);
+    k_finalize_objective<<<g->n_slices, 256, 0, st>>>(g->dg, reg_prefix, part_ic, part_reg, S,
+                                                       active);
     return cudaGetLastError();
 }
 

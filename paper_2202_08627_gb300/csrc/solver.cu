@@ -11,10 +11,22 @@
 //   4. stop when (f - f_new) / max(|f|, |f_new|, 1) < tol or after max_iter.
 //
 // Execution: one "round" per host iteration = direction for the slices that
-// need one, one trial step + objective/gradient evaluation for every slice in
-// line search, Armijo test, and the memory update of accepted slices.  All
-// per-slice decisions are taken on the device by one-thread-per-slice scalar
-// kernels; the host reads back one summary word per round to stop.
+// need one, one trial step + objective evaluation for every slice in line
+// search, Armijo test, the gradient and the memory update of accepted slices.
+// All per-slice decisions are taken on the device by one-thread-per-slice
+// scalar kernels; the host reads back one summary word per round to stop.
+//
+// Radon calls per iteration (the paper removes superfluous ones, "Algorithmic
+// improvements"): R is linear, so along a search direction the projection of
+// a trial u + alpha d is P(u) + alpha P(d).  The solver keeps per slice Pu,
+// the projections at the current iterate, and Pt, those at the latest trial:
+// the first trial of an iteration is projected (prep + projector), and every
+// backtracking trial takes Pt <- Pu + (alpha / alpha_prev) (Pt - Pu), a
+// sinogram axpy, so the cost of a rejected trial is the IC kernel alone.  The
+// regulariser's value is summed by the trial-point kernel, and the adjoint
+// (the gradient) runs only for slices whose trial was accepted; Pu <- Pt then.
+// Each iteration's first trial is a fresh projection, so no rounding drift
+// accumulates in Pu across iterations.
 //
 // Vectors are the batched vol layout (float4 per voxel, pad lane kept at 0);
 // vector kernels work on VEC_BLK-element blocks that each belong to one slice
@@ -37,8 +49,12 @@ namespace ei {
 
 struct SliceState {
     double f, f_t, gd, gg, alpha, gamma, f0;
+    double alpha_p;             // the step of the trial whose projections Pt holds
+    double ratio;               // backtracking trial: alpha / alpha_p of the previous trial
     int k, count, head, trials;
     int status, converged, reset, evals;
+    int projections, adjoints;  // projector and adjoint evaluations of the slice
+    int pad_;
 };
 
 struct Solver {
@@ -50,6 +66,8 @@ struct Solver {
     double *row_sum = nullptr;          // [rows]
     float4 *u = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
     float4 *Sr = nullptr, *Yr = nullptr;    // rings of `ring` slots
+    float *Pu = nullptr, *Pt = nullptr;     // proj layout: projections of u and of the trial
+    double *part_reg = nullptr;             // [solver blocks] regulariser partial sums
     float *meas_stage = nullptr;            // device copy of host s_exp
     float4 *vol_stage = nullptr;            // device copy of host x0 / solution
     double *part[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -57,6 +75,7 @@ struct Solver {
     double *alpha_i = nullptr;              // [m][S]
     SliceState *st = nullptr;               // [S]
     int *mask_dir = nullptr, *mask_ls = nullptr, *mask_acc = nullptr;
+    int *mask_first = nullptr, *mask_bt = nullptr;   // trial projected / interpolated
     int *summary = nullptr;                 // [2]: slices still running, slices in line search
     int *summary_h = nullptr;               // pinned host copy
     cudaStream_t stream = nullptr;          // the solver's own stream (capturable)
@@ -70,14 +89,14 @@ struct SolverDev {
     int m, ring;
     double *rho, *alpha_i;
     SliceState *st;
-    int *mask_dir, *mask_ls, *mask_acc;
+    int *mask_dir, *mask_ls, *mask_acc, *mask_first, *mask_bt;
 };
 
 static SolverDev dev_view(const Solver *s)
 {
     return SolverDev{s->u,  s->g,  s->d,   s->xt,     s->gt,      s->Sr,   s->Yr,
                      s->vol_count, s->m, s->ring, s->rho, s->alpha_i, s->st,
-                     s->mask_dir, s->mask_ls, s->mask_acc};
+                     s->mask_dir, s->mask_ls, s->mask_acc, s->mask_first, s->mask_bt};
 }
 
 // --------------------------------------------------------------------------
@@ -87,6 +106,7 @@ struct VecBlock {
     int s;            // slice
     int64_t begin;    // first float4 (batched vol layout)
     int64_t end;      // one past the last
+    bool off;         // a block of the slice's offsets segment (not voxels)
 };
 
 __device__ __forceinline__ VecBlock vec_block(const DevGeom &dg)
@@ -100,8 +120,10 @@ __device__ __forceinline__ VecBlock vec_block(const DevGeom &dg)
         lb -= dg.vec_nvb[b.s];
         b.begin = dg.off_start[b.s] + lb * VEC_BLK;
         b.end = dg.off_start[b.s] + min((int64_t)dg.off_len[b.s], (lb + 1) * (int64_t)VEC_BLK);
+        b.off = true;
         return b;
     }
+    b.off = false;
     b.begin = si.vol_off + lb * VEC_BLK;
     b.end = si.vol_off + min(nvox, (lb + 1) * (int64_t)VEC_BLK);
     return b;
@@ -145,6 +167,73 @@ __device__ __forceinline__ int slot_of(const SolverDev &sv, int s, int i)
 }
 
 __device__ __forceinline__ float4 f4(float x, float y, float z) { return make_float4(x, y, z, 0.f); }
+
+// One voxel's regulariser term sum_c reg1_c x_c^2 (Eq. 5) in FP64; a lane
+// with a zero weight (the delta and sigma lanes of the linked unknown) adds
+// nothing, whatever it holds.
+__device__ __forceinline__ double reg_term(float4 x, float4 reg1)
+{
+    double r = (double)(reg1.x * x.x * x.x);
+    if (reg1.y != 0.f) r += (double)(reg1.y * x.y * x.y);
+    if (reg1.z != 0.f) r += (double)(reg1.z * x.z * x.z);
+    return r;
+}
+
+// The regulariser's value per vector block (0 for an offsets block).
+__global__ void k_reg_partials(DevGeom dg, const float4 *__restrict__ v, float4 reg1,
+                               double *__restrict__ part, const int *__restrict__ active)
+{
+    __shared__ double red[32];
+    const VecBlock b = vec_block(dg);
+    if (active && !active[b.s]) return;
+    double acc = 0.0;
+    if (!b.off)
+        for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) acc += reg_term(v[i], reg1);
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+cudaError_t launch_reg_partials(const DevGeom &dg, const float4 *v, float4 reg1, double *part,
+                                const int *active, cudaStream_t st)
+{
+    if (dg.total_vec == 0) return cudaSuccess;
+    k_reg_partials<<<dg.total_vec, VEC_THREADS, 0, st>>>(dg, v, reg1, part, active);
+    return cudaGetLastError();
+}
+
+// Sinogram rows of the trial projections Pt (one block per row (slice, angle),
+// all three planes; slices with mask[s], all when null):
+//   k_sino_backtrack: Pt = Pu + ratio (Pt - Pu), the projections of
+//     u + alpha d from those of u and of u + alpha_p d (R is linear);
+//   k_sino_commit:    Pu = Pt (the trial was accepted).
+template <bool COMMIT>
+__global__ void k_sino_rows(DevGeom dg, SolverDev sv, float *__restrict__ Pu,
+                            float *__restrict__ Pt, const int *__restrict__ mask)
+{
+    const int row = blockIdx.x;
+    const int s = find_slice(dg.ic_prefix, dg.n_slices, row);
+    if (mask && !mask[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int a = row - dg.ic_prefix[s];
+    const float r = COMMIT ? 0.f : (float)sv.st[s].ratio;
+    const int64_t plane = (int64_t)si.n_theta * si.n_dp;
+    const int nq = si.n_dp >> 2;
+    for (int c = 0; c < 3; ++c) {
+        // rows start on 16-byte boundaries (n_dp and every offset are multiples of 4)
+        float4 *u4 = reinterpret_cast<float4 *>(Pu + si.proj_off + c * plane + (int64_t)a * si.n_dp);
+        float4 *t4 = reinterpret_cast<float4 *>(Pt + si.proj_off + c * plane + (int64_t)a * si.n_dp);
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const float4 pt = t4[i];
+            if (COMMIT) {
+                u4[i] = pt;
+            } else {
+                const float4 pu = u4[i];
+                t4[i] = make_float4(fmaf(r, pt.x - pu.x, pu.x), fmaf(r, pt.y - pu.y, pu.y),
+                                    fmaf(r, pt.z - pu.z, pu.z), fmaf(r, pt.w - pu.w, pu.w));
+            }
+        }
+    }
+}
 
 // --------------------------------------------------------------------------
 // vector kernels
@@ -215,16 +304,25 @@ __global__ void k_offsets_apply(DevGeom dg, int which, float scale, const float4
     }
 }
 
+// Orthonormal DCT-II vector k of length n at j (the ring-mode basis).
+__device__ __forceinline__ double dct2_basis(int k, int j, int n)
+{
+    return sqrt((k == 0 ? 1.0 : 2.0) / n) * cospi((double)k * (j + 0.5) / n);
+}
+
 // the offsets segments of the gradient gv: scale * dS/dm_o (row sums of
 // dS/dshift) and scale * dS/dm_r (FP64 sums over the slice's angles in
-// order), the latter minus its mean over the slice when both offsets are
-// unknowns (the gauge (m_o + a, m_r - a) leaves S unchanged, so the iteration
-// keeps the mean of m_r fixed)
-__global__ void k_offsets_grad(DevGeom dg, int which, float scale, const float *__restrict__ shift,
-                               const double *__restrict__ row_sum, float4 *__restrict__ gv,
-                               const int *__restrict__ active)
+// order).  The latter is then restricted to ring frequencies, minus its
+// components along the ring_k lowest DCT-II modes (FP64 sums in a fixed
+// order), or with ring_k = 0 and both offsets unknowns minus its mean over
+// the slice (the gauge (m_o + a, m_r - a) leaves S unchanged, so the
+// iteration keeps the mean of m_r fixed).
+__global__ void k_offsets_grad(DevGeom dg, int which, int ring_k, float scale,
+                               const float *__restrict__ shift, const double *__restrict__ row_sum,
+                               float4 *__restrict__ gv, const int *__restrict__ active)
 {
     __shared__ double red[32];
+    __shared__ double coef[EI_MAX_RING_MODES];
     const int s = blockIdx.x;
     if (active && !active[s]) return;
     const SliceInfo si = dg.slices[s];
@@ -241,6 +339,22 @@ __global__ void k_offsets_grad(DevGeom dg, int which, float scale, const float *
         for (int a = 0; a < si.n_theta; ++a) acc += (double)shift[si.sino_off + (int64_t)a * si.n_dp + j];
         off_elem(gv, st, n_mo + j) = (float)acc;     // unscaled for now
         part += acc;
+    }
+    if (ring_k > 0) {
+        __syncthreads();                             // every column sum is in place
+        for (int k = threadIdx.x; k < ring_k; k += blockDim.x) {
+            double c = 0.0;
+            for (int j = 0; j < n_mr; ++j) c += (double)off_elem(gv, st, n_mo + j) * dct2_basis(k, j, n_mr);
+            coef[k] = c;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_mr; j += blockDim.x) {
+            float &e = off_elem(gv, st, n_mo + j);
+            double r = (double)e;
+            for (int k = 0; k < ring_k; ++k) r -= coef[k] * dct2_basis(k, j, n_mr);
+            e = (float)(r * scale);
+        }
+        return;
     }
     // fixed-order block reduction of the column sums
     for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
@@ -404,16 +518,22 @@ __global__ void k_reset_dir(DevGeom dg, SolverDev sv)
     }
 }
 
-// trial point xt = u + alpha d
-__global__ void k_trial(DevGeom dg, SolverDev sv)
+// trial point xt = u + alpha d, and the regulariser's value at it (part_reg)
+__global__ void k_trial(DevGeom dg, SolverDev sv, float4 reg1, double *__restrict__ part_reg)
 {
+    __shared__ double red[32];
     const VecBlock b = vec_block(dg);
     if (!sv.mask_ls[b.s]) return;
     const float al = (float)sv.st[b.s].alpha;
+    double acc = 0.0;
     for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
         const float4 uv = sv.u[e], dv = sv.d[e];
-        sv.xt[e] = f4(fmaf(al, dv.x, uv.x), fmaf(al, dv.y, uv.y), fmaf(al, dv.z, uv.z));
+        const float4 x = f4(fmaf(al, dv.x, uv.x), fmaf(al, dv.y, uv.y), fmaf(al, dv.z, uv.z));
+        sv.xt[e] = x;
+        if (!b.off) acc += reg_term(x, reg1);
     }
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) part_reg[blockIdx.x] = t;
 }
 
 // accepted step: S_head = xt - u, Y_head = gt - g, u = xt, g = gt; partial s.y, s.s, y.y
@@ -471,6 +591,8 @@ __global__ void k_init_state(DevGeom dg, SolverDev sv, const double *__restrict_
         q.f = q.f0 = S[s];
         q.gamma = 1.0;
         q.evals = 1;
+        q.projections = 1;
+        q.adjoints = 1;
         const bool ok = isfinite(q.f);
         q.status = ok ? EI_OK : EI_ERR_NONFINITE;
         sv.mask_dir[s] = ok;
@@ -533,6 +655,22 @@ __global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ 
         q.trials = 0;
         sv.mask_ls[s] = 1;
     }
+    // this round's trial of every slice in line search: an iteration's first
+    // trial is projected, a backtracking one interpolated from Pu and Pt
+    for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
+        sv.mask_first[s] = 0;
+        sv.mask_bt[s] = 0;
+        if (!sv.mask_ls[s]) continue;
+        SliceState &q = sv.st[s];
+        if (q.trials == 0) {
+            sv.mask_first[s] = 1;
+            q.projections += 1;
+        } else {
+            sv.mask_bt[s] = 1;
+            q.ratio = q.alpha / q.alpha_p;
+        }
+        q.alpha_p = q.alpha;
+    }
 }
 
 // Armijo test of the trial point
@@ -545,6 +683,7 @@ __global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S,
         q.evals += 1;
         if (isfinite(ft) && ft <= q.f + o.c1 * q.alpha * q.gd) {
             q.f_t = ft;
+            q.adjoints += 1;
             sv.mask_ls[s] = 0;
             sv.mask_acc[s] = 1;
         } else {
@@ -679,6 +818,11 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(salloc(s, &s->mask_dir, S));
     EI_CUDA_TRY(salloc(s, &s->mask_ls, S));
     EI_CUDA_TRY(salloc(s, &s->mask_acc, S));
+    EI_CUDA_TRY(salloc(s, &s->mask_first, S));
+    EI_CUDA_TRY(salloc(s, &s->mask_bt, S));
+    EI_CUDA_TRY(salloc(s, &s->Pu, (size_t)g->proj_count));
+    EI_CUDA_TRY(salloc(s, &s->Pt, (size_t)g->proj_count));
+    EI_CUDA_TRY(salloc(s, &s->part_reg, NB));
     EI_CUDA_TRY(salloc(s, &s->summary, 2));
     EI_CUDA_TRY(cudaMallocHost(&s->summary_h, 2 * sizeof(int)));
     EI_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
@@ -703,6 +847,38 @@ static bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Traced launches of the solver's Radon-class and IC kernels (events when
+// tracing is on, every launch counted).
+static cudaError_t solver_project(ei_geometry *g, float *proj, float link, const int *active,
+                                  cudaStream_t st)
+{
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_project(g, proj, link, active, st);
+    trace_end(g, TK_PROJECT, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
+static cudaError_t solver_ic(ei_geometry *g, const float *proj, const float *meas, float link,
+                             const int *active, cudaStream_t st)
+{
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_ic(g, proj, meas, nullptr, g->part_ic, IC_OBJECTIVE_GRAD, link, active, st);
+    trace_end(g, TK_IC, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
+static cudaError_t solver_adjoint(ei_geometry *g, const float4 *v, float4 *out, const EvalConsts &c,
+                                  const int *active, cudaStream_t st)
+{
+    cudaEvent_t b = trace_begin(g, st);
+    cudaError_t e = launch_backproject(g, v, out, c.out_mult, c.reg2, c.link, active, st);
+    trace_end(g, TK_BACKPROJECT, b, st);
+    count_launches(g, 1);
+    return e;
+}
+
 // deadline: the time budget's end (opts->max_seconds > 0), checked before each
 // round; *timed_out tells whether it stopped the rounds
 static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
@@ -714,26 +890,23 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     const DevGeom &dg = sv->dgx;              // the solver's blocks (with offsets segments)
     const int NB = dg.total_vec;
     const int NBv = g->dg.total_vec;          // the volumes' blocks only
+    const int NR = g->dg.total_ic;            // sinogram rows
     const int T = VEC_THREADS;
     const int ow = sv->off_which;
     const float os = g->off_scale;
-    // one evaluation at vector v (gradient into gv): offsets to the model's
-    // tables first, their gradient after
-    auto eval = [&](float4 *v, float4 *gv, const int *active) -> cudaError_t {
-        if (ow) {
-            k_offsets_apply<<<g->n_slices, 256, 0, st>>>(dg, ow, os, v, active);
-            count_launches(g, 1);
-        }
-        EI_CUDA_TRY(evaluate(g, v, meas, g->S_dev, gv, true, active, st));
-        if (ow) {
-            EI_CUDA_TRY(launch_shift_grad(g, g->proj, meas, sv->shift, sv->row_sum, active, st));
-            k_offsets_grad<<<g->n_slices, 256, 0, st>>>(dg, ow, os, sv->shift, sv->row_sum, gv, active);
-            count_launches(g, 2);
-        }
+    const EvalConsts ec = eval_consts(g, true);   // the solver's scaled unknowns
+    const bool linked = g->link_gamma > 0.f;
+    // the gradient's offsets segments at the points whose projections are in Pt
+    // (after the model's tables hold their offsets)
+    auto offsets_gradient = [&](float4 *gv, const int *active) -> cudaError_t {
+        EI_CUDA_TRY(launch_shift_grad(g, sv->Pt, meas, sv->shift, sv->row_sum, active, st));
+        k_offsets_grad<<<g->n_slices, 256, 0, st>>>(dg, ow, (ow & EI_OFFSET_MR) ? g->ring_modes : 0,
+                                                    os, sv->shift, sv->row_sum, gv, active);
+        count_launches(g, 2);
         return cudaGetLastError();
     };
     // linked mode iterates on h alone: the other lanes of u start and stay at 0
-    const float on1 = g->link_gamma > 0.f ? 0.f : 1.f;
+    const float on1 = linked ? 0.f : 1.f;
     const float4 inv = make_float4(1.f / g->scale[0], on1 / g->scale[1], on1 / g->scale[2], 0.f);
     const float4 sc = make_float4(g->scale[0], on1 * g->scale[1], on1 * g->scale[2], 0.f);
     Opts o{opts->tol, opts->c1, opts->curv_eps, opts->max_iter, opts->max_trials};
@@ -741,7 +914,8 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
 
     sv->has_state = false;                    // until this solve completes
     if (opts->resume) {
-        // continue from the kept state: u, its gradient, the memory, the slices' records
+        // continue from the kept state: u, its gradient and projections, the memory,
+        // the slices' records
         k_resume_state<<<1, scalar_threads, 0, st>>>(dg, dv, opts->max_iter, sv->summary);
         count_launches(g, 1);
         EI_CUDA_TRY(cudaGetLastError());
@@ -751,20 +925,34 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         count_launches(g, 1);
         if (ow) {
             k_offsets_to_u<<<g->n_slices, 256, 0, st>>>(dg, ow, 1.f / os, sv->u);
-            count_launches(g, 1);
+            k_offsets_apply<<<g->n_slices, 256, 0, st>>>(dg, ow, os, sv->u, nullptr);
+            count_launches(g, 2);
         }
         EI_CUDA_TRY(cudaGetLastError());
-        EI_CUDA_TRY(eval(sv->u, sv->g, nullptr));
-        k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
+        // the initial evaluation: S, the gradient and the projections Pu at u
+        EI_CUDA_TRY(launch_reg_partials(dg, sv->u, ec.reg1, sv->part_reg, nullptr, st));
+        EI_CUDA_TRY(launch_prep(g, sv->u, ec.mult, linked, nullptr, st));
+        count_launches(g, 2);
+        EI_CUDA_TRY(solver_project(g, sv->Pt, ec.link, nullptr, st));
+        EI_CUDA_TRY(solver_ic(g, sv->Pt, meas, ec.link, nullptr, st));
+        EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, dg.vec_prefix, sv->part_reg,
+                                              g->S_dev, nullptr, st));
         count_launches(g, 1);
+        EI_CUDA_TRY(solver_adjoint(g, sv->u, sv->g, ec, nullptr, st));
+        if (ow) EI_CUDA_TRY(offsets_gradient(sv->g, nullptr));
+        if (NR > 0) k_sino_rows<true><<<NR, 256, 0, st>>>(g->dg, dv, sv->Pu, sv->Pt, nullptr);
+        k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
+        count_launches(g, 2);
         EI_CUDA_TRY(cudaGetLastError());
         *evals = 1;
     }
     EI_CUDA_TRY(cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     EI_CUDA_TRY(cudaStreamSynchronize(st));
 
-    // one round: direction for the slices that need one, a trial step and its
-    // evaluation for every slice in line search, Armijo, memory update, summary
+    // one round: direction for the slices that need one; a trial step and its
+    // objective for every slice in line search (projected when it is the
+    // iteration's first trial, interpolated otherwise); Armijo; the gradient,
+    // projections and memory update of accepted slices; summary
     auto round = [&]() -> cudaError_t {
         double *pa = sv->part[0], *pb = sv->part[1];
         k_tl_first<<<NB, T, 0, st>>>(dg, dv, pa);
@@ -780,16 +968,35 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         k_tl_end<<<NB, T, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
         k_ls_start<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
         k_reset_dir<<<NB, T, 0, st>>>(dg, dv);
-        k_trial<<<NB, T, 0, st>>>(dg, dv);
+        k_trial<<<NB, T, 0, st>>>(dg, dv, ec.reg1, sv->part_reg);
+        // direction: first + m down + mid + m up + end + ls_start + reset; trial
+        count_launches(g, 2 * sv->m + 5 + 1);
         EI_CUDA_TRY(cudaGetLastError());
-        EI_CUDA_TRY(eval(sv->xt, sv->gt, sv->mask_ls));
+        // the trial's projections: first trials projected, later ones interpolated
+        EI_CUDA_TRY(launch_prep(g, sv->xt, ec.mult, linked, sv->mask_first, st));
+        count_launches(g, 1);
+        EI_CUDA_TRY(solver_project(g, sv->Pt, ec.link, sv->mask_first, st));
+        if (NR > 0) k_sino_rows<false><<<NR, 256, 0, st>>>(g->dg, dv, sv->Pu, sv->Pt, sv->mask_bt);
+        count_launches(g, 1);
+        if (ow) {
+            k_offsets_apply<<<g->n_slices, 256, 0, st>>>(dg, ow, os, sv->xt, sv->mask_ls);
+            count_launches(g, 1);
+        }
+        // the objective at the trial: data term (its per-pixel gradient too) + regulariser
+        EI_CUDA_TRY(solver_ic(g, sv->Pt, meas, ec.link, sv->mask_ls, st));
+        EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, dg.vec_prefix, sv->part_reg,
+                                              g->S_dev, sv->mask_ls, st));
         k_armijo<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, o);
+        count_launches(g, 2);
+        EI_CUDA_TRY(cudaGetLastError());
+        // accepted trials: the gradient, the projections Pu, the memory update
+        EI_CUDA_TRY(solver_adjoint(g, sv->xt, sv->gt, ec, sv->mask_acc, st));
+        if (ow) EI_CUDA_TRY(offsets_gradient(sv->gt, sv->mask_acc));
+        if (NR > 0) k_sino_rows<true><<<NR, 256, 0, st>>>(g->dg, dv, sv->Pu, sv->Pt, sv->mask_acc);
         k_accept<<<NB, T, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2]);
         k_update<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2], o,
                                                sv->summary);
-        // direction: first + m down + mid + m up + end + ls_start + reset; then trial,
-        // armijo, accept, update (the evaluation counts its own launches)
-        count_launches(g, 2 * sv->m + 5 + 4);
+        count_launches(g, 3);
         EI_CUDA_TRY(cudaGetLastError());
         return cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     };
@@ -927,6 +1134,8 @@ int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_s
             if (report->f_final) report->f_final[s] = hs[s].f;
             if (report->f_initial) report->f_initial[s] = hs[s].f0;
             if (report->slice_evaluations) report->slice_evaluations[s] = hs[s].evals;
+            if (report->slice_projections) report->slice_projections[s] = hs[s].projections;
+            if (report->slice_adjoints) report->slice_adjoints[s] = hs[s].adjoints;
         }
     }
     if (report) {
@@ -949,7 +1158,7 @@ struct StateHeader {
     uint64_t shape_hash;
 };
 
-static const uint64_t kStateMagic = 0x4549534f4c564531ull;   // "EISOLVE1"
+static const uint64_t kStateMagic = 0x4549534f4c564532ull;   // "EISOLVE2"
 
 static int64_t solver_vol_count(const ei_geometry *g)
 {
@@ -979,10 +1188,13 @@ static StateHeader state_header(const ei_geometry *g, int m)
 }
 
 // The state's pieces in checkpoint order: device pointer and bytes.
-static std::vector<std::pair<void *, size_t>> state_pieces(const Solver *s, int n_slices)
+static std::vector<std::pair<void *, size_t>> state_pieces(const Solver *s, const ei_geometry *g)
 {
-    const size_t V = (size_t)s->vol_count * sizeof(float4), S = (size_t)n_slices;
+    const size_t V = (size_t)s->vol_count * sizeof(float4), S = (size_t)g->n_slices;
+    const size_t P = (size_t)g->proj_count * sizeof(float);
     return {{s->u, V},
+            {s->Pu, P},
+            {s->Pt, P},
             {s->g, V},
             {s->d, V},
             {s->Sr, V * s->ring},
@@ -998,8 +1210,8 @@ size_t solver_state_size(const ei_geometry *g, int m)
 {
     const size_t V = (size_t)solver_vol_count(g) * sizeof(float4), S = (size_t)g->n_slices;
     const size_t ring = (size_t)m + 1;
-    return sizeof(StateHeader) + V * (3 + 2 * ring) + sizeof(double) * ring * S +
-           sizeof(SliceState) * S + 3 * sizeof(int) * S;
+    return sizeof(StateHeader) + V * (3 + 2 * ring) + 2 * sizeof(float) * (size_t)g->proj_count +
+           sizeof(double) * ring * S + sizeof(SliceState) * S + 3 * sizeof(int) * S;
 }
 
 int solver_save(const ei_geometry *g, void *buf, size_t bytes)
@@ -1014,7 +1226,7 @@ int solver_save(const ei_geometry *g, void *buf, size_t bytes)
     char *p = static_cast<char *>(buf);
     cudaError_t e = cudaMemcpy(p, &h, sizeof h, cudaMemcpyDefault);
     p += sizeof h;
-    for (const auto &pc : state_pieces(s, g->n_slices)) {
+    for (const auto &pc : state_pieces(s, g)) {
         if (e != cudaSuccess) break;
         e = cudaMemcpy(p, pc.first, pc.second, cudaMemcpyDefault);
         p += pc.second;
@@ -1057,7 +1269,7 @@ int solver_load(ei_geometry *g, int m, const void *buf, size_t bytes)
     Solver *s = g->solver;
     s->has_state = false;
     p += sizeof h;
-    for (const auto &pc : state_pieces(s, g->n_slices)) {
+    for (const auto &pc : state_pieces(s, g)) {
         if (e != cudaSuccess) break;
         e = cudaMemcpy(pc.first, p, pc.second, cudaMemcpyDefault);
         p += pc.second;

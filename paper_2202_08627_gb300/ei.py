@@ -70,7 +70,8 @@ class ei_solve_report(ctypes.Structure):
                 ("converged", ctypes.POINTER(c_int)), ("f_final", ctypes.POINTER(c_double)),
                 ("f_initial", ctypes.POINTER(c_double)),
                 ("slice_evaluations", ctypes.POINTER(c_int)), ("evaluations", c_int),
-                ("seconds", c_double)]
+                ("seconds", c_double), ("slice_projections", ctypes.POINTER(c_int)),
+                ("slice_adjoints", ctypes.POINTER(c_int))]
 
 
 class ei_peaks(ctypes.Structure):
@@ -96,10 +97,10 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout",
             "ei_solver_state_size", "ei_solver_save", "ei_solver_load",
             "ei_unet_get_optimizer", "ei_unet_set_optimizer", "ei_fail_alloc_after",
-            "ei_fail_alloc_pending", "ei_live_allocations"]
+            "ei_fail_alloc_pending", "ei_live_allocations", "ei_set_ring_modes"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 8
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 11
 
 _lib = None
 
@@ -154,6 +155,8 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_single_shot_eq3.restype = c_int
     lib.ei_set_offset_unknowns.argtypes = [c_void_p, c_int, c_double]
     lib.ei_set_offset_unknowns.restype = c_int
+    lib.ei_set_ring_modes.argtypes = [c_void_p, c_int]
+    lib.ei_set_ring_modes.restype = c_int
     lib.ei_get_offsets.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.ei_get_offsets.restype = c_int
     lib.ei_unet_get_optimizer.argtypes = [c_void_p, c_void_p, c_void_p, P(c_int)]
@@ -507,6 +510,8 @@ class SolveReport:
     evaluations: int
     seconds: float
     return_status: int
+    slice_projections: np.ndarray = None
+    slice_adjoints: np.ndarray = None
 
 
 def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbfgs_m=10,
@@ -532,15 +537,17 @@ def ei_reconstruct(geom: Geometry, s_exp, vol_inout, tol=1e-6, max_iter=100, lbf
     ff = np.zeros(S, np.float64)
     f0 = np.zeros(S, np.float64)
     ev = np.zeros(S, np.int32)
+    npj = np.zeros(S, np.int32)
+    nad = np.zeros(S, np.int32)
     ip = ctypes.POINTER(c_int)
     dp = ctypes.POINTER(c_double)
     rep = ei_solve_report(it.ctypes.data_as(ip), st.ctypes.data_as(ip), cv.ctypes.data_as(ip),
                           ff.ctypes.data_as(dp), f0.ctypes.data_as(dp), ev.ctypes.data_as(ip),
-                          0, 0.0)
+                          0, 0.0, npj.ctypes.data_as(ip), nad.ctypes.data_as(ip))
     rc = load_library().ei_reconstruct(geom.handle, _dptr(s_exp, "s_exp", torch.float32),
                                        _dptr(vol_inout, "vol_inout", torch.float32),
                                        ctypes.byref(o), ctypes.byref(rep), _stream_ptr(stream))
-    out = SolveReport(it, st, cv, ff, f0, ev, rep.evaluations, rep.seconds, rc)
+    out = SolveReport(it, st, cv, ff, f0, ev, rep.evaluations, rep.seconds, rc, npj, nad)
     budget_stop = rc == EI_ERR_TIMEOUT and max_seconds > 0 and bool((st == EI_ERR_TIMEOUT).any())
     if raise_on_error and rc not in (EI_OK, EI_ERR_LINESEARCH, EI_ERR_NONFINITE) and not budget_stop:
         raise EIError(rc, "ei_reconstruct")
@@ -584,11 +591,12 @@ def ei_objective_grad_noalloc(n: int, n_theta: int, n_det: int, pitch_cm: float,
                               grad=None, lam=(1e-2, 1e-2, 1e-2), scale=(1.0, 1e-6, 1.0),
                               theta=None, m_o=None, m_r=None, stream=None) -> None:
     """S and its gradient for one slice without any device allocation, for
-    callers that cannot allocate GPU memory (during stream capture, inside a
-    framework that owns the device memory, or in loops that cannot afford
-    cudaMalloc's synchronisation).  Arguments as ei_setup_geometry (one
-    uniform slice) plus ei_objective_grad's arrays; flat_* / m_o / m_r are
-    numpy arrays or CUDA tensors."""
+    callers that may not allocate GPU memory (a framework that owns the device
+    memory, or a loop that cannot afford cudaMalloc's synchronisation).
+    Arguments as ei_setup_geometry (one uniform slice) plus ei_objective_grad's
+    arrays; flat_* / m_o / m_r are numpy arrays or contiguous float32 CUDA
+    tensors (other tensors are refused rather than converted, which would
+    allocate)."""
     import torch
     keep = []
 
@@ -596,8 +604,8 @@ def ei_objective_grad_noalloc(n: int, n_theta: int, n_det: int, pitch_cm: float,
         if a is None:
             return None
         if isinstance(a, torch.Tensor):
-            a = a.contiguous().float()
-            keep.append(a)
+            if a.dtype != torch.float32 or not a.is_contiguous() or not a.is_cuda:
+                raise ValueError("per-pixel tensors must be contiguous float32 CUDA tensors")
             return a.data_ptr()
         arr = np.ascontiguousarray(a, dtype=np.float32)
         keep.append(arr)
@@ -662,6 +670,12 @@ def ei_set_offset_unknowns(geom: Geometry, which: int, scale: float = 0.01) -> N
     EI_OFFSET_MR (0 = fixed), solver scaling m / scale."""
     _check(load_library().ei_set_offset_unknowns(geom.handle, int(which), float(scale)),
            "ei_set_offset_unknowns")
+
+
+def ei_set_ring_modes(geom: Geometry, K: int) -> None:
+    """Restrict the solver's m_r steps to ring frequencies: orthogonal to the K
+    lowest DCT-II modes across each slice's detector (0 = no restriction)."""
+    _check(load_library().ei_set_ring_modes(geom.handle, int(K)), "ei_set_ring_modes")
 
 
 def ei_get_offsets(geom: Geometry):

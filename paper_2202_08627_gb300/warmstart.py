@@ -222,7 +222,7 @@ def time_to_tolerance(G: ei.Geometry, s_exp, starts: Sequence[str], tol: float, 
     for start in starts:
         vol = G.empty("vol", s_exp.device)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
         if start == "single_shot":
             ei.ei_single_shot_fbp(G, s_exp, vol)
@@ -230,14 +230,19 @@ def time_to_tolerance(G: ei.Geometry, s_exp, starts: Sequence[str], tol: float, 
             cnn_warm_start(net, G, s_exp, vol)
         elif start != "zero":
             raise ValueError(start)
+        em.record()
         rep = ei.ei_reconstruct(G, s_exp, vol, tol=tol, max_iter=max_iter, raise_on_error=False)
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) * 1e-3
         it = rep.iterations
         out[start] = {"seconds": t, "seconds_per_1024_slice": t / eq,
+                      "ms_per_1024_slice": 1e3 * t / eq,
+                      "start_seconds": e0.elapsed_time(em) * 1e-3,
                       "iterations_mean": float(it.mean()),
                       "iterations_median": float(np.median(it)), "iterations_max": int(it.max()),
+                      "projections_per_iteration": float(rep.slice_projections.sum()) /
+                      max(1, int(it.sum())),
                       "converged": int(rep.converged.sum()), "slices": int(len(it)),
                       "f_final": rep.f_final.tolist()}
         del vol

@@ -109,3 +109,14 @@ def test_allocation_failure_trigger_without_a_gpu(lib):
     ei.ei_fail_alloc_after(-1)
     assert ei.ei_fail_alloc_pending() == -1
     assert ei.ei_live_allocations() == 0
+
+
+def test_solve_report_layout_and_ring_modes_argument_checks(lib):
+    from paper_2202_08627_gb300 import ei
+    # six pointers, int + padding, double, then the per-slice projection and
+    # adjoint counts (the C layout on both the x86 and the Arm build)
+    assert ctypes.sizeof(ei.ei_solve_report) == 80
+    assert ei.ei_solve_report.seconds.offset == 56
+    assert ei.ei_solve_report.slice_projections.offset == 64
+    assert ei.ei_solve_report.slice_adjoints.offset == 72
+    assert lib.ei_set_ring_modes(None, 4) == ei.EI_ERR_ARG

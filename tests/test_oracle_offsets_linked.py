@@ -87,3 +87,24 @@ def test_linked_cost_is_three_channel_cost_at_linked_volume(oracle):
     S0, _ = oracle.objective_grad_linked(np.zeros_like(hvol), s_exp, geom, GAMMA, want_grad=False)
     S30, _ = oracle.objective_grad(np.zeros_like(x), s_exp, geom, want_grad=False)
     assert abs(S0 - S30) <= 1e-12 * abs(S30)
+
+
+def test_ring_projection_keeps_ring_frequencies_only(oracle):
+    """The restriction of m_r to ring frequencies is the orthogonal projector
+    onto the complement of the K lowest cosine modes: built here from the
+    textbook DCT-II vectors b_k(j) = sqrt((2 - [k = 0]) / N) cos(pi k (j + 1/2) / N),
+    it maps b_k (k < K) to 0 and b_k (k >= K) to itself, is symmetric and
+    idempotent, and K = 1 is the zero-mean gauge of the joint solve."""
+    N, K = 48, 6
+    j = np.arange(N)
+    B = np.stack([np.sqrt((2.0 - (k == 0)) / N) * np.cos(np.pi * k * (j + 0.5) / N) for k in range(N)])
+    np.testing.assert_allclose(B @ B.T, np.eye(N), atol=1e-12)
+    Pm = np.stack([oracle.ring_project(e, K) for e in np.eye(N)])      # the projector's matrix
+    for k in range(N):
+        want = np.zeros(N) if k < K else B[k]
+        np.testing.assert_allclose(oracle.ring_project(B[k], K), want, atol=1e-12)
+    np.testing.assert_allclose(Pm, Pm.T, atol=1e-12)
+    np.testing.assert_allclose(Pm @ Pm, Pm, atol=1e-12)
+    g = inputs.uniform_noise(N, 77)
+    np.testing.assert_allclose(oracle.ring_project(g, 1), g - g.mean(), atol=1e-12)
+    np.testing.assert_array_equal(oracle.ring_project(g, 0), g)
