@@ -17,15 +17,21 @@ With --asym a > 0 the true flat is not a Gaussian: the periodised Gaussian
 times (1 + a sin 2 pi (m - c)), so the Gaussian fit has a model error.
 
 Reconstructions: the iterative method (linked unknown h, relative change
-1e-6) with m_r fixed at 0 or among the unknowns, the iterative method with
-the averaged flat scans themselves as a sampled flat (no fit, "iter_tab"),
-the iterative method with the true flat ("iter_true_flat", the bound), and
-the single-shot retrieval of Eq. 3 + FBP.  Measures: the CNR of Eq. 7
+1e-6) with m_r fixed at 0, among the unknowns ("iter_mr"), or among the
+unknowns restricted to ring frequencies ("iter_mr_ring": its steps orthogonal
+to the n/16 lowest DCT-II modes across the detector, ei_set_ring_modes), the
+iterative method with the averaged flat scans themselves as a sampled flat
+(no fit, "iter_tab"), the iterative method with the true flat
+("iter_true_flat", the bound), and the single-shot retrieval of Eq. 3 + FBP.
+The regulariser weight is the paper's lambda = 1e-2 unless --lam is given:
+with intensities normalised by the flat amplitude, the paper's value makes
+the regulariser at the true object several times the noise part of the cost,
+so the study can also run at smaller values.  Measures: the CNR of Eq. 7
 between every pair of granules over discs of 0.6 granule radius; the FRC of Eq. 6 between the
 reconstructions of the odd and of the even angles (independent noise), over
 the central 140/220 of the slice, with the 0.5 cutoff.
 
-    python -m paper_2202_08627_gb300.ring_study --n 256 --n-theta 400 [--asym 0.15]
+    python -m paper_2202_08627_gb300.ring_study --n 256 --n-theta 400 [--asym 0.15] [--lam 1e-3]
 """
 from __future__ import annotations
 
@@ -111,12 +117,17 @@ def estimate_flat(f):
     return A_e, c_e, w_e
 
 
-def geometry(n, theta, A, c, w):
+def geometry(n, theta, A, c, w, lam: float = inputs.LAMBDA):
     return ei.ei_setup_geometry(
         n_m=1, m=[SLOPE_M], z_cm=inputs.Z_CM, period_cm=inputs.PERIOD_CM, kappa_sigma=inputs.KAPPA,
         flat_A=A, flat_c=c, flat_w=w, n=n, n_theta=len(theta), n_det=n,
-        pitch_cm=inputs.pitch_for(n), n_slices=1, theta=theta, lam=(inputs.LAMBDA,) * 3,
+        pitch_cm=inputs.pitch_for(n), n_slices=1, theta=theta, lam=(lam,) * 3,
         scale=inputs.SCALE)
+
+
+def ring_modes(n_det: int) -> int:
+    """DCT-II modes kept out of m_r in "iter_mr_ring": periods above 32 pixels."""
+    return max(1, n_det // 16)
 
 
 def measure(n, theta, A, c, w, seed, device="cuda", asym: float = 0.0):
@@ -136,11 +147,13 @@ def measure(n, theta, A, c, w, seed, device="cuda", asym: float = 0.0):
 
 
 def reconstruct(n, theta, flat, s_exp, mode: str, tol: float = 1e-6, max_iter: int = 300,
-                table=None):
+                table=None, lam: float = inputs.LAMBDA):
     """h [n][n] from one of: "iter" (m_r = 0), "iter_mr" (m_r among the
-    unknowns), "eq3" (single shot), with the flat IC `flat` = (A, c, w) or, for
-    the iterative modes when `table` ([n_det][K]) is given, that sampled flat."""
-    G = geometry(n, theta, *flat)
+    unknowns), "iter_mr_ring" (m_r among the unknowns, restricted to ring
+    frequencies), "eq3" (single shot), with the flat IC `flat` = (A, c, w) or,
+    for the iterative modes when `table` ([n_det][K]) is given, that sampled
+    flat."""
+    G = geometry(n, theta, *flat, lam=lam)
     if table is not None and mode != "eq3":
         ei.ei_set_flat_table(G, np.ascontiguousarray(table, dtype=np.float32))
     vol = G.empty("vol", s_exp.device)
@@ -149,8 +162,10 @@ def reconstruct(n, theta, flat, s_exp, mode: str, tol: float = 1e-6, max_iter: i
         ei.ei_single_shot_eq3(G, s_exp, 0, GAMMA, vol)
     else:
         ei.ei_set_linked(G, GAMMA)
-        if mode == "iter_mr":
+        if mode in ("iter_mr", "iter_mr_ring"):
             ei.ei_set_offset_unknowns(G, ei.EI_OFFSET_MR, 0.01)
+        if mode == "iter_mr_ring":
+            ei.ei_set_ring_modes(G, ring_modes(n))
         rep = ei.ei_reconstruct(G, s_exp, vol, tol=tol, max_iter=max_iter, raise_on_error=False)
         info = {"iterations": int(rep.iterations[0]), "converged": bool(rep.converged[0])}
     h = G.unpack_volume(vol)[0][0]
@@ -164,7 +179,8 @@ def subset(s_exp, n_theta, n_dp, idx, device):
 
 
 def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed: int = 3,
-        device="cuda", asym: float = 0.0):
+        device="cuda", asym: float = 0.0, lam: float = inputs.LAMBDA,
+        modes: Sequence[str] = ("eq3", "iter", "iter_mr", "iter_mr_ring")):
     import torch
     theta = inputs.angles(n_theta)
     A, c, w = inputs.flat_ic(seed, n)
@@ -182,13 +198,13 @@ def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed
     def study(R, method, mode, flat, table, err):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h, info = reconstruct(n, theta, flat, s_exp, mode, table=table)
+        h, info = reconstruct(n, theta, flat, s_exp, mode, table=table, lam=lam)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         h_odd, _ = reconstruct(n, theta[odd], flat, subset(s_exp, n_theta, n_dp, odd, device), mode,
-                               table=table)
+                               table=table, lam=lam)
         h_even, _ = reconstruct(n, theta[even], flat, subset(s_exp, n_theta, n_dp, even, device),
-                                mode, table=table)
+                                mode, table=table, lam=lam)
         curve = metrics.frc(h_odd[crop, crop], h_even[crop, crop])
         row = {"flat_scans": R, "method": method, "seconds": dt, **info,
                "cnr": {"%d-%d" % p: metrics.cnr(h, masks[p[0]], masks[p[1]]) for p in pairs},
@@ -204,10 +220,13 @@ def run(n: int = 256, n_theta: int = 400, repeats: Sequence[int] = (1, 20), seed
         err = {"c_rms": float(np.sqrt(np.mean((flat[1] - c) ** 2))),
                "w_rel_rms": float(np.sqrt(np.mean((flat[2] / w - 1) ** 2))),
                "A_rel_rms": float(np.sqrt(np.mean((flat[0] / A - 1) ** 2)))}
-        for mode in ("eq3", "iter", "iter_mr"):
-            study(R, mode, mode, flat, None, err)
-        study(R, "iter_tab", "iter", flat, flat_table(scans), err)
-    return {"n": n, "n_theta": n_theta, "gamma_cm": GAMMA, "m": SLOPE_M, "asym": asym, "rows": rows}
+        for mode in modes:
+            if mode != "iter_tab":
+                study(R, mode, mode, flat, None, err)
+        if "iter_tab" in modes or asym != 0.0:
+            study(R, "iter_tab", "iter", flat, flat_table(scans), err)
+    return {"n": n, "n_theta": n_theta, "gamma_cm": GAMMA, "m": SLOPE_M, "asym": asym, "lam": lam,
+            "ring_modes": ring_modes(n), "rows": rows}
 
 
 def main(argv=None):
@@ -218,9 +237,13 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--asym", type=float, default=0.0,
                     help="asymmetry of the true flat IC (0: Gaussian)")
+    ap.add_argument("--lam", type=float, default=inputs.LAMBDA, help="regulariser weight")
+    ap.add_argument("--modes", default="eq3,iter,iter_mr,iter_mr_ring,iter_tab",
+                    help="comma-separated reconstructions")
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
-    print(json.dumps(run(args.n, args.n_theta, seed=args.seed, asym=args.asym)))
+    print(json.dumps(run(args.n, args.n_theta, seed=args.seed, asym=args.asym, lam=args.lam,
+                         modes=tuple(args.modes.split(",")))))
 
 
 if __name__ == "__main__":
