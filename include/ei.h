@@ -74,8 +74,8 @@ typedef enum {
     EI_ERR_LINESEARCH = 4,   /* Armijo backtracking found no acceptable step */
     EI_ERR_TIMEOUT = 5,      /* a kernel's bounded wait ran out, or a solve's time budget
                                 (ei_solve_opts.max_seconds) did */
-    EI_ERR_DEVICE_CHECK = 6, /* reserved for kernels' own bounds checks (no build of the
-                                library returns it) */
+    EI_ERR_DEVICE_CHECK = 6, /* a kernel's index bounds check fired (only the build with
+                                device checks, libei_check.so, has them) */
     EI_ERR_ALLOC = 7         /* workspace allocation failed */
 } ei_status;
 
@@ -494,6 +494,26 @@ int ei_measure_peaks(ei_peaks *out, void *stream);
  * copy failed; the CUDA context stays usable.
  */
 int ei_selftest_wait_timeout(unsigned limit_us, int *status_out);
+
+/*
+ * Debug build with device-side bounds checks (SURVEY-style sanitizer
+ * stand-in; the library built with -DEI_DEVICE_CHECKS as libei_check.so).
+ * The projector and the adjoint index the packed volume and gradient rows
+ * through zero margins sized on the host, without checks; in the check build
+ * every such data-dependent index is verified, a failed check stores
+ * EI_ERR_DEVICE_CHECK in the geometry's device status word (returned by the
+ * next synchronising call: ei_reconstruct, or ei_objective_grad with a host
+ * S_out) and the access is clamped into its array.  Results are otherwise
+ * bit-identical to the regular build's.
+ *   ei_device_checks_enabled: 1 in the check build, 0 otherwise.
+ *   ei_selftest_device_check: runs a checked read whose index leaves its
+ *     logical range but not its buffer (synchronous, on the current device)
+ *     and stores the recorded status in *status_out: EI_ERR_DEVICE_CHECK in
+ *     the check build, 0 in the regular one.  EI_ERR_ARG for NULL, EI_ERR_CUDA
+ *     if the launch or copy failed.
+ */
+int ei_device_checks_enabled(void);
+int ei_selftest_device_check(int *status_out);
 
 /*
  * Failure injection on the host, for testing the clean-up paths.  Every

@@ -11,6 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libei.so")
+# the debug build: device-side bounds checks in the projector and the adjoint
+CHECK_LIB = os.path.join(HERE, "libei_check.so")
+CHECK_OBJ = os.path.join(HERE, "_build_check")
 SOURCES = ["ei_api.cu", "k_project.cu", "k_ic.cu", "k_backproject.cu", "solver.cu",
            "ei_noalloc.cu", "k_fbp.cu", "nn_kernels.cu", "nn_unet.cu", "k_peaks.cu", "nn_conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -57,6 +60,12 @@ def build(force: bool = False, verbose: bool = False, extra=(), lib: str = LIB,
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, lib)
     return lib
+
+
+def build_checked(force: bool = False) -> str:
+    """The library with device-side bounds checks (-DEI_DEVICE_CHECKS) as
+    libei_check.so beside the regular one (load it with EI_LIBRARY)."""
+    return build(force=force, extra=("-DEI_DEVICE_CHECKS",), lib=CHECK_LIB, obj_dir=CHECK_OBJ)
 
 
 if __name__ == "__main__":

@@ -101,7 +101,10 @@ static int take_device_status(ei_geometry *g, cudaStream_t st)
         return EI_ERR_CUDA;
     if (h == 0) return EI_OK;
     cudaMemsetAsync(g->dev_status, 0, sizeof(int), st);
-    record_message("a kernel's bounded wait for its input rows ran out (status %d)", h);
+    if (h == EI_ERR_DEVICE_CHECK)
+        record_message("a kernel's index bounds check fired (build with device checks)");
+    else
+        record_message("a kernel's bounded wait for its input rows ran out (status %d)", h);
     return h;
 }
 
@@ -219,6 +222,7 @@ EvalConsts eval_consts(const ei_geometry *g, bool scaled)
 cudaError_t evaluate(ei_geometry *g, const float4 *v, const float *meas, double *S_dev,
                      float4 *grad, bool scaled, const int *active, cudaStream_t st)
 {
+    NvtxRange range(grad ? "objective and gradient" : "objective");
     const EvalConsts c = eval_consts(g, scaled);
     const bool linked = c.link > 0.f;
     EI_CUDA_TRY(counted_prep(g, v, c.mult, linked, active, st));
@@ -355,6 +359,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
 {
     if (!d || !out || n_slices < 1) return EI_ERR_ARG;
     *out = nullptr;
+    NvtxRange range("ei_setup_geometry");
     if (d->n_m < 1 || d->n_m > EI_MAX_NM || !d->m) return EI_ERR_ARG;
     if (!(d->z_cm >= 0) || !(d->period_cm > 0) || !(d->kappa_sigma >= 0)) return EI_ERR_ARG;
     if (!d->flat_A || !d->flat_c || !d->flat_w) return EI_ERR_ARG;
@@ -575,6 +580,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     dg.ic_prefix = d_ic;
     dg.prep_prefix = d_prep;
     dg.vec_prefix = d_vec;
+    dg.status = g->dev_status;
     select_variants(g, 0, 0, false);
     g->ic_variant = ic_pipe_fits(dg.max_ndp, dg.mc.n_m) ? 1 : 0;
     *out = g;
@@ -680,6 +686,7 @@ static int autotune_timed(ei_geometry *g, float4 *adj_out, cudaStream_t st);
 int ei_autotune(ei_geometry *g, int flags, void *stream)
 {
     if (!g) return EI_ERR_ARG;
+    NvtxRange range("ei_autotune");
     const std::string key = tune_key(g), path = tune_cache_path();
     if (!(flags & EI_TUNE_FORCE)) {
         FILE *f = fopen(path.c_str(), "r");

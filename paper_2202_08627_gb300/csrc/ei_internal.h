@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -9,6 +10,40 @@
 #include "../../include/ei.h"
 
 namespace ei {
+
+// Debug build (-DEI_DEVICE_CHECKS, built beside the library as
+// libei_check.so): the kernels whose loads rely on zero margins sized on the
+// host (projector, adjoint) check every data-dependent index; a failed check
+// records EI_ERR_DEVICE_CHECK in the device status word and the access is
+// clamped into its array, so it never leaves it.  In the regular build the
+// checks compile away.
+#ifdef EI_DEVICE_CHECKS
+constexpr bool kDeviceChecks = true;
+#else
+constexpr bool kDeviceChecks = false;
+#endif
+
+#ifdef __CUDACC__
+// i when lo <= i <= hi; otherwise (check builds only) the status word records
+// the failure and the nearest bound is returned.
+__device__ __forceinline__ int checked_index(int i, int lo, int hi, int *status)
+{
+    if (kDeviceChecks && (i < lo || i > hi)) {
+        if (status) atomicCAS(status, 0, (int)EI_ERR_DEVICE_CHECK);
+        return i < lo ? lo : hi;
+    }
+    return i;
+}
+#endif
+
+// An NVTX range for the lifetime of the object (phases of the library's
+// calls, visible to profilers that record NVTX, e.g. ncu --nvtx).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-slice constants, resident in device memory (one entry per slice).
 struct SliceInfo {
@@ -146,6 +181,9 @@ struct DevGeom {
     // f(t, k / flat_k) over one mask period, rows in the order of det_off
     const float *flat_tab = nullptr;
     int flat_k = 0;
+    // device status word of the kernels' bounded waits and (check builds)
+    // bounds checks; may be null
+    int *status = nullptr;
 };
 
 #ifdef __CUDACC__

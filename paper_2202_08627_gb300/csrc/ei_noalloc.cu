@@ -131,6 +131,7 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     const size_t o_pic = cv.take((size_t)nth * sizeof(double));
     const size_t o_preg = cv.take((size_t)n_vec * sizeof(double));
     const size_t o_S = cv.take(sizeof(double));
+    const size_t o_status = cv.take(sizeof(int));
     if (cv.used > (size_t)EI_NOALLOC_SCRATCH_BYTES) return EI_ERR_ARG;
 
     // ---- the per-pixel and per-angle inputs (host or device arrays), checked
@@ -198,6 +199,7 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
         e = cudaMemcpyAsync(base + o_pix, pix.data(), ndp * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gA, 0, (size_t)gp * sizeof(float4), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_gB, 0, (size_t)gp * sizeof(float2), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_status, 0, sizeof(int), st);
     if (e != cudaSuccess) return status_of(e);
 
     // ---- a geometry view over the scratch (no host or device allocation)
@@ -230,6 +232,7 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     dg.total_vec = n_vec;
     dg.max_ndp = ndp;
     dg.max_n_theta = nth;
+    dg.status = (int *)(base + o_status);
     dg.mc.z_over_p = (float)(d->z_cm / d->period_cm);
     dg.mc.kappa = (float)d->kappa_sigma;
     dg.mc.n_m = d->n_m;
@@ -256,5 +259,11 @@ extern "C" int ei_objective_grad_noalloc(const ei_geometry_desc *d, const float 
     e = cudaMemcpyAsync(S_out, g.S_dev, sizeof(double), cudaMemcpyDefault, st);
     if (e == cudaSuccess && attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
         e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && kDeviceChecks) {      // check builds: report a fired bounds check
+        int h = 0;
+        e = cudaMemcpyAsync(&h, base + o_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && h != 0) return h;
+    }
     return status_of(e);
 }

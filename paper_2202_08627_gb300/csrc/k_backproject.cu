@@ -59,6 +59,15 @@ struct AdjShared {
     int jb[ADJ_CHUNK];      // mirror variant: J_B
 };
 
+// Check builds: the entries J + jj .. J + jj + span of a packed gradient row
+// lie within its margins, [-marg, n_dp + marg - 1] (pixel units); returns
+// the (clamped) jj.  Regular builds: jj.
+__device__ __forceinline__ int row_entry(int jj, int J, int span, const SliceInfo &si, int *status)
+{
+    if (!kDeviceChecks) return jj;
+    return checked_index(J + jj, -si.marg, si.n_dp + si.marg - 1 - span, status) - J;
+}
+
 // One voxel's output: out = out_mult R^T g + reg2 v; linked: the unknown h
 // in the mu lane, dS/dh = R^T (g_mu + link g_delta), the sinogram the IC
 // kernel combined.
@@ -140,7 +149,7 @@ __device__ __forceinline__ void backproject_single_item(
                 for (int p = 0; p < PASSES; ++p) {
                     const float vl = fmaf((float)p, step, v0);
                     const float fl = floorf(vl);
-                    const int jj = (int)fl;
+                    const int jj = row_entry((int)fl, J, 0, si, dg.status);
                     const float d0 = vl - fl;
                     const float w0 = fmaxf(0.f, fmaf(-d0, cs.z, cs.w));
                     const float w1 = fmaxf(0.f, fmaf(d0, cs.z, jp.z));
@@ -186,14 +195,15 @@ __device__ __forceinline__ void backproject_single_item(
 template <int PASSES, bool LINKED, bool SWAP>
 __device__ __forceinline__ void pair_angle(float (&acc)[PASSES][2][3], const float4 *rA,
                                            const float2 *rB, float v0, float step, float a,
-                                           float4 cs, float4 jp)
+                                           float4 cs, float4 jp, int J, const SliceInfo &si,
+                                           int *status)
 {
     constexpr int LO = SWAP ? 1 : 0, HI = SWAP ? 0 : 1;    // lower-u voxel: left unless cos < 0
 #pragma unroll
     for (int p = 0; p < PASSES; ++p) {
         const float vl = fmaf((float)p, step, v0);
         const float fl = floorf(vl);
-        const int jj = (int)fl;
+        const int jj = row_entry((int)fl, J, 1, si, status);
         const float d0 = vl - fl;
         float dh = d0 + a;
         const bool o = dh >= 1.f;
@@ -284,9 +294,11 @@ __device__ __forceinline__ void backproject_pair_item(
                 const float v0 = fmaf(fx, cs.x, fmaf(-fy, cs.y, jp.y)) + fminf(cs.x, 0.f);
                 const float step = -16.f * cs.y;
                 if (cs.x >= 0.f)
-                    pair_angle<PASSES, LINKED, false>(acc, rowA + J, rowB + J, v0, step, cs.x, cs, jp);
+                    pair_angle<PASSES, LINKED, false>(acc, rowA + J, rowB + J, v0, step, cs.x, cs, jp,
+                                                      J, si, dg.status);
                 else
-                    pair_angle<PASSES, LINKED, true>(acc, rowA + J, rowB + J, v0, step, -cs.x, cs, jp);
+                    pair_angle<PASSES, LINKED, true>(acc, rowA + J, rowB + J, v0, step, -cs.x, cs, jp,
+                                                     J, si, dg.status);
                 rowA += si.gw;
                 rowB += si.gw;
             }
@@ -327,15 +339,18 @@ __device__ __forceinline__ void backproject_pair_item(
 // is exact only up to FP32 rounding of d, so results agree with the other
 // variants to FP32 rounding, not bit for bit.
 template <bool LINKED, bool SWAP, int q0, int q1>
-__device__ __forceinline__ void mirror_pair_angle(float (&acc)[4][2][3], const float4 *rA,
-                                                  const float2 *rB, const float4 *mA,
-                                                  const float2 *mB, float vl, float a, float4 cs,
-                                                  float4 jp)
+__device__ __forceinline__ void mirror_pair_angle(float (&acc)[4][2][3], const float4 *row_a,
+                                                  const float2 *row_b, float vl, float a,
+                                                  float4 cs, float4 jp, int J, int JM,
+                                                  const SliceInfo &si, int *status)
 {
-    // vl: detector position of the pair's lower-u voxel; a = |cos|; q0, q1:
-    // the acc indices of the pair (direct) and of its point mirror
+    // vl: detector position of the pair's lower-u voxel (relative to J); a =
+    // |cos|; q0, q1: the acc indices of the pair (direct) and of its point
+    // mirror; row_a / row_b: the row's entry of pixel 0; the image of entry
+    // J + jj is JM - jj, JM = n_det - 3 - J
     const float fl = floorf(vl);
-    const int jj = (int)fl;
+    const int ed = J + row_entry((int)fl, J, 1, si, status);          // the pair's entry
+    const int em = JM + row_entry(-(int)fl, JM, 1, si, status);       // its image's entry
     const float d0 = vl - fl;
     float dh = d0 + a;
     const bool o = dh >= 1.f;
@@ -347,29 +362,29 @@ __device__ __forceinline__ void mirror_pair_angle(float (&acc)[4][2][3], const f
     // which takes voxel h's weights at the mirrored pixels
     constexpr int LO = SWAP ? 1 : 0, HI = SWAP ? 0 : 1;
     if (LINKED) {
-        const float2 t = __ldg(rB + jj);                                         // slots 0, 1
-        const float g2 = __ldg(reinterpret_cast<const float *>(rB + jj + 1) + 1);      // slot 2
+        const float2 t = __ldg(row_b + ed);                                      // slots 0, 1
+        const float g2 = __ldg(reinterpret_cast<const float *>(row_b + ed + 1) + 1);   // slot 2
         acc[q0][LO][0] = fmaf(w0l, t.x, fmaf(w1l, t.y, acc[q0][LO][0]));
         acc[q0][HI][0] = fmaf(s0, t.x, fmaf(s1, t.y, fmaf(s2, g2, acc[q0][HI][0])));
-        const float2 u = __ldg(mB - jj);                                         // slots 2, 1
-        const float g0 = __ldg(reinterpret_cast<const float *>(mB - jj + 1) + 1);      // slot 0
+        const float2 u = __ldg(row_b + em);                                      // slots 2, 1
+        const float g0 = __ldg(reinterpret_cast<const float *>(row_b + em + 1) + 1);   // slot 0
         acc[q1][LO][0] = fmaf(w0l, g0, fmaf(w1l, u.y, acc[q1][LO][0]));
         acc[q1][HI][0] = fmaf(s0, g0, fmaf(s1, u.y, fmaf(s2, u.x, acc[q1][HI][0])));
     } else {
-        const float4 ta = __ldg(rA + jj);       // slot 0 (mu, delta, sigma), slot 1 mu
-        const float2 tb = __ldg(rB + jj);       // slot 1 (delta, sigma)
-        const float m2 = __ldg(reinterpret_cast<const float *>(rA + jj + 1) + 3);  // slot 2 mu
-        const float2 tc = __ldg(rB + jj + 1);   // slot 2 (delta, sigma)
+        const float4 ta = __ldg(row_a + ed);       // slot 0 (mu, delta, sigma), slot 1 mu
+        const float2 tb = __ldg(row_b + ed);       // slot 1 (delta, sigma)
+        const float m2 = __ldg(reinterpret_cast<const float *>(row_a + ed + 1) + 3);  // slot 2 mu
+        const float2 tc = __ldg(row_b + ed + 1);   // slot 2 (delta, sigma)
         acc[q0][LO][0] = fmaf(w0l, ta.x, fmaf(w1l, ta.w, acc[q0][LO][0]));
         acc[q0][LO][1] = fmaf(w0l, ta.y, fmaf(w1l, tb.x, acc[q0][LO][1]));
         acc[q0][LO][2] = fmaf(w0l, ta.z, fmaf(w1l, tb.y, acc[q0][LO][2]));
         acc[q0][HI][0] = fmaf(s0, ta.x, fmaf(s1, ta.w, fmaf(s2, m2, acc[q0][HI][0])));
         acc[q0][HI][1] = fmaf(s0, ta.y, fmaf(s1, tb.x, fmaf(s2, tc.x, acc[q0][HI][1])));
         acc[q0][HI][2] = fmaf(s0, ta.z, fmaf(s1, tb.y, fmaf(s2, tc.y, acc[q0][HI][2])));
-        const float4 ma = __ldg(mA - jj);       // slot 2 (mu, delta, sigma), slot 1 mu
-        const float2 mb = __ldg(mB - jj);       // slot 1 (delta, sigma)
-        const float n0 = __ldg(reinterpret_cast<const float *>(mA - jj + 1) + 3);  // slot 0 mu
-        const float2 mc = __ldg(mB - jj + 1);   // slot 0 (delta, sigma)
+        const float4 ma = __ldg(row_a + em);       // slot 2 (mu, delta, sigma), slot 1 mu
+        const float2 mb = __ldg(row_b + em);       // slot 1 (delta, sigma)
+        const float n0 = __ldg(reinterpret_cast<const float *>(row_a + em + 1) + 3);  // slot 0 mu
+        const float2 mc = __ldg(row_b + em + 1);   // slot 0 (delta, sigma)
         acc[q1][LO][0] = fmaf(w0l, n0, fmaf(w1l, ma.w, acc[q1][LO][0]));
         acc[q1][LO][1] = fmaf(w0l, mc.x, fmaf(w1l, mb.x, acc[q1][LO][1]));
         acc[q1][LO][2] = fmaf(w0l, mc.y, fmaf(w1l, mb.y, acc[q1][LO][2]));
@@ -451,25 +466,27 @@ __device__ __forceinline__ void backproject_mirror_item(
                 const float vB = fmaf(fx, cs.x, fmaf(fy, cs.y, jp.w)) + lo;
                 const float step = 16.f * cs.y;
                 const float a = fabsf(cs.x);
-                const float4 *aA = rowA + JA, *aM = rowA + (nm3 - JA);
-                const float2 *bA = rowB + JA, *bM = rowB + (nm3 - JA);
-                const float4 *cA = rowA + JB, *cM = rowA + (nm3 - JB);
-                const float2 *dA = rowB + JB, *dM = rowB + (nm3 - JB);
+                const int JMA = nm3 - JA, JMB = nm3 - JB;
+                int *const st = dg.status;
                 if (cs.x >= 0.f) {
 #pragma unroll
                     for (int p = 0; p < PASSES; ++p) {
-                        mirror_pair_angle<LINKED, false, 0, 1>(acc[p], aA, bA, aM, bM,
-                                                               fmaf((float)p, -step, vA), a, cs, jp);
-                        mirror_pair_angle<LINKED, false, 2, 3>(acc[p], cA, dA, cM, dM,
-                                                               fmaf((float)p, step, vB), a, cs, jp);
+                        mirror_pair_angle<LINKED, false, 0, 1>(acc[p], rowA, rowB,
+                                                               fmaf((float)p, -step, vA), a, cs, jp,
+                                                               JA, JMA, si, st);
+                        mirror_pair_angle<LINKED, false, 2, 3>(acc[p], rowA, rowB,
+                                                               fmaf((float)p, step, vB), a, cs, jp,
+                                                               JB, JMB, si, st);
                     }
                 } else {
 #pragma unroll
                     for (int p = 0; p < PASSES; ++p) {
-                        mirror_pair_angle<LINKED, true, 0, 1>(acc[p], aA, bA, aM, bM,
-                                                              fmaf((float)p, -step, vA), a, cs, jp);
-                        mirror_pair_angle<LINKED, true, 2, 3>(acc[p], cA, dA, cM, dM,
-                                                              fmaf((float)p, step, vB), a, cs, jp);
+                        mirror_pair_angle<LINKED, true, 0, 1>(acc[p], rowA, rowB,
+                                                              fmaf((float)p, -step, vA), a, cs, jp,
+                                                              JA, JMA, si, st);
+                        mirror_pair_angle<LINKED, true, 2, 3>(acc[p], rowA, rowB,
+                                                              fmaf((float)p, step, vB), a, cs, jp,
+                                                              JB, JMB, si, st);
                     }
                 }
                 rowA += si.gw;

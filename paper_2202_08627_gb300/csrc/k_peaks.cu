@@ -185,3 +185,41 @@ extern "C" int ei_selftest_wait_timeout(unsigned limit_us, int *status_out)
     *status_out = st;
     return EI_OK;
 }
+
+// Bounds-check self-test: 32 threads each read element i + skew of a
+// 64-float buffer through checked_index with the logical range [0, 31]; with
+// skew = 8 the last eight indices fall outside that range but inside the
+// buffer, so the read stays in bounds whether or not the check fires.
+__global__ void k_check_selftest(const float *buf, float *out, int skew, int *status)
+{
+    const int i = ei::checked_index((int)threadIdx.x + skew, 0, 31, status);
+    out[threadIdx.x] = buf[i];
+}
+
+extern "C" int ei_device_checks_enabled(void) { return ei::kDeviceChecks ? 1 : 0; }
+
+extern "C" int ei_selftest_device_check(int *status_out)
+{
+    using namespace ei;
+    if (!status_out) return EI_ERR_ARG;
+    float *buf = nullptr;
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 96 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, 96 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_check_selftest<<<1, 32>>>(buf, buf + 64, 8, d);
+        e = cudaGetLastError();
+    }
+    int st = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (buf) cudaFree(buf);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return EI_ERR_CUDA;
+    }
+    *status_out = st;
+    return EI_OK;
+}

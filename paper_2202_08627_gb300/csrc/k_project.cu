@@ -164,8 +164,12 @@ __device__ __forceinline__ RaySetup ray_setup(const AngleInfo &an, int j, int n,
 // at i0 and its difference to the next).
 template <int UNROLL, bool LINKED>
 __device__ __forceinline__ void ray_rows(const RaySetup &rs, int o0, int o1, const float4 *A,
-                                         const float2 *B, int64_t w, float (&acc)[3])
+                                         const float2 *B, int64_t w, float (&acc)[3],
+                                         int *status)
 {
+    // the sampled position lies in [-1, n) by construction (ray_setup): entry
+    // i0 + 1 of the row's n + 1; check builds verify it
+    const int n = (int)w - 1;
     if (o0 > o1) return;
     const float inv32 = 2.3283064365386963e-10f;   // 2^-32
     long long pos = rs.base + (long long)o0 * rs.p1;
@@ -180,7 +184,7 @@ __device__ __forceinline__ void ray_rows(const RaySetup &rs, int o0, int o1, con
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
             const long long q = pos + u * p1;
-            const int i0 = (int)(q >> 32);                     // floor of the position
+            const int i0 = checked_index((int)(q >> 32), -1, n - 1, status);   // floor of the position
             f[u] = (float)(unsigned)(q & 0xffffffffLL) * inv32;
             if (!LINKED) va[u] = __ldg(rowA + u * w + i0);
             vb[u] = __ldg(rowB + u * w + i0);
@@ -200,7 +204,7 @@ __device__ __forceinline__ void ray_rows(const RaySetup &rs, int o0, int o1, con
         rowB += UNROLL * w;
     }
     for (; o <= o1; ++o) {
-        const int i0 = (int)(pos >> 32);
+        const int i0 = checked_index((int)(pos >> 32), -1, n - 1, status);
         const float f = (float)(unsigned)(pos & 0xffffffffLL) * inv32;
         const float2 vb = __ldg(rowB + i0);
         if (LINKED) {
@@ -242,13 +246,17 @@ __device__ __forceinline__ void project_ray(const SliceInfo &si, const AngleInfo
                                             const float2 *__restrict__ xpB,
                                             const float4 *__restrict__ xtA,
                                             const float2 *__restrict__ xtB, float *out,
-                                            int64_t plane, float link)
+                                            int64_t plane, float link, int *status)
 {
     const RaySetup rs = ray_setup(an, j, si.n, si.n_det);
     const int64_t off = si.pp_off + 1;
     float acc[3] = {0.f, 0.f, 0.f};
+    if (kDeviceChecks && rs.o_lo <= rs.o_hi)       // rows of the slice
+        if (checked_index(rs.o_lo, 0, si.n - 1, status) != rs.o_lo ||
+            checked_index(rs.o_hi, 0, si.n - 1, status) != rs.o_hi)
+            return;
     ray_rows<UNROLL, LINKED>(rs, rs.o_lo, rs.o_hi, (an.col_dom ? xtA : xpA) + off,
-                             (an.col_dom ? xtB : xpB) + off, si.n + 1, acc);
+                             (an.col_dom ? xtB : xpB) + off, si.n + 1, acc, status);
     ray_store<LINKED>(out, plane, acc, an.pch, link);
 }
 
@@ -299,7 +307,8 @@ __device__ __forceinline__ void project_item(const DevGeom &dg, const int *prefi
         out[2 * plane] = 0.f;
         return;
     }
-    project_ray<UNROLL, LINKED>(si, dg.ang[si.ang_off + a], j, xpA, xpB, xtA, xtB, out, plane, link);
+    project_ray<UNROLL, LINKED>(si, dg.ang[si.ang_off + a], j, xpA, xpB, xtA, xtB, out, plane, link,
+                                dg.status);
 }
 
 // One block per work item.

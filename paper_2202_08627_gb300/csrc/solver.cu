@@ -921,6 +921,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         EI_CUDA_TRY(cudaGetLastError());
         *evals = 0;
     } else {
+        NvtxRange init("initial evaluation");
         k_to_scaled<<<NBv, T, 0, st>>>(g->dg, x_dev, sv->u, inv);
         count_launches(g, 1);
         if (ow) {
@@ -1031,6 +1032,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
             *timed_out = true;                // between rounds: nothing in flight
             break;
         }
+        NvtxRange rr("solver round");
         if (exec) {
             err = cudaGraphLaunch(exec, st);
             g->launches += launches_per_round;
@@ -1056,6 +1058,7 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
 int reconstruct(ei_geometry *g, const float *s_exp, float *vol_inout, const ei_solve_opts *opts,
                 ei_solve_report *report, cudaStream_t st)
 {
+    NvtxRange range("ei_reconstruct");
     const auto t0 = std::chrono::steady_clock::now();
     if (opts->resume && !(g->solver && g->solver->has_state && g->solver->m == opts->lbfgs_m &&
                           g->solver->off_which == g->off_which)) {

@@ -97,7 +97,8 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_unet_set_tensor_path", "ei_set_flat_table", "ei_selftest_wait_timeout",
             "ei_solver_state_size", "ei_solver_save", "ei_solver_load",
             "ei_unet_get_optimizer", "ei_unet_set_optimizer", "ei_fail_alloc_after",
-            "ei_fail_alloc_pending", "ei_live_allocations", "ei_set_ring_modes"]
+            "ei_fail_alloc_pending", "ei_live_allocations", "ei_set_ring_modes",
+            "ei_device_checks_enabled", "ei_selftest_device_check"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
 N_FWD_VARIANTS, N_ADJ_VARIANTS = 13, 11
@@ -171,6 +172,10 @@ def load_library(path: str = None) -> ctypes.CDLL:
     lib.ei_solver_load.restype = c_int
     lib.ei_selftest_wait_timeout.argtypes = [ctypes.c_uint, P(c_int)]
     lib.ei_selftest_wait_timeout.restype = c_int
+    lib.ei_device_checks_enabled.argtypes = []
+    lib.ei_device_checks_enabled.restype = c_int
+    lib.ei_selftest_device_check.argtypes = [P(c_int)]
+    lib.ei_selftest_device_check.restype = c_int
     lib.ei_fail_alloc_after.argtypes = [c_int]
     lib.ei_fail_alloc_after.restype = c_int
     lib.ei_fail_alloc_pending.argtypes = [P(c_int)]
@@ -695,6 +700,20 @@ def ei_selftest_wait_timeout(limit_us: int) -> int:
     st = c_int(-1)
     _check(load_library().ei_selftest_wait_timeout(int(limit_us), ctypes.byref(st)),
            "ei_selftest_wait_timeout")
+    return st.value
+
+
+def ei_device_checks_enabled() -> bool:
+    """True for the build with device-side bounds checks (libei_check.so)."""
+    return bool(load_library().ei_device_checks_enabled())
+
+
+def ei_selftest_device_check() -> int:
+    """Runs a checked read whose index leaves its logical range but not its
+    buffer; returns the recorded status (EI_ERR_DEVICE_CHECK in the check
+    build, 0 in the regular one)."""
+    st = c_int(-1)
+    _check(load_library().ei_selftest_device_check(ctypes.byref(st)), "ei_selftest_device_check")
     return st.value
 
 

@@ -120,3 +120,7 @@ def test_solve_report_layout_and_ring_modes_argument_checks(lib):
     assert ei.ei_solve_report.slice_projections.offset == 64
     assert ei.ei_solve_report.slice_adjoints.offset == 72
     assert lib.ei_set_ring_modes(None, 4) == ei.EI_ERR_ARG
+
+
+def test_regular_build_has_no_device_checks(lib):
+    assert lib.ei_device_checks_enabled() == 0
