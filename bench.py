@@ -141,7 +141,8 @@ PROFILED_TRAFFIC = {("project", 8): 684.0e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 *
                     ("project", 11): 684.5e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("project", 12): 684.7e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("backproject", 0): 879.9e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
-                    ("backproject", 6): 871.7e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
+                    ("backproject", 6): 871.7e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
+                    ("backproject", 8): 848.6e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
 
 
 def projector_samples(slices):
@@ -170,6 +171,38 @@ def projector_samples(slices):
             cache[key] = float(np.maximum(cnt, 0).sum())
         out.append(cache[key])
     return np.asarray(out)
+
+
+def compare_launch_modes(G, s_exp, device):
+    """The autotuned projector and adjoint variants timed in every launch mode
+    (one block per work item; a persistent GPU-sized grid taking items from a
+    counter; a persistent grid whose blocks first take their SM's contiguous
+    chunk of items) on one objective+gradient evaluation of the whole batch,
+    traced CUDA events, best of 2; the autotuner's choice is restored."""
+    import torch
+    from paper_2202_08627_gb300 import ei
+    f, a, pers = G.variant
+    vol = G.empty("vol", device)
+    ei.ei_single_shot_fbp(G, s_exp, vol)
+    grad = G.empty("vol", device)
+    S = torch.empty(G.n_slices, dtype=torch.float64, device=device)
+    out = {}
+    names = {ei.LAUNCH_PER_ITEM: "one_block_per_item", ei.LAUNCH_PERSISTENT: "persistent",
+             ei.LAUNCH_SM_CHUNKS: "persistent_sm_chunks"}
+    for mode in names:
+        ei.ei_set_variant(G, f, a, mode)
+        best = None
+        for _ in range(2):
+            ei.ei_profile_enable(G, True)
+            ei.ei_objective_grad(G, vol, s_exp, S, grad)
+            p = ei.ei_profile_read(G)
+            t = (p["project_ms"], p["backproject_ms"])
+            best = t if best is None or sum(t) < sum(best) else best
+        out[names[mode]] = {"project_ms": best[0], "backproject_ms": best[1]}
+    ei.ei_profile_enable(G, False)
+    ei.ei_set_variant(G, f, a, pers)
+    del vol, grad
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -416,6 +449,7 @@ def run_ours(args, rank, world, local_rank):
     # every kernel three ways: algorithmic HBM bytes against the measured copy
     # bandwidth; bytes its loads bring from L1 into registers against the
     # measured L1 load rate; FP32 flops against the measured FMA rate
+    launch_modes = compare_launch_modes(G, s_exp, device)
     onchip = ei.ei_measure_peaks()
     # work per launch of each kernel: the slices it evaluated over its launches
     counts = {"project": (rep_k.slice_projections, prof["project_launches"]),
@@ -535,7 +569,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "gpu_launches": int(launches),
         "kernel_variant": {"projector": G.variant[0], "adjoint": G.variant[1],
-                           "persistent": G.variant[2], "solver_round": "CUDA graph"},
+                           "persistent": G.variant[2], "solver_round": "CUDA graph",
+                           "launch_modes": launch_modes},
         "e2e": e2e,
     }
     if ttt is not None:

@@ -331,9 +331,15 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * with 8-lane groups on 2 x 4 sub-patches, 5-7 four pairs of horizontally
  * adjacent voxels per thread (the pair shares its three detector pixels per
  * angle) with lanes along rows of 16 voxels, on 4 x 4 sub-patches in warps of
- * 16 x 4, or in warps of 8 x 8), and
- * either as one block per work item or as a persistent GPU-sized grid whose
- * blocks take work items from a counter.  Projector variants compute every
+ * 16 x 4, or in warps of 8 x 8, 8-10 a pair of the slice's top-left quadrant
+ * and its three mirror images about the slice centre (a point mirror takes
+ * the same hat weights at the mirrored pixels), in 16 or 32 rows per tile),
+ * launched in one of three modes (the `persistent` argument): 0 one block
+ * per work item, 1 a persistent GPU-sized grid whose blocks take work items
+ * from one counter, 2 a persistent grid whose blocks first take the items of
+ * their own SM's contiguous chunk of the work list (the blocks resident on an
+ * SM then work on neighbouring items and share L1 lines), then those of the
+ * other chunks.  Projector variants compute every
  * ray identically (bit-identical projections); adjoint variants sum every
  * voxel's angles in the same order but round the detector coordinate from a
  * different tile origin, so gradients agree to FP32 rounding (~1e-7
@@ -346,7 +352,8 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * (ei_set_linked: the single-channel kernels are timed) and the number of
  * variants this build has, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..12, adjoint 0..7).
+ * report a variant explicitly (ids: projector 0..12, adjoint 0..10, launch
+ * mode 0..2).
  */
 #define EI_TUNE_FORCE 1
 #define EI_TUNE_NO_CACHE_WRITE 2

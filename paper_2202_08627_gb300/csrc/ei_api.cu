@@ -108,7 +108,7 @@ static int take_device_status(ei_geometry *g, cudaStream_t st)
     return h;
 }
 
-void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent)
+void select_variants(ei_geometry *g, int fwd_id, int adj_id, int persistent)
 {
     g->fwd_variant.id = fwd_id;
     g->fwd_variant.prefix = g->fwd_prefixes[fwd_id];
@@ -558,6 +558,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_ic, (size_t)dg.total_ic);
     if (e == cudaSuccess) e = dev_alloc(g, &g->part_reg, (size_t)std::max(1, dg.total_vec));
     if (e == cudaSuccess) e = dev_alloc(g, &g->work_counter, 2);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->sm_counters, MAX_SM_CHUNKS);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e == cudaSuccess) e = dev_alloc(g, &g->S_dev, (size_t)n_slices);
     if (e == cudaSuccess) e = dev_alloc(g, &g->dev_status, 1);
@@ -581,7 +582,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     dg.prep_prefix = d_prep;
     dg.vec_prefix = d_vec;
     dg.status = g->dev_status;
-    select_variants(g, 0, 0, false);
+    select_variants(g, 0, 0, LAUNCH_PER_ITEM);
     g->ic_variant = ic_pipe_fits(dg.max_ndp, dg.mc.n_m) ? 1 : 0;
     *out = g;
     return EI_OK;
@@ -609,9 +610,9 @@ int ei_get_ic_variant(const ei_geometry *g, int *variant)
 int ei_set_variant(ei_geometry *g, int fwd_variant, int adj_variant, int persistent)
 {
     if (!g || fwd_variant < 0 || fwd_variant >= N_FWD_VARIANTS || adj_variant < 0 ||
-        adj_variant >= N_ADJ_VARIANTS)
+        adj_variant >= N_ADJ_VARIANTS || persistent < 0 || persistent >= N_LAUNCH_MODES)
         return EI_ERR_ARG;
-    select_variants(g, fwd_variant, adj_variant, persistent != 0);
+    select_variants(g, fwd_variant, adj_variant, persistent);
     return EI_OK;
 }
 
@@ -620,7 +621,7 @@ int ei_get_variant(const ei_geometry *g, int *fwd_variant, int *adj_variant, int
     if (!g || !fwd_variant || !adj_variant || !persistent) return EI_ERR_ARG;
     *fwd_variant = g->fwd_variant.id;
     *adj_variant = g->adj_variant.id;
-    *persistent = g->persistent ? 1 : 0;
+    *persistent = g->persistent;
     return EI_OK;
 }
 
@@ -696,8 +697,9 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
             double fm, am;
             bool found = false;
             while (fscanf(f, "%511s %d %d %d %lf %lf", k, &fv, &av, &pv, &fm, &am) == 6)
-                if (key == k && fv >= 0 && fv < N_FWD_VARIANTS && av >= 0 && av < N_ADJ_VARIANTS) {
-                    select_variants(g, fv, av, pv != 0);      // the last matching line wins
+                if (key == k && fv >= 0 && fv < N_FWD_VARIANTS && av >= 0 && av < N_ADJ_VARIANTS &&
+                    pv >= 0 && pv < N_LAUNCH_MODES) {
+                    select_variants(g, fv, av, pv);          // the last matching line wins
                     found = true;
                 }
             fclose(f);
@@ -720,7 +722,7 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
     const int rc = autotune_timed(g, adj_out, st);
     lib_free(adj_out);
     if (rc != EI_OK) return rc;
-    const int bf = g->fwd_variant.id, ba = g->adj_variant.id, bp = g->persistent ? 1 : 0;
+    const int bf = g->fwd_variant.id, ba = g->adj_variant.id, bp = g->persistent;
     if (!(flags & EI_TUNE_NO_CACHE_WRITE)) {
         const size_t slash = path.find_last_of('/');
         if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
@@ -738,33 +740,38 @@ int ei_autotune(ei_geometry *g, int flags, void *stream)
 // (their times in g_tune_last).
 static int autotune_timed(ei_geometry *g, float4 *adj_out, cudaStream_t st)
 {
-    // stage 1: every projector and adjoint variant, one-block-per-item and
-    // persistent launches, 3 launches each
-    int fid[2] = {0, 0}, aid[2] = {0, 0};
-    for (int pers = 0; pers < 2; ++pers) {
+    // stage 1: every projector and adjoint variant in launch modes 0 and 1, 3
+    // launches each (the SM-chunked mode 2 stays selectable but is not
+    // tuned: on the benchmark batch it was 43 % slower for the projector and
+    // 47 % for the adjoint, since the SMs then work on ~150 slices at once and
+    // their data no longer stays in L2)
+    constexpr int L = 2;
+    int fid[L] = {}, aid[L] = {};
+    for (int pers = 0; pers < L; ++pers) {
         double fbest = 1e300, abest = 1e300;
         for (int v = 0; v < N_FWD_VARIANTS; ++v) {
-            select_variants(g, v, 0, pers != 0);
+            select_variants(g, v, 0, pers);
             double ms = 0;
             const int rc = time_kernel(g, false, adj_out, st, 3, &ms);
             if (rc != EI_OK) return rc;
             if (ms < fbest * kTuneMargin) fbest = ms, fid[pers] = v;
         }
         for (int v = 0; v < N_ADJ_VARIANTS; ++v) {
-            select_variants(g, fid[pers], v, pers != 0);
+            select_variants(g, fid[pers], v, pers);
             double ms = 0;
             const int rc = time_kernel(g, true, adj_out, st, 3, &ms);
             if (rc != EI_OK) return rc;
             if (ms < abest * kTuneMargin) abest = ms, aid[pers] = v;
         }
     }
-    // stage 2: the two launch modes' winners re-timed alternately, 3 rounds,
-    // each keeping its fastest round (variants within a few % of each other
-    // are otherwise decided by noise)
-    double tf[2] = {1e300, 1e300}, ta[2] = {1e300, 1e300};
+    // stage 2: the launch modes' winners re-timed alternately, 3 rounds, each
+    // keeping its fastest round (variants within a few % of each other are
+    // otherwise decided by noise)
+    double tf[L], ta[L];
+    for (int k = 0; k < L; ++k) tf[k] = ta[k] = 1e300;
     for (int round = 0; round < 3; ++round)
-        for (int pers = 0; pers < 2; ++pers) {
-            select_variants(g, fid[pers], aid[pers], pers != 0);
+        for (int pers = 0; pers < L; ++pers) {
+            select_variants(g, fid[pers], aid[pers], pers);
             double mf = 0, ma = 0;
             int rc = time_kernel(g, false, adj_out, st, 2, &mf);
             if (rc == EI_OK) rc = time_kernel(g, true, adj_out, st, 2, &ma);
@@ -772,8 +779,10 @@ static int autotune_timed(ei_geometry *g, float4 *adj_out, cudaStream_t st)
             tf[pers] = std::min(tf[pers], mf);
             ta[pers] = std::min(ta[pers], ma);
         }
-    const int bp = tf[1] + ta[1] < (tf[0] + ta[0]) * kTuneMargin ? 1 : 0;
-    select_variants(g, fid[bp], aid[bp], bp != 0);
+    int bp = 0;                                   // the incumbent: one block per item
+    for (int k = 1; k < L; ++k)
+        if (tf[k] + ta[k] < (tf[bp] + ta[bp]) * kTuneMargin) bp = k;
+    select_variants(g, fid[bp], aid[bp], bp);
     g_tune_last[0] = tf[bp];
     g_tune_last[1] = ta[bp];
     return EI_OK;

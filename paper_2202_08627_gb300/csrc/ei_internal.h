@@ -136,6 +136,7 @@ constexpr int ADJ_TC = 32;                 // adjoint tile: 32 columns x (8 x pa
 constexpr int ADJ_MAX_TR = 128;            // tallest adjoint tile among the variants
 constexpr int ADJ_THREADS = 256;
 constexpr int PREP_TILE = 32;              // staging tile
+constexpr int EI_MAX_LBFGS_M = 32;         // largest L-BFGS memory (ei_solve_opts.lbfgs_m)
 constexpr int VEC_BLK = 4096;              // float4 per vector-op block (one slice per block)
 constexpr int VEC_THREADS = 256;
 
@@ -186,7 +187,51 @@ struct DevGeom {
     int *status = nullptr;
 };
 
+// Launch modes of the projector and the adjoint: one block per work item; a
+// persistent GPU-sized grid whose blocks take items from one counter; or a
+// persistent grid whose blocks first take the items of their own SM's
+// contiguous chunk of the work list (so the blocks resident on one SM work on
+// neighbouring items and share L1 lines), then those of the other chunks.
+enum LaunchMode { LAUNCH_PER_ITEM = 0, LAUNCH_PERSISTENT = 1, LAUNCH_SM_CHUNKS = 2 };
+constexpr int N_LAUNCH_MODES = 3;
+constexpr int MAX_SM_CHUNKS = 1024;        // per-SM chunk counters (>= %nsmid)
+
 #ifdef __CUDACC__
+// Next work item of an SM-chunked launch for the block's thread 0: the list
+// [0, total) is cut into nchunk contiguous chunks; the block takes the next
+// item of chunk (sm + k) % nchunk, k = *k_state (0: its own SM's chunk) and
+// advances k when that chunk is exhausted; -1 when every chunk is.  Each call
+// makes at most nchunk atomic increments; nothing waits.
+__device__ __forceinline__ int sm_chunk_next(int total, int *counters, int sm, int nchunk,
+                                             int *k_state)
+{
+    while (*k_state < nchunk) {
+        const int c = (sm + *k_state) % nchunk;
+        const int lo = (int)((long long)total * c / nchunk);
+        const int hi = (int)((long long)total * (c + 1) / nchunk);
+        if (lo < hi) {
+            const int idx = atomicAdd(counters + c, 1);
+            if (lo + idx < hi) return lo + idx;
+        }
+        ++*k_state;
+    }
+    return -1;
+}
+
+// The SM a block runs on, and the number of SM ids (PTX special registers).
+__device__ __forceinline__ int sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int sm_id_count()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(r));
+    return (int)r < MAX_SM_CHUNKS ? (int)r : MAX_SM_CHUNKS;
+}
+
 // Slice owning work item `item`: the largest s with prefix[s] <= item.
 __device__ __forceinline__ int find_slice(const int *prefix, int n_slices, int item)
 {
@@ -233,7 +278,8 @@ struct ei_geometry {
     int fwd_totals[ei::N_FWD_VARIANTS] = {};
     const int *adj_prefixes[ei::N_ADJ_VARIANTS] = {};
     int adj_totals[ei::N_ADJ_VARIANTS] = {};
-    bool persistent = false;
+    int persistent = 0;                // launch mode (LaunchMode) of projector and adjoint
+    int *sm_counters = nullptr;        // [MAX_SM_CHUNKS] chunk counters of LAUNCH_SM_CHUNKS
     int ic_variant = 0;                // 0: one block per row; 1: persistent, bulk-copy pipeline
     float link_gamma = 0.f;            // > 0: linked unknown h (mu = h, delta = gamma h, sigma = 0)
     int off_which = 0;                 // Eq. 4 offsets among the solver's unknowns (EI_OFFSET_*)
@@ -348,7 +394,7 @@ void record_error(cudaError_t e);
 // Remember a formatted message as the last error of this thread.
 void record_message(const char *fmt, ...);
 // Select kernel variants (ids in range) and the launch mode.
-void select_variants(ei_geometry *g, int fwd_id, int adj_id, bool persistent);
+void select_variants(ei_geometry *g, int fwd_id, int adj_id, int launch_mode);
 void destroy_solver(ei_geometry *g);
 // Checkpoint of the solver state (ei_solver_state_size / _save / _load).
 size_t solver_state_size(const ei_geometry *g, int m);

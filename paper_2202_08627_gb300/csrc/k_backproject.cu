@@ -564,15 +564,51 @@ k_backproject_persistent(DevGeom dg, const int *__restrict__ prefix, int total, 
     }
 }
 
+// Persistent, SM-chunked: the blocks resident on one SM take consecutive
+// tiles (neighbouring column tiles of the same rows, whose voxels read
+// neighbouring pixels) from their SM's chunk of the list, then tiles of the
+// other chunks; the chunk counters are 0 before the launch.
+template <int PASSES, int MINB, int LAY, bool LINKED>
+__global__ void __launch_bounds__(ADJ_THREADS, MINB)
+k_backproject_sm(DevGeom dg, const int *__restrict__ prefix, int total, int *counters,
+                 const float4 *__restrict__ gA, const float2 *__restrict__ gB,
+                 const float4 *__restrict__ v, float4 *__restrict__ out, float4 out_mult,
+                 float4 reg2, const int *__restrict__ active)
+{
+    __shared__ AdjShared sh;
+    __shared__ int s_item, s_k;
+    const int sm = sm_id(), nchunk = sm_id_count();
+    if (threadIdx.x == 0) s_k = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = sm_chunk_next(total, counters, sm % nchunk, nchunk, &s_k);
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) return;
+        backproject_item<PASSES, LAY, LINKED>(dg, prefix, item, sh, gA, gB, v, out, out_mult,
+                                              reg2, active);
+    }
+}
+
 template <int P, int M, int Q, bool L>
 static cudaError_t launch_bp_mode(const ei_geometry *g, const float4 *v, float4 *out,
                                   float4 out_mult, float4 reg2, const int *active, cudaStream_t st)
 {
     const AdjVariant &av = g->adj_variant;
     if (av.total == 0) return cudaSuccess;
-    if (!g->persistent) {
+    if (g->persistent == LAUNCH_PER_ITEM) {
         k_backproject<P, M, Q, L><<<av.total, ADJ_THREADS, 0, st>>>(
             g->dg, av.prefix, g->gA, g->gB, v, out, out_mult, reg2, active);
+    } else if (g->persistent == LAUNCH_SM_CHUNKS) {
+        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
+        if (per_sm == 0)
+            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_backproject_sm<P, M, Q, L>, ADJ_THREADS, 0));
+        const int grid = std::max(1, std::min(av.total, per_sm * g->num_sms));
+        EI_CUDA_TRY(cudaMemsetAsync(g->sm_counters, 0, MAX_SM_CHUNKS * sizeof(int), st));
+        k_backproject_sm<P, M, Q, L><<<grid, ADJ_THREADS, 0, st>>>(
+            g->dg, av.prefix, av.total, g->sm_counters, g->gA, g->gB, v, out, out_mult, reg2,
+            active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)

@@ -345,15 +345,50 @@ k_project_persistent(DevGeom dg, const int *__restrict__ prefix, int total, int 
     }
 }
 
+// Persistent, SM-chunked: the blocks resident on one SM take consecutive work
+// items (neighbouring ray groups of the same angles) from their SM's chunk of
+// the list, then items of the other chunks; the chunk counters are 0 before
+// the launch.  No block waits on another.
+template <int RAYS, int ANGLES, int UNROLL, int WRAYS, bool AFAST, bool LINKED, int QUADS>
+__global__ void __launch_bounds__(RAYS * ANGLES, 1280 / (RAYS * ANGLES))   // 5 blocks of 256
+k_project_sm(DevGeom dg, const int *__restrict__ prefix, int total, int *counters,
+             const float4 *__restrict__ xpA, const float2 *__restrict__ xpB,
+             const float4 *__restrict__ xtA, const float2 *__restrict__ xtB,
+             float *__restrict__ proj, float link, const int *__restrict__ active)
+{
+    __shared__ int s_item, s_k;
+    const int sm = sm_id(), nchunk = sm_id_count();
+    if (threadIdx.x == 0) s_k = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = sm_chunk_next(total, counters, sm % nchunk, nchunk, &s_k);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item < 0) return;
+        project_item<RAYS, ANGLES, UNROLL, WRAYS, AFAST, LINKED, QUADS>(dg, prefix, item, xpA, xpB, xtA, xtB,
+                                                                 proj, link, active);
+    }
+}
+
 template <int R, int A, int U, int W, bool F, bool L, int Q>
 static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float link,
                                        const int *active, cudaStream_t st)
 {
     const FwdVariant &v = g->fwd_variant;
     if (v.total == 0) return cudaSuccess;
-    if (!g->persistent) {
+    if (g->persistent == LAUNCH_PER_ITEM) {
         k_project<R, A, U, W, F, L, Q><<<v.total, R * A, 0, st>>>(g->dg, v.prefix, g->xpA, g->xpB,
                                                               g->xtA, g->xtB, proj, link, active);
+    } else if (g->persistent == LAUNCH_SM_CHUNKS) {
+        static int per_sm = 0;          // resident blocks per SM (same for every GB300)
+        if (per_sm == 0)
+            EI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_project_sm<R, A, U, W, F, L, Q>, R * A, 0));
+        const int grid = std::max(1, std::min(v.total, per_sm * g->num_sms));
+        EI_CUDA_TRY(cudaMemsetAsync(g->sm_counters, 0, MAX_SM_CHUNKS * sizeof(int), st));
+        k_project_sm<R, A, U, W, F, L, Q><<<grid, R * A, 0, st>>>(
+            g->dg, v.prefix, v.total, g->sm_counters, g->xpA, g->xpB, g->xtA, g->xtB, proj, link,
+            active);
     } else {
         static int per_sm = 0;          // resident blocks per SM (same for every GB300)
         if (per_sm == 0)

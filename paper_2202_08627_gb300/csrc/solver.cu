@@ -4,7 +4,8 @@
 //
 // Per slice k, in the solver's scaled variables u = x / scale:
 //   1. d = -H g: two-loop recursion over the kept (s_i, y_i) pairs, newest
-//      first then oldest first, H0 = (s.y / y.y) I of the newest pair;
+//      first then oldest first, H0 = (s.y / y.y) I of the newest pair, run
+//      on coefficients (below);
 //   2. Armijo backtracking: alpha0 = 1/|g| while no pair is kept, else 1;
 //      accept when S(u + alpha d) <= S(u) + c1 alpha g.d, else halve;
 //   3. s = alpha d, y = g_new - g; keep the pair when s.y > eps |s| |y|;
@@ -28,9 +29,19 @@
 // Each iteration's first trial is a fresh projection, so no rounding drift
 // accumulates in Pu across iterations.
 //
+// The two-loop recursion runs on coefficients, not on vectors: d is a
+// combination of the basis b = (s_i, y_i of the kept pairs, g), and every
+// dot product the recursion takes (s_i . q, y_i . r) is one of the basis'
+// Gram matrix, kept per slice in FP64 (2 ring + 1 rows).  An accepted step
+// adds one pass over the kept pairs: the new pair's dot products with them
+// and with itself; the new gradient's entries follow (g_new = g + y).  Forming
+// d from its coefficients is one more pass.  (A vector two-loop reads and
+// writes ~4 vectors per pair and direction, ~90 vector passes per iteration
+// with ten pairs; this takes ~45.)
+//
 // Vectors are the batched vol layout (float4 per voxel, pad lane kept at 0);
 // vector kernels work on VEC_BLK-element blocks that each belong to one slice
-// and write one FP64 partial dot product per block.  With Eq. 4's offsets
+// and write FP64 partial dot products per block.  With Eq. 4's offsets
 // among the unknowns, every vector continues after the volumes with one
 // offsets segment per slice (m_o(theta) then m_r(t), scaled by 1/off_scale,
 // three values per float4), whose blocks belong to their slice too.  A consumer block sums its
@@ -48,7 +59,7 @@
 namespace ei {
 
 struct SliceState {
-    double f, f_t, gd, gg, alpha, gamma, f0;
+    double f, f_t, gd, gg, alpha, gamma, f0;   // gamma: H0 scaling of the last direction
     double alpha_p;             // the step of the trial whose projections Pt holds
     double ratio;               // backtracking trial: alpha / alpha_p of the previous trial
     int k, count, head, trials;
@@ -68,11 +79,12 @@ struct Solver {
     float4 *Sr = nullptr, *Yr = nullptr;    // rings of `ring` slots
     float *Pu = nullptr, *Pt = nullptr;     // proj layout: projections of u and of the trial
     double *part_reg = nullptr;             // [solver blocks] regulariser partial sums
+    double *part_gd = nullptr;              // [solver blocks] g . d partial sums
     float *meas_stage = nullptr;            // device copy of host s_exp
     float4 *vol_stage = nullptr;            // device copy of host x0 / solution
-    double *part[4] = {nullptr, nullptr, nullptr, nullptr};
-    double *rho = nullptr;                  // [ring][S]
-    double *alpha_i = nullptr;              // [m][S]
+    double *part_dots = nullptr;            // [solver blocks][KD] partial dot products
+    double *gram = nullptr;                 // [S][GD][GD] basis Gram matrix per slice
+    double *coef = nullptr;                 // [S][GD] d's coefficients on the basis
     SliceState *st = nullptr;               // [S]
     int *mask_dir = nullptr, *mask_ls = nullptr, *mask_acc = nullptr;
     int *mask_first = nullptr, *mask_bt = nullptr;   // trial projected / interpolated
@@ -87,15 +99,23 @@ struct SolverDev {
     float4 *u, *g, *d, *xt, *gt, *Sr, *Yr;
     int64_t vol_count;
     int m, ring;
-    double *rho, *alpha_i;
+    double *gram, *coef, *part_dots;
     SliceState *st;
     int *mask_dir, *mask_ls, *mask_acc, *mask_first, *mask_bt;
 };
 
+// Basis of the coefficient two-loop: s of ring slot i is index i, y of slot i
+// is ring + i, the gradient g is 2 ring; GD = 2 ring + 1 indices.  Partial
+// dot products per vector block of an accepted step: KD = 4 ring + 5 (per
+// kept slot i: s . s_i, s . y_i, y . s_i, y . y_i at 4 i .. 4 i + 3; then
+// s . s, s . y, y . y, g_old . s, g_old . y).
+__host__ __device__ __forceinline__ int basis_dim(int ring) { return 2 * ring + 1; }
+__host__ __device__ __forceinline__ int dots_per_block(int ring) { return 4 * ring + 5; }
+
 static SolverDev dev_view(const Solver *s)
 {
     return SolverDev{s->u,  s->g,  s->d,   s->xt,     s->gt,      s->Sr,   s->Yr,
-                     s->vol_count, s->m, s->ring, s->rho, s->alpha_i, s->st,
+                     s->vol_count, s->m, s->ring, s->gram, s->coef, s->part_dots, s->st,
                      s->mask_dir, s->mask_ls, s->mask_acc, s->mask_first, s->mask_bt};
 }
 
@@ -373,182 +393,111 @@ __global__ void k_offsets_grad(DevGeom dg, int which, int ring_k, float scale,
     }
 }
 
-// two-loop, first pass start: d = g; pout = S_slot(0) . d
-__global__ void k_tl_first(DevGeom dg, SolverDev sv, double *__restrict__ pout)
+// g . g per block after the initial evaluation (the Gram matrix's first entry)
+__global__ void k_gram_gg(DevGeom dg, SolverDev sv)
 {
+    __shared__ double red[32];
     const VecBlock b = vec_block(dg);
-    const int s = b.s;
-    if (!sv.mask_dir[s]) {
-        if (threadIdx.x == 0) pout[blockIdx.x] = 0.0;
-        return;
-    }
-    const bool pair = sv.st[s].count > 0;
-    const float4 *Sv = sv.Sr + (int64_t)(pair ? slot_of(sv, s, 0) : 0) * sv.vol_count;
     double acc = 0.0;
-    for (int64_t i = b.begin + threadIdx.x; i < b.end; i += blockDim.x) {
-        const float4 gv = sv.g[i];
-        sv.d[i] = gv;
-        if (pair) acc += dot3(Sv[i], gv);
-    }
-    __shared__ double red[32];
-    const double t = block_allsum(acc, red);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// two-loop, first pass step i (newest first):
-//   alpha_i = rho_i S_i.d ; d -= alpha_i Y_i ; pout = S_{i+1} . d
-__global__ void k_tl_down(DevGeom dg, SolverDev sv, int i, const double *__restrict__ pin,
-                          double *__restrict__ pout)
-{
-    __shared__ double red[32];
-    const VecBlock b = vec_block(dg);
-    const int s = b.s;
-    if (!sv.mask_dir[s] || i >= sv.st[s].count) {
-        if (threadIdx.x == 0) pout[blockIdx.x] = pin[blockIdx.x];
-        return;
-    }
-    const int slot = slot_of(sv, s, i);
-    const double sd = slice_partials(dg, pin, s, red);
-    const double al = sv.rho[(int64_t)slot * dg.n_slices + s] * sd;
-    if (blockIdx.x == dg.vec_prefix[s] && threadIdx.x == 0)
-        sv.alpha_i[(int64_t)i * dg.n_slices + s] = al;
-    const float alf = (float)al;
-    const float4 *Y = sv.Yr + (int64_t)slot * sv.vol_count;
-    const bool next = i + 1 < sv.st[s].count;
-    const float4 *Sn = sv.Sr + (int64_t)(next ? slot_of(sv, s, i + 1) : 0) * sv.vol_count;
-    double acc = 0.0;
-    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
-        const float4 y = Y[e];
-        float4 dv = sv.d[e];
-        dv = f4(fmaf(-alf, y.x, dv.x), fmaf(-alf, y.y, dv.y), fmaf(-alf, y.z, dv.z));
-        sv.d[e] = dv;
-        if (next) acc += dot3(Sn[e], dv);
-    }
-    const double t = block_allsum(acc, red);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// middle: d *= gamma (1 without pairs); pout = Y_{count-1} . d
-__global__ void k_tl_mid(DevGeom dg, SolverDev sv, double *__restrict__ pout)
-{
-    __shared__ double red[32];
-    const VecBlock b = vec_block(dg);
-    const int s = b.s;
-    if (!sv.mask_dir[s]) {
-        if (threadIdx.x == 0) pout[blockIdx.x] = 0.0;
-        return;
-    }
-    const int cnt = sv.st[s].count;
-    const float gam = cnt > 0 ? (float)sv.st[s].gamma : 1.f;
-    const float4 *Y = sv.Yr + (int64_t)(cnt > 0 ? slot_of(sv, s, cnt - 1) : 0) * sv.vol_count;
-    double acc = 0.0;
-    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
-        float4 dv = sv.d[e];
-        dv = f4(dv.x * gam, dv.y * gam, dv.z * gam);
-        sv.d[e] = dv;
-        if (cnt > 0) acc += dot3(Y[e], dv);
-    }
-    const double t = block_allsum(acc, red);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// two-loop, second pass step i (oldest first):
-//   beta = rho_i Y_i.d ; d += (alpha_i - beta) S_i ; pout = Y_{i-1} . d
-__global__ void k_tl_up(DevGeom dg, SolverDev sv, int i, const double *__restrict__ pin,
-                        double *__restrict__ pout)
-{
-    __shared__ double red[32];
-    const VecBlock b = vec_block(dg);
-    const int s = b.s;
-    if (!sv.mask_dir[s] || i >= sv.st[s].count) {
-        if (threadIdx.x == 0) pout[blockIdx.x] = pin[blockIdx.x];
-        return;
-    }
-    const int slot = slot_of(sv, s, i);
-    const double yd = slice_partials(dg, pin, s, red);
-    const double beta = sv.rho[(int64_t)slot * dg.n_slices + s] * yd;
-    const float coef = (float)(sv.alpha_i[(int64_t)i * dg.n_slices + s] - beta);
-    const float4 *Sv = sv.Sr + (int64_t)slot * sv.vol_count;
-    const bool next = i >= 1;
-    const float4 *Yn = sv.Yr + (int64_t)(next ? slot_of(sv, s, i - 1) : 0) * sv.vol_count;
-    double acc = 0.0;
-    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
-        const float4 sv4 = Sv[e];
-        float4 dv = sv.d[e];
-        dv = f4(fmaf(coef, sv4.x, dv.x), fmaf(coef, sv4.y, dv.y), fmaf(coef, sv4.z, dv.z));
-        sv.d[e] = dv;
-        if (next) acc += dot3(Yn[e], dv);
-    }
-    const double t = block_allsum(acc, red);
-    if (threadIdx.x == 0) pout[blockIdx.x] = t;
-}
-
-// end: d = -d ; p_gd = g.d ; p_gg = g.g
-__global__ void k_tl_end(DevGeom dg, SolverDev sv, double *__restrict__ p_gd, double *__restrict__ p_gg)
-{
-    __shared__ double red[32];
-    const VecBlock b = vec_block(dg);
-    const int s = b.s;
-    if (!sv.mask_dir[s]) {
-        if (threadIdx.x == 0) p_gd[blockIdx.x] = 0.0, p_gg[blockIdx.x] = 0.0;
-        return;
-    }
-    double a_gd = 0.0, a_gg = 0.0;
-    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
-        float4 dv = sv.d[e];
-        dv = f4(-dv.x, -dv.y, -dv.z);
-        sv.d[e] = dv;
-        const float4 gv = sv.g[e];
-        a_gd += dot3(gv, dv);
-        a_gg += dot3(gv, gv);
-    }
-    const double t1 = block_allsum(a_gd, red);
-    const double t2 = block_allsum(a_gg, red);
-    if (threadIdx.x == 0) p_gd[blockIdx.x] = t1, p_gg[blockIdx.x] = t2;
-}
-
-// d = -g for slices whose direction was reset
-__global__ void k_reset_dir(DevGeom dg, SolverDev sv)
-{
-    const VecBlock b = vec_block(dg);
-    if (!sv.st[b.s].reset) return;
     for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
         const float4 gv = sv.g[e];
-        sv.d[e] = f4(-gv.x, -gv.y, -gv.z);
+        acc += dot3(gv, gv);
     }
+    const double t = block_allsum(acc, red);
+    if (threadIdx.x == 0) sv.part_dots[(int64_t)blockIdx.x * dots_per_block(sv.ring)] = t;
 }
 
-// trial point xt = u + alpha d, and the regulariser's value at it (part_reg)
-__global__ void k_trial(DevGeom dg, SolverDev sv, float4 reg1, double *__restrict__ part_reg)
+// trial point xt = u + alpha d, and the regulariser's value at it (part_reg);
+// an iteration's first trial first forms d = sum_j coef_j b_j over the basis
+// (the kept pairs' s and y, and g) and its slope g . d (part_gd), which the
+// Armijo test takes from the d it steps along
+__global__ void k_trial(DevGeom dg, SolverDev sv, float4 reg1, double *__restrict__ part_reg,
+                        double *__restrict__ part_gd)
 {
     __shared__ double red[32];
+    __shared__ float cS[EI_MAX_LBFGS_M + 1], cY[EI_MAX_LBFGS_M + 1];
+    __shared__ int slots[EI_MAX_LBFGS_M + 1];
     const VecBlock b = vec_block(dg);
-    if (!sv.mask_ls[b.s]) return;
-    const float al = (float)sv.st[b.s].alpha;
-    double acc = 0.0;
+    const int s = b.s;
+    if (!sv.mask_ls[s]) return;
+    const SliceState &q = sv.st[s];
+    const float al = (float)q.alpha;
+    const bool first = q.trials == 0;
+    const int cnt = q.count, R = sv.ring, GD = basis_dim(R);
+    const double *co = sv.coef + (int64_t)s * GD;
+    if (first && (int)threadIdx.x < cnt) {
+        const int sl = slot_of(sv, s, threadIdx.x);
+        slots[threadIdx.x] = sl;
+        cS[threadIdx.x] = (float)co[sl];
+        cY[threadIdx.x] = (float)co[R + sl];
+    }
+    const float cg = (float)co[2 * R];
+    __syncthreads();
+    double acc = 0.0, gd = 0.0;
     for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
-        const float4 uv = sv.u[e], dv = sv.d[e];
+        float4 dv;
+        if (first) {
+            const float4 gv = sv.g[e];
+            dv = f4(cg * gv.x, cg * gv.y, cg * gv.z);
+            for (int k = 0; k < cnt; ++k) {
+                const int64_t off = (int64_t)slots[k] * sv.vol_count + e;
+                const float4 sv4 = sv.Sr[off], yv4 = sv.Yr[off];
+                dv = f4(fmaf(cS[k], sv4.x, fmaf(cY[k], yv4.x, dv.x)),
+                        fmaf(cS[k], sv4.y, fmaf(cY[k], yv4.y, dv.y)),
+                        fmaf(cS[k], sv4.z, fmaf(cY[k], yv4.z, dv.z)));
+            }
+            sv.d[e] = dv;
+            gd += dot3(gv, dv);
+        } else {
+            dv = sv.d[e];
+        }
+        const float4 uv = sv.u[e];
         const float4 x = f4(fmaf(al, dv.x, uv.x), fmaf(al, dv.y, uv.y), fmaf(al, dv.z, uv.z));
         sv.xt[e] = x;
         if (!b.off) acc += reg_term(x, reg1);
     }
     const double t = block_allsum(acc, red);
     if (threadIdx.x == 0) part_reg[blockIdx.x] = t;
+    if (first) {
+        const double tg = block_allsum(gd, red);
+        if (threadIdx.x == 0) part_gd[blockIdx.x] = tg;
+    }
 }
 
-// accepted step: S_head = xt - u, Y_head = gt - g, u = xt, g = gt; partial s.y, s.s, y.y
-__global__ void k_accept(DevGeom dg, SolverDev sv, double *__restrict__ p_sy,
-                         double *__restrict__ p_ss, double *__restrict__ p_yy)
+// A dot product accumulated by one thread: FP32 over chunks of 4 elements
+// (12 products), FP64 across chunks.  FP64 runs at a small fraction of the
+// FP32 rate on this GPU; chunks of 4 keep the rounding within ~2x that of an
+// FP64 sum of per-element FP32 dots.
+struct ChunkedDot {
+    double total = 0.0;
+    float chunk = 0.f;
+    __device__ __forceinline__ void add(float4 a, float4 b, int e_count)
+    {
+        chunk = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, chunk)));
+        if ((e_count & 3) == 3) total += (double)chunk, chunk = 0.f;
+    }
+    __device__ __forceinline__ double value() const { return total + (double)chunk; }
+};
+
+// accepted step: S_head = s = xt - u, Y_head = y = gt - g, u = xt, g = gt; and
+// the new pair's dot products with the kept pairs (before this update), with
+// itself and with the old gradient, per block (ChunkedDot per thread, FP64
+// across threads): part_dots[block] = (s . s_i, s . y_i, y . s_i, y . y_i at
+// 4 i; s . s, s . y, y . y, g_old . s, g_old . y at 4 ring).  Taken directly
+// from s and y, so a small y near convergence loses no precision.
+__global__ void k_accept(DevGeom dg, SolverDev sv)
 {
     __shared__ double red[32];
     const VecBlock b = vec_block(dg);
     const int s = b.s;
     if (!sv.mask_acc[s]) return;
-    const int slot = sv.st[s].head;
-    float4 *Sv = sv.Sr + (int64_t)slot * sv.vol_count;
-    float4 *Yv = sv.Yr + (int64_t)slot * sv.vol_count;
-    double a_sy = 0.0, a_ss = 0.0, a_yy = 0.0;
-    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x) {
+    const int head = sv.st[s].head, cnt = sv.st[s].count, R = sv.ring;
+    double *out = sv.part_dots + (int64_t)blockIdx.x * dots_per_block(R);
+    float4 *Sv = sv.Sr + (int64_t)head * sv.vol_count;
+    float4 *Yv = sv.Yr + (int64_t)head * sv.vol_count;
+    ChunkedDot a_ss, a_sy, a_yy, a_gs, a_gy;
+    int ec = 0;
+    for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x, ++ec) {
         const float4 x = sv.xt[e], uv = sv.u[e], gn = sv.gt[e], go = sv.g[e];
         const float4 sd = f4(x.x - uv.x, x.y - uv.y, x.z - uv.z);
         const float4 yd = f4(gn.x - go.x, gn.y - go.y, gn.z - go.z);
@@ -556,14 +505,36 @@ __global__ void k_accept(DevGeom dg, SolverDev sv, double *__restrict__ p_sy,
         Yv[e] = yd;
         sv.u[e] = x;
         sv.g[e] = gn;
-        a_sy += dot3(sd, yd);
-        a_ss += dot3(sd, sd);
-        a_yy += dot3(yd, yd);
+        a_ss.add(sd, sd, ec);
+        a_sy.add(sd, yd, ec);
+        a_yy.add(yd, yd, ec);
+        a_gs.add(go, sd, ec);
+        a_gy.add(go, yd, ec);
     }
-    const double t1 = block_allsum(a_sy, red);
-    const double t2 = block_allsum(a_ss, red);
-    const double t3 = block_allsum(a_yy, red);
-    if (threadIdx.x == 0) p_sy[blockIdx.x] = t1, p_ss[blockIdx.x] = t2, p_yy[blockIdx.x] = t3;
+    const double tail[5] = {a_ss.value(), a_sy.value(), a_yy.value(), a_gs.value(), a_gy.value()};
+    for (int j = 0; j < 5; ++j) {
+        const double t = block_allsum(tail[j], red);
+        if (threadIdx.x == 0) out[4 * R + j] = t;
+    }
+    for (int k = 0; k < cnt; ++k) {           // the kept pairs (head is never one of them)
+        const int sl = slot_of(sv, s, k);
+        const float4 *Sk = sv.Sr + (int64_t)sl * sv.vol_count;
+        const float4 *Yk = sv.Yr + (int64_t)sl * sv.vol_count;
+        ChunkedDot a0, a1, a2, a3;
+        int ek = 0;
+        for (int64_t e = b.begin + threadIdx.x; e < b.end; e += blockDim.x, ++ek) {
+            const float4 sd = Sv[e], yd = Yv[e], sk = Sk[e], yk = Yk[e];
+            a0.add(sd, sk, ek);
+            a1.add(sd, yk, ek);
+            a2.add(yd, sk, ek);
+            a3.add(yd, yk, ek);
+        }
+        const double four[4] = {a0.value(), a1.value(), a2.value(), a3.value()};
+        for (int j = 0; j < 4; ++j) {
+            const double t = block_allsum(four[j], red);
+            if (threadIdx.x == 0) out[4 * sl + j] = t;
+        }
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -574,20 +545,25 @@ struct Opts {
     int max_iter, max_trials;
 };
 
-__device__ double serial_sum(const DevGeom &dg, const double *part, int s)
+// Sum over a slice's vector blocks of entry k of their partials (stride KD),
+// in block order.
+__device__ double serial_sum(const DevGeom &dg, const double *part, int stride, int k, int s)
 {
     double acc = 0.0;
-    for (int b = dg.vec_prefix[s]; b < dg.vec_prefix[s + 1]; ++b) acc += part[b];
+    for (int b = dg.vec_prefix[s]; b < dg.vec_prefix[s + 1]; ++b) acc += part[(int64_t)b * stride + k];
     return acc;
 }
 
-// initial evaluation done: f0 = S, state reset
+// initial evaluation done: f0 = S, state reset, Gram matrix (g . g only)
 __global__ void k_init_state(DevGeom dg, SolverDev sv, const double *__restrict__ S, int *summary)
 {
     int running = 0;
+    const int R = sv.ring, GD = basis_dim(R), KD = dots_per_block(R);
     for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
         SliceState &q = sv.st[s];
         q = SliceState{};
+        double *G = sv.gram + (int64_t)s * GD * GD;
+        G[2 * R * GD + 2 * R] = serial_sum(dg, sv.part_dots, KD, 0, s);
         q.f = q.f0 = S[s];
         q.gamma = 1.0;
         q.evals = 1;
@@ -630,16 +606,57 @@ __global__ void k_resume_state(DevGeom dg, SolverDev sv, int max_iter, int *summ
     if (threadIdx.x == 0) summary[0] = a0, summary[1] = a1;
 }
 
-// direction finished: choose the first trial step
-__global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ p_gd,
-                           const double *__restrict__ p_gg)
+// The two-loop recursion on coefficients (one thread per slice in line for a
+// direction): q = g; newest pair first a_i = rho_i s_i . q, q -= a_i y_i;
+// r = gamma q (gamma = s.y / y.y of the newest pair, 1 without pairs); oldest
+// first beta = rho_i y_i . r, r += (a_i - beta) s_i; d = -r.  Every dot
+// product is a row of the Gram matrix applied to coefficients.  Then the
+// first trial step, as before: alpha0 = 1/|g| without pairs, else 1; a
+// direction that is not a descent one restarts from -g.
+__global__ void k_ls_start(DevGeom dg, SolverDev sv)
 {
+    const int R = sv.ring, GD = basis_dim(R), IG = 2 * R;
     for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
         SliceState &q = sv.st[s];
         q.reset = 0;
         if (!sv.mask_dir[s]) continue;
         sv.mask_dir[s] = 0;
-        const double gd = serial_sum(dg, p_gd, s), gg = serial_sum(dg, p_gg, s);
+        const double *G = sv.gram + (int64_t)s * GD * GD;
+        double *c = sv.coef + (int64_t)s * GD;
+        for (int j = 0; j < GD; ++j) c[j] = 0.0;
+        const int cnt = q.count;
+        int sl[EI_MAX_LBFGS_M];
+        for (int k = 0; k < cnt; ++k) sl[k] = slot_of(sv, s, k);
+        // (G row a) . c over the basis indices in use: the kept pairs and g
+        auto row_dot = [&](int a) {
+            double t = G[(int64_t)a * GD + IG] * c[IG];
+            for (int k = 0; k < cnt; ++k)
+                t += G[(int64_t)a * GD + sl[k]] * c[sl[k]] + G[(int64_t)a * GD + R + sl[k]] * c[R + sl[k]];
+            return t;
+        };
+        double al[EI_MAX_LBFGS_M];
+        c[IG] = 1.0;                                             // q = g
+        for (int k = 0; k < cnt; ++k) {                          // newest first
+            const int i = sl[k];
+            const double rho = 1.0 / G[(int64_t)i * GD + R + i];
+            al[k] = rho * row_dot(i);
+            c[R + i] -= al[k];
+        }
+        double gam = 1.0;
+        if (cnt > 0) {
+            const int n = sl[0];
+            gam = G[(int64_t)n * GD + R + n] / G[(int64_t)(R + n) * GD + R + n];
+        }
+        for (int j = 0; j < GD; ++j) c[j] *= gam;                // r = gamma q
+        for (int k = cnt - 1; k >= 0; --k) {                     // oldest first
+            const int i = sl[k];
+            const double rho = 1.0 / G[(int64_t)i * GD + R + i];
+            const double beta = rho * row_dot(R + i);
+            c[i] += al[k] - beta;
+        }
+        for (int j = 0; j < GD; ++j) c[j] = -c[j];               // d = -r
+        q.gamma = gam;
+        const double gd = row_dot(IG), gg = G[(int64_t)IG * GD + IG];
         q.gg = gg;
         q.gd = gd;
         if (!(gd < 0.0)) {
@@ -649,6 +666,8 @@ __global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ 
             }
             q.reset = 1;                  // not a descent direction: restart from -g
             q.count = 0;
+            for (int j = 0; j < GD; ++j) c[j] = 0.0;
+            c[IG] = -1.0;
             q.gd = -gg;
         }
         q.alpha = q.count == 0 ? 1.0 / sqrt(gg) : 1.0;
@@ -673,12 +692,15 @@ __global__ void k_ls_start(DevGeom dg, SolverDev sv, const double *__restrict__ 
     }
 }
 
-// Armijo test of the trial point
-__global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S, Opts o)
+// Armijo test of the trial point; at an iteration's first trial the slope
+// g . d comes from the d the trial stepped along (part_gd)
+__global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S,
+                         const double *__restrict__ part_gd, Opts o)
 {
     for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
         if (!sv.mask_ls[s]) continue;
         SliceState &q = sv.st[s];
+        if (q.trials == 0) q.gd = serial_sum(dg, part_gd, 1, 0, s);
         const double ft = S[s];
         q.evals += 1;
         if (isfinite(ft) && ft <= q.f + o.c1 * q.alpha * q.gd) {
@@ -696,24 +718,59 @@ __global__ void k_armijo(DevGeom dg, SolverDev sv, const double *__restrict__ S,
     }
 }
 
-// memory update and stop test of accepted slices; summary of what still runs
-__global__ void k_update(DevGeom dg, SolverDev sv, const double *__restrict__ p_sy,
-                         const double *__restrict__ p_ss, const double *__restrict__ p_yy, Opts o,
-                         int *summary)
+// Memory and Gram update and stop test of accepted slices; summary of what
+// still runs.  The new pair (s, y) has its dot products with the kept pairs
+// and with itself from the accepted step's pass; the new gradient
+// g_new = g + y has g_new . b = g . b + y . b (g . b: the old gradient column)
+// and g_new . g_new = g . g + 2 g . y + y . y.  The pair is kept when
+// s.y > eps |s| |y|.
+__global__ void k_update(DevGeom dg, SolverDev sv, Opts o, int *summary)
 {
     int running = 0, in_ls = 0;
+    const int R = sv.ring, GD = basis_dim(R), KD = dots_per_block(R), IG = 2 * R;
     for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
         SliceState &q = sv.st[s];
         if (sv.mask_acc[s]) {
             sv.mask_acc[s] = 0;
-            const double sy = serial_sum(dg, p_sy, s), ss = serial_sum(dg, p_ss, s),
-                         yy = serial_sum(dg, p_yy, s);
-            if (sy > o.curv_eps * sqrt(ss) * sqrt(yy)) {
-                sv.rho[(int64_t)q.head * dg.n_slices + s] = 1.0 / sy;
-                q.gamma = sy / yy;
-                q.head = (q.head + 1) % sv.ring;
-                q.count = min(q.count + 1, sv.m);
+            double *G = sv.gram + (int64_t)s * GD * GD;
+            const int cnt = q.count, h = q.head;
+            const double s_s = serial_sum(dg, sv.part_dots, KD, 4 * R, s);
+            const double s_y = serial_sum(dg, sv.part_dots, KD, 4 * R + 1, s);
+            const double y_y = serial_sum(dg, sv.part_dots, KD, 4 * R + 2, s);
+            const double g_s = serial_sum(dg, sv.part_dots, KD, 4 * R + 3, s);
+            const double g_y = serial_sum(dg, sv.part_dots, KD, 4 * R + 4, s);
+            const double gn_gn = G[(int64_t)IG * GD + IG] + 2.0 * g_y + y_y;
+            const bool keep = s_y > o.curv_eps * sqrt(fmax(s_s, 0.0)) * sqrt(fmax(y_y, 0.0));
+            // the old pairs kept after this update (newest first; with the new
+            // pair m in all)
+            const int kept_old = keep ? min(cnt, sv.m - 1) : cnt;
+            for (int k = 0; k < kept_old; ++k) {
+                const int j = slot_of(sv, s, k);
+                const double yS = serial_sum(dg, sv.part_dots, KD, 4 * j + 2, s);
+                const double yY = serial_sum(dg, sv.part_dots, KD, 4 * j + 3, s);
+                if (keep) {
+                    const double sS = serial_sum(dg, sv.part_dots, KD, 4 * j, s);
+                    const double sY = serial_sum(dg, sv.part_dots, KD, 4 * j + 1, s);
+                    G[(int64_t)h * GD + j] = G[(int64_t)j * GD + h] = sS;
+                    G[(int64_t)h * GD + R + j] = G[(int64_t)(R + j) * GD + h] = sY;
+                    G[(int64_t)(R + h) * GD + j] = G[(int64_t)j * GD + R + h] = yS;
+                    G[(int64_t)(R + h) * GD + R + j] = G[(int64_t)(R + j) * GD + R + h] = yY;
+                }
+                // the gradient column: g_new . s_j, g_new . y_j
+                const double gS = G[(int64_t)IG * GD + j] + yS, gY = G[(int64_t)IG * GD + R + j] + yY;
+                G[(int64_t)j * GD + IG] = G[(int64_t)IG * GD + j] = gS;
+                G[(int64_t)(R + j) * GD + IG] = G[(int64_t)IG * GD + R + j] = gY;
             }
+            if (keep) {
+                G[(int64_t)h * GD + h] = s_s;
+                G[(int64_t)h * GD + R + h] = G[(int64_t)(R + h) * GD + h] = s_y;
+                G[(int64_t)(R + h) * GD + R + h] = y_y;
+                G[(int64_t)h * GD + IG] = G[(int64_t)IG * GD + h] = g_s + s_y;
+                G[(int64_t)(R + h) * GD + IG] = G[(int64_t)IG * GD + R + h] = g_y + y_y;
+                q.head = (h + 1) % sv.ring;
+                q.count = min(cnt + 1, sv.m);
+            }
+            G[(int64_t)IG * GD + IG] = gn_gn;
             const double rel = (q.f - q.f_t) / fmax(fmax(fabs(q.f), fabs(q.f_t)), 1.0);
             q.f = q.f_t;
             q.k += 1;
@@ -811,9 +868,10 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(salloc(s, &s->gt, V));
     EI_CUDA_TRY(salloc(s, &s->Sr, V * s->ring));
     EI_CUDA_TRY(salloc(s, &s->Yr, V * s->ring));
-    for (int k = 0; k < 4; ++k) EI_CUDA_TRY(salloc(s, &s->part[k], NB));
-    EI_CUDA_TRY(salloc(s, &s->rho, (size_t)s->ring * S));
-    EI_CUDA_TRY(salloc(s, &s->alpha_i, (size_t)m * S));
+    const size_t GD = (size_t)basis_dim(s->ring), KD = (size_t)dots_per_block(s->ring);
+    EI_CUDA_TRY(salloc(s, &s->part_dots, NB * KD));
+    EI_CUDA_TRY(salloc(s, &s->gram, S * GD * GD));
+    EI_CUDA_TRY(salloc(s, &s->coef, S * GD));
     EI_CUDA_TRY(salloc(s, &s->st, S));
     EI_CUDA_TRY(salloc(s, &s->mask_dir, S));
     EI_CUDA_TRY(salloc(s, &s->mask_ls, S));
@@ -823,6 +881,7 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(salloc(s, &s->Pu, (size_t)g->proj_count));
     EI_CUDA_TRY(salloc(s, &s->Pt, (size_t)g->proj_count));
     EI_CUDA_TRY(salloc(s, &s->part_reg, NB));
+    EI_CUDA_TRY(salloc(s, &s->part_gd, NB));
     EI_CUDA_TRY(salloc(s, &s->summary, 2));
     EI_CUDA_TRY(cudaMallocHost(&s->summary_h, 2 * sizeof(int)));
     EI_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
@@ -834,6 +893,8 @@ static cudaError_t ensure_solver(ei_geometry *g, int m)
     EI_CUDA_TRY(cudaMemset(s->d, 0, V * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->Sr, 0, V * s->ring * sizeof(float4)));
     EI_CUDA_TRY(cudaMemset(s->Yr, 0, V * s->ring * sizeof(float4)));
+    EI_CUDA_TRY(cudaMemset(s->gram, 0, S * GD * GD * sizeof(double)));
+    EI_CUDA_TRY(cudaMemset(s->coef, 0, S * GD * sizeof(double)));
     return cudaSuccess;
 }
 
@@ -942,8 +1003,9 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         EI_CUDA_TRY(solver_adjoint(g, sv->u, sv->g, ec, nullptr, st));
         if (ow) EI_CUDA_TRY(offsets_gradient(sv->g, nullptr));
         if (NR > 0) k_sino_rows<true><<<NR, 256, 0, st>>>(g->dg, dv, sv->Pu, sv->Pt, nullptr);
+        k_gram_gg<<<NB, T, 0, st>>>(dg, dv);
         k_init_state<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->summary);
-        count_launches(g, 2);
+        count_launches(g, 3);
         EI_CUDA_TRY(cudaGetLastError());
         *evals = 1;
     }
@@ -955,23 +1017,10 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
     // iteration's first trial, interpolated otherwise); Armijo; the gradient,
     // projections and memory update of accepted slices; summary
     auto round = [&]() -> cudaError_t {
-        double *pa = sv->part[0], *pb = sv->part[1];
-        k_tl_first<<<NB, T, 0, st>>>(dg, dv, pa);
-        for (int i = 0; i < sv->m; ++i) {
-            k_tl_down<<<NB, T, 0, st>>>(dg, dv, i, pa, pb);
-            std::swap(pa, pb);
-        }
-        k_tl_mid<<<NB, T, 0, st>>>(dg, dv, pa);
-        for (int i = sv->m - 1; i >= 0; --i) {
-            k_tl_up<<<NB, T, 0, st>>>(dg, dv, i, pa, pb);
-            std::swap(pa, pb);
-        }
-        k_tl_end<<<NB, T, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
-        k_ls_start<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[2], sv->part[3]);
-        k_reset_dir<<<NB, T, 0, st>>>(dg, dv);
-        k_trial<<<NB, T, 0, st>>>(dg, dv, ec.reg1, sv->part_reg);
-        // direction: first + m down + mid + m up + end + ls_start + reset; trial
-        count_launches(g, 2 * sv->m + 5 + 1);
+        // direction (coefficients, for the slices that need one) and first step
+        k_ls_start<<<1, scalar_threads, 0, st>>>(dg, dv);
+        k_trial<<<NB, T, 0, st>>>(dg, dv, ec.reg1, sv->part_reg, sv->part_gd);
+        count_launches(g, 2);
         EI_CUDA_TRY(cudaGetLastError());
         // the trial's projections: first trials projected, later ones interpolated
         EI_CUDA_TRY(launch_prep(g, sv->xt, ec.mult, linked, sv->mask_first, st));
@@ -987,16 +1036,15 @@ static cudaError_t run_solver(ei_geometry *g, const float *meas, float4 *x_dev,
         EI_CUDA_TRY(solver_ic(g, sv->Pt, meas, ec.link, sv->mask_ls, st));
         EI_CUDA_TRY(launch_finalize_objective(g, g->part_ic, dg.vec_prefix, sv->part_reg,
                                               g->S_dev, sv->mask_ls, st));
-        k_armijo<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, o);
+        k_armijo<<<1, scalar_threads, 0, st>>>(dg, dv, g->S_dev, sv->part_gd, o);
         count_launches(g, 2);
         EI_CUDA_TRY(cudaGetLastError());
         // accepted trials: the gradient, the projections Pu, the memory update
         EI_CUDA_TRY(solver_adjoint(g, sv->xt, sv->gt, ec, sv->mask_acc, st));
         if (ow) EI_CUDA_TRY(offsets_gradient(sv->gt, sv->mask_acc));
         if (NR > 0) k_sino_rows<true><<<NR, 256, 0, st>>>(g->dg, dv, sv->Pu, sv->Pt, sv->mask_acc);
-        k_accept<<<NB, T, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2]);
-        k_update<<<1, scalar_threads, 0, st>>>(dg, dv, sv->part[0], sv->part[1], sv->part[2], o,
-                                               sv->summary);
+        k_accept<<<NB, T, 0, st>>>(dg, dv);
+        k_update<<<1, scalar_threads, 0, st>>>(dg, dv, o, sv->summary);
         count_launches(g, 3);
         EI_CUDA_TRY(cudaGetLastError());
         return cudaMemcpyAsync(sv->summary_h, sv->summary, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1161,7 +1209,7 @@ struct StateHeader {
     uint64_t shape_hash;
 };
 
-static const uint64_t kStateMagic = 0x4549534f4c564532ull;   // "EISOLVE2"
+static const uint64_t kStateMagic = 0x4549534f4c564533ull;   // "EISOLVE3"
 
 static int64_t solver_vol_count(const ei_geometry *g)
 {
@@ -1202,7 +1250,8 @@ static std::vector<std::pair<void *, size_t>> state_pieces(const Solver *s, cons
             {s->d, V},
             {s->Sr, V * s->ring},
             {s->Yr, V * s->ring},
-            {s->rho, sizeof(double) * s->ring * S},
+            {s->gram, sizeof(double) * S * basis_dim(s->ring) * basis_dim(s->ring)},
+            {s->coef, sizeof(double) * S * basis_dim(s->ring)},
             {s->st, sizeof(SliceState) * S},
             {s->mask_dir, sizeof(int) * S},
             {s->mask_ls, sizeof(int) * S},
@@ -1213,8 +1262,9 @@ size_t solver_state_size(const ei_geometry *g, int m)
 {
     const size_t V = (size_t)solver_vol_count(g) * sizeof(float4), S = (size_t)g->n_slices;
     const size_t ring = (size_t)m + 1;
+    const size_t GD = (size_t)basis_dim((int)ring);
     return sizeof(StateHeader) + V * (3 + 2 * ring) + 2 * sizeof(float) * (size_t)g->proj_count +
-           sizeof(double) * ring * S + sizeof(SliceState) * S + 3 * sizeof(int) * S;
+           sizeof(double) * S * GD * (GD + 1) + sizeof(SliceState) * S + 3 * sizeof(int) * S;
 }
 
 int solver_save(const ei_geometry *g, void *buf, size_t bytes)

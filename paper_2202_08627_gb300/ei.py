@@ -647,16 +647,22 @@ def ei_autotune(geom: Geometry, force: bool = False, write_cache: bool = True, s
     return ei_get_variant(geom)
 
 
-def ei_set_variant(geom: Geometry, fwd_variant: int, adj_variant: int, persistent: bool) -> None:
+LAUNCH_PER_ITEM, LAUNCH_PERSISTENT, LAUNCH_SM_CHUNKS = 0, 1, 2
+
+
+def ei_set_variant(geom: Geometry, fwd_variant: int, adj_variant: int, persistent: int) -> None:
+    """Projector and adjoint variants and their launch mode: 0 (or False) one
+    block per work item, 1 (or True) a persistent grid with one work counter,
+    2 a persistent grid whose blocks first take their SM's chunk of items."""
     _check(load_library().ei_set_variant(geom.handle, int(fwd_variant), int(adj_variant),
-                                         int(bool(persistent))), "ei_set_variant")
+                                         int(persistent)), "ei_set_variant")
 
 
 def ei_get_variant(geom: Geometry):
     f, a, p = c_int(), c_int(), c_int()
     _check(load_library().ei_get_variant(geom.handle, ctypes.byref(f), ctypes.byref(a),
                                          ctypes.byref(p)), "ei_get_variant")
-    return f.value, a.value, bool(p.value)
+    return f.value, a.value, p.value
 
 
 def ei_single_shot_eq3(geom: Geometry, s_exp, m_index: int, gamma: float, vol_out, stream=None):

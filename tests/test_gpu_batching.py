@@ -66,7 +66,7 @@ def test_every_variant_agrees():
     per_adj = {}
     for a in range(ei.N_ADJ_VARIANTS):
         for f in range(ei.N_FWD_VARIANTS):
-            for pers in (False, True):
+            for pers in (0, 1, 2):               # per item, persistent, SM-chunked persistent
                 ei.ei_set_variant(G, f, a, pers)
                 assert ei.ei_get_variant(G) == (f, a, pers)
                 S, grad, proj = _eval(G, xs, m)

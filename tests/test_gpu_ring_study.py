@@ -5,9 +5,9 @@ them).  A small case of the study's setup: three granules, one mask position
 on the IC slope, the homogeneous-sample model (mu = h, delta = gamma h), the
 flat IC fitted per pixel to one noisy flat scan.  The reconstruction solves
 for h and m_r together, with m_r restricted to ring frequencies (its steps
-orthogonal to the lowest DCT-II modes across the detector); it must follow
-the FP64 oracle running the same algorithm, keep m_r free of those modes, and
-give the study's measures.
+orthogonal to the lowest DCT-II modes across the detector); over its first
+ten iterations it must follow the FP64 oracle running the same algorithm,
+keep m_r free of those modes, and give the study's measures.
 """
 import numpy as np
 import pytest
@@ -47,6 +47,10 @@ def _case(n=64, n_theta=60, seed=5):
     return theta, flat, s_exp, geom
 
 
+ITERS = 10     # the FP64 objective still falls by > 8e-7 relative per iteration here,
+               # within what the FP32 objective resolves (after ~12 it falls by < 1e-7)
+
+
 @pytest.mark.parametrize("K", [4, 1])
 def test_ring_restricted_m_r_follows_the_oracle(K):
     from paper_2202_08627_gb300 import ei
@@ -57,7 +61,7 @@ def test_ring_restricted_m_r_follows_the_oracle(K):
     ei.ei_set_offset_unknowns(G, ei.EI_OFFSET_MR, osc)
     ei.ei_set_ring_modes(G, K)
     vol = G.empty("vol")
-    rep = ei.ei_reconstruct(G, G.pack_meas([s_exp]), vol, tol=0.0, max_iter=20)
+    rep = ei.ei_reconstruct(G, G.pack_meas([s_exp]), vol, tol=0.0, max_iter=ITERS)
     _, m_r = ei.ei_get_offsets(G)
 
     og = geom(flat)
@@ -72,8 +76,8 @@ def test_ring_restricted_m_r_follows_the_oracle(K):
         _, g_mr = oracle.offset_grads(x, s_exp, og)
         return S, np.concatenate([gh.ravel(), osc * oracle.ring_project(g_mr, K)])
 
-    w_ref, rep_ref = oracle.lbfgs(fun, np.zeros(nv + n), oracle.SolveOptions(tol=0.0, max_iter=20))
-    assert rep.iterations[0] == rep_ref.iterations == 20
+    w_ref, rep_ref = oracle.lbfgs(fun, np.zeros(nv + n), oracle.SolveOptions(tol=0.0, max_iter=ITERS))
+    assert rep.iterations[0] == rep_ref.iterations == ITERS
     assert abs(rep.f_initial[0] - rep_ref.f_history[0]) <= 1e-5 * rep_ref.f_history[0]
     assert abs(rep.f_final[0] - rep_ref.f_history[-1]) <= 1e-4 * rep_ref.f_history[-1], \
         (rep.f_final[0], rep_ref.f_history[-1])
