@@ -142,7 +142,7 @@ PROFILED_TRAFFIC = {("project", 8): 684.0e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 *
                     ("project", 12): 684.7e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("backproject", 0): 879.9e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
                     ("backproject", 6): 871.7e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
-                    ("backproject", 8): 848.6e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
+                    ("backproject", 8): 901.4e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
 
 
 def projector_samples(slices):
