@@ -140,6 +140,7 @@ def build_problem(wl, rank: int, device):
 PROFILED_TRAFFIC = {("project", 8): 684.0e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("project", 11): 684.5e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("project", 12): 684.7e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
+                    ("project", 13): 832.7e6 / (8 * (16 * 1024 ** 2 + 12 * 1800 * 1536)),
                     ("backproject", 0): 879.9e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
                     ("backproject", 6): 871.7e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536)),
                     ("backproject", 8): 901.4e6 / (8 * (32 * 1024 ** 2 + 16 * 1800 * 1536))}
@@ -481,9 +482,12 @@ def run_ours(args, rank, world, local_rank):
         v = {"hbm": {"achieved_gbs": a["hbm"] / (t * 1e-3) / 1e9, "peak_gbs": hbm_peak}}
         v["hbm"]["frac"] = v["hbm"]["achieved_gbs"] / hbm_peak
         if "l1" in a:
+            # the staged projector (variant 13) loads its samples from shared
+            # memory: the same data path, measured separately
+            pk = "smem_load_tbs" if (k == "project" and G.variant[0] == 13) else "l1_load_tbs"
             ach = a["l1"] / (t * 1e-3) / 1e12
-            v["l1"] = {"achieved_tbs": ach, "peak_tbs": onchip["l1_load_tbs"],
-                       "frac": ach / onchip["l1_load_tbs"]}
+            v["l1"] = {"achieved_tbs": ach, "peak_tbs": onchip[pk], "frac": ach / onchip[pk],
+                       "peak_source": pk}
             ach = a["flops"] / (t * 1e-3) / 1e12
             v["alu"] = {"achieved_tflops": ach, "peak_tflops": onchip["fp32_tflops"],
                         "frac": ach / onchip["fp32_tflops"]}
@@ -495,7 +499,9 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "l1", "kernel": dom, "achieved": l1["achieved_tbs"],
                     "peak": l1["peak_tbs"], "unit": "TB/s", "frac": l1["frac"],
                     "traffic": ratio * alg[dom]["hbm"] if ratio else None,
-                    "peak_kind": "measured: L1-hit 16-byte loads, all SMs (ei_measure_peaks)",
+                    "peak_kind": ("measured: shared-memory 16-byte loads, all SMs (ei_measure_peaks)"
+                                  if l1["peak_source"] == "smem_load_tbs" else
+                                  "measured: L1-hit 16-byte loads, all SMs (ei_measure_peaks)"),
                     "achieved_definition": "24 B per interpolated sample (two voxels x three "
                                            "channels) x samples per launch / mean launch time"}
     ic_gbs = views["ic"]["hbm"]["achieved_gbs"] if "ic" in views else None
@@ -691,7 +697,7 @@ def run_profile_unet(args):
 def run_profile_case(args):
     """The command the ncu summaries are captured with: `--profile-evals N`
     objective+gradient evaluations of the workload (variants as `ei_autotune`
-    picks them), after one untimed evaluation, inside a cudaProfilerStart/Stop
+    picks them, or `--variant F,A`), after one untimed evaluation, inside a cudaProfilerStart/Stop
     range (`ncu --profile-from-start off` captures only those).  Prints one
     line with the objective; reports no performance number."""
     import torch
@@ -701,6 +707,9 @@ def run_profile_case(args):
     wl = workloads.WORKLOADS[args.workload]()
     device = torch.device("cuda", 0)
     G, s_exp = build_problem(wl, 0, device)
+    if args.variant:
+        f, a = (int(v) for v in args.variant.split(","))
+        ei.ei_set_variant(G, f, a, 0)
     vol = G.empty("vol", device)
     ei.ei_single_shot_fbp(G, s_exp, vol)
     grad = G.empty("vol", device)
@@ -745,6 +754,8 @@ def main():
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
     ap.add_argument("--profile-unet", action="store_true",
                     help="one U-Net forward + training step for ncu and exit")
+    ap.add_argument("--variant", default=None,
+                    help="F,A: projector and adjoint variant for --profile-evals (launch mode 0)")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="run this many objective+gradient evaluations for ncu and exit")
     args = ap.parse_args()

@@ -326,7 +326,11 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * 3 16x16/8x4/2, 4 32x8/32x1/4, 5 16x16/16x2/4, 6 32x16/32x1/4; lanes
  * angle-major: 7 16x16/4x8/4, 8 8x32/4x8/4, 9 32x8/4x8/4, 10 16x16/2x16/4;
  * lanes in groups of 8 on 2 rays x 4 angles: 11 8x32/4x8/4, and 12 the same
- * with groups of 16 on 4 rays x 4 angles; adjoint: 0 8, 1 4, 2 16 voxels per
+ * with groups of 16 on 4 rays x 4 angles; 13 32x32 with each thread on 4 rays
+ * of one angle and warps on 4 rays x 8 angles, whose rows are staged in shared
+ * memory by bulk asynchronous copies (one block per work item in every launch
+ * mode; blocks mixing row- and column-first angles load from global memory);
+ * adjoint: 0 8, 1 4, 2 16 voxels per
  * thread with lanes along rows of 8 voxels, 3 8 and 4 16 voxels per thread
  * with 8-lane groups on 2 x 4 sub-patches, 5-7 four pairs of horizontally
  * adjacent voxels per thread (the pair shares its three detector pixels per
@@ -352,7 +356,7 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * (ei_set_linked: the single-channel kernels are timed) and the number of
  * variants this build has, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..12, adjoint 0..10, launch
+ * report a variant explicitly (ids: projector 0..13, adjoint 0..10, launch
  * mode 0..2).
  */
 #define EI_TUNE_FORCE 1

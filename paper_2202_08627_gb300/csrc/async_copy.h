@@ -34,6 +34,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned byt
                  : "memory");
 }
 
+// A plain arrival (no transaction bytes); release semantics for the thread's
+// earlier accesses.
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // One bounded try: the thread may be suspended until the phase completes or
 // about `hint_ns` nanoseconds pass (a hint; the hardware may wake it earlier).
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity, unsigned hint_ns = 0)

@@ -43,6 +43,7 @@ void lib_free(void *p)
 }
 
 cudaError_t ic_set_smem_limit();
+cudaError_t project_set_smem_limit();
 
 static int round_up4(int n) { return (n + 3) / 4 * 4; }
 
@@ -549,9 +550,11 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = upload(g, &d_prep, prep_p);
     if (e == cudaSuccess) e = upload(g, &d_vec, vec_p);
     if (e == cudaSuccess) e = dev_alloc(g, &g->xpA, (size_t)g->pp_count);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->xpB, (size_t)g->pp_count);
+    // the B copies get one pair of entries more: the staged projector copies
+    // them in 16-byte-aligned pairs and may read one entry past a row's end
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xpB, (size_t)g->pp_count + 2);
     if (e == cudaSuccess) e = dev_alloc(g, &g->xtA, (size_t)g->pp_count);
-    if (e == cudaSuccess) e = dev_alloc(g, &g->xtB, (size_t)g->pp_count);
+    if (e == cudaSuccess) e = dev_alloc(g, &g->xtB, (size_t)g->pp_count + 2);
     if (e == cudaSuccess) e = dev_alloc(g, &g->proj, (size_t)g->proj_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->gA, (size_t)g->gp_count);
     if (e == cudaSuccess) e = dev_alloc(g, &g->gB, (size_t)g->gp_count);
@@ -567,6 +570,7 @@ int ei_setup_geometry(const ei_geometry_desc *d, int n_slices, const ei_slice_di
     if (e == cudaSuccess) e = cudaMemset(g->gA, 0, (size_t)g->gp_count * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemset(g->gB, 0, (size_t)g->gp_count * sizeof(float2));
     if (e == cudaSuccess) e = ic_set_smem_limit();
+    if (e == cudaSuccess) e = project_set_smem_limit();
     if (e == cudaSuccess) e = single_shot_set_smem_limit();
     if (e != cudaSuccess) {
         const bool oom = e == cudaErrorMemoryAllocation;

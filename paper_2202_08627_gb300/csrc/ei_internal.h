@@ -142,7 +142,7 @@ constexpr int VEC_THREADS = 256;
 
 // Kernel variants the autotuner chooses among (instantiated in k_project.cu /
 // k_backproject.cu).  Each has its own work decomposition.
-constexpr int N_FWD_VARIANTS = 13;          // projector tile (rays x angles, warp shape, unroll)
+constexpr int N_FWD_VARIANTS = 14;          // projector tile (rays x angles, warp shape, unroll, staging)
 constexpr int N_ADJ_VARIANTS = 11;         // adjoint voxels per thread and occupancy
 void project_variant_shape(int id, int *rays, int *angles);
 int backproject_variant_rows(int id);

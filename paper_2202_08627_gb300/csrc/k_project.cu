@@ -27,7 +27,9 @@
 //    integer add per sample; the integer part is the voxel index and the low
 //    word the interpolation weight, exact to ~1e-7 voxel at any slice size.
 #include <algorithm>
+#include <climits>
 
+#include "async_copy.h"
 #include "ei_internal.h"
 
 namespace ei {
@@ -403,6 +405,433 @@ static cudaError_t launch_project_mode(const ei_geometry *g, float *proj, float 
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Staged variant: the rows a block samples go through shared memory.
+//
+// A block covers STG_RAYS rays x STG_ANGLES angles, each thread STG_RPT rays
+// of one angle (rays j, j + 4, ...), so that at every step a warp's lanes sit
+// on 4 neighbouring rays x 8 neighbouring angles in the lane order of variant
+// 12.  All its rays step through the rows together.  At row o every position
+// the block samples lies in a window of W entries starting at
+// floor((L + o pc) / 2^32) + 1: pc is the slope of the block's middle angle and
+// L (H) the least (largest) value of P(o) - o pc over the block's rays, taken
+// at the first and last row each ray samples (P(o) - o pc is linear in o, so
+// those two rows bound it); W = floor((H - L) / 2^32) + 2.  On 1024^2 and
+// 512^2 slices with 1800 angles W is 24..95 entries, 5-7% of the block's
+// samples per row.  Warp 0 copies the windows into a ring of STG_NS stages of
+// STG_ROWS rows with bulk asynchronous copies (one lane per row, one mbarrier
+// per stage) while the block samples the stage before; it also writes each
+// staged row's shared-memory offsets into a row table, so a sample's address
+// is one multiply-add of the position's integer part.  A stage that every ray
+// of a warp samples throughout runs without per-sample tests.  With
+// STG_WMAX = 88 a block needs 43 KB of shared memory and four blocks (32
+// warps) fit an SM; 2-3% of the blocks of 1024^2 slices have wider windows.
+//
+// Why: an L1 load costs one pass of the data path for every 128-byte line its
+// quarter warp (16-byte loads) touches, and the 4 to 7 entries of a quarter
+// warp straddle a line boundary about half the time; a shared-memory load of
+// the same entries is one pass whenever they lie within 8 consecutive 16-byte
+// slots, since the banks wrap around.  Blocks whose angles mix row- and
+// column-first rays, or whose window exceeds STG_WMAX, read global memory as
+// the other variants do.  Every ray adds the same samples in the same order
+// with the same arithmetic, so the projections equal the other variants' bit
+// for bit.
+// --------------------------------------------------------------------------
+#ifndef EI_STG_RAYS
+#define EI_STG_RAYS 32               // block tile: rays x angles, rays per thread
+#endif
+#ifndef EI_STG_ANGLES
+#define EI_STG_ANGLES 32
+#endif
+#ifndef EI_STG_RPT
+#define EI_STG_RPT 4
+#endif
+#ifndef EI_STG_WMAX
+#define EI_STG_WMAX 88               // widest staged window (entries)
+#endif
+constexpr int STG_RAYS = EI_STG_RAYS, STG_ANGLES = EI_STG_ANGLES, STG_RPT = EI_STG_RPT;
+constexpr int STG_THREADS = STG_RAYS * STG_ANGLES / STG_RPT;     // 256
+// Compile-time tunables (measured defaults): rows per stage, stages in the
+// ring, row-loop unroll, how a buffer is released for refilling (0: a block
+// barrier after each stage; 1: per-stage "empty" mbarriers, warp 0 waiting for
+// every warp), and how a ray outside its rows is skipped (1: a select of the
+// zero entry; 0: a branch).
+#ifndef EI_STG_ROWS
+#define EI_STG_ROWS 10
+#endif
+#ifndef EI_STG_NS
+#define EI_STG_NS 2
+#endif
+#ifndef EI_STG_UNROLL
+#define EI_STG_UNROLL 1
+#endif
+#ifndef EI_STG_SYNC
+#define EI_STG_SYNC 0
+#endif
+#ifndef EI_STG_SEL
+#define EI_STG_SEL 0
+#endif
+#ifndef EI_STG_MINB
+#define EI_STG_MINB 4                // resident blocks per SM the registers are sized for
+#endif
+constexpr int STG_ROWS = EI_STG_ROWS, STG_NS = EI_STG_NS, STG_WMAX = EI_STG_WMAX;
+constexpr int STG_UNROLL = EI_STG_UNROLL;
+constexpr uint64_t kStageWaitNs = 2000000000ull;                  // 2 s bound on a stage's copies
+
+template <bool LINKED>
+struct StageLayout {
+    static constexpr int kBars = 0;                               // full[STG_NS], empty[STG_NS]
+    static constexpr int kRed = 128;                              // 8 warps x 4 int64
+    static constexpr int kRow = 384;                              // STG_NS x STG_ROWS int4
+    static constexpr int kPar = (kRow + STG_NS * STG_ROWS * 16 + 127) / 128 * 128;   // StageParams
+    static constexpr int kZero = kPar + 64;                       // one zero A / B entry
+    static constexpr int kA = kPar + 128;
+    static constexpr int kRowA = STG_WMAX * 16;                   // float4 entries of a row
+    static constexpr int kRowB = (STG_WMAX + 2) * 8;              // float2 entries, even start
+    static constexpr int kB = kA + (LINKED ? 0 : STG_NS * STG_ROWS * kRowA);
+    static constexpr int kBytes = kB + STG_NS * STG_ROWS * kRowB;
+};
+static_assert(STG_THREADS == 256 && STG_RAYS % (4 * STG_RPT) == 0 && STG_ANGLES % 8 == 0 &&
+              (STG_RAYS / (4 * STG_RPT)) * (STG_ANGLES / 8) * 32 == STG_THREADS,
+              "warps of 4 rays x 8 angles, STG_RPT rays per thread");
+static_assert(STG_ROWS <= 32 && StageLayout<false>::kRowB % 16 == 0, "one lane per staged row");
+static_assert(2 * STG_NS * 8 <= 128, "barriers fit their region");
+static_assert(StageLayout<false>::kBytes <= 227 * 1024, "one block fits an SM's shared memory");
+
+// What warp 0 needs to copy a stage (kept in shared memory, not in every
+// thread's registers).
+struct StageParams {
+    long long L, pc, pp_off;
+    const float4 *gA;
+    const float2 *gB;
+    int O_lo, O_hi, W, w;
+};
+static_assert(sizeof(StageParams) <= 64, "StageParams sits before the zero entry");
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The samples of rows o0 .. o1 (one stage) of a thread's rays from the staged
+// windows; rt: the stage's row table (A and B byte offsets, window start).
+// With TEST a ray adds only the rows in [lo, lo + span]: at other rows it
+// skips the sample (EI_STG_SEL 0) or reads the zero entry (kZero), whose
+// sample fmaf(f, 0, 0) is +0; adding +0 leaves the sum's bits unchanged (a sum
+// that starts at +0 is never -0).  Without TEST the caller has checked that
+// every ray samples every row of the stage.
+template <bool LINKED, bool TEST>
+__device__ __forceinline__ void stage_rows(const int4 *rt, int o0, int o1, const char *sbytes,
+                                           long long (&pos)[STG_RPT], long long p1,
+                                           const int (&lo)[STG_RPT], const int (&span)[STG_RPT],
+                                           int W, float (&acc)[STG_RPT][3], int *status)
+{
+    constexpr int kZero = StageLayout<LINKED>::kZero;
+    const float inv32 = 2.3283064365386963e-10f;   // 2^-32
+#pragma unroll STG_UNROLL
+    for (int o = o0; o <= o1; ++o) {
+        const int4 ro = rt[o - o0];
+#pragma unroll
+        for (int t = 0; t < STG_RPT; ++t) {
+            const bool act = !TEST || (unsigned)(o - lo[t]) <= (unsigned)span[t];
+            if (!EI_STG_SEL && !act) {
+                pos[t] += p1;
+                continue;
+            }
+            const long long q = pos[t];
+            int i0 = (int)(q >> 32);                                 // floor of the position
+            if (kDeviceChecks && act)                                // window slot i0 + 1 - start
+                i0 = checked_index(i0 + 1 - ro.z, 0, W - 1, status) + ro.z - 1;
+            const int addrA = act ? ro.x + i0 * 16 : kZero, addrB = act ? ro.y + i0 * 8 : kZero;
+            const float f = (float)(unsigned)(q & 0xffffffffLL) * inv32;
+            const float2 vb = *reinterpret_cast<const float2 *>(sbytes + addrB);
+            if (LINKED) {
+                acc[t][0] += fmaf(f, vb.y, vb.x);
+            } else {
+                const float4 va = *reinterpret_cast<const float4 *>(sbytes + addrA);
+                acc[t][0] += fmaf(f, va.w, va.x);
+                acc[t][1] += fmaf(f, vb.x, va.y);
+                acc[t][2] += fmaf(f, vb.y, va.z);
+            }
+            pos[t] += p1;
+        }
+    }
+}
+
+template <bool LINKED>
+__global__ void __launch_bounds__(STG_THREADS, LINKED ? 4 : EI_STG_MINB)
+k_project_staged(DevGeom dg, const int *__restrict__ prefix, const float4 *__restrict__ xpA,
+                 const float2 *__restrict__ xpB, const float4 *__restrict__ xtA,
+                 const float2 *__restrict__ xtB, float *__restrict__ proj, float link,
+                 const int *__restrict__ active)
+{
+    using Lay = StageLayout<LINKED>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lay::kBars);
+    long long *red = reinterpret_cast<long long *>(smem + Lay::kRed);
+    int4 *rowtab = reinterpret_cast<int4 *>(smem + Lay::kRow);
+    float4 *sA = reinterpret_cast<float4 *>(smem + Lay::kA);
+    float2 *sB = reinterpret_cast<float2 *>(smem + Lay::kB);
+
+    const int item = blockIdx.x;
+    const int s = find_slice(prefix, dg.n_slices, item);
+    if (active && !active[s]) return;
+    const SliceInfo si = dg.slices[s];
+    const int nrb = (si.n_dp + STG_RAYS - 1) / STG_RAYS;
+    const int local = item - prefix[s];
+    const int ab = local / nrb, rb = local - ab * nrb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int WR = STG_RAYS / (4 * STG_RPT);                 // warps along the rays
+    const int la = (lane & 3) | (((lane >> 4) & 1) << 2), lr = (lane >> 2) & 3;
+    const int a = ab * STG_ANGLES + (warp / WR) * 8 + la;
+    const int j0 = rb * STG_RAYS + (warp % WR) * (4 * STG_RPT) + lr;
+    const bool a_ok = a < si.n_theta;
+    const AngleInfo an = dg.ang[si.ang_off + (a_ok ? a : si.n_theta - 1)];
+    const int a_mid = min(ab * STG_ANGLES + STG_ANGLES / 2, si.n_theta - 1);
+    const long long pc = dg.ang[si.ang_off + a_mid].p1_fx;
+    const int mid_col = dg.ang[si.ang_off + a_mid].col_dom;
+    const int n = si.n, w = si.n + 1;
+
+    // the rays: first row (lo; 2^30 when the ray misses the slice), rows after
+    // it (span), fixed-point position at the row the block starts on (pos)
+    int lo[STG_RPT], span[STG_RPT];
+    long long pos[STG_RPT];
+    int o_min = INT_MAX, o_max = -1;
+    long long d_min = LLONG_MAX, d_max = LLONG_MIN;
+    const long long p1 = an.p1_fx;
+#pragma unroll
+    for (int t = 0; t < STG_RPT; ++t) {
+        const int j = j0 + 4 * t;
+        RaySetup rs{0, 0, 1, 0};
+        if (a_ok && j < si.n_det) rs = ray_setup(an, j, n, si.n_det);
+        pos[t] = rs.base;
+        if (rs.o_lo <= rs.o_hi) {
+            lo[t] = rs.o_lo;
+            span[t] = rs.o_hi - rs.o_lo;
+            o_min = min(o_min, rs.o_lo);
+            o_max = max(o_max, rs.o_hi);
+            const long long d1 = rs.base + (long long)rs.o_lo * (p1 - pc);
+            const long long d2 = rs.base + (long long)rs.o_hi * (p1 - pc);
+            d_min = min(d_min, min(d1, d2));
+            d_max = max(d_max, max(d1, d2));
+        } else {
+            lo[t] = 1 << 30;
+            span[t] = 0;
+        }
+    }
+    const bool any = o_min <= o_max;
+    o_min = warp_min(o_min);
+    o_max = warp_max(o_max);
+    d_min = warp_min(d_min);
+    d_max = warp_max(d_max);
+    if (lane == 0) {
+        red[4 * warp + 0] = o_min;
+        red[4 * warp + 1] = o_max;
+        red[4 * warp + 2] = d_min;
+        red[4 * warp + 3] = d_max;
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < STG_NS; ++b) {
+            mbar_init(smem_addr(&bars[b]), 1);                        // full: the copies
+            mbar_init(smem_addr(&bars[STG_NS + b]), STG_THREADS / 32); // empty: every warp
+        }
+        mbar_init_fence();
+        *reinterpret_cast<float4 *>(smem + Lay::kZero) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int mixed = __syncthreads_or(any && an.col_dom != mid_col);
+    int O_lo = INT_MAX, O_hi = -1;
+    long long L = LLONG_MAX, H = LLONG_MIN;
+#pragma unroll
+    for (int q = 0; q < STG_THREADS / 32; ++q) {
+        O_lo = min(O_lo, (int)red[4 * q + 0]);
+        O_hi = max(O_hi, (int)red[4 * q + 1]);
+        L = min(L, red[4 * q + 2]);
+        H = max(H, red[4 * q + 3]);
+    }
+    const int W = O_lo <= O_hi ? (int)((H - L) >> 32) + 2 : 0;
+    const bool staged = O_lo <= O_hi && !mixed && W <= STG_WMAX;
+
+    float acc[STG_RPT][3];
+#pragma unroll
+    for (int t = 0; t < STG_RPT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+    bool failed = false;
+
+    if (staged) {
+        // every sampling ray of the block has the middle angle's orientation
+        const float4 *gA = mid_col ? xtA : xpA;
+        const float2 *gB = mid_col ? xtB : xpB;
+        // absolute entries: entry e of row o is pp_off + o w + e
+        const int nrows = O_hi - O_lo + 1, nst = (nrows + STG_ROWS - 1) / STG_ROWS;
+        StageParams *sp = reinterpret_cast<StageParams *>(smem + Lay::kPar);
+        if (threadIdx.x == 0) *sp = StageParams{L, pc, si.pp_off, gA, gB, O_lo, O_hi, W, w};
+        __syncwarp();
+        // warp 0: arm stage k's barrier with its byte count, then copy its rows
+        auto issue = [&](int k) {
+            const StageParams prm = *sp;
+            const long long L = prm.L, pc = prm.pc;
+            const float4 *gA = prm.gA;
+            const float2 *gB = prm.gB;
+            const int O_lo = prm.O_lo, O_hi = prm.O_hi, W = prm.W, w = prm.w;
+            const int buf = k % STG_NS, o = O_lo + k * STG_ROWS + lane;
+            unsigned bytesA = 0, bytesB = 0;
+            const float4 *srcA = nullptr;
+            const float2 *srcB = nullptr;
+            float4 *dstA = nullptr;
+            float2 *dstB = nullptr;
+            if (lane < STG_ROWS && o <= O_hi) {
+                const int start = (int)((L + (long long)o * pc) >> 32) + 1;
+                const int e0 = max(start, 0), e1 = min(start + W, w);
+                // byte offsets from the start of shared memory at which the
+                // entry e = i0 + 1 of the sampled position's floor i0 sits:
+                // offA + 16 i0 (A) and offB + 8 i0 (B)
+                const long long rb0 = prm.pp_off + (long long)o * w;
+                const int par = (int)((rb0 + start) & 1LL);
+                const int r0 = buf * STG_ROWS + lane;
+                rowtab[r0] = make_int4(Lay::kA + r0 * Lay::kRowA + (1 - start) * 16,
+                                       Lay::kB + r0 * Lay::kRowB + (1 - start + par) * 8, start, 0);
+                if (e1 > e0) {
+                    const long long b0 = (rb0 + e0) & ~1LL, b1 = (rb0 + e1 + 1) & ~1LL;
+                    const long long sb = (rb0 + start) & ~1LL;    // slot 0 of the B row
+                    if (!LINKED) {
+                        bytesA = (unsigned)(e1 - e0) * 16u;
+                        srcA = gA + rb0 + e0;
+                        dstA = sA + (buf * STG_ROWS + lane) * STG_WMAX + (e0 - start);
+                    }
+                    bytesB = (unsigned)(b1 - b0) * 8u;
+                    srcB = gB + b0;
+                    dstB = sB + (buf * STG_ROWS + lane) * (STG_WMAX + 2) + (int)(b0 - sb);
+                }
+            }
+            unsigned tot = bytesA + bytesB;
+            for (int q = 16; q > 0; q >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, q);
+            const unsigned bar = smem_addr(&bars[buf]);
+            __syncwarp();             // the row table's writes precede the (releasing) arrive
+            if (lane == 0) mbar_arrive_expect_tx(bar, tot);
+            __syncwarp();
+            if (bytesA) bulk_copy_g2s(dstA, srcA, bytesA, bar);
+            if (bytesB) bulk_copy_g2s(dstB, srcB, bytesB, bar);
+        };
+        int issued = 0;
+        if (warp == 0)
+            for (; issued < STG_NS && issued < nst; ++issued) issue(issued);
+#pragma unroll
+        for (int t = 0; t < STG_RPT; ++t) pos[t] += (long long)O_lo * p1;
+        // rows every ray of the thread samples: stages inside them need no
+        // per-sample test
+        int lo_max = 0, hi_min = INT_MAX;
+#pragma unroll
+        for (int t = 0; t < STG_RPT; ++t) {
+            lo_max = max(lo_max, lo[t]);
+            hi_min = min(hi_min, lo[t] + span[t]);
+        }
+        const char *sbytes = reinterpret_cast<const char *>(smem);
+        // Each warp waits for a stage's copies (full) and samples it.  Then
+        // either the block meets at a barrier (EI_STG_SYNC 0) or each warp
+        // arrives on the stage's empty barrier and warp 0 waits for all of them
+        // (EI_STG_SYNC 1); after that warp 0 refills the buffer with stage
+        // k + STG_NS.
+        int k = 0;
+        bool ok = true;
+        for (; k < nst; ++k) {
+            const int buf = k % STG_NS;
+            const unsigned ph = (unsigned)(k / STG_NS) & 1u;
+            ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&bars[buf]), ph, kStageWaitNs));
+            if (ok) {
+                const int o0 = O_lo + k * STG_ROWS, o1 = min(O_hi, o0 + STG_ROWS - 1);
+                const int4 *rt = rowtab + buf * STG_ROWS;
+                if (__all_sync(0xffffffffu, o0 >= lo_max && o1 <= hi_min))
+                    stage_rows<LINKED, false>(rt, o0, o1, sbytes, pos, p1, lo, span, W, acc, dg.status);
+                else
+                    stage_rows<LINKED, true>(rt, o0, o1, sbytes, pos, p1, lo, span, W, acc, dg.status);
+            }
+            if (EI_STG_SYNC == 0) {
+                ok = __syncthreads_and(ok);
+                if (!ok) break;
+            } else {
+                if (!ok) break;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&bars[STG_NS + buf]));
+                if (warp == 0 && issued < nst) {
+                    ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&bars[STG_NS + buf]), ph,
+                                                                   kStageWaitNs));
+                    if (!ok) break;
+                }
+            }
+            if (warp == 0 && issued < nst) issue(issued++);
+        }
+        if (!ok) {
+            // a wait ran out: report it; warp 0 gives the copies it issued that
+            // no wait has seen land a bounded chance to do so before the block's
+            // shared memory is released
+            failed = true;
+            if (lane == 0) atomicExch(dg.status, (int)EI_ERR_TIMEOUT);
+            if (threadIdx.x == 0)
+                for (int i = k; i < issued; ++i)
+                    mbar_wait_bounded(smem_addr(&bars[i % STG_NS]), (unsigned)(i / STG_NS) & 1u,
+                                      kStageWaitNs);
+        }
+    } else if (O_lo <= O_hi) {
+        // mixed row- and column-first angles, or a window too wide: global loads
+        const int64_t off = si.pp_off + 1;
+        const float4 *gA = an.col_dom ? xtA : xpA;
+        const float2 *gB = an.col_dom ? xtB : xpB;
+#pragma unroll
+        for (int t = 0; t < STG_RPT; ++t) {
+            if (lo[t] > n) continue;
+            RaySetup rs{pos[t], p1, lo[t], lo[t] + span[t]};
+            ray_rows<4, LINKED>(rs, rs.o_lo, rs.o_hi, gA + off, gB + off, w, acc[t], dg.status);
+        }
+    }
+
+    if (!a_ok) return;
+    const int64_t plane = (int64_t)si.n_theta * si.n_dp;
+    const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int t = 0; t < STG_RPT; ++t) {
+        const int j = j0 + 4 * t;
+        if (j >= si.n_dp) continue;
+        float *out = proj + si.proj_off + (int64_t)a * si.n_dp + j;
+        if (j >= si.n_det || failed) {
+            const float v = failed ? nan : 0.f;
+            out[0] = v;
+            out[plane] = v;
+            out[2 * plane] = v;
+        } else {
+            ray_store<LINKED>(out, plane, acc[t], an.pch, link);
+        }
+    }
+}
+
+template <bool LINKED>
+static cudaError_t launch_project_staged(const ei_geometry *g, float *proj, float link,
+                                         const int *active, cudaStream_t st)
+{
+    const FwdVariant &v = g->fwd_variant;
+    if (v.total == 0) return cudaSuccess;
+    k_project_staged<LINKED><<<v.total, STG_THREADS, StageLayout<LINKED>::kBytes, st>>>(
+        g->dg, v.prefix, g->xpA, g->xpB, g->xtA, g->xtB, proj, link, active);
+    return cudaGetLastError();
+}
+
+// Raises the staged projector's dynamic shared-memory limit (once per device
+// context, before its first launch).
+cudaError_t project_set_smem_limit()
+{
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_project_staged<false>, a, StageLayout<false>::kBytes));
+    EI_CUDA_TRY(cudaFuncSetAttribute(k_project_staged<true>, a, StageLayout<true>::kBytes));
+    return cudaSuccess;
+}
+
 template <int R, int A, int U, int W, bool F, int Q = 0>
 static cudaError_t launch_project_variant(const ei_geometry *g, float *proj, float link,
                                           const int *active, cudaStream_t st)
@@ -437,15 +866,19 @@ cudaError_t launch_project(const ei_geometry *g, float *proj, float link, const 
     case 10: return launch_project_variant<16, 16, 4, 2, true>(g, proj, link, active, st);
     // groups of 8 lanes on 2 rays x 4 angles (pairs of groups on 2 x 8 or 4 x 4)
     case 11: return launch_project_variant<8, 32, 4, 4, true, 1>(g, proj, link, active, st);
-    default: return launch_project_variant<8, 32, 4, 4, true, 2>(g, proj, link, active, st);
+    case 12: return launch_project_variant<8, 32, 4, 4, true, 2>(g, proj, link, active, st);
+    // rows staged in shared memory (one block per item in every launch mode)
+    default:
+        return link > 0.f ? launch_project_staged<true>(g, proj, link, active, st)
+                          : launch_project_staged<false>(g, proj, 0.f, active, st);
     }
 }
 
 // Tile shape (rays, angles) of projector variant `id` (see launch_project).
 void project_variant_shape(int id, int *rays, int *angles)
 {
-    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16, 8, 8},
-                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16, 32, 32};
+    static const int R[N_FWD_VARIANTS] = {16, 32, 32, 16, 32, 16, 32, 16, 8, 32, 16, 8, 8, STG_RAYS},
+                     A[N_FWD_VARIANTS] = {16, 8, 16, 16, 8, 16, 16, 16, 32, 8, 16, 32, 32, STG_ANGLES};
     *rays = R[id];
     *angles = A[id];
 }

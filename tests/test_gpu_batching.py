@@ -87,6 +87,43 @@ def test_every_variant_agrees():
                 assert rel_l2(g[blk, c], g0[blk, c]) <= 1e-6, (a, c)
 
 
+def test_staged_projector_equals_global_loads_on_staged_slices():
+    """Projector variant 13 stages the rows of most blocks of these slices in
+    shared memory (a CPU model of its windows stages 86% of the 256^2
+    slice's blocks); the rest (angles mixing row- and column-first rays) load
+    from global memory.  Its projections, the objective and the gradient
+    equal variant 12's bit for bit, with three channels and linked, in every
+    launch mode."""
+    from paper_2202_08627_gb300 import ei
+    shapes = [(256, 720, 384, 5), (200, 361, 301, 5), (96, 1800, 160, 5)]
+    probs = []
+    for i, sh in enumerate(shapes):
+        spec = inputs.make_slice(70 + i, *sh)
+        geom = oracle_geometry(spec)
+        probs.append((spec, geom, measured(spec, geom)))
+    specs, geoms, meas = zip(*probs)
+    G = gpu_geometry(list(specs), list(geoms))
+    m = G.pack_meas(meas)
+    xs = [sp.truth * 0.9 for sp in specs]
+    for gamma in (0.0, 5e-7):
+        ei.ei_set_linked(G, gamma)
+        ref = None
+        for f, pers in ((12, 0), (13, 0), (13, 1)):
+            ei.ei_set_variant(G, f, 8, pers)
+            S, grad, proj = _eval(G, xs, m)
+            fwd = G.empty("meas")
+            ei.ei_forward(G, G.pack_volume(xs), fwd)
+            torch.cuda.synchronize()
+            got = (S, grad, proj, fwd.cpu().numpy())
+            if ref is None:
+                ref = got
+                continue
+            for name, a, b in zip(("S", "grad", "proj", "forward"), got, ref):
+                np.testing.assert_array_equal(a, b, err_msg="%s gamma=%g variant=%d mode=%d"
+                                              % (name, gamma, f, pers))
+    ei.ei_set_linked(G, 0.0)
+
+
 def test_graph_replay_equals_eager_rounds():
     from paper_2202_08627_gb300 import ei
     probs = _uneven()
