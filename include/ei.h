@@ -337,7 +337,10 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * angle) with lanes along rows of 16 voxels, on 4 x 4 sub-patches in warps of
  * 16 x 4, or in warps of 8 x 8, 8-10 a pair of the slice's top-left quadrant
  * and its three mirror images about the slice centre (a point mirror takes
- * the same hat weights at the mirrored pixels), in 16 or 32 rows per tile),
+ * the same hat weights at the mirrored pixels), in 16 or 32 rows per tile,
+ * 11-13 the same over gradient rows whose entry j holds pixel j and its
+ * mirror pixel n_det - 1 - j, a voxel and its point mirror advanced by one
+ * paired FP32 FMA (fma.rn.f32x2; results equal those of 8-10 bit for bit)),
  * launched in one of three modes (the `persistent` argument): 0 one block
  * per work item, 1 a persistent GPU-sized grid whose blocks take work items
  * from one counter, 2 a persistent grid whose blocks first take the items of
@@ -356,7 +359,7 @@ int ei_profile_read(ei_geometry *g, ei_profile *out);
  * (ei_set_linked: the single-channel kernels are timed) and the number of
  * variants this build has, and read back on later calls
  * unless EI_TUNE_FORCE is set.  ei_set_variant / ei_get_variant select and
- * report a variant explicitly (ids: projector 0..13, adjoint 0..10, launch
+ * report a variant explicitly (ids: projector 0..13, adjoint 0..13, launch
  * mode 0..2).
  */
 #define EI_TUNE_FORCE 1

@@ -117,6 +117,7 @@ void select_variants(ei_geometry *g, int fwd_id, int adj_id, int persistent)
     g->adj_variant.id = adj_id;
     g->adj_variant.prefix = g->adj_prefixes[adj_id];
     g->adj_variant.total = g->adj_totals[adj_id];
+    g->dg.gmirror = adj_mirror_layout(adj_id) ? 1 : 0;
     g->persistent = persistent;
 }
 

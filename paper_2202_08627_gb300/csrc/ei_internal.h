@@ -143,7 +143,9 @@ constexpr int VEC_THREADS = 256;
 // Kernel variants the autotuner chooses among (instantiated in k_project.cu /
 // k_backproject.cu).  Each has its own work decomposition.
 constexpr int N_FWD_VARIANTS = 14;          // projector tile (rays x angles, warp shape, unroll, staging)
-constexpr int N_ADJ_VARIANTS = 11;         // adjoint voxels per thread and occupancy
+constexpr int N_ADJ_VARIANTS = 14;         // adjoint voxels per thread and occupancy
+// Adjoint variants that read the mirror-interleaved gradient layout.
+inline bool adj_mirror_layout(int id) { return id >= 11; }
 void project_variant_shape(int id, int *rays, int *angles);
 int backproject_variant_rows(int id);
 int backproject_variant_items(int id, int n);
@@ -185,6 +187,10 @@ struct DevGeom {
     // device status word of the kernels' bounded waits and (check builds)
     // bounds checks; may be null
     int *status = nullptr;
+    // layout of the packed gradient sinogram the IC kernels and k_pack_sino
+    // write: 0 pair-packed (entry j: pixels j and j + 1), 1 mirror-interleaved
+    // (entry j: pixels j and n_det - 1 - j), as the selected adjoint variant reads
+    int gmirror = 0;
 };
 
 // Launch modes of the projector and the adjoint: one block per work item; a

@@ -394,8 +394,112 @@ __device__ __forceinline__ void mirror_pair_angle(float (&acc)[4][2][3], const f
     }
 }
 
-// Voxel rows of a mirror-variant tile: 16 per pass.
-template <int PASSES, bool LINKED>
+// Two FP32 lanes in one 64-bit register: fma.rn.f32x2 computes each lane as
+// a single correctly rounded fmaf, so a pair of accumulators advanced with it
+// holds exactly what two fmaf chains would.
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 fma_x2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 splat_x2(float w)
+{
+    f32x2 d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(w));
+    return d;
+}
+
+__device__ __forceinline__ float2 unpack_x2(f32x2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+// The mirror-interleaved layout (written by the IC kernels and k_pack_sino
+// when a variant below is selected): entry j of a row holds pixel j and its
+// mirror pixel n_det - 1 - j, A = (mu_j, mu_m, delta_j, delta_m) and
+// B = (sigma_j, sigma_m) (linked: B = (g_j, g_m)), zero outside [0, n_det).
+// A voxel's taps j..j+2 and its point mirror's taps n_det-1-j.. are then the
+// two lanes of the same three entries, and both take the same weights, so
+// one fma.rn.f32x2 advances a channel of the voxel and of its image: half the
+// FMA instructions of mirror_pair_angle, and 6 loads instead of 8 for the same
+// 72 bytes.  The sums are formed in mirror_pair_angle's order, so the results
+// equal its bit for bit.
+template <bool LINKED, bool SWAP>
+__device__ __forceinline__ void mirror_pair_angle_x2(f32x2 (&acc)[2][3], const ulonglong2 *row_a,
+                                                     const f32x2 *row_b, float vl, float a,
+                                                     float4 cs, float4 jp, int J,
+                                                     const SliceInfo &si, int *status)
+{
+    const float fl = floorf(vl);
+    const int e = J + row_entry((int)fl, J, 2, si, status);           // entries e .. e + 2
+    const float d0 = vl - fl;
+    float dh = d0 + a;
+    const bool o = dh >= 1.f;
+    dh = o ? dh - 1.f : dh;
+    const float w0l = fmaxf(0.f, fmaf(-d0, cs.z, cs.w)), w1l = fmaxf(0.f, fmaf(d0, cs.z, jp.z));
+    const float w0h = fmaxf(0.f, fmaf(-dh, cs.z, cs.w)), w1h = fmaxf(0.f, fmaf(dh, cs.z, jp.z));
+    constexpr int LO = SWAP ? 1 : 0, HI = SWAP ? 0 : 1;
+    // tap by tap, last tap first (each sum keeps mirror_pair_angle's order:
+    // the tap of pixel j + 2, then j + 1, then j), so that only one entry's
+    // data and its weights are live at a time
+    {
+        const f32x2 S2 = splat_x2(o ? w1h : 0.f);
+        if (LINKED) {
+            acc[HI][0] = fma_x2(S2, __ldg(row_b + e + 2), acc[HI][0]);
+        } else {
+            const ulonglong2 t = __ldg(row_a + e + 2);
+            const f32x2 u = __ldg(row_b + e + 2);
+            acc[HI][0] = fma_x2(S2, t.x, acc[HI][0]);
+            acc[HI][1] = fma_x2(S2, t.y, acc[HI][1]);
+            acc[HI][2] = fma_x2(S2, u, acc[HI][2]);
+        }
+    }
+    {
+        const f32x2 W1 = splat_x2(w1l), S1 = splat_x2(o ? w0h : w1h);
+        if (LINKED) {
+            const f32x2 t = __ldg(row_b + e + 1);
+            acc[LO][0] = fma_x2(W1, t, acc[LO][0]);
+            acc[HI][0] = fma_x2(S1, t, acc[HI][0]);
+        } else {
+            const ulonglong2 t = __ldg(row_a + e + 1);
+            const f32x2 u = __ldg(row_b + e + 1);
+            acc[LO][0] = fma_x2(W1, t.x, acc[LO][0]);
+            acc[LO][1] = fma_x2(W1, t.y, acc[LO][1]);
+            acc[LO][2] = fma_x2(W1, u, acc[LO][2]);
+            acc[HI][0] = fma_x2(S1, t.x, acc[HI][0]);
+            acc[HI][1] = fma_x2(S1, t.y, acc[HI][1]);
+            acc[HI][2] = fma_x2(S1, u, acc[HI][2]);
+        }
+    }
+    {
+        const f32x2 W0 = splat_x2(w0l), S0 = splat_x2(o ? 0.f : w0h);
+        if (LINKED) {
+            const f32x2 t = __ldg(row_b + e);
+            acc[LO][0] = fma_x2(W0, t, acc[LO][0]);
+            acc[HI][0] = fma_x2(S0, t, acc[HI][0]);
+        } else {
+            const ulonglong2 t = __ldg(row_a + e);
+            const f32x2 u = __ldg(row_b + e);
+            acc[LO][0] = fma_x2(W0, t.x, acc[LO][0]);
+            acc[LO][1] = fma_x2(W0, t.y, acc[LO][1]);
+            acc[LO][2] = fma_x2(W0, u, acc[LO][2]);
+            acc[HI][0] = fma_x2(S0, t.x, acc[HI][0]);
+            acc[HI][1] = fma_x2(S0, t.y, acc[HI][1]);
+            acc[HI][2] = fma_x2(S0, u, acc[HI][2]);
+        }
+    }
+}
+
+// Voxel rows of a mirror-variant tile: 16 per pass.  X2: the gradient rows
+// are in the mirror-interleaved layout and a voxel and its point mirror share
+// fma.rn.f32x2 instructions (mirror_pair_angle_x2).
+template <int PASSES, bool LINKED, bool X2>
 __device__ __forceinline__ void backproject_mirror_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
@@ -426,6 +530,15 @@ __device__ __forceinline__ void backproject_mirror_item(
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int h = 0; h < 2; ++h) acc[p][q][h][0] = acc[p][q][h][1] = acc[p][q][h][2] = 0.f;
+    // X2: acc2[p][family][voxel of the pair][channel] holds images (0, 1) of
+    // family A and (2, 3) of family B as the two lanes
+    f32x2 acc2[PASSES][2][2][3];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) acc2[p][q][h][0] = acc2[p][q][h][1] = acc2[p][q][h][2] = 0ull;
 
     {
         const float4 *rowA0 = gA + si.gp_off + si.marg;
@@ -468,7 +581,31 @@ __device__ __forceinline__ void backproject_mirror_item(
                 const float a = fabsf(cs.x);
                 const int JMA = nm3 - JA, JMB = nm3 - JB;
                 int *const st = dg.status;
-                if (cs.x >= 0.f) {
+                if constexpr (X2) {
+                    const ulonglong2 *ra = reinterpret_cast<const ulonglong2 *>(rowA);
+                    const f32x2 *rb = reinterpret_cast<const f32x2 *>(rowB);
+                    if (cs.x >= 0.f) {
+#pragma unroll
+                        for (int p = 0; p < PASSES; ++p) {
+                            mirror_pair_angle_x2<LINKED, false>(acc2[p][0], ra, rb,
+                                                                fmaf((float)p, -step, vA), a, cs,
+                                                                jp, JA, si, st);
+                            mirror_pair_angle_x2<LINKED, false>(acc2[p][1], ra, rb,
+                                                                fmaf((float)p, step, vB), a, cs,
+                                                                jp, JB, si, st);
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < PASSES; ++p) {
+                            mirror_pair_angle_x2<LINKED, true>(acc2[p][0], ra, rb,
+                                                               fmaf((float)p, -step, vA), a, cs,
+                                                               jp, JA, si, st);
+                            mirror_pair_angle_x2<LINKED, true>(acc2[p][1], ra, rb,
+                                                               fmaf((float)p, step, vB), a, cs,
+                                                               jp, JB, si, st);
+                        }
+                    }
+                } else if (cs.x >= 0.f) {
 #pragma unroll
                     for (int p = 0; p < PASSES; ++p) {
                         mirror_pair_angle<LINKED, false, 0, 1>(acc[p], rowA, rowB,
@@ -495,6 +632,20 @@ __device__ __forceinline__ void backproject_mirror_item(
         }
     }
 
+    if constexpr (X2) {
+#pragma unroll
+        for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+            for (int f = 0; f < 2; ++f)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 u = unpack_x2(acc2[p][f][h][c]);
+                        acc[p][2 * f][h][c] = u.x;
+                        acc[p][2 * f + 1][h][c] = u.y;
+                    }
+    }
 #pragma unroll
     for (int p = 0; p < PASSES; ++p) {
         const int r = r_t + dr0 + 16 * p, rm = n - 1 - r;
@@ -512,16 +663,17 @@ __device__ __forceinline__ void backproject_mirror_item(
 
 // LAY: 0 lanes along rows of 8 voxels, 1 lanes on 2 x 4 sub-patches, 2 voxel
 // pairs along rows, 3 voxel pairs on 4 x 4 sub-patches (warps of 16 x 4), 4 the
-// same sub-patches in warps of 8 x 8, 5 pairs with their mirror images.
+// same sub-patches in warps of 8 x 8, 5 pairs with their mirror images, 6 the
+// same over mirror-interleaved gradient rows with paired FMAs.
 template <int PASSES, int LAY, bool LINKED>
 __device__ __forceinline__ void backproject_item(
     const DevGeom &dg, const int *prefix, int item, AdjShared &sh, const float4 *__restrict__ gA,
     const float2 *__restrict__ gB, const float4 *__restrict__ v, float4 *__restrict__ out,
     float4 out_mult, float4 reg2, const int *__restrict__ active)
 {
-    if constexpr (LAY == 5)
-        backproject_mirror_item<PASSES, LINKED>(dg, prefix, item, sh, gA, gB, v, out, out_mult,
-                                                reg2, active);
+    if constexpr (LAY >= 5)
+        backproject_mirror_item<PASSES, LINKED, LAY == 6>(dg, prefix, item, sh, gA, gB, v, out,
+                                                          out_mult, reg2, active);
     else if constexpr (LAY >= 2)
         backproject_pair_item<PASSES, LINKED, LAY - 2>(dg, prefix, item, sh, gA, gB, v, out,
                                                        out_mult, reg2, active);
@@ -650,14 +802,18 @@ cudaError_t launch_backproject(const ei_geometry *g, const float4 *v, float4 *ou
     // voxel pairs with their three mirror images, quadrant tiles of 16 or 32 rows
     case 8: return launch_bp_variant<1, 4, 5>(g, v, out, out_mult, reg2, link, active, st);
     case 9: return launch_bp_variant<1, 3, 5>(g, v, out, out_mult, reg2, link, active, st);
-    default: return launch_bp_variant<2, 2, 5>(g, v, out, out_mult, reg2, link, active, st);
+    case 10: return launch_bp_variant<2, 2, 5>(g, v, out, out_mult, reg2, link, active, st);
+    // the same with the mirror-interleaved gradient rows and paired FMAs
+    case 11: return launch_bp_variant<1, 4, 6>(g, v, out, out_mult, reg2, link, active, st);
+    case 12: return launch_bp_variant<1, 3, 6>(g, v, out, out_mult, reg2, link, active, st);
+    default: return launch_bp_variant<2, 2, 6>(g, v, out, out_mult, reg2, link, active, st);
     }
 }
 
 // Voxel rows per tile of adjoint variant `id` (see launch_backproject).
 int backproject_variant_rows(int id)
 {
-    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64, 64, 16, 16, 32};
+    static const int R[N_ADJ_VARIANTS] = {64, 32, 128, 64, 128, 64, 64, 64, 16, 16, 32, 16, 16, 32};
     return R[id];
 }
 
@@ -672,8 +828,9 @@ int backproject_variant_items(int id, int n)
 
 // ----------------------------------------------------------------------------
 // Packed gradient sinogram from a user sino4 array ([n_theta][n_dp] float4 per
-// slice): entries of pixels j = -1 .. n_det - 1 of every row; the margins are
-// zero from set-up.  One block per row.
+// slice): entries of pixels j = -1 .. n_det - 1 of every row, pair-packed or
+// (dg.gmirror) mirror-interleaved; the margins are zero from set-up.  One
+// block per row.
 // ----------------------------------------------------------------------------
 __global__ void k_pack_sino(DevGeom dg, const float4 *__restrict__ sino4, float4 *__restrict__ gA,
                             float2 *__restrict__ gB)
@@ -685,6 +842,13 @@ __global__ void k_pack_sino(DevGeom dg, const float4 *__restrict__ sino4, float4
     const float4 *src = sino4 + si.sino_off + (int64_t)a * si.n_dp;
     const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
     for (int j = (int)threadIdx.x - 1; j < si.n_det; j += blockDim.x) {
+        if (dg.gmirror) {              // pixel j and its mirror n_det - 1 - j
+            const float4 d = j >= 0 ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 m = j >= 0 ? src[si.n_det - 1 - j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            gA[dst + j] = make_float4(d.x, m.x, d.y, m.y);
+            gB[dst + j] = make_float2(d.z, m.z);
+            continue;
+        }
         const float4 lo = j >= 0 ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 hi = j + 1 < si.n_det ? src[j + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
         gA[dst + j] = make_float4(lo.x, lo.y, lo.z, hi.x);

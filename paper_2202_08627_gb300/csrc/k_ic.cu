@@ -252,7 +252,23 @@ __global__ void k_ic(DevGeom dg, const float *__restrict__ proj, const float *__
         const float *gdl = reinterpret_cast<const float *>(s_pd4);
         const float *gsg = reinterpret_cast<const float *>(s_gv4);
         const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
-        if (link > 0.f) {
+        if (dg.gmirror) {
+            // mirror-interleaved row: entry j holds pixel j and pixel nd - 1 - j
+            // (zero outside [0, nd)); linked: g_mu + gamma g_delta only
+            for (int j = (int)threadIdx.x - 1; j < ndp; j += blockDim.x) {
+                const bool in = j >= 0 && j < nd;
+                const int jm = nd - 1 - j;
+                if (link > 0.f) {
+                    gB[dst + j] = in ? make_float2(fmaf(link, gdl[j], gmu[j]),
+                                                   fmaf(link, gdl[jm], gmu[jm]))
+                                     : make_float2(0.f, 0.f);
+                } else {
+                    gA[dst + j] = in ? make_float4(gmu[j], gmu[jm], gdl[j], gdl[jm])
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                    gB[dst + j] = in ? make_float2(gsg[j], gsg[jm]) : make_float2(0.f, 0.f);
+                }
+            }
+        } else if (link > 0.f) {
             // linked unknown (Eq. 4): the single sinogram g_mu + gamma g_delta,
             // pair-packed in gB, is all the adjoint needs
             for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
@@ -575,7 +591,31 @@ k_ic_pipe(DevGeom dg, const float *__restrict__ proj, const float *__restrict__ 
             //            = (z/period)/(2 pitch) (gsw(j-1) - gsw(j+1) + e(j) gsw(j)),
             // e(j) = +1 at j = nd - 1, -1 at j = 0 (gsw(-1) = gsw(nd) = 0)
             const float kdt = 0.5f * h_in;
-            for (int j = (int)threadIdx.x - 1; j < ndp && (int)threadIdx.x < n_cons; j += n_cons) {
+            if (dg.gmirror) {
+                // mirror-interleaved row: entry j holds pixel j and pixel nd - 1 - j
+                // (zero outside [0, nd)), each value as the pair-packed row has it
+                auto gdelta = [&](int i) {
+                    const float ei = (i == nd - 1 ? 1.f : 0.f) - (i == 0 ? 1.f : 0.f);
+                    return kdt * fmaf(ei, g_sw[i], g_sw[i - 1] - g_sw[i + 1]);
+                };
+                for (int j = (int)threadIdx.x - 1; j < ndp && (int)threadIdx.x < n_cons; j += n_cons) {
+                    const bool in = j >= 0 && j < nd;
+                    const int jm = in ? nd - 1 - j : 0;
+                    const int jj = in ? j : 0;
+                    const float dj = gdelta(jj), dm = gdelta(jm);
+                    if (link > 0.f) {
+                        gB[m.gp_off + j] = in ? make_float2(fmaf(link, dj, g_mu[jj]),
+                                                            fmaf(link, dm, g_mu[jm]))
+                                              : make_float2(0.f, 0.f);
+                    } else {
+                        gA[m.gp_off + j] = in ? make_float4(g_mu[jj], g_mu[jm], dj, dm)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                        gB[m.gp_off + j] = in ? make_float2(g_v[jj], g_v[jm]) : make_float2(0.f, 0.f);
+                    }
+                }
+            }
+            for (int j = (int)threadIdx.x - 1; j < ndp && (int)threadIdx.x < n_cons && !dg.gmirror;
+                 j += n_cons) {
                 const float gm1 = g_sw[j - 1], g0 = g_sw[j], g1 = g_sw[j + 1], g2 = g_sw[j + 2];
                 const float e0 = (j == nd - 1 ? 1.f : 0.f) - (j == 0 ? 1.f : 0.f);
                 const float e1 = (j + 1 == nd - 1 ? 1.f : 0.f) - (j + 1 == 0 ? 1.f : 0.f);

@@ -101,7 +101,7 @@ EXPORTED = ["ei_setup_geometry", "ei_destroy_geometry", "ei_get_layout", "ei_get
             "ei_device_checks_enabled", "ei_selftest_device_check"]
 EI_OFFSET_MO, EI_OFFSET_MR = 1, 2
 EI_TUNE_FORCE, EI_TUNE_NO_CACHE_WRITE = 1, 2
-N_FWD_VARIANTS, N_ADJ_VARIANTS = 14, 11
+N_FWD_VARIANTS, N_ADJ_VARIANTS = 14, 14
 
 _lib = None
 

@@ -78,6 +78,10 @@ def test_every_variant_agrees():
                 # every projector variant: bit-identical projections
                 np.testing.assert_array_equal(proj, per_adj[0][2], err_msg=str((f, a, pers)))
     S0, g0, _ = per_adj[0]
+    # variants 11-13 read mirror-interleaved gradient rows with paired FMAs:
+    # the same sums as 8-10 in the same order
+    for a in (11, 12, 13):
+        np.testing.assert_array_equal(per_adj[a][1], per_adj[a - 3][1], err_msg=str(a))
     for a in range(1, ei.N_ADJ_VARIANTS):
         S, g, _ = per_adj[a]
         np.testing.assert_array_equal(S, S0)
@@ -121,6 +125,41 @@ def test_staged_projector_equals_global_loads_on_staged_slices():
             for name, a, b in zip(("S", "grad", "proj", "forward"), got, ref):
                 np.testing.assert_array_equal(a, b, err_msg="%s gamma=%g variant=%d mode=%d"
                                               % (name, gamma, f, pers))
+    ei.ei_set_linked(G, 0.0)
+
+
+def test_mirror_interleaved_adjoint_equals_pair_packed():
+    """Adjoint variants 11-13 read gradient rows whose entry j holds pixel j
+    and its mirror pixel n_det - 1 - j (written by the IC kernels and, for
+    ei_backproject, by k_pack_sino) and advance a voxel and its point mirror
+    with one paired FP32 FMA; variants 8-10 read the pair-packed rows with
+    scalar FMAs in the same order.  Gradients (three channels and linked) and
+    plain back-projections are equal bit for bit, and switching the layout
+    back and forth leaves nothing stale."""
+    from paper_2202_08627_gb300 import ei
+    probs = _uneven()
+    specs, geoms, meas = zip(*probs)
+    G = gpu_geometry(list(specs), list(geoms))
+    m = G.pack_meas(meas)
+    xs = [sp.truth * 0.9 for sp in specs]
+    rng = np.random.default_rng(5)
+    sino = torch.from_numpy(rng.standard_normal((G.sino4_count, 4)).astype(np.float32)).cuda()
+    first = {}
+    for gamma in (0.0, 5e-7):
+        ei.ei_set_linked(G, gamma)
+        for a in (8, 11, 9, 12, 10, 13, 8):
+            ei.ei_set_variant(G, 12, a, 0)
+            S, grad, _ = _eval(G, xs, m)
+            bp = G.empty("vol")
+            ei.ei_backproject(G, sino, bp)
+            torch.cuda.synchronize()
+            got = (S, grad, bp.cpu().numpy())
+            key = (gamma, a if a < 11 else a - 3)
+            if key not in first:
+                first[key] = got
+                continue
+            for name, x, y in zip(("S", "grad", "backproject"), got, first[key]):
+                np.testing.assert_array_equal(x, y, err_msg="%s gamma=%g variant=%d" % (name, gamma, a))
     ei.ei_set_linked(G, 0.0)
 
 
