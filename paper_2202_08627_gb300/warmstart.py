@@ -91,10 +91,10 @@ class WarmStartNet:
         if n == self.crop:
             return self.train_net
         if n not in self._infer:
-            # four times the training batch's pixels per forward: the deep
-            # levels of a single 1024^2 image leave the GPU half idle (per image
-            # 4.08 ms at batch 1, 3.56 ms at batch 4; 512^2: 1.02 ms at 4,
-            # 0.89 ms at 16); every image's output is the same at any batch
+            # four times the training batch's pixels per forward (measured per
+            # 1024^2 image: 4.08 ms at batch 1, 3.56 ms at batch 4; per 512^2
+            # image: 1.02 ms at 4, 0.89 ms at 16); every image's output is the
+            # same at any batch
             b = max(1, min(16, (4 * self.crop * self.crop * self.batch) // (n * n)))
             self._infer[n] = ei.UNet(levels=self.levels, base=self.base, batch=b, height=n,
                                      width=n, seed=0)
