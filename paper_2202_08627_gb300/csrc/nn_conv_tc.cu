@@ -43,7 +43,15 @@ namespace {
 
 constexpr int TC_M = 128;            // pixels per CTA (tcgen05 M)
 constexpr int TC_BK = 32;            // input channels per stage
-constexpr int TC_STAGES = 4;
+// stages of the operand ring and chunks copied ahead of the MMAs (compile-time
+// tunables; DEPTH < STAGES)
+#ifndef EI_TC_STAGES
+#define EI_TC_STAGES 4
+#endif
+#ifndef EI_TC_DEPTH
+#define EI_TC_DEPTH 2
+#endif
+constexpr int TC_STAGES = EI_TC_STAGES;
 constexpr uint64_t kTcWaitNs = 1000000000ull;
 
 // shared-memory descriptor: start, LBO (K direction), SBO (8-row groups),
@@ -160,7 +168,7 @@ k_conv_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int 
             cp_async16(Bs + tile_off(n, kg), wsrc + (int64_t)n * Cin + kg * 8, 16u);
         }
     };
-    constexpr int DEPTH = 2;                   // chunks in flight ahead of the MMA
+    constexpr int DEPTH = EI_TC_DEPTH;         // chunks in flight ahead of the MMA
     static_assert(DEPTH < TC_STAGES, "a stage must be free before its refill");
 #pragma unroll
     for (int i = 0; i < DEPTH; ++i) {
@@ -358,7 +366,8 @@ k_conv_wgrad_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2
                        pin ? 16u : 0u);
         }
     };
-    constexpr int DEPTH = 2;                   // chunks in flight ahead of the MMA
+    constexpr int DEPTH = EI_TC_DEPTH;         // chunks in flight ahead of the MMA
+    static_assert(DEPTH < TC_STAGES, "a stage must be free before its refill");
 #pragma unroll
     for (int i = 0; i < DEPTH; ++i) {
         if (i < nK) issue(i);
