@@ -697,7 +697,8 @@ def run_profile_unet(args):
 def run_profile_case(args):
     """The command the ncu summaries are captured with: `--profile-evals N`
     objective+gradient evaluations of the workload (variants as `ei_autotune`
-    picks them, or `--variant F,A`), after one untimed evaluation, inside a cudaProfilerStart/Stop
+    picks them, or `--variant F,A`; `--linked`: the linked single unknown of
+    Eq. 4), after one untimed evaluation, inside a cudaProfilerStart/Stop
     range (`ncu --profile-from-start off` captures only those).  Prints one
     line with the objective; reports no performance number."""
     import torch
@@ -707,6 +708,8 @@ def run_profile_case(args):
     wl = workloads.WORKLOADS[args.workload]()
     device = torch.device("cuda", 0)
     G, s_exp = build_problem(wl, 0, device)
+    if args.linked:
+        ei.ei_set_linked(G, LINKED_GAMMA)
     if args.variant:
         f, a = (int(v) for v in args.variant.split(","))
         ei.ei_set_variant(G, f, a, 0)
@@ -754,6 +757,8 @@ def main():
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
     ap.add_argument("--profile-unet", action="store_true",
                     help="one U-Net forward + training step for ncu and exit")
+    ap.add_argument("--linked", action="store_true",
+                    help="--profile-evals on the linked single unknown (gamma = LINKED_GAMMA)")
     ap.add_argument("--variant", default=None,
                     help="F,A: projector and adjoint variant for --profile-evals (launch mode 0)")
     ap.add_argument("--profile-evals", type=int, default=0,

@@ -54,11 +54,13 @@ __device__ void block_inclusive_scan(float *v, int n, double *tot)
 
 // Ram-Lak filter with the FBP scale, q = (pi / n_theta) / pitch^2
 // (p/4 - sum_odd p(j-d) / (pi^2 d^2)), of three rows (w[d] = 1/(pi^2 d^2) at odd
-// d, prepared by the caller), then the pair-packed write for the adjoint: the
-// entry of pixel j holds q(j) and q(j + 1).  Ends with the block's writes.
+// d, prepared by the caller), then the write for the adjoint in the layout
+// the selected adjoint variant reads: pair-packed (the entry of pixel j holds
+// q(j) and q(j + 1)) or, with `mirror`, mirror-interleaved (pixel j and pixel
+// n_det - 1 - j).  Ends with the block's writes.
 __device__ void ramp_filter_write(const SliceInfo &si, int a, const float *pm, const float *pd,
                                   const float *ps, float *qm, float *qd, float *qs,
-                                  const float *w, float4 *gA, float2 *gB)
+                                  const float *w, float4 *gA, float2 *gB, bool mirror)
 {
     const int nd = si.n_det;
     const float K = 3.14159265358979f / (float)si.n_theta / (si.pitch * si.pitch);
@@ -74,6 +76,13 @@ __device__ void ramp_filter_write(const SliceInfo &si, int a, const float *pm, c
     __syncthreads();
     const int64_t dst = si.gp_off + (int64_t)a * si.gw + si.marg;
     for (int j = (int)threadIdx.x - 1; j < nd; j += blockDim.x) {
+        if (mirror) {
+            const int jm = nd - 1 - j;
+            gA[dst + j] = j >= 0 ? make_float4(qm[j], qm[jm], qd[j], qd[jm])
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            gB[dst + j] = j >= 0 ? make_float2(qs[j], qs[jm]) : make_float2(0.f, 0.f);
+            continue;
+        }
         float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
         if (j >= 0) lx = qm[j], ly = qd[j], lz = qs[j];
         if (j + 1 < nd) hx = qm[j + 1], hy = qd[j + 1], hz = qs[j + 1];
@@ -139,7 +148,7 @@ __global__ void k_single_shot(DevGeom dg, const float *__restrict__ meas, float4
 
     // ---- ramp filter and FBP scale, written pair-packed for the adjoint
     float *qm = reinterpret_cast<float *>(tot + blockDim.x);   // filtered rows (3 x max_ndp)
-    ramp_filter_write(si, a, pm, pd, ps, qm, qm + mx, qm + 2 * mx, w, gA, gB);
+    ramp_filter_write(si, a, pm, pd, ps, qm, qm + mx, qm + 2 * mx, w, gA, gB, dg.gmirror != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +250,7 @@ __global__ void k_single_shot_eq3(DevGeom dg, const float *__restrict__ meas, in
         pd[j] = gamma * p;
     }
     __syncthreads();
-    ramp_filter_write(si, a, ph, pd, zero, q, q + mx, q + 2 * mx, w, gA, gB);
+    ramp_filter_write(si, a, ph, pd, zero, q, q + mx, q + 2 * mx, w, gA, gB, dg.gmirror != 0);
 }
 
 static const int kEq3SmemLimit = 220 * 1024;     // 9 rows: n_det up to 6257 pixels

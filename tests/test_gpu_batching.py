@@ -131,10 +131,11 @@ def test_staged_projector_equals_global_loads_on_staged_slices():
 def test_mirror_interleaved_adjoint_equals_pair_packed():
     """Adjoint variants 11-13 read gradient rows whose entry j holds pixel j
     and its mirror pixel n_det - 1 - j (written by the IC kernels and, for
-    ei_backproject, by k_pack_sino) and advance a voxel and its point mirror
-    with one paired FP32 FMA; variants 8-10 read the pair-packed rows with
-    scalar FMAs in the same order.  Gradients (three channels and linked) and
-    plain back-projections are equal bit for bit, and switching the layout
+    ei_backproject, by k_pack_sino, for the single-shot starts by their row
+    filter) and advance a voxel and its point mirror with one paired FP32 FMA;
+    variants 8-10 read the pair-packed rows with scalar FMAs in the same
+    order.  Gradients (three channels and linked), plain back-projections and
+    both single-shot starts are equal bit for bit, and switching the layout
     back and forth leaves nothing stale."""
     from paper_2202_08627_gb300 import ei
     probs = _uneven()
@@ -152,13 +153,18 @@ def test_mirror_interleaved_adjoint_equals_pair_packed():
             S, grad, _ = _eval(G, xs, m)
             bp = G.empty("vol")
             ei.ei_backproject(G, sino, bp)
+            fbp = G.empty("vol")
+            ei.ei_single_shot_fbp(G, m, fbp)
+            eq3 = G.empty("vol")
+            ei.ei_single_shot_eq3(G, m, 2, 5e-7, eq3)
             torch.cuda.synchronize()
-            got = (S, grad, bp.cpu().numpy())
+            got = (S, grad, bp.cpu().numpy(), fbp.cpu().numpy(), eq3.cpu().numpy())
             key = (gamma, a if a < 11 else a - 3)
             if key not in first:
                 first[key] = got
                 continue
-            for name, x, y in zip(("S", "grad", "backproject"), got, first[key]):
+            for name, x, y in zip(("S", "grad", "backproject", "single-shot FBP", "Eq. 3 single shot"),
+                                  got, first[key]):
                 np.testing.assert_array_equal(x, y, err_msg="%s gamma=%g variant=%d" % (name, gamma, a))
     ei.ei_set_linked(G, 0.0)
 
