@@ -455,6 +455,214 @@ static cudaError_t launch_wgrad_tc(const Tensor &x1, const Tensor *x2, const bf1
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// 3 x 3 convolutions by row patches.  A CTA computes 16 output rows x 8
+// output columns of one image (GEMM rows r = 8 y + x, M = 128) x NT output
+// channels.  The reduction runs over (32-channel chunk, kernel row dy): a stage
+// holds the 16 x 10 input pixels of the chunk at rows y + dy, columns
+// x - 1 .. x + 8, in the K-major no-swizzle layout (core matrices of 8
+// consecutive pixels of a row x 16 bytes; 2560 bytes between 8-channel groups,
+// 160 between output rows), and the three taps' weights.  Tap dx's A operand
+// is the same tile started dx + 1 pixels (16 bytes each) further, so an input
+// pixel is staged 3 times instead of 9 (once per tap) and each stage feeds 6
+// MMAs instead of 2.  Partial patches at the image's bottom and right edges
+// read zeros and store nothing for the missing pixels.
+// ----------------------------------------------------------------------------
+constexpr int C3_PR = 16, C3_PC = 8, C3_PW = C3_PC + 2;   // patch rows, columns, staged columns
+constexpr int C3_LBO = C3_PR * C3_PW * 16;                // 2560: next 8 input channels
+constexpr int C3_SBO = C3_PW * 16;                        // 160: next output row
+constexpr int C3_A_BYTES = 4 * C3_LBO;                    // 10240: 32 channels
+static_assert(C3_PR * C3_PC == TC_M, "a patch is one tcgen05 M tile");
+
+template <int NT>
+struct Conv3Shape {
+    static constexpr int kStages = NT >= 256 ? 3 : 4;
+    static constexpr int kBTap = NT * TC_BK * 2;
+    static constexpr int kStageBytes = C3_A_BYTES + 3 * kBTap;
+    static constexpr int kSmem = kStages * kStageBytes;
+};
+
+// shared-memory descriptor with explicit strides (no swizzle)
+__device__ __forceinline__ uint64_t smem_desc_s(unsigned addr, int lbo, int sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128)
+k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int C2,
+           const bf16 *__restrict__ Wk, const float *__restrict__ bias, int Cout, int B, int H,
+           int W, int relu, bf16 *__restrict__ Y1, int split, int acc1, bf16 *__restrict__ Y2,
+           int acc2, int *__restrict__ status)
+{
+    using S = Conv3Shape<NT>;
+    constexpr int STAGES = S::kStages;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar_mma[STAGES];
+    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_y = (H + C3_PR - 1) / C3_PR, tiles_x = (W + C3_PC - 1) / C3_PC;
+    const int t_img = blockIdx.x / (tiles_y * tiles_x), t_rem = blockIdx.x - t_img * tiles_y * tiles_x;
+    const int y0 = (t_rem / tiles_x) * C3_PR, x0 = (t_rem % tiles_x) * C3_PC;
+    const int co0 = blockIdx.y * NT;
+    const int Cin = C1 + C2;
+    const int chunks = Cin / TC_BK;
+    const int nK = 3 * chunks;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bar_mma[s]), 1);
+        mbar_init(smem_addr(&bar_done), 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_base;
+    // D f32, A bf16, B bf16, both K-major, N >> 3, M >> 4
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NT >> 3) << 17) |
+                           ((unsigned)(TC_M >> 4) << 24);
+
+    // stage kc = (chunk kc / 3, kernel row dy = kc % 3 - 1), cp.async, one commit group each
+    auto issue = [&](int kc) {
+        unsigned char *As = tc_smem + (kc % STAGES) * S::kStageBytes;
+        unsigned char *Bs = As + C3_A_BYTES;
+        const int c = kc / 3, dyi = kc - 3 * c, dy = dyi - 1, c0 = c * TC_BK;
+        // A: 16 x 10 pixels x 32 channels (zero outside the image)
+        for (int e = tid; e < C3_PR * C3_PW * 4; e += 128) {
+            const int pi = e >> 2, kg = e & 3;
+            const int yy = pi / C3_PW, xx = pi - yy * C3_PW;
+            const int iy = y0 + yy + dy, ix = x0 + xx - 1;
+            const bool inb = iy >= 0 && iy < H && ix >= 0 && ix < W;
+            const int64_t q = ((int64_t)t_img * H + iy) * W + ix;
+            const bf16 *src = X1;
+            if (inb) src = c0 < C1 ? X1 + q * C1 + c0 : X2 + q * C2 + (c0 - C1);
+            cp_async16(As + kg * C3_LBO + pi * 16, inb ? src + kg * 8 : X1, inb ? 16u : 0u);
+        }
+        // B: the three taps (dy, dx = -1, 0, 1), NT output x 32 input channels,
+        // K-major, tap flipped as in k_conv_tc
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int tap = dyi * 3 + t;
+            const bf16 *wsrc = Wk + ((int64_t)(8 - tap) * Cout + co0) * Cin + c0;
+            unsigned char *Bt = Bs + t * S::kBTap;
+#pragma unroll
+            for (int i = 0; i < NT * 4 / 128; ++i) {
+                const int e = tid + i * 128;
+                const int n = e >> 2, kg = e & 3;
+                cp_async16(Bt + tile_off(n, kg), wsrc + (int64_t)n * Cin + kg * 8, 16u);
+            }
+        }
+    };
+    constexpr int DEPTH = EI_TC_DEPTH;
+    static_assert(DEPTH < STAGES, "a stage must be free before its refill");
+#pragma unroll
+    for (int i = 0; i < DEPTH; ++i) {
+        if (i < nK) issue(i);
+        cp_async_commit();
+    }
+    bool aborted = false;
+    for (int kc = 0; kc < nK; ++kc) {
+        bool ok = true;
+        const int kn = kc + DEPTH;
+        if (kn < nK) {
+            if (kn >= STAGES)
+                ok = mbar_wait_bounded(smem_addr(&bar_mma[kn % STAGES]), ((kn / STAGES) - 1) & 1,
+                                       kTcWaitNs);
+            if (ok) issue(kn);
+        }
+        cp_async_commit();
+        cp_async_wait<DEPTH>();                // this thread's copies of stage kc landed
+        proxy_fence_async();                   // the tensor core reads what the copies wrote
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned a_addr = smem_addr(tc_smem + (kc % STAGES) * S::kStageBytes);
+            const unsigned b_addr = a_addr + C3_A_BYTES;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const unsigned at = a_addr + t * 16, bt = b_addr + t * S::kBTap;
+                tc_mma(tmem, smem_desc_s(at, C3_LBO, C3_SBO), smem_desc(bt), idesc,
+                       kc > 0 || t > 0 ? 1u : 0u);
+                tc_mma(tmem, smem_desc_s(at + 2 * C3_LBO, C3_LBO, C3_SBO), smem_desc(bt + 256),
+                       idesc, 1u);
+            }
+            tc_commit(smem_addr(&bar_mma[kc % STAGES]));
+        }
+    }
+    cp_async_wait<0>();                        // no copy outlives the block
+    if (tid == 0) tc_commit(smem_addr(&bar_done));
+    const bool done = mbar_wait_bounded(smem_addr(&bar_done), 0, kTcWaitNs);
+    const bool failed = __syncthreads_or(aborted || !done);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (failed) {
+        if (tid == 0) atomicExch(status, 1);
+    } else {
+        // warp w reads lanes 32w .. 32w + 31 (rows r = 8 y + x); the loads are
+        // warp-collective, the stores only for pixels inside the image
+        const int r = tid, yy = y0 + (r >> 3), xx = x0 + (r & 7);
+        const bool in = yy < H && xx < W;
+        const int64_t p = ((int64_t)t_img * H + yy) * W + xx;
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        for (int c = 0; c < NT; c += 16) {
+            unsigned v[16];
+            tc_ld16(lane_base + c, v);
+            if (!in) continue;
+            const int co = co0 + c;
+            const bool first = co < split;
+            bf16 *dst = first ? Y1 + p * split + co : Y2 + p * (Cout - split) + (co - split);
+            const int acc_mode = first ? acc1 : acc2;
+            __align__(16) __nv_bfloat162 outv[8];
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                float a = __uint_as_float(v[j]), b = __uint_as_float(v[j + 1]);
+                if (bias) a += bias[co + j], b += bias[co + j + 1];
+                if (relu) a = fmaxf(a, 0.f), b = fmaxf(b, 0.f);
+                if (acc_mode) {
+                    const float2 o = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(dst)[j / 2]);
+                    a += o.x, b += o.y;
+                }
+                outv[j / 2] = __floats2bfloat162_rn(a, b);
+            }
+            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(outv)[0];
+            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(outv)[1];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
+}
+
+template <int NT>
+static cudaError_t launch_conv3_tc(const Tensor &x1, const Tensor *x2, int cout, const bf16 *Wk,
+                                   const float *bias, bool relu, bf16 *y1, int split, bool acc1,
+                                   bf16 *y2, bool acc2, int *status, cudaStream_t st)
+{
+    constexpr int smem = Conv3Shape<NT>::kSmem;
+    static bool attr = false;
+    if (!attr) {
+        EI_NN_TRY(cudaFuncSetAttribute(k_conv3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    const int tiles = ((x1.H + C3_PR - 1) / C3_PR) * ((x1.W + C3_PC - 1) / C3_PC);
+    dim3 grid(x1.B * tiles, cout / NT);
+    k_conv3_tc<NT><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0, Wk,
+                                            bias, cout, x1.B, x1.H, x1.W, relu, y1, split, acc1, y2,
+                                            acc2, status);
+    return cudaGetLastError();
+}
+
 bool wgrad_tc_supported(int cin, int cout, int c1)
 {
     const int nt = cout >= 256 ? 256 : cout;
@@ -489,6 +697,15 @@ cudaError_t conv_forward_tc(const Tensor &x1, const Tensor *x2, int cout, int ks
 #define EI_TC_CASE(K, N)                                                                     \
     if (ks == K && nt == N)                                                                  \
         return launch_tc<K, N>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+#ifndef EI_CONV3_TAPWISE
+    // 3 x 3: row patches (each input pixel staged once per kernel row)
+    if (ks == 3) {
+        if (nt == 32) return launch_conv3_tc<32>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+        if (nt == 64) return launch_conv3_tc<64>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+        if (nt == 128) return launch_conv3_tc<128>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+        if (nt == 256) return launch_conv3_tc<256>(x1, x2, cout, Wk, bias, relu, y1, split, acc1, y2, acc2, status, st);
+    }
+#endif
     EI_TC_CASE(3, 32) EI_TC_CASE(3, 64) EI_TC_CASE(3, 128) EI_TC_CASE(3, 256)
     EI_TC_CASE(1, 32) EI_TC_CASE(1, 64) EI_TC_CASE(1, 128) EI_TC_CASE(1, 256)
 #undef EI_TC_CASE
