@@ -474,9 +474,12 @@ constexpr int C3_SBO = C3_PW * 16;                        // 160: next output ro
 constexpr int C3_A_BYTES = 4 * C3_LBO;                    // 10240: 32 channels
 static_assert(C3_PR * C3_PC == TC_M, "a patch is one tcgen05 M tile");
 
+#ifndef EI_C3_STAGES
+#define EI_C3_STAGES 3               // stages (measured: 3 beats 4, more resident CTAs)
+#endif
 template <int NT>
 struct Conv3Shape {
-    static constexpr int kStages = NT >= 256 ? 3 : 4;
+    static constexpr int kStages = NT >= 256 ? 3 : EI_C3_STAGES;
     static constexpr int kBTap = NT * TC_BK * 2;
     static constexpr int kStageBytes = C3_A_BYTES + 3 * kBTap;
     static constexpr int kSmem = kStages * kStageBytes;
