@@ -674,8 +674,9 @@ __global__ void k_ls_start(DevGeom dg, SolverDev sv)
         q.trials = 0;
         sv.mask_ls[s] = 1;
     }
-    // this round's trial of every slice in line search: an iteration's first
-    // trial is projected, a backtracking one interpolated from Pu and Pt
+    // the trial of every slice in line search in the current solver round: an
+    // iteration's first trial is projected, a backtracking one interpolated
+    // from Pu and Pt
     for (int s = threadIdx.x; s < dg.n_slices; s += blockDim.x) {
         sv.mask_first[s] = 0;
         sv.mask_bt[s] = 0;
