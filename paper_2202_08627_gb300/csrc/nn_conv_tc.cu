@@ -477,11 +477,23 @@ static_assert(C3_PR * C3_PC == TC_M, "a patch is one tcgen05 M tile");
 #ifndef EI_C3_STAGES
 #define EI_C3_STAGES 3               // stages (measured: 3 beats 4, more resident CTAs)
 #endif
-template <int NT>
+// HALO: a stage holds one 32-channel chunk's 18 x 10 input pixels (rows
+// y - 1 .. y + 16) and all nine taps' weights; tap (dy, dx) reads the tile
+// started dy + 1 rows and dx + 1 pixels further, so each input pixel is staged
+// once per chunk and a stage feeds 18 MMAs.
+constexpr int C3H_LBO = (C3_PR + 2) * C3_PW * 16;         // 2880
+constexpr int C3H_A_BYTES = 4 * C3H_LBO;                  // 11520
+#ifndef EI_C3_HALO_MAXNT
+#define EI_C3_HALO_MAXNT 64          // largest NT that stages whole halos (0: none)
+#endif
+template <int NT, bool HALO = false>
 struct Conv3Shape {
-    static constexpr int kStages = NT >= 256 ? 3 : EI_C3_STAGES;
+    static constexpr int kStages = HALO ? (NT >= 64 ? 2 : 3) : (NT >= 256 ? 3 : EI_C3_STAGES);
+    static constexpr int kTaps = HALO ? 9 : 3;
+    static constexpr int kLBO = HALO ? C3H_LBO : C3_LBO;
+    static constexpr int kABytes = HALO ? C3H_A_BYTES : C3_A_BYTES;
     static constexpr int kBTap = NT * TC_BK * 2;
-    static constexpr int kStageBytes = C3_A_BYTES + 3 * kBTap;
+    static constexpr int kStageBytes = kABytes + kTaps * kBTap;
     static constexpr int kSmem = kStages * kStageBytes;
 };
 
@@ -492,14 +504,14 @@ __device__ __forceinline__ uint64_t smem_desc_s(unsigned addr, int lbo, int sbo)
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-template <int NT>
+template <int NT, bool HALO>
 __global__ void __launch_bounds__(128)
 k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int C2,
            const bf16 *__restrict__ Wk, const float *__restrict__ bias, int Cout, int B, int H,
            int W, int relu, bf16 *__restrict__ Y1, int split, int acc1, bf16 *__restrict__ Y2,
            int acc2, int *__restrict__ status)
 {
-    using S = Conv3Shape<NT>;
+    using S = Conv3Shape<NT, HALO>;
     constexpr int STAGES = S::kStages;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t bar_mma[STAGES];
@@ -512,7 +524,7 @@ k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int
     const int co0 = blockIdx.y * NT;
     const int Cin = C1 + C2;
     const int chunks = Cin / TC_BK;
-    const int nK = 3 * chunks;
+    const int nK = HALO ? chunks : 3 * chunks;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bar_mma[s]), 1);
@@ -536,10 +548,12 @@ k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int
     // stage kc = (chunk kc / 3, kernel row dy = kc % 3 - 1), cp.async, one commit group each
     auto issue = [&](int kc) {
         unsigned char *As = tc_smem + (kc % STAGES) * S::kStageBytes;
-        unsigned char *Bs = As + C3_A_BYTES;
-        const int c = kc / 3, dyi = kc - 3 * c, dy = dyi - 1, c0 = c * TC_BK;
-        // A: 16 x 10 pixels x 32 channels (zero outside the image)
-        for (int e = tid; e < C3_PR * C3_PW * 4; e += 128) {
+        unsigned char *Bs = As + S::kABytes;
+        const int c = HALO ? kc : kc / 3, dyi = HALO ? 0 : kc - 3 * c, dy = dyi - 1;
+        const int c0 = c * TC_BK;
+        // A: 16 (HALO: 18) x 10 pixels x 32 channels (zero outside the image)
+        constexpr int AROWS = HALO ? C3_PR + 2 : C3_PR;
+        for (int e = tid; e < AROWS * C3_PW * 4; e += 128) {
             const int pi = e >> 2, kg = e & 3;
             const int yy = pi / C3_PW, xx = pi - yy * C3_PW;
             const int iy = y0 + yy + dy, ix = x0 + xx - 1;
@@ -547,13 +561,13 @@ k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int
             const int64_t q = ((int64_t)t_img * H + iy) * W + ix;
             const bf16 *src = X1;
             if (inb) src = c0 < C1 ? X1 + q * C1 + c0 : X2 + q * C2 + (c0 - C1);
-            cp_async16(As + kg * C3_LBO + pi * 16, inb ? src + kg * 8 : X1, inb ? 16u : 0u);
+            cp_async16(As + kg * S::kLBO + pi * 16, inb ? src + kg * 8 : X1, inb ? 16u : 0u);
         }
         // B: the three taps (dy, dx = -1, 0, 1), NT output x 32 input channels,
         // K-major, tap flipped as in k_conv_tc
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int tap = dyi * 3 + t;
+        for (int t = 0; t < S::kTaps; ++t) {
+            const int tap = HALO ? t : dyi * 3 + t;
             const bf16 *wsrc = Wk + ((int64_t)(8 - tap) * Cout + co0) * Cin + c0;
             unsigned char *Bt = Bs + t * S::kBTap;
 #pragma unroll
@@ -564,7 +578,7 @@ k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int
             }
         }
     };
-    constexpr int DEPTH = EI_TC_DEPTH;
+    constexpr int DEPTH = EI_TC_DEPTH < STAGES ? EI_TC_DEPTH : STAGES - 1;
     static_assert(DEPTH < STAGES, "a stage must be free before its refill");
 #pragma unroll
     for (int i = 0; i < DEPTH; ++i) {
@@ -591,13 +605,16 @@ k_conv3_tc(const bf16 *__restrict__ X1, int C1, const bf16 *__restrict__ X2, int
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const unsigned a_addr = smem_addr(tc_smem + (kc % STAGES) * S::kStageBytes);
-            const unsigned b_addr = a_addr + C3_A_BYTES;
+            const unsigned b_addr = a_addr + S::kABytes;
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const unsigned at = a_addr + t * 16, bt = b_addr + t * S::kBTap;
-                tc_mma(tmem, smem_desc_s(at, C3_LBO, C3_SBO), smem_desc(bt), idesc,
+            for (int t = 0; t < S::kTaps; ++t) {
+                // tap t's tile: HALO (dy, dx) = (t / 3 - 1, t % 3 - 1) starts dy + 1 rows
+                // and dx + 1 pixels into the halo; otherwise dx = t - 1
+                const unsigned at = a_addr + (HALO ? (t / 3) * C3_SBO + (t % 3) * 16 : t * 16);
+                const unsigned bt = b_addr + t * S::kBTap;
+                tc_mma(tmem, smem_desc_s(at, S::kLBO, C3_SBO), smem_desc(bt), idesc,
                        kc > 0 || t > 0 ? 1u : 0u);
-                tc_mma(tmem, smem_desc_s(at + 2 * C3_LBO, C3_LBO, C3_SBO), smem_desc(bt + 256),
+                tc_mma(tmem, smem_desc_s(at + 2 * S::kLBO, S::kLBO, C3_SBO), smem_desc(bt + 256),
                        idesc, 1u);
             }
             tc_commit(smem_addr(&bar_mma[kc % STAGES]));
@@ -652,15 +669,16 @@ static cudaError_t launch_conv3_tc(const Tensor &x1, const Tensor *x2, int cout,
                                    const float *bias, bool relu, bf16 *y1, int split, bool acc1,
                                    bf16 *y2, bool acc2, int *status, cudaStream_t st)
 {
-    constexpr int smem = Conv3Shape<NT>::kSmem;
+    constexpr bool HALO = NT <= EI_C3_HALO_MAXNT;
+    constexpr int smem = Conv3Shape<NT, HALO>::kSmem;
     static bool attr = false;
     if (!attr) {
-        EI_NN_TRY(cudaFuncSetAttribute(k_conv3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        EI_NN_TRY(cudaFuncSetAttribute(k_conv3_tc<NT, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr = true;
     }
     const int tiles = ((x1.H + C3_PR - 1) / C3_PR) * ((x1.W + C3_PC - 1) / C3_PC);
     dim3 grid(x1.B * tiles, cout / NT);
-    k_conv3_tc<NT><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0, Wk,
+    k_conv3_tc<NT, HALO><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0, Wk,
                                             bias, cout, x1.B, x1.H, x1.W, relu, y1, split, acc1, y2,
                                             acc2, status);
     return cudaGetLastError();
