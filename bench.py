@@ -668,6 +668,49 @@ def run_sweep_n(args):
                       "m": SLOPE_M, "rows": rows}), flush=True)
 
 
+def run_unet_timing(args):
+    """CUDA-event timings of the warm-start network as the benchmark uses it:
+    the forward pass per image of the inference batches (4 x 1024^2, 16 x
+    512^2) and the training step of 16 x 256^2 crops, each the mean of several
+    calls after a warm-up.  One JSON line."""
+    import torch
+    from paper_2202_08627_gb300 import build, ei
+    torch.cuda.set_device(0)
+    build.build()
+    out = {}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    for n, b in ((1024, 4), (512, 16)):
+        net = ei.UNet(levels=4, base=32, batch=b, height=n, width=n, seed=0)
+        x = torch.rand(b, n, n, 3, device="cuda", generator=g)
+        y = torch.empty_like(x)
+        net.forward(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(4):
+            net.forward(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        out["forward_ms_per_image_%d" % n] = e0.elapsed_time(e1) / (4 * b)
+        net.close()
+    net = ei.UNet(levels=4, base=32, batch=16, height=256, width=256, seed=0)
+    x = torch.rand(16, 256, 256, 3, device="cuda", generator=g)
+    t = torch.rand(16, 256, 256, 3, device="cuda", generator=g)
+    for _ in range(3):
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.train_step(x, t, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    out["train_step_ms_16x256"] = e0.elapsed_time(e1) / 10
+    net.close()
+    print(json.dumps({"run": "unet_timing", **out}), flush=True)
+
+
 def run_profile_unet(args):
     """The command the U-Net launch list is captured with: the warm-start
     network of the benchmark (4 levels, base 32, batch 16 of 256 x 256), one
@@ -755,6 +798,8 @@ def main():
                     help="single-m linked model: time to tolerance from 0 and from Eq. 3, then exit")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the FP64 oracle on the host cores (1, 3 and all threads) and exit")
+    ap.add_argument("--unet-timing", action="store_true",
+                    help="CUDA-event timings of the warm-start U-Net (forward per image, training step)")
     ap.add_argument("--profile-unet", action="store_true",
                     help="one U-Net forward + training step for ncu and exit")
     ap.add_argument("--linked", action="store_true",
@@ -766,6 +811,8 @@ def main():
     args = ap.parse_args()
     if args.profile_evals > 0:
         return run_profile_case(args)
+    if args.unet_timing:
+        return run_unet_timing(args)
     if args.profile_unet:
         return run_profile_unet(args)
     if args.oracle_timing:
