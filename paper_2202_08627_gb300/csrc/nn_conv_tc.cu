@@ -25,6 +25,8 @@
 // dgrad (a forward convolution of dY with the flipped, transposed weights) it
 // is the forward copy itself, so no extra weight layout exists.
 //
+// 3 x 3 layers run on k_conv3_tc (below), which stages input pixels per row
+// patch (or whole halo) once for several taps; 1 x 1 layers on k_conv_tc.
 // The weight gradients (k_conv_wgrad_tc, below) run on the same pipeline with
 // the pixels as the reduction dimension and MN-major operand tiles.
 //
