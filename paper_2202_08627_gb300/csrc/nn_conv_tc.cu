@@ -256,11 +256,8 @@ static cudaError_t launch_tc(const Tensor &x1, const Tensor *x2, int cout, const
                              bf16 *y2, bool acc2, int *status, cudaStream_t st)
 {
     constexpr int smem = TC_STAGES * (TC_M * TC_BK * 2 + NT * TC_BK * 2);
-    static bool attr = false;
-    if (!attr) {
-        EI_NN_TRY(cudaFuncSetAttribute(k_conv_tc<KS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current context
+    EI_NN_TRY(cudaFuncSetAttribute(k_conv_tc<KS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int P = x1.B * x1.H * x1.W;
     dim3 grid((P + TC_M - 1) / TC_M, cout / NT);
     k_conv_tc<KS, NT><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0,
@@ -440,12 +437,9 @@ static cudaError_t launch_wgrad_tc(const Tensor &x1, const Tensor *x2, const bf1
                                    float *partial, int nsplit, int *status, cudaStream_t st)
 {
     constexpr int smem = TC_STAGES * (TC_M * TC_BK * 2 + NT * TC_BK * 2);
-    static bool attr = false;
-    if (!attr) {
-        EI_NN_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<KS, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current context
+    EI_NN_TRY(cudaFuncSetAttribute(k_conv_wgrad_tc<KS, NT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int P = x1.B * x1.H * x1.W;
     const int cin = x1.C + (x2 ? x2->C : 0);
     const int R = KS * KS * cin;
@@ -673,11 +667,8 @@ static cudaError_t launch_conv3_tc(const Tensor &x1, const Tensor *x2, int cout,
 {
     constexpr bool HALO = NT <= EI_C3_HALO_MAXNT;
     constexpr int smem = Conv3Shape<NT, HALO>::kSmem;
-    static bool attr = false;
-    if (!attr) {
-        EI_NN_TRY(cudaFuncSetAttribute(k_conv3_tc<NT, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current context
+    EI_NN_TRY(cudaFuncSetAttribute(k_conv3_tc<NT, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int tiles = ((x1.H + C3_PR - 1) / C3_PR) * ((x1.W + C3_PC - 1) / C3_PC);
     dim3 grid(x1.B * tiles, cout / NT);
     k_conv3_tc<NT, HALO><<<grid, 128, smem, st>>>(x1.d, x1.C, x2 ? x2->d : nullptr, x2 ? x2->C : 0, Wk,
