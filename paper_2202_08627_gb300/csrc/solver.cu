@@ -791,7 +791,7 @@ __global__ void k_update(DevGeom dg, SolverDev sv, Opts o, int *summary)
 }
 
 // --------------------------------------------------------------------------
-// host driver
+// host side: allocation, rounds, checkpoints
 // --------------------------------------------------------------------------
 template <class T>
 static cudaError_t salloc(Solver *s, T **p, size_t count)
